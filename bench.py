@@ -1,0 +1,440 @@
+#!/usr/bin/env python
+"""Benchmark of the PowerLU hot path (Zhang & Mascagni, arXiv 2002.07138) on GB300.
+
+One step = one fixed-rank PowerLU call (Alg. bpowerlu with Alg. gpowerlu:
+Gaussian sketch, v passes over A, LU re-orthogonalisation, QR, final pass,
+two LUs and the tail products) through the C ABI, on a seeded synthetic A
+already resident in HBM.  Default workload: m = n = 8192, sigma_i = exp(-i/20)
+plus a 1e-6 N(0,1)/sqrt(n) floor, k = 100, l = 110, v = 3, A stored in FP32
+(larger than L2, so no flush is needed between steps).
+
+value = algorithmic pass flops (2 m n l per power pass + 2 m n k for the
+last pass) over the whole call time, in TFLOP/s, summed over ranks.
+Also reported: ms per pass and TFLOP/s per pass from the pass kernels alone,
+the relative Frobenius error, the same call with FP64 passes ("FP64 plain"),
+an end-to-end number through host buffers, the roofline of the dominant
+kernel (timed live with CUDA events) and the FP64 CPU oracle timed on the
+host cores.
+
+--impl reference times the oracle (the plain FP64 CPU implementation of the
+paper's algorithms) on the host cores on the same workload and metric.
+Multi-GPU (torchrun): replicas only -- every rank factors its own matrix,
+no data-path collective; value sums the ranks' work over the slowest rank.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PowerLU ms & TFLOP/s per pass of A at stated rel. error, mixed vs FP64 plain"
+
+
+def workloads():
+    import synth
+    return {"fixed_rank_8192": synth.FIXED_RANK_8192, "mixed_32768": synth.MIXED_32768,
+            "plain_2000x1500": synth.PLAIN_2000x1500}
+
+
+def pass_flops(m, n, k, l, v):
+    return 2.0 * m * n * l * (v - 1) + 2.0 * m * n * k
+
+
+def lu_flops(rows, cols):
+    # sum_j 2 (rows - j - 1)(cols - j - 1) + (rows - j - 1) divisions, FP64
+    return sum(2.0 * (rows - j - 1) * (cols - j - 1) + (rows - j - 1) for j in range(cols))
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ distributed
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo")
+    return ws, rank, local
+
+
+def dist_barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def dist_max(ws, x):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- reference
+def oracle_call(A, w, seed):
+    import oracle
+    t0 = time.perf_counter()
+    p, q, L, U = oracle.powerlu(A, w.k, w.l, w.v, seed=seed)
+    return time.perf_counter() - t0, (p, q, L, U)
+
+
+def build_host_matrix(w, seed_offset=0):
+    """The workload's A as a float64 numpy array (built on the GPU when one is
+    present, then copied; otherwise with numpy)."""
+    import numpy as np
+    try:
+        import torch
+        if torch.cuda.is_available():
+            from dataclasses import replace
+            Ad = replace(w, seed=w.seed + seed_offset).build("cuda")
+            A = Ad.double().cpu().numpy()
+            del Ad
+            torch.cuda.empty_cache()
+            return np.asfortranarray(A)
+    except Exception:
+        pass
+    from dataclasses import replace
+    A = replace(w, seed=w.seed + seed_offset).build("cpu")
+    return np.asfortranarray(A.astype(np.float64))
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    A = build_host_matrix(w)
+    flops = pass_flops(w.m, w.n, w.k, w.l, w.v)
+    for i in range(args.warmup):
+        oracle_call(A, w, seed=i)
+    times = []
+    for i in range(args.steps):
+        dt, _ = oracle_call(A, w, seed=i)
+        times.append(dt)
+    total = sum(times)
+    value = flops * args.steps / total / 1e12
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "l": w.l, "v": w.v,
+                   "storage": "f64 (host)", "l2_flush": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": "one full oracle PowerLU call per step on the same matrix"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ ours
+def time_calls(torch, fn, reps, stream):
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    s.record(stream)
+    for _ in range(reps):
+        fn()
+    e.record(stream)
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def kernel_rooflines(torch, plu, ctx, Ad, w, prec, stream, peaks):
+    """Time each step's kernel(s) alone with CUDA events on the library's
+    stream and return {name: (ms per launch, launches per step, roofline)}."""
+    m, n, k, l, v = w.m, w.n, w.k, w.l, w.v
+    X = plu.colmajor_empty(n, l)
+    X.normal_()
+    Z = plu.colmajor_empty(m, l)
+    Z.normal_()
+    out = {}
+    sm_clock_ghz = peaks["sm_max_mhz"] / 1e3
+    fp32_alu = 152 * 128 * 2 * sm_clock_ghz * 1e9 / 1e12          # TFLOP/s
+    fp64_peak = 1.25                                             # nominal, TFLOP/s
+
+    # pass A X (trans 0) in the workload precision
+    ms = time_calls(torch, lambda: plu.plu_pass(ctx, Ad, 0, X, prec, out=Z), 5, stream)
+    fl = 2.0 * m * n * l
+    abytes = m * n * Ad.element_size()
+    if prec == "fp64":
+        rf = {"bound": "alu", "achieved": fl / ms / 1e9, "peak": fp64_peak, "unit": "TFLOP/s",
+              "peak_source": "nominal FP64 1.25 TFLOP/s"}
+    elif prec == "fp32":
+        rf = {"bound": "alu", "achieved": fl / ms / 1e9, "peak": fp32_alu, "unit": "TFLOP/s",
+              "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % peaks["sm_max_mhz"]}
+    else:
+        rf = {"bound": "hbm", "achieved": abytes / ms / 1e6, "peak": peaks["hbm_gbs"],
+              "unit": "GB/s", "peak_source": "measured"}
+    out["pass"] = (ms, v, rf, "k_gemm (A X)")
+    # re-orthogonalising LU of the m x l panel
+    Zc = Z.clone()
+    ms = time_calls(torch, lambda: (Zc.copy_(Z), plu.plu_lu_reorth(ctx, Zc)), 3, stream)
+    ms_copy = time_calls(torch, lambda: Zc.copy_(Z), 3, stream)
+    ms = max(ms - ms_copy, 1e-6)
+    fl = lu_flops(m, l)
+    out["panel_lu"] = (ms, max(v - 2, 0) + 2, {"bound": "alu", "achieved": fl / ms / 1e9,
+                                               "peak": fp64_peak, "unit": "TFLOP/s",
+                                               "peak_source": "nominal FP64 1.25 TFLOP/s"},
+                       "k_panel_lu")
+    # CholeskyQR2 of the n x l basis
+    Xc = X.clone()
+    ms = time_calls(torch, lambda: (Xc.copy_(X), plu.plu_qr(ctx, Xc)), 3, stream)
+    ms_copy = time_calls(torch, lambda: Xc.copy_(X), 3, stream)
+    ms = max(ms - ms_copy, 1e-6)
+    fl = 2 * (2.0 * n * l * l + 2.0 * n * l * l + l ** 3 / 3.0 + l ** 3 / 3.0)
+    out["qr"] = (ms, 1, {"bound": "alu", "achieved": fl / ms / 1e9, "peak": fp64_peak,
+                         "unit": "TFLOP/s", "peak_source": "nominal FP64 1.25 TFLOP/s"},
+                 "cholqr2")
+    return out
+
+
+def run_ours(args, w):
+    import numpy as np
+    import torch
+    from dataclasses import replace
+
+    import paper_2002_07138_gb300 as plu
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    device = local
+    peaks = {"hbm_gbs": 6791.0, "bf16_tflops": 1934.6, "sm_max_mhz": 2070.0}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks.update(json.load(f))
+    except OSError:
+        peaks["source"] = "fallback"
+
+    wr = replace(w, seed=w.seed + rank)
+    Ad = wr.build("cuda")                                       # column-major FP32 (or FP64)
+    stream = torch.cuda.current_stream()
+    ctx = plu.Context(device, stream.cuda_stream)
+    prec = args.prec
+    flops = pass_flops(w.m, w.n, w.k, w.l, w.v)
+
+    def call(seed, A=Ad, pr=prec):
+        return plu.plu_powerlu(ctx, A, w.k, w.l, w.v, seed=seed, prec=pr)
+
+    for i in range(args.warmup):
+        call(i)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(device)
+    clocks.start()
+    time.sleep(0.3)
+    dist_barrier(ws)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    reps = []
+    for i in range(args.steps):
+        reps.append(call(1000 + i)[4])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist_barrier(ws)
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    ms_max = dist_max(ws, ms_total)
+    value = flops * args.steps * ws / (ms_max / 1e3) / 1e12
+    launches = int(sum(r["launches"] for r in reps))
+    ms_pass = statistics.mean(r["ms_passes"] / r["passes"] for r in reps)
+
+    # accuracy of one call (outside the timed region)
+    def rel_error(res, A):
+        p, q, L, U = res[:4]
+        Ap = A.double()[p.long()][:, q.long()]
+        return float(torch.linalg.norm(Ap - L @ U) / torch.linalg.norm(A.double()))
+
+    err = rel_error(call(7), Ad)
+    opt = float(np.sqrt(np.sum(w.sigma_values()[w.k:] ** 2) / np.sum(w.sigma_values() ** 2)))
+
+    # FP64 plain: the same workload with every step in FP64
+    A64 = synth_colmajor(Ad.double())
+    fp64 = {}
+    if not args.skip_fp64:
+        call(0, A64, "fp64")
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        nrep = 2
+        t0.record(stream)
+        r64 = [call(2000 + i, A64, "fp64")[4] for i in range(nrep)]
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = t0.elapsed_time(t1) / nrep
+        fp64 = {"ms_per_step": ms64,
+                "ms_per_pass": statistics.mean(r["ms_passes"] / r["passes"] for r in r64),
+                "rel_error": rel_error(call(7, A64, "fp64"), Ad),
+                "tflops_per_pass": (flops / w.v) / (statistics.mean(
+                    r["ms_passes"] / r["passes"] for r in r64) / 1e3) / 1e12}
+    del A64
+
+    # end to end through host buffers: H2D of A, the call, D2H of p, q, L, U
+    Ah = torch.empty(Ad.shape[1], Ad.shape[0], dtype=Ad.dtype, pin_memory=True).t()
+    Ah.copy_(Ad)
+    Ae = plu.colmajor_empty(w.m, w.n, dtype=Ad.dtype)
+    ph = torch.empty(w.m, dtype=torch.int32, pin_memory=True)
+    qh = torch.empty(w.n, dtype=torch.int32, pin_memory=True)
+    Lh = torch.empty(w.k, w.m, dtype=torch.float64, pin_memory=True).t()
+    Uh = torch.empty(w.n, w.k, dtype=torch.float64, pin_memory=True).t()
+
+    def e2e_step(seed):
+        Ae.copy_(Ah, non_blocking=True)
+        p, q, L, U, _ = call(seed, Ae)
+        ph.copy_(p, non_blocking=True)
+        qh.copy_(q, non_blocking=True)
+        Lh.copy_(L, non_blocking=True)
+        Uh.copy_(U, non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_step(0)
+    ne = max(2, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for i in range(ne):
+        e2e_step(3000 + i)
+    e2e_ms = dist_max(ws, 1e3 * (time.perf_counter() - t0) / ne)
+    h2d = w.m * w.n * Ad.element_size()
+    d2h = 4 * (w.m + w.n) + 8 * (w.m * w.k + w.k * w.n)
+
+    # roofline of the dominant kernel (timed alone, live)
+    kr = kernel_rooflines(torch, plu, ctx, Ad, w, prec, stream, peaks)
+    share = {name: ms * cnt for name, (ms, cnt, _, _) in kr.items()}
+    dom = max(share, key=share.get)
+    ms_dom, cnt_dom, rf, kname = kr[dom]
+    rf = dict(rf)
+    rf["frac"] = rf["achieved"] / rf["peak"]
+    rf["traffic"] = None
+    rf["kernel"] = kname
+    rf["ms_per_launch"] = ms_dom
+    rf["share_of_step"] = share[dom] / (ms_total / args.steps)
+
+    # CPU baseline: the FP64 oracle on the host cores, one call on the same A
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        Ahost = Ad.double().cpu().numpy()
+        dt, _ = oracle_call(Ahost, w, seed=0)
+        cpu = {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
+               "kind": "oracle", "sample": "one full oracle PowerLU call (FP64, numpy BLAS) on "
+               "the same %dx%d matrix, %.1f s" % (w.m, w.n, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "bf16": "bf16",
+                      "fp8": "fp8e4m3"}[prec], "data": "synthetic",
+            "config": {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "l": w.l, "v": w.v,
+                       "sigma": w.sigma, "storage": "f32" if Ad.dtype == torch.float32 else "f64",
+                       "pass_precision": prec, "between_passes": "f64",
+                       "l2_flush": "inputs larger than L2 (A is %.0f MB)" % (h2d / 1e6),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "ms_per_pass": ms_pass,
+            "tflops_per_pass": (flops / w.v) / (ms_pass / 1e3) / 1e12,
+            "rel_error": err, "eckart_young_optimum": opt,
+            "fp64_plain": fp64,
+            "speedup_vs_fp64_plain": (fp64["ms_per_step"] / (ms_max / args.steps)) if fp64 else None,
+            "e2e": {"value": flops * ws / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                    "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "roofline": rf,
+            "kernel_ms": {name: {"ms_per_launch": ms, "launches_per_step": cnt}
+                          for name, (ms, cnt, _, _) in kr.items()},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+def synth_colmajor(t):
+    import synth
+    return synth.colmajor(t)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fixed_rank_8192", choices=sorted(workloads()))
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "tf32", "bf16", "fp8"])
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    w = workloads()[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

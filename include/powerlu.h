@@ -1,0 +1,195 @@
+/*
+ * powerlu.h -- C ABI of a GB300 (sm_103a) implementation of the hot path of
+ * PowerLU, the pass-efficient randomized LU of Zhang & Mascagni,
+ * "Pass-Efficient Randomized LU Algorithms for Computing Low-Rank Matrix
+ * Approximation" (arXiv 2002.07138).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are column-major: entry (i, j) of an R x C matrix M with
+ *    leading dimension ld >= max(R, 1) lives at M[i + j * ld].
+ *  - Every matrix and index pointer is DEVICE memory owned by the caller,
+ *    unless the argument says "host".  The library never frees or keeps a
+ *    caller pointer beyond the call.
+ *  - Work is enqueued on the context's CUDA stream.  Entry points that
+ *    produce factors end with one stream synchronisation and return the
+ *    device status of the call (PLU_ETIMEOUT, PLU_ENUMERIC, ...), unless
+ *    plu_set_async(ctx, 1) was called; then they return after enqueueing
+ *    and plu_check() reports the device status later.
+ *  - Arguments are validated on the host before anything is launched; a
+ *    violation returns PLU_EINVAL and launches nothing.
+ *  - plu_last_error() describes the last non-PLU_OK status of a context.
+ *  - A context is used by one host thread at a time.
+ *
+ * Index vectors are 0-based int32: p (length m) and q (length n) encode
+ * P and Q by  (P A Q^T)(i, j) = A(p[i], q[j]).
+ */
+#ifndef POWERLU_H
+#define POWERLU_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Arithmetic of the passes over A (Sec. 3.3 counts them; v passes).
+ * PLU_FP64: FP64 FMA.  PLU_FP32: FP32 FMA, FP32 accumulation.
+ * PLU_TF32, PLU_BF16, PLU_FP8_E4M3: tensor-core products with FP32
+ * accumulation (A converted to the operand type); the last pass Y = A V_k
+ * (and G = A V) is then taken in split precision.  Everything between the
+ * passes (LU, QR, rank, tail) is FP64 in every mode. */
+typedef enum {
+    PLU_FP64 = 0,
+    PLU_TF32 = 1,
+    PLU_BF16 = 2,
+    PLU_FP8_E4M3 = 3,
+    PLU_FP32 = 4
+} plu_prec;
+
+/* Element type of A. */
+typedef enum { PLU_F64 = 0, PLU_F32 = 1 } plu_dtype;
+
+typedef enum {
+    PLU_OK = 0,
+    PLU_EINVAL = 1,        /* bad argument (host check, nothing launched)       */
+    PLU_ENOMEM = 2,        /* workspace allocation failed                        */
+    PLU_ECUDA = 3,         /* a CUDA runtime call failed                         */
+    PLU_ENUMERIC = 4,      /* non-finite value or zero pivot in a final LU       */
+    PLU_ETIMEOUT = 5,      /* a device-side wait ran out of its iteration budget */
+    PLU_TOL_NOT_MET = 6,   /* fixed precision: l columns did not reach eps       */
+    PLU_EUNSUPPORTED = 7   /* combination not built (e.g. precision for dtype)   */
+} plu_status;
+
+/* Dense input matrix A (m x n), column-major, device memory, not owned. */
+typedef struct {
+    int64_t m, n, ld;
+    int32_t dtype;          /* plu_dtype */
+    const void* data;
+} plu_matrix;
+
+/* Per-call report (host struct, filled when a non-NULL pointer is given). */
+typedef struct {
+    double ms_total;        /* device time of the call (CUDA events)             */
+    double ms_passes;       /* device time of the kernels that read A            */
+    int32_t passes;         /* number of passes over A launched                  */
+    int32_t rank;           /* k used for the factors                            */
+    double indicator;       /* fixed precision: sqrt(max(E,0))/||A||_F, else -1  */
+    double normA2;          /* fixed precision: ||A||_F^2, else -1               */
+    int32_t info1, info2;   /* first zero pivot (1-based) of lu(Y), lu(B^T)      */
+    double flops_passes;    /* algorithmic flops of the passes, 2 m n cols each   */
+    double bytes_passes;    /* algorithmic bytes of the passes (A + operands)    */
+    int32_t launches;       /* library kernels launched by the call              */
+    int32_t reserved;
+} plu_report;
+
+typedef struct plu_ctx plu_ctx;
+
+/* Create a context bound to `device` and the CUDA stream `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  The context owns a
+ * device workspace that grows on demand and is freed by plu_destroy. */
+plu_status plu_create(plu_ctx** ctx, int device, void* cuda_stream);
+void plu_destroy(plu_ctx* ctx);
+const char* plu_last_error(const plu_ctx* ctx);
+plu_status plu_set_stream(plu_ctx* ctx, void* cuda_stream);
+/* async != 0: factor calls return after enqueueing (no synchronisation). */
+plu_status plu_set_async(plu_ctx* ctx, int async);
+/* Synchronise the stream and return (then clear) the device status. */
+plu_status plu_check(plu_ctx* ctx);
+/* Iteration budget of every device-side wait (grid barriers); <= 0 restores
+ * the default (about a second).  A tiny budget makes the waits give up and
+ * the call return PLU_ETIMEOUT, with the context still usable. */
+plu_status plu_set_wait_budget(plu_ctx* ctx, int64_t spins);
+
+/* ---------------------------------------------------------------------
+ * Steps of the hot path, one entry point each (Sec. 3, Alg. gpowerlu).
+ * ------------------------------------------------------------------- */
+
+/* a1. Gaussian test matrix Omega (Alg. bpowerlu step 1; Alg. gpowerlu):
+ * out (rows x cols, ld) receives i.i.d. N(0,1) values, entry (i, j) being the
+ * Box-Muller output number t = i + j*rows of the Philox4x32-10 stream
+ * (key = seed, counter = (t/2, stream_id)).  The same (seed, stream_id,
+ * rows, cols) gives bit-identical values on every call. */
+plu_status plu_gaussian(plu_ctx* ctx, int64_t rows, int64_t cols, uint64_t seed,
+                        uint32_t stream_id, double* out, int64_t ld);
+
+/* a2/a4/a6. One pass over A (the products of Alg. gpowerlu and Alg.
+ * bpowerlu step 3): Y = A X (trans = 0; X n x cols, Y m x cols) or
+ * Y = A^T X (trans = 1; X m x cols, Y n x cols), in arithmetic `prec`.
+ * X and Y are FP64 and must not overlap. */
+plu_status plu_pass(plu_ctx* ctx, const plu_matrix* A, int trans, const double* X,
+                    int64_t ldx, int cols, plu_prec prec, double* Y, int64_t ldy);
+
+/* a3. [X, ~] = lu(X) in place (Alg. gpowerlu, the LU re-orthogonalisation):
+ * X (rows x cols, rows >= cols) is overwritten by the permuted unit lower
+ * factor P^T L of the partial-pivoting LU P X = L U (ties: first row in the
+ * LAPACK swap order).  U is discarded. */
+plu_status plu_lu_reorth(plu_ctx* ctx, int64_t rows, int cols, double* X, int64_t ldx);
+
+/* a3/a8. [L, U, P] = lu(X) (Alg. bpowerlu steps 4 and 6): X (rows x cols,
+ * rows >= cols) is read; perm (rows) receives P as perm[i] = source row of
+ * row i of P X; L (rows x cols, ldL) the unit lower trapezoidal factor in
+ * pivoted order; U (cols x cols, ldU) the upper triangular factor.  X is
+ * used as scratch and destroyed.  info (device int32, nullable) receives the
+ * first zero-pivot column (1-based) or 0. */
+plu_status plu_getrf(plu_ctx* ctx, int64_t rows, int cols, double* X, int64_t ldx,
+                     int32_t* perm, double* L, int64_t ldL, double* U, int64_t ldU,
+                     int32_t* info);
+
+/* a5. [V, ~] = qr(X) (Alg. gpowerlu, last step): X (rows x cols) is
+ * overwritten by Q with orthonormal columns, X = Q R, R_ii > 0.  R (cols x
+ * cols, ldR) receives R when non-NULL.  FP64 CholeskyQR2. */
+plu_status plu_qr(plu_ctx* ctx, int64_t rows, int cols, double* X, int64_t ldx,
+                  double* R, int64_t ldR);
+
+/* a7. Blocked rank determination (Alg. adaptivewithoutupdating; precise != 0
+ * adds the per-column loop of Sec. 6.4): from G = A V (rows x cols) and
+ * normA2 = ||A||_F^2 (host value), find the first block of b columns (or
+ * column) with E <= eps^2 ||A||_F^2, E = ||A||_F^2 - sum ||G(:, j)||^2
+ * (Thm. errorerror, FP64).  k_out and E_out are host pointers.  Returns
+ * PLU_TOL_NOT_MET (k = cols) when the tolerance is not met. */
+plu_status plu_rank(plu_ctx* ctx, int64_t rows, int cols, const double* G, int64_t ldg,
+                    double normA2, double eps, int b, int precise, int* k_out,
+                    double* E_out);
+
+/* ||A||_F^2 in FP64 (Alg. adaptivewithoutupdating step 1); out is a host
+ * pointer.  One pass over A. */
+plu_status plu_norm2(plu_ctx* ctx, const plu_matrix* A, double* out);
+
+/* ---------------------------------------------------------------------
+ * Whole algorithms.
+ * ------------------------------------------------------------------- */
+
+/* Fixed rank (Def. lowrank): Alg. bpowerlu with steps 1-2 replaced by
+ * Alg. gpowerlu.  1 <= k <= l < min(m, n), v >= 2.  Outputs: p (m), q (n),
+ * L (m x k, ldL >= m), U (k x n, ldU >= k) with P A Q^T ~= L U.
+ * Exactly v passes over A. */
+plu_status plu_powerlu(plu_ctx* ctx, const plu_matrix* A, int k, int l, int v,
+                       uint64_t seed, plu_prec prec, int32_t* p, int32_t* q,
+                       double* L, int64_t ldL, double* U, int64_t ldU,
+                       plu_report* rep);
+
+/* Fixed precision: Alg. powerlufp on Alg. adaptivewithoutupdating
+ * (precise != 0: the per-column refinement of Sec. 6.4).  0 < eps < 1,
+ * 1 <= b <= l < min(m, n), v >= 2.  *k_out (host) receives the rank;
+ * L must hold m x l (ldL >= m) and U l x n (ldU >= l); the first k columns
+ * of L and rows of U are the factors.  Returns PLU_TOL_NOT_MET with k = l
+ * and valid factors when l columns do not reach eps.  One stream
+ * synchronisation to read k.  v + 1 passes over A (one for ||A||_F). */
+plu_status plu_powerlu_fp(plu_ctx* ctx, const plu_matrix* A, double eps, int b, int l,
+                          int v, int precise, uint64_t seed, plu_prec prec, int* k_out,
+                          int32_t* p, int32_t* q, double* L, int64_t ldL, double* U,
+                          int64_t ldU, plu_report* rep);
+
+/* Single pass (Alg. singlepasslu, Sec. 5): Omega m x k, G = A^T Omega and
+ * H = A G from one read of A, then two LUs.  1 <= k < min(m, n).
+ * Outputs as plu_powerlu. */
+plu_status plu_singlepass(plu_ctx* ctx, const plu_matrix* A, int k, uint64_t seed,
+                          plu_prec prec, int32_t* p, int32_t* q, double* L, int64_t ldL,
+                          double* U, int64_t ldU, plu_report* rep);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POWERLU_H */

@@ -106,16 +106,13 @@ def powerlu(A, k, l, v, seed, return_basis=False):
     return p, q, L, U
 
 
-def adaptive_rank(A, eps, b, l, v, seed, precise=False):
-    """Alg. adaptivewithoutupdating (precise=True: with the per-column loop
-    of Sec. 6.4).  Returns (k, V, G, E, met): V n x l, G = A V m x l, E the
-    residual indicator after k columns (Thm. errorerror), met whether
-    E <= eps^2 ||A||_F^2 was reached."""
-    Ac = _wrap(A)
-    E = float(np.sum(Ac.A * Ac.A))
+def rank_scan(G, normA2, eps, b, precise=False):
+    """The loop of Alg. adaptivewithoutupdating (steps 4-10), or with the
+    per-column refinement of Sec. 6.4, on G = A V and E = ||A||_F^2.
+    Returns (k, E, met)."""
+    E = float(normA2)
     acc = eps * eps * E
-    V = gpowerlu(Ac, l, v, seed)
-    G = Ac.mul(V)
+    l = G.shape[1]
     k = 0
     met = False
     nblocks = (l + b - 1) // b
@@ -137,6 +134,19 @@ def adaptive_rank(A, eps, b, l, v, seed, precise=False):
                 met = True
         if met:
             break
+    return k, E, met
+
+
+def adaptive_rank(A, eps, b, l, v, seed, precise=False):
+    """Alg. adaptivewithoutupdating (precise=True: with the per-column loop
+    of Sec. 6.4).  Returns (k, V, G, E, met): V n x l, G = A V m x l, E the
+    residual indicator after k columns (Thm. errorerror), met whether
+    E <= eps^2 ||A||_F^2 was reached."""
+    Ac = _wrap(A)
+    E0 = float(np.sum(Ac.A * Ac.A))
+    V = gpowerlu(Ac, l, v, seed)
+    G = Ac.mul(V)
+    k, E, met = rank_scan(G, E0, eps, b, precise)
     return k, V, G, E, met
 
 

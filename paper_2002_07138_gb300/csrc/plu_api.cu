@@ -1,0 +1,594 @@
+// C ABI entry points (include/powerlu.h): argument checks, workspace
+// layout and the order of the steps of PowerLU (Alg. bpowerlu with
+// Alg. gpowerlu), PowerLU_FP (Alg. powerlufp on Alg. adaptivewithoutupdating)
+// on one CUDA stream.
+#include "plu_internal.h"
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+using namespace plu;
+
+thread_local long long plu::g_launches = 0;
+
+struct plu_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    char* ws = nullptr;
+    size_t ws_cap = 0;
+    int* d_status = nullptr;   // device status word (DevStatus)
+    int* h_status = nullptr;   // pinned mirror
+    int* d_kmet = nullptr;     // rank scan results (k, met)
+    double* d_scal = nullptr;  // device scalars: [0] ||A||_F^2, [1] E
+    int* h_kmet = nullptr;
+    double* h_scal = nullptr;
+    int async = 0;
+    int64_t spin_budget = kDefaultSpin;
+    char err[512] = {0};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    static constexpr int64_t kDefaultSpin = 16LL << 20;
+};
+
+namespace {
+
+constexpr uint32_t kStreamOmegaN = 1;   // n x l (odd v)
+constexpr uint32_t kStreamOmegaM = 2;   // m x l (even v)
+constexpr uint32_t kStreamOmegaSP = 3;  // m x k (single pass)
+
+plu_status fail(plu_ctx* c, plu_status st, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define PLU_CUDA(ctx, call)                                                                  \
+    do {                                                                                     \
+        cudaError_t _e = (call);                                                             \
+        if (_e != cudaSuccess)                                                               \
+            return fail(ctx, PLU_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), \
+                        __FILE__, __LINE__);                                                 \
+    } while (0)
+
+#define PLU_TRY(expr)                      \
+    do {                                   \
+        plu_status _s = (expr);            \
+        if (_s != PLU_OK) return _s;       \
+    } while (0)
+
+plu_status ensure_ws(plu_ctx* c, size_t bytes) {
+    if (bytes <= c->ws_cap) return PLU_OK;
+    size_t want = bytes + (bytes >> 3) + (1 << 20);
+    if (c->ws) {
+        PLU_CUDA(c, cudaStreamSynchronize(c->stream));
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_cap = 0;
+    }
+    if (cudaMalloc(&c->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        c->ws = nullptr;
+        return fail(c, PLU_ENOMEM, "workspace allocation of %zu bytes failed", want);
+    }
+    c->ws_cap = want;
+    return PLU_OK;
+}
+
+// Two-phase layout: first count, then carve.
+struct Layout {
+    size_t total = 0;
+    size_t add(size_t bytes) {
+        size_t off = (total + 255) & ~size_t(255);
+        total = off + bytes;
+        return off;
+    }
+};
+
+plu_status bind(plu_ctx* c) {
+    if (!c) return PLU_EINVAL;
+    PLU_CUDA(c, cudaSetDevice(c->device));
+    return PLU_OK;
+}
+
+plu_status check_matrix(plu_ctx* c, const plu_matrix* A) {
+    if (!A || !A->data) return fail(c, PLU_EINVAL, "A is NULL");
+    if (A->m < 1 || A->n < 1) return fail(c, PLU_EINVAL, "A must be at least 1 x 1");
+    if (A->ld < A->m) return fail(c, PLU_EINVAL, "ld (%lld) < m (%lld)", (long long)A->ld, (long long)A->m);
+    if (A->dtype != PLU_F32 && A->dtype != PLU_F64) return fail(c, PLU_EINVAL, "bad dtype %d", A->dtype);
+    if (A->m > (int64_t(1) << 31) - 1 || A->n > (int64_t(1) << 31) - 1)
+        return fail(c, PLU_EINVAL, "dimensions must fit int32");
+    return PLU_OK;
+}
+
+plu_status check_prec(plu_ctx* c, int prec) {
+    if (prec == PLU_FP64 || prec == PLU_FP32) return PLU_OK;
+    if (prec == PLU_TF32 || prec == PLU_BF16 || prec == PLU_FP8_E4M3)
+        return fail(c, PLU_EUNSUPPORTED, "precision %d is not built in this library", prec);
+    return fail(c, PLU_EINVAL, "bad precision %d", prec);
+}
+
+// Finish a call: read the device status word unless asynchronous.
+plu_status finish(plu_ctx* c) {
+    if (c->async) return PLU_OK;
+    return plu_check(c);
+}
+
+plu_status dev_status_to_plu(plu_ctx* c, int st) {
+    if (st == DEV_OK) return PLU_OK;
+    if (st == DEV_TIMEOUT) return fail(c, PLU_ETIMEOUT, "a device-side wait ran out of its budget");
+    return fail(c, PLU_ENUMERIC, "non-finite value or breakdown in an FP64 factorisation");
+}
+
+// ---- workspace needs of the steps
+size_t pass_ws(int64_t M, int64_t N, int64_t K, int prec, int sms) {
+    size_t b = gemm_partials_bytes(M, N, K, prec, sms) + 256;
+    if (prec == PLU_FP32) b += size_t(K) * N * sizeof(float) + 256;
+    return b;
+}
+
+plu_status do_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X, int64_t ldx,
+                   int cols, int prec, double* Y, int64_t ldy, char* ws) {
+    const int64_t M = trans ? A->n : A->m;
+    const int64_t K = trans ? A->m : A->n;
+    Workspace w;
+    w.base = ws;
+    w.cap = pass_ws(M, cols, K, prec, c->num_sms);
+    void* part = w.take(gemm_partials_bytes(M, cols, K, prec, c->num_sms));
+    float* b32 = nullptr;
+    if (prec == PLU_FP32) b32 = static_cast<float*>(w.take(size_t(K) * cols * sizeof(float)));
+    PLU_CUDA(c, launch_gemm_simt(trans, M, cols, K, A->data, A->dtype, A->ld, X, ldx, Y, ldy, prec,
+                                 part, b32, c->num_sms, c->stream));
+    return PLU_OK;
+}
+
+struct PowerLUPlan {
+    // offsets into the workspace
+    size_t V, Z, step, L1, U1T, BT, U2T, tailpart, cn, total;
+};
+
+// Shared by the fixed-rank and fixed-precision drivers: workspace for
+// Alg. gpowerlu (basis V n x l, products Z m x l, step scratch) and the tail
+// (Alg. bpowerlu steps 4-8) at rank kmax.
+PowerLUPlan plan_powerlu(int64_t m, int64_t n, int l, int kmax, int prec, int sms) {
+    Layout lay;
+    PowerLUPlan p{};
+    p.V = lay.add(size_t(n) * l * sizeof(double));
+    p.Z = lay.add(size_t(m) * l * sizeof(double));
+    size_t step = pass_ws(m, l, n, prec, sms);
+    size_t t = pass_ws(n, l, m, prec, sms);
+    if (t > step) step = t;
+    t = panel_scratch_bytes(m > n ? m : n, l);
+    if (t > step) step = t;
+    t = qr_scratch_bytes(n, l, sms);
+    if (t > step) step = t;
+    p.step = lay.add(step);
+    p.L1 = lay.add(size_t(m) * kmax * sizeof(double));
+    p.U1T = lay.add(size_t(kmax) * kmax * sizeof(double));
+    p.BT = lay.add(size_t(n) * kmax * sizeof(double));
+    p.U2T = lay.add(size_t(kmax) * kmax * sizeof(double));
+    size_t tp = gemm_f64_partials_bytes(n, kmax, kmax, sms);
+    t = gemm_f64_partials_bytes(m, kmax, kmax, sms);
+    if (t > tp) tp = t;
+    p.tailpart = lay.add(tp);
+    p.cn = lay.add(size_t(l) * sizeof(double) + norm2_scratch_bytes(sms));
+    p.total = lay.total + 256;
+    return p;
+}
+
+struct PassTimer {
+    plu_ctx* c;
+    bool on;
+    cudaEvent_t ev[64];
+    int n = 0;
+    explicit PassTimer(plu_ctx* ctx, bool enable) : c(ctx), on(enable) {}
+    ~PassTimer() {
+        for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
+    }
+    void mark() {
+        if (!on || n >= 64) return;
+        cudaEventCreate(&ev[n]);
+        cudaEventRecord(ev[n], c->stream);
+        ++n;
+    }
+    // sum of the (start, stop) pairs
+    double pairs_ms() {
+        double s = 0.0;
+        for (int i = 0; i + 1 < n; i += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) s += ms;
+        }
+        return s;
+    }
+};
+
+// Alg. gpowerlu into V (n x l).  Returns the number of passes launched.
+plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t seed, int prec,
+                        double* V, double* Z, char* step, PassTimer& pt, int* passes) {
+    const int64_t m = A->m, n = A->n;
+    const int p = (v - 1) / 2;
+    int np = 0;
+    auto pass = [&](int trans, const double* X, int64_t ldx, double* Y, int64_t ldy) -> plu_status {
+        pt.mark();
+        PLU_TRY(do_pass(c, A, trans, X, ldx, l, prec, Y, ldy, step));
+        pt.mark();
+        ++np;
+        return PLU_OK;
+    };
+    auto reorth = [&](int64_t rows, double* X) -> plu_status {
+        PLU_CUDA(c, launch_panel_lu(rows, l, X, rows, 0, nullptr, nullptr, 0, 0, nullptr, 0, 0,
+                                    nullptr, step, c->d_status, c->spin_budget, c->num_sms,
+                                    c->stream));
+        return PLU_OK;
+    };
+    auto qr = [&](double* X) -> plu_status {
+        PLU_CUDA(c, launch_cholqr2(n, l, X, n, nullptr, 0, step, c->d_status, c->num_sms, c->stream));
+        return PLU_OK;
+    };
+    if (v % 2 == 0) {
+        PLU_CUDA(c, launch_gaussian(m, l, seed, kStreamOmegaM, Z, m, c->stream));
+        PLU_TRY(pass(1, Z, m, V, n));                 // A^T Omega
+        if (v > 2) PLU_TRY(reorth(n, V));
+        else PLU_TRY(qr(V));
+    } else {
+        PLU_CUDA(c, launch_gaussian(n, l, seed, kStreamOmegaN, V, n, c->stream));
+    }
+    for (int i = 1; i <= p; ++i) {
+        PLU_TRY(pass(0, V, n, Z, m));                 // A V
+        PLU_TRY(reorth(m, Z));
+        PLU_TRY(pass(1, Z, m, V, n));                 // A^T V
+        if (i == p) PLU_TRY(qr(V));
+        else PLU_TRY(reorth(n, V));
+    }
+    *passes = np;
+    return PLU_OK;
+}
+
+// Alg. bpowerlu steps 4-8 on Y (m x k, ld m, destroyed) and Vk (n x k, ld n).
+plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const double* Vk,
+                    char* ws, const PowerLUPlan& pl, char* step, int32_t* p, int32_t* q,
+                    double* L, int64_t ldL, double* U, int64_t ldU, int32_t* info2dev) {
+    double* L1 = reinterpret_cast<double*>(ws + pl.L1);
+    double* U1T = reinterpret_cast<double*>(ws + pl.U1T);
+    double* BT = reinterpret_cast<double*>(ws + pl.BT);
+    double* U2T = reinterpret_cast<double*>(ws + pl.U2T);
+    void* tp = ws + pl.tailpart;
+    // [L1, U1, P] = lu(Y)
+    PLU_CUDA(c, launch_panel_lu(m, k, Y, m, 1, p, L1, m, 0, U1T, k, 1, info2dev, step, c->d_status,
+                                c->spin_budget, c->num_sms, c->stream));
+    // B^T = Vk U1^T
+    PLU_CUDA(c, launch_gemm_f64(0, 0, n, k, k, Vk, n, U1T, k, BT, n, tp, c->num_sms, c->stream));
+    // [L2, U2, Q] = lu(B^T); U = L2^T written straight into U
+    PLU_CUDA(c, launch_panel_lu(n, k, BT, n, 1, q, U, ldU, 1, U2T, k, 1, info2dev + 1, step,
+                                c->d_status, c->spin_budget, c->num_sms, c->stream));
+    // L = L1 U2^T
+    PLU_CUDA(c, launch_gemm_f64(0, 0, m, k, k, L1, m, U2T, k, L, ldL, tp, c->num_sms, c->stream));
+    return PLU_OK;
+}
+
+void fill_pass_report(plu_report* rep, const plu_matrix* A, int passes_l, int l, int k_last,
+                      int prec, bool final_pass) {
+    const double mn = double(A->m) * double(A->n);
+    const double abytes = mn * (A->dtype == PLU_F32 ? 4.0 : 8.0);
+    double fl = 2.0 * mn * l * passes_l;
+    double by = (abytes + double(A->m + A->n) * l * 8.0) * passes_l;
+    if (final_pass) {
+        fl += 2.0 * mn * k_last;
+        by += abytes + double(A->m + A->n) * k_last * 8.0;
+    }
+    (void)prec;
+    rep->flops_passes = fl;
+    rep->bytes_passes = by;
+}
+
+}  // namespace
+
+// ======================================================================
+extern "C" {
+
+plu_status plu_create(plu_ctx** out, int device, void* cuda_stream) {
+    if (!out) return PLU_EINVAL;
+    *out = nullptr;
+    plu_ctx* c = new (std::nothrow) plu_ctx();
+    if (!c) return PLU_ENOMEM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        delete c;
+        return PLU_ECUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMalloc(&c->d_status, 64) != cudaSuccess ||
+        cudaMallocHost(&c->h_status, 64) != cudaSuccess) {
+        cudaGetLastError();
+        plu_destroy(c);
+        return PLU_ECUDA;
+    }
+    c->d_kmet = c->d_status + 4;
+    c->d_scal = reinterpret_cast<double*>(c->d_status + 8);
+    c->h_kmet = c->h_status + 4;
+    c->h_scal = reinterpret_cast<double*>(c->h_status + 8);
+    if (cudaMemset(c->d_status, 0, 64) != cudaSuccess ||
+        cudaEventCreate(&c->ev[0]) != cudaSuccess || cudaEventCreate(&c->ev[1]) != cudaSuccess) {
+        cudaGetLastError();
+        plu_destroy(c);
+        return PLU_ECUDA;
+    }
+    *out = c;
+    return PLU_OK;
+}
+
+void plu_destroy(plu_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    if (c->ws) cudaFree(c->ws);
+    if (c->d_status) cudaFree(c->d_status);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+const char* plu_last_error(const plu_ctx* c) { return c ? c->err : "NULL context"; }
+
+plu_status plu_set_stream(plu_ctx* c, void* s) {
+    if (!c) return PLU_EINVAL;
+    c->stream = static_cast<cudaStream_t>(s);
+    return PLU_OK;
+}
+
+plu_status plu_set_async(plu_ctx* c, int async) {
+    if (!c) return PLU_EINVAL;
+    c->async = async ? 1 : 0;
+    return PLU_OK;
+}
+
+plu_status plu_set_wait_budget(plu_ctx* c, int64_t spins) {
+    if (!c) return PLU_EINVAL;
+    c->spin_budget = spins > 0 ? spins : plu_ctx::kDefaultSpin;
+    return PLU_OK;
+}
+
+plu_status plu_check(plu_ctx* c) {
+    PLU_TRY(bind(c));
+    PLU_CUDA(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PLU_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int st = c->h_status[0];
+    if (st != DEV_OK) {
+        PLU_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+        PLU_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return dev_status_to_plu(c, st);
+}
+
+plu_status plu_gaussian(plu_ctx* c, int64_t rows, int64_t cols, uint64_t seed, uint32_t stream_id,
+                        double* out, int64_t ld) {
+    PLU_TRY(bind(c));
+    if (rows < 0 || cols < 0 || (rows * cols > 0 && !out) || ld < (rows > 1 ? rows : 1))
+        return fail(c, PLU_EINVAL, "bad gaussian arguments");
+    PLU_CUDA(c, launch_gaussian(rows, cols, seed, stream_id, out, ld, c->stream));
+    return finish(c);
+}
+
+plu_status plu_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X, int64_t ldx,
+                    int cols, plu_prec prec, double* Y, int64_t ldy) {
+    PLU_TRY(bind(c));
+    PLU_TRY(check_matrix(c, A));
+    PLU_TRY(check_prec(c, prec));
+    const int64_t M = trans ? A->n : A->m;
+    const int64_t K = trans ? A->m : A->n;
+    if (cols < 1 || !X || !Y || ldx < K || ldy < M) return fail(c, PLU_EINVAL, "bad pass operands");
+    PLU_TRY(ensure_ws(c, pass_ws(M, cols, K, prec, c->num_sms)));
+    PLU_TRY(do_pass(c, A, trans, X, ldx, cols, prec, Y, ldy, c->ws));
+    return finish(c);
+}
+
+plu_status plu_lu_reorth(plu_ctx* c, int64_t rows, int cols, double* X, int64_t ldx) {
+    PLU_TRY(bind(c));
+    if (cols < 1 || rows < cols || !X || ldx < rows || cols > 2048)
+        return fail(c, PLU_EINVAL, "lu_reorth needs rows >= cols >= 1, cols <= 2048, ldx >= rows");
+    PLU_TRY(ensure_ws(c, panel_scratch_bytes(rows, cols)));
+    PLU_CUDA(c, launch_panel_lu(rows, cols, X, ldx, 0, nullptr, nullptr, 0, 0, nullptr, 0, 0, nullptr,
+                                c->ws, c->d_status, c->spin_budget, c->num_sms, c->stream));
+    return finish(c);
+}
+
+plu_status plu_getrf(plu_ctx* c, int64_t rows, int cols, double* X, int64_t ldx, int32_t* perm,
+                     double* L, int64_t ldL, double* U, int64_t ldU, int32_t* info) {
+    PLU_TRY(bind(c));
+    if (cols < 1 || rows < cols || !X || ldx < rows || cols > 2048 || !perm || !L || !U ||
+        ldL < rows || ldU < cols)
+        return fail(c, PLU_EINVAL, "getrf needs rows >= cols >= 1, cols <= 2048 and valid outputs");
+    PLU_TRY(ensure_ws(c, panel_scratch_bytes(rows, cols)));
+    PLU_CUDA(c, launch_panel_lu(rows, cols, X, ldx, 1, perm, L, ldL, 0, U, ldU, 0, info, c->ws,
+                                c->d_status, c->spin_budget, c->num_sms, c->stream));
+    return finish(c);
+}
+
+plu_status plu_qr(plu_ctx* c, int64_t rows, int cols, double* X, int64_t ldx, double* R, int64_t ldR) {
+    PLU_TRY(bind(c));
+    if (cols < 1 || rows < cols || !X || ldx < rows || (R && ldR < cols))
+        return fail(c, PLU_EINVAL, "qr needs rows >= cols >= 1");
+    PLU_TRY(ensure_ws(c, qr_scratch_bytes(rows, cols, c->num_sms)));
+    PLU_CUDA(c, launch_cholqr2(rows, cols, X, ldx, R, ldR, c->ws, c->d_status, c->num_sms, c->stream));
+    return finish(c);
+}
+
+plu_status plu_norm2(plu_ctx* c, const plu_matrix* A, double* out) {
+    PLU_TRY(bind(c));
+    PLU_TRY(check_matrix(c, A));
+    if (!out) return fail(c, PLU_EINVAL, "out is NULL");
+    PLU_TRY(ensure_ws(c, norm2_scratch_bytes(c->num_sms)));
+    PLU_CUDA(c, launch_norm2(A->data, A->dtype, A->m, A->n, A->ld, c->d_scal, c->ws, c->num_sms,
+                             c->stream));
+    PLU_CUDA(c, cudaMemcpyAsync(c->h_scal, c->d_scal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    PLU_TRY(plu_check(c));
+    *out = c->h_scal[0];
+    return PLU_OK;
+}
+
+plu_status plu_rank(plu_ctx* c, int64_t rows, int cols, const double* G, int64_t ldg, double normA2,
+                    double eps, int b, int precise, int* k_out, double* E_out) {
+    PLU_TRY(bind(c));
+    if (rows < 1 || cols < 1 || !G || ldg < rows || !(eps > 0.0 && eps < 1.0) || b < 1 || !k_out)
+        return fail(c, PLU_EINVAL, "bad rank arguments");
+    PLU_TRY(ensure_ws(c, size_t(cols) * sizeof(double) + 256));
+    double* cn = reinterpret_cast<double*>(c->ws);
+    c->h_scal[0] = normA2;
+    PLU_CUDA(c, cudaMemcpyAsync(c->d_scal, c->h_scal, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    PLU_CUDA(c, launch_colnorm2(rows, cols, G, ldg, cn, c->stream));
+    PLU_CUDA(c, launch_rank_scan(cn, cols, c->d_scal, eps, b, precise, c->d_kmet, c->d_scal + 1,
+                                 c->stream));
+    PLU_CUDA(c, cudaMemcpyAsync(c->h_kmet, c->d_kmet, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PLU_CUDA(c, cudaMemcpyAsync(c->h_scal + 1, c->d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
+    PLU_TRY(plu_check(c));
+    *k_out = c->h_kmet[0];
+    if (E_out) *E_out = c->h_scal[1];
+    return c->h_kmet[1] ? PLU_OK : fail(c, PLU_TOL_NOT_MET, "tolerance not met within %d columns", cols);
+}
+
+plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uint64_t seed,
+                       plu_prec prec, int32_t* p, int32_t* q, double* L, int64_t ldL, double* U,
+                       int64_t ldU, plu_report* rep) {
+    PLU_TRY(bind(c));
+    PLU_TRY(check_matrix(c, A));
+    PLU_TRY(check_prec(c, prec));
+    const int64_t m = A->m, n = A->n;
+    const int64_t mn = m < n ? m : n;
+    if (k < 1 || l < k || l >= mn) return fail(c, PLU_EINVAL, "need 1 <= k <= l < min(m, n)");
+    if (v < 2) return fail(c, PLU_EINVAL, "need v >= 2 passes");
+    if (l > 2048) return fail(c, PLU_EINVAL, "l > 2048 is not supported");
+    if (!p || !q || !L || !U || ldL < m || ldU < k) return fail(c, PLU_EINVAL, "bad outputs");
+    const PowerLUPlan pl = plan_powerlu(m, n, l, k, prec, c->num_sms);
+    PLU_TRY(ensure_ws(c, pl.total));
+    char* ws = c->ws;
+    double* V = reinterpret_cast<double*>(ws + pl.V);
+    double* Z = reinterpret_cast<double*>(ws + pl.Z);
+    char* step = ws + pl.step;
+    PassTimer pt(c, rep != nullptr);
+    const long long launches0 = g_launches;
+    if (rep) PLU_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+    int np = 0;
+    PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pt, &np));
+    // Y = A V(:, 1:k) (Alg. bpowerlu step 3), the v-th pass
+    pt.mark();
+    PLU_TRY(do_pass(c, A, 0, V, n, k, prec, Z, m, step));
+    pt.mark();
+    ++np;
+    int32_t* info = reinterpret_cast<int32_t*>(ws + pl.cn);
+    PLU_TRY(run_tail(c, m, n, k, Z, V, ws, pl, step, p, q, L, ldL, U, ldU, info));
+    if (rep) {
+        PLU_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+        int32_t hinfo[2] = {0, 0};
+        PLU_CUDA(c, cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, c->stream));
+        PLU_CUDA(c, cudaStreamSynchronize(c->stream));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+        memset(rep, 0, sizeof(*rep));
+        rep->ms_total = ms;
+        rep->ms_passes = pt.pairs_ms();
+        rep->passes = np;
+        rep->rank = k;
+        rep->indicator = -1.0;
+        rep->normA2 = -1.0;
+        rep->info1 = hinfo[0];
+        rep->info2 = hinfo[1];
+        fill_pass_report(rep, A, np - 1, l, k, prec, true);
+        rep->launches = int32_t(g_launches - launches0);
+    }
+    return finish(c);
+}
+
+plu_status plu_powerlu_fp(plu_ctx* c, const plu_matrix* A, double eps, int b, int l, int v,
+                          int precise, uint64_t seed, plu_prec prec, int* k_out, int32_t* p,
+                          int32_t* q, double* L, int64_t ldL, double* U, int64_t ldU,
+                          plu_report* rep) {
+    PLU_TRY(bind(c));
+    PLU_TRY(check_matrix(c, A));
+    PLU_TRY(check_prec(c, prec));
+    const int64_t m = A->m, n = A->n;
+    const int64_t mn = m < n ? m : n;
+    if (!(eps > 0.0 && eps < 1.0)) return fail(c, PLU_EINVAL, "need 0 < eps < 1");
+    if (b < 1 || l < b || l >= mn) return fail(c, PLU_EINVAL, "need 1 <= b <= l < min(m, n)");
+    if (v < 2) return fail(c, PLU_EINVAL, "need v >= 2 passes");
+    if (l > 2048) return fail(c, PLU_EINVAL, "l > 2048 is not supported");
+    if (!k_out || !p || !q || !L || !U || ldL < m || ldU < l) return fail(c, PLU_EINVAL, "bad outputs");
+    const PowerLUPlan pl = plan_powerlu(m, n, l, l, prec, c->num_sms);
+    PLU_TRY(ensure_ws(c, pl.total));
+    char* ws = c->ws;
+    double* V = reinterpret_cast<double*>(ws + pl.V);
+    double* Z = reinterpret_cast<double*>(ws + pl.Z);
+    char* step = ws + pl.step;
+    double* cn = reinterpret_cast<double*>(ws + pl.cn);
+    void* nscr = ws + pl.cn + ((size_t(l) * sizeof(double) + 255) & ~size_t(255));
+    PassTimer pt(c, rep != nullptr);
+    const long long launches0 = g_launches;
+    if (rep) PLU_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+    // E = ||A||_F^2 (Alg. adaptivewithoutupdating step 1)
+    pt.mark();
+    PLU_CUDA(c, launch_norm2(A->data, A->dtype, m, n, A->ld, c->d_scal, nscr, c->num_sms, c->stream));
+    pt.mark();
+    int np = 0;
+    PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pt, &np));
+    // G = A V (step 3), the v-th pass
+    pt.mark();
+    PLU_TRY(do_pass(c, A, 0, V, n, l, prec, Z, m, step));
+    pt.mark();
+    ++np;
+    PLU_CUDA(c, launch_colnorm2(m, l, Z, m, cn, c->stream));
+    PLU_CUDA(c, launch_rank_scan(cn, l, c->d_scal, eps, b, precise, c->d_kmet, c->d_scal + 1, c->stream));
+    PLU_CUDA(c, cudaMemcpyAsync(c->h_kmet, c->d_kmet, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PLU_CUDA(c, cudaMemcpyAsync(c->h_scal, c->d_scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    PLU_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int k = c->h_kmet[0];
+    const int met = c->h_kmet[1];
+    if (k < 1 || k > l) return fail(c, PLU_ECUDA, "rank scan returned k = %d", k);
+    int32_t* info = reinterpret_cast<int32_t*>(c->d_kmet + 2);
+    PLU_TRY(run_tail(c, m, n, k, Z, V, ws, pl, step, p, q, L, ldL, U, ldU, info));
+    *k_out = k;
+    if (rep) {
+        PLU_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+        int32_t hinfo[2] = {0, 0};
+        PLU_CUDA(c, cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, c->stream));
+        PLU_CUDA(c, cudaStreamSynchronize(c->stream));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+        memset(rep, 0, sizeof(*rep));
+        rep->ms_total = ms;
+        rep->ms_passes = pt.pairs_ms();
+        rep->passes = np + 1;
+        rep->rank = k;
+        const double nA2 = c->h_scal[0], E = c->h_scal[1];
+        rep->normA2 = nA2;
+        rep->indicator = nA2 > 0 ? sqrt((E > 0 ? E : 0.0) / nA2) : 0.0;
+        rep->info1 = hinfo[0];
+        rep->info2 = hinfo[1];
+        fill_pass_report(rep, A, np, l, 0, prec, false);
+        rep->launches = int32_t(g_launches - launches0);
+    }
+    plu_status st = finish(c);
+    if (st != PLU_OK) return st;
+    return met ? PLU_OK : fail(c, PLU_TOL_NOT_MET, "tolerance not met within l = %d columns", l);
+}
+
+plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed, plu_prec prec,
+                          int32_t* p, int32_t* q, double* L, int64_t ldL, double* U, int64_t ldU,
+                          plu_report* rep) {
+    (void)A; (void)k; (void)seed; (void)prec; (void)p; (void)q; (void)L; (void)ldL; (void)U;
+    (void)ldU; (void)rep;
+    PLU_TRY(bind(c));
+    return fail(c, PLU_EUNSUPPORTED, "single-pass LU is not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,239 @@
+// SIMT skinny GEMMs: the passes over A in FP64 (PLU_FP64) and FP32
+// (PLU_FP32) arithmetic, and the small FP64 products between passes.
+//
+// A pass of Alg. gpowerlu / Alg. bpowerlu is Y = A X (m x n by n x l) or
+// Y = A^T X (n x m by m x l) with column-major A.  On GB300 FP64 FMA runs at
+// about 1/64 of the FP32 rate (~1 TFLOP/s), so the FP64 products are bound by
+// the FP64 pipe, not by HBM: a 64x64x16 register-tiled kernel (4x4 outputs per
+// thread, operands staged through padded shared memory) saturates it.  When
+// the output has too few 64x64 tiles to fill 152 SMs the reduction dimension
+// is split; each split writes its partial tile and a second kernel sums the
+// splits in a fixed order, so results do not depend on scheduling.
+#include "plu_internal.h"
+
+namespace plu {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+template <typename T> __device__ __forceinline__ T to_acc(float x) { return T(x); }
+
+// C partial (split z) = op(A)[M x Kz] * op(B)[Kz x N].
+//   op(A)(i, k) = TRANSA ? A[k + i*lda] : A[i + k*lda]
+//   op(B)(k, j) = TRANSB ? B[j + k*ldb] : B[k + j*ldb]
+template <typename TA, typename TB, typename TC, bool TRANSA, bool TRANSB>
+__global__ void __launch_bounds__(NT)
+k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t lda,
+            const TB* __restrict__ B, int64_t ldb, TC* __restrict__ P, int64_t kchunk) {
+    __shared__ TC As[2][BK][BM + 1];
+    __shared__ TC Bs[2][BK][BN + 1];
+    const int t = threadIdx.x;
+    const int tx = t % 16, ty = t / 16;
+    const int64_t i0 = int64_t(blockIdx.x) * BM;
+    const int64_t j0 = int64_t(blockIdx.y) * BN;
+    const int64_t kbeg = int64_t(blockIdx.z) * kchunk;
+    const int64_t kend = min(K, kbeg + kchunk);
+
+    TC ra[4], rb[4];
+    auto load_a = [&](int64_t k0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int ii, kk;
+            if (TRANSA) { kk = t % 16; ii = t / 16 + 16 * r; }
+            else        { ii = t % 64; kk = t / 64 + 4 * r; }
+            const int64_t gi = i0 + ii, gk = k0 + kk;
+            TC v = TC(0);
+            if (gi < M && gk < kend) v = TC(TRANSA ? A[gk + gi * lda] : A[gi + gk * lda]);
+            ra[r] = v;
+        }
+    };
+    auto load_b = [&](int64_t k0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int jj, kk;
+            if (TRANSB) { jj = t % 64; kk = t / 64 + 4 * r; }
+            else        { kk = t % 16; jj = t / 16 + 16 * r; }
+            const int64_t gj = j0 + jj, gk = k0 + kk;
+            TC v = TC(0);
+            if (gj < N && gk < kend) v = TC(TRANSB ? B[gj + gk * ldb] : B[gk + gj * ldb]);
+            rb[r] = v;
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int ii, kk;
+            if (TRANSA) { kk = t % 16; ii = t / 16 + 16 * r; }
+            else        { ii = t % 64; kk = t / 64 + 4 * r; }
+            As[buf][kk][ii] = ra[r];
+            int jj, kb;
+            if (TRANSB) { jj = t % 64; kb = t / 64 + 4 * r; }
+            else        { kb = t % 16; jj = t / 16 + 16 * r; }
+            Bs[buf][kb][jj] = rb[r];
+        }
+    };
+
+    TC acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = TC(0);
+
+    int buf = 0;
+    if (kbeg < kend) {
+        load_a(kbeg);
+        load_b(kbeg);
+        store(0);
+    }
+    __syncthreads();
+    for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+        const bool more = k0 + BK < kend;
+        if (more) {
+            load_a(k0 + BK);
+            load_b(k0 + BK);
+        }
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            TC av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[buf][kk][ty + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[buf][kk][tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+        if (more) store(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+    }
+    TC* Pz = P + int64_t(blockIdx.z) * M * N;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int64_t gi = i0 + ty + 16 * a;
+        if (gi >= M) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int64_t gj = j0 + tx + 16 * b;
+            if (gj < N) Pz[gi + gj * M] = acc[a][b];
+        }
+    }
+}
+
+// C(i, j) = sum_z P[z](i, j), z in increasing order, in FP64.
+template <typename TC>
+__global__ void k_reduce_splits(int64_t M, int64_t N, int splits, const TC* __restrict__ P,
+                                double* __restrict__ C, int64_t ldc) {
+    const int64_t total = M * N;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        double sum = 0.0;
+        for (int z = 0; z < splits; ++z) sum += double(P[int64_t(z) * total + e]);
+        const int64_t i = e % M, j = e / M;
+        C[i + j * ldc] = sum;
+    }
+}
+
+__global__ void k_f64_to_f32(int64_t rows, int64_t cols, const double* __restrict__ X,
+                             int64_t ldx, float* __restrict__ Y) {
+    const int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = e % rows, j = e / rows;
+        Y[e] = float(X[i + j * ldx]);
+    }
+}
+
+int choose_splits(int64_t M, int64_t N, int64_t K, int num_sms) {
+    const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    const int64_t target = 4LL * num_sms;
+    int64_t splits = (target + tiles - 1) / tiles;
+    const int64_t max_by_k = (K + 8 * BK - 1) / (8 * BK);     // >= 8 k-steps per split
+    if (splits > max_by_k) splits = max_by_k;
+    if (splits < 1) splits = 1;
+    if (splits > 256) splits = 256;
+    return int(splits);
+}
+
+int grid_1d(int64_t work, int num_sms) {
+    int64_t b = (work + 255) / 256;
+    const int64_t cap = int64_t(num_sms) * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return int(b);
+}
+
+template <typename TA, typename TB, typename TC, bool TA_T, bool TB_T>
+cudaError_t run(int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda, const TB* B,
+                int64_t ldb, double* C, int64_t ldc, void* partials, int num_sms,
+                cudaStream_t s) {
+    const int splits = choose_splits(M, N, K, num_sms);
+    int64_t kchunk = (K + splits - 1) / splits;
+    kchunk = (kchunk + BK - 1) / BK * BK;
+    dim3 grid(unsigned((M + BM - 1) / BM), unsigned((N + BN - 1) / BN), unsigned(splits));
+    TC* P = static_cast<TC*>(partials);
+    count_launch();
+    k_gemm_simt<TA, TB, TC, TA_T, TB_T><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, P, kchunk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_reduce_splits<TC><<<grid_1d(M * N, num_sms), 256, 0, s>>>(M, N, splits, P, C, ldc);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t gemm_partials_bytes(int64_t M, int64_t N, int64_t K, int prec, int num_sms) {
+    const int splits = choose_splits(M, N, K, num_sms);
+    const size_t el = (prec == PLU_FP32) ? sizeof(float) : sizeof(double);
+    return size_t(splits) * size_t(M) * size_t(N) * el;
+}
+
+size_t gemm_f64_partials_bytes(int64_t M, int64_t N, int64_t K, int num_sms) {
+    return gemm_partials_bytes(M, N, K, PLU_FP64, num_sms);
+}
+
+cudaError_t launch_gemm_simt(int trans, int64_t M, int64_t N, int64_t K, const void* A,
+                             int dtype, int64_t lda, const double* B, int64_t ldb,
+                             double* C, int64_t ldc, int prec, void* partials,
+                             float* b32_scratch, int num_sms, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (prec == PLU_FP32) {
+        count_launch();
+        k_f64_to_f32<<<grid_1d(K * N, num_sms), 256, 0, s>>>(K, N, B, ldb, b32_scratch);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (dtype == PLU_F32) {
+            const float* Af = static_cast<const float*>(A);
+            return trans ? run<float, float, float, true, false>(M, N, K, Af, lda, b32_scratch, K, C, ldc, partials, num_sms, s)
+                         : run<float, float, float, false, false>(M, N, K, Af, lda, b32_scratch, K, C, ldc, partials, num_sms, s);
+        }
+        const double* Ad = static_cast<const double*>(A);
+        return trans ? run<double, float, float, true, false>(M, N, K, Ad, lda, b32_scratch, K, C, ldc, partials, num_sms, s)
+                     : run<double, float, float, false, false>(M, N, K, Ad, lda, b32_scratch, K, C, ldc, partials, num_sms, s);
+    }
+    if (dtype == PLU_F32) {
+        const float* Af = static_cast<const float*>(A);
+        return trans ? run<float, double, double, true, false>(M, N, K, Af, lda, B, ldb, C, ldc, partials, num_sms, s)
+                     : run<float, double, double, false, false>(M, N, K, Af, lda, B, ldb, C, ldc, partials, num_sms, s);
+    }
+    const double* Ad = static_cast<const double*>(A);
+    return trans ? run<double, double, double, true, false>(M, N, K, Ad, lda, B, ldb, C, ldc, partials, num_sms, s)
+                 : run<double, double, double, false, false>(M, N, K, Ad, lda, B, ldb, C, ldc, partials, num_sms, s);
+}
+
+cudaError_t launch_gemm_f64(int transA, int transB, int64_t M, int64_t N, int64_t K,
+                            const double* A, int64_t lda, const double* B, int64_t ldb,
+                            double* C, int64_t ldc, void* partials, int num_sms,
+                            cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (transA) {
+        return transB ? run<double, double, double, true, true>(M, N, K, A, lda, B, ldb, C, ldc, partials, num_sms, s)
+                      : run<double, double, double, true, false>(M, N, K, A, lda, B, ldb, C, ldc, partials, num_sms, s);
+    }
+    return transB ? run<double, double, double, false, true>(M, N, K, A, lda, B, ldb, C, ldc, partials, num_sms, s)
+                  : run<double, double, double, false, false>(M, N, K, A, lda, B, ldb, C, ldc, partials, num_sms, s);
+}
+
+}  // namespace plu

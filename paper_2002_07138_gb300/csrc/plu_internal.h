@@ -1,0 +1,97 @@
+// Internal declarations shared by the CUDA translation units of the
+// library (not part of the C ABI; see include/powerlu.h for that).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/powerlu.h"
+
+namespace plu {
+
+// Device status word codes (written by kernels, read by the host).
+enum DevStatus : int {
+    DEV_OK = 0,
+    DEV_TIMEOUT = 1,     // a grid barrier ran out of its spin budget
+    DEV_NUMERIC = 2,     // Cholesky breakdown / non-finite value
+};
+
+// Kernels launched by this host thread (the per-call report counts them).
+extern thread_local long long g_launches;
+inline void count_launch(long long n = 1) { g_launches += n; }
+
+// Largest grid of the cooperative kernels (one candidate slot per CTA).
+constexpr int kMaxGrid = 1024;
+
+// Workspace carved out of the context's device buffer.
+struct Workspace {
+    char* base = nullptr;
+    size_t cap = 0;
+    size_t used = 0;
+    void* take(size_t bytes) {
+        size_t off = (used + 255) & ~size_t(255);
+        if (off + bytes > cap) return nullptr;
+        used = off + bytes;
+        return base + off;
+    }
+};
+
+// ---------------------------------------------------------------- RNG (a1)
+cudaError_t launch_gaussian(int64_t rows, int64_t cols, uint64_t seed, uint32_t stream_id,
+                            double* out, int64_t ld, cudaStream_t s);
+
+// ----------------------------------------------------------- SIMT passes
+// C (M x N, FP64, ldc) = op(A) * B with op(A) = A (trans = 0, A is M x K) or
+// A^T (trans = 1, A is K x M); A of element type dtype (lda), B FP64 (K x N).
+// prec selects FP64 FMA or FP32 FMA (B converted to FP32).  `partials` must
+// hold gemm_partials_bytes(...) bytes (split-K partial sums).
+size_t gemm_partials_bytes(int64_t M, int64_t N, int64_t K, int prec, int num_sms);
+cudaError_t launch_gemm_simt(int trans, int64_t M, int64_t N, int64_t K, const void* A,
+                             int dtype, int64_t lda, const double* B, int64_t ldb,
+                             double* C, int64_t ldc, int prec, void* partials,
+                             float* b32_scratch, int num_sms, cudaStream_t s);
+// FP64 GEMM with transposed-B option for the small products of the tail:
+// C = A * op(B), op(B) = B (K x N) or B^T (B is N x K).
+cudaError_t launch_gemm_f64(int transA, int transB, int64_t M, int64_t N, int64_t K,
+                            const double* A, int64_t lda, const double* B, int64_t ldb,
+                            double* C, int64_t ldc, void* partials, int num_sms,
+                            cudaStream_t s);
+size_t gemm_f64_partials_bytes(int64_t M, int64_t N, int64_t K, int num_sms);
+
+// ------------------------------------------------------- panel LU (a3, a8)
+struct PanelScratch;   // defined in plu_panel.cu
+size_t panel_scratch_bytes(int64_t rows, int cols);
+// Factor X (rows x cols) in place with partial pivoting (virtual row order).
+// mode 0: leave X = P^T L (reorthogonalisation).
+// mode 1: write perm, L (pivoted order) and U (or U^T when u_trans), or L^T
+//         when l_trans; X is destroyed.
+cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int mode,
+                            int32_t* perm, double* L, int64_t ldL, int l_trans,
+                            double* U, int64_t ldU, int u_trans, int32_t* info,
+                            void* scratch, int* dev_status, int64_t spin_budget,
+                            int num_sms, cudaStream_t s);
+
+// --------------------------------------------------------------- QR (a5)
+size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms);
+cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, double* R,
+                           int64_t ldR, void* scratch, int* dev_status, int num_sms,
+                           cudaStream_t s);
+
+// -------------------------------------------------------- rank and norms
+size_t norm2_scratch_bytes(int num_sms);
+cudaError_t launch_norm2(const void* A, int dtype, int64_t m, int64_t n, int64_t lda,
+                         double* out, void* scratch, int num_sms, cudaStream_t s);
+cudaError_t launch_colnorm2(int64_t rows, int cols, const double* G, int64_t ldg,
+                            double* out, cudaStream_t s);
+// k/E/met from column norms (one thread): out[0] = k, out[1] = met (ints);
+// E written to *E_out (device double).
+cudaError_t launch_rank_scan(const double* colnorm2, int cols, const double* normA2,
+                             double eps, int b, int precise, int* k_met, double* E_out,
+                             cudaStream_t s);
+
+// -------------------------------------------------------------- helpers
+cudaError_t launch_copy_cols(int64_t rows, int cols, const double* src, int64_t lds,
+                             double* dst, int64_t ldd, cudaStream_t s);
+
+}  // namespace plu

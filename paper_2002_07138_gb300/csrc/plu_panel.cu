@@ -1,0 +1,304 @@
+// Partial-pivoting LU of a tall-skinny FP64 panel (rows x cols, rows >= cols):
+// the re-orthogonalising [X, ~] = lu(X) of Alg. gpowerlu (a3) and the
+// [L, U, P] = lu(Y) / lu(B^T) of Alg. bpowerlu steps 4 and 6 (a8).
+//
+// One cooperative (co-resident) grid; CTA b owns a contiguous block of rows
+// and keeps them in place ("virtual" pivoting: rows never move).  Column j:
+//   1. each CTA finds the largest |x_ij| among its not-yet-pivoted rows,
+//      ties going to the row with the smallest current position, and
+//      publishes (|x|, position, row) -- warp shuffles, then shared memory;
+//   2. grid barrier (one per column; bounded spin, error word on timeout);
+//   3. every CTA reduces the published candidates to the same pivot row r,
+//      applies LAPACK's row interchange to the positions of its own rows
+//      (r takes position j, the row at position j takes r's old position),
+//      stages row r's columns j.. in shared memory, and eliminates:
+//      l_ij = x_ij / u_jj, x_ic -= l_ij u_jc for its other active rows, and
+//      computes its candidate for column j+1 in the same sweep.
+// A column whose candidates are all exactly zero is skipped (no division),
+// as LAPACK does; the first such column is reported in `info`.
+// The tie rule reproduces LAPACK's idamax on the row-swapped matrix: the
+// first maximum in the current row order.
+//
+// After the sweep each row holds its multipliers left of its pivot step and,
+// for pivot rows, the U row from the pivot step on.  A finalising kernel
+// writes either P^T L in place (a3) or perm, L (pivoted order) and U (a8).
+#include "plu_internal.h"
+
+#include <climits>
+
+namespace plu {
+
+struct Cand {
+    double v;
+    int pos;
+    int row;
+};
+
+struct PanelScratch {
+    unsigned int barrier;
+    int info;
+    int any_nan;
+    int pad;
+    Cand cand[2][kMaxGrid];
+};
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int kMaxCols = 2048;
+
+__device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
+    // true when a should be the pivot rather than b: larger |x| first, then
+    // the smaller current position; NaN loses to every number
+    if (a.row < 0) return false;
+    if (b.row < 0) return true;
+    const bool an = a.v != a.v, bn = b.v != b.v;
+    if (an || bn) return an && bn ? a.pos < b.pos : bn;
+    if (a.v > b.v) return true;
+    if (a.v < b.v) return false;
+    return a.pos < b.pos;
+}
+
+__device__ __forceinline__ Cand shfl_cand(const Cand& c, int src_lane_xor) {
+    Cand o;
+    o.v = __shfl_xor_sync(0xffffffffu, c.v, src_lane_xor);
+    o.pos = __shfl_xor_sync(0xffffffffu, c.pos, src_lane_xor);
+    o.row = __shfl_xor_sync(0xffffffffu, c.row, src_lane_xor);
+    return o;
+}
+
+__device__ __forceinline__ Cand warp_best(Cand c) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const Cand o = shfl_cand(c, off);
+        if (better(o, c)) c = o;
+    }
+    return c;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+    return *reinterpret_cast<const volatile int*>(p);
+}
+
+// Grid-wide barrier over co-resident CTAs with a bounded spin.  Returns false
+// (in every thread of the CTA) when the barrier failed: this CTA ran out of
+// budget (and set *status) or another CTA reported an error.
+__device__ bool grid_barrier(unsigned* bar, unsigned target, int* status, int64_t budget) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int good = 1;
+        int64_t spins = 0;
+        while (ld_acquire_u32(bar) < target) {
+            if (ld_volatile_i32(status) != DEV_OK) { good = 0; break; }
+            if (++spins > budget) {
+                atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+                good = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ Cand block_best(Cand c, Cand* red) {
+    c = warp_best(c);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = c;
+    __syncthreads();
+    if (warp == 0) {
+        Cand x = (lane < NT / 32) ? red[lane] : Cand{-1.0, INT_MAX, -1};
+        x = warp_best(x);
+        if (lane == 0) red[0] = x;
+    }
+    __syncthreads();
+    const Cand out = red[0];
+    __syncthreads();
+    return out;
+}
+
+__global__ void __launch_bounds__(NT)
+k_panel_lu(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
+           PanelScratch* __restrict__ ps, int* __restrict__ pos, int* __restrict__ pivstep,
+           int* __restrict__ status, int64_t budget) {
+    extern __shared__ double urow[];
+    __shared__ Cand red[NT / 32];
+    __shared__ Cand piv;
+    const int nb = gridDim.x;
+    const int t = threadIdx.x;
+    const int64_t per = (rows + nb - 1) / nb;
+    const int64_t r0 = int64_t(blockIdx.x) * per;
+    const int64_t r1 = min(rows, r0 + per);
+    const int steps = int(rows < int64_t(cols) ? rows : int64_t(cols));
+
+    // own rows start unpivoted at their natural position; candidate for column 0
+    Cand best{-1.0, INT_MAX, -1};
+    for (int64_t i = r0 + t; i < r1; i += NT) {
+        pos[i] = int(i);
+        pivstep[i] = -1;
+        const double a = fabs(X[i]);
+        const Cand c{a, int(i), int(i)};
+        if (better(c, best)) best = c;
+    }
+
+    for (int j = 0; j < steps; ++j) {
+        const Cand cb = block_best(best, red);
+        if (t == 0) ps->cand[j & 1][blockIdx.x] = cb;
+        if (!grid_barrier(&ps->barrier, unsigned(j + 1) * unsigned(nb), status, budget)) return;
+        if (t < 32) {
+            Cand g{-1.0, INT_MAX, -1};
+            for (int b = t; b < nb; b += 32) {
+                const Cand* src = &ps->cand[j & 1][b];
+                Cand c;
+                c.v = __ldcg(&src->v);
+                c.pos = __ldcg(&src->pos);
+                c.row = __ldcg(&src->row);
+                if (better(c, g)) g = c;
+            }
+            g = warp_best(g);
+            if (t == 0) piv = g;
+        }
+        __syncthreads();
+        const Cand pv = piv;
+        if (pv.row < 0) {                    // no comparable candidate (NaN panel)
+            if (blockIdx.x == 0 && t == 0) atomicCAS(status, DEV_OK, DEV_NUMERIC);
+            return;
+        }
+        // LAPACK interchange on the positions of own rows; retire the pivot row
+        for (int64_t i = r0 + t; i < r1; i += NT) {
+            if (i == pv.row) {
+                pos[i] = j;
+                pivstep[i] = j;
+            } else if (pos[i] == j) {
+                pos[i] = pv.pos;
+            }
+        }
+        for (int c = j + t; c < cols; c += NT) urow[c] = __ldcg(&X[pv.row + int64_t(c) * ldx]);
+        if (blockIdx.x == 0 && t == 0) {
+            if (pv.v == 0.0 && ps->info == 0) ps->info = j + 1;
+            if (!(pv.v <= 1.7976931348623157e308)) ps->any_nan = 1;   // pivot inf or NaN
+        }
+        __syncthreads();
+        const double ujj = urow[j];
+        best = Cand{-1.0, INT_MAX, -1};
+        const bool next = j + 1 < steps;
+        for (int64_t i = r0 + t; i < r1; i += NT) {
+            if (pivstep[i] >= 0) continue;
+            double* xi = X + i;
+            if (ujj != 0.0) {
+                const double lij = xi[int64_t(j) * ldx] / ujj;
+                xi[int64_t(j) * ldx] = lij;
+                for (int c = j + 1; c < cols; ++c) {
+                    double* p = xi + int64_t(c) * ldx;
+                    *p = fma(-lij, urow[c], *p);
+                }
+            }
+            if (next) {
+                const Cand c{fabs(xi[int64_t(j + 1) * ldx]), pos[i], int(i)};
+                if (better(c, best)) best = c;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_panel_finalize(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
+                                 int mode, const int* __restrict__ pos,
+                                 const int* __restrict__ pivstep, int32_t* __restrict__ perm,
+                                 double* __restrict__ L, int64_t ldL, int l_trans,
+                                 double* __restrict__ U, int64_t ldU, int u_trans,
+                                 const PanelScratch* __restrict__ ps, int32_t* __restrict__ info,
+                                 int* __restrict__ status) {
+    const int r = int(rows < int64_t(cols) ? rows : int64_t(cols));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (info) *info = ps->info;
+        if (ps->any_nan) atomicCAS(status, DEV_OK, DEV_NUMERIC);
+    }
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < rows;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int s = pivstep[i];
+        if (mode == 0) {
+            if (s >= 0) {
+                X[i + int64_t(s) * ldx] = 1.0;
+                for (int c = s + 1; c < cols; ++c) X[i + int64_t(c) * ldx] = 0.0;
+            }
+            continue;
+        }
+        const int64_t pp = pos[i];
+        perm[pp] = int32_t(i);
+        for (int c = 0; c < r; ++c) {
+            double v;
+            if (s >= 0 && c == s) v = 1.0;
+            else if (s >= 0 && c > s) v = 0.0;
+            else v = X[i + int64_t(c) * ldx];
+            if (l_trans) L[c + pp * ldL] = v;
+            else L[pp + int64_t(c) * ldL] = v;
+        }
+        if (s >= 0) {
+            for (int c = 0; c < cols; ++c) {
+                const double v = (c >= s) ? X[i + int64_t(c) * ldx] : 0.0;
+                if (u_trans) U[c + int64_t(s) * ldU] = v;
+                else U[s + int64_t(c) * ldU] = v;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+size_t panel_scratch_bytes(int64_t rows, int cols) {
+    (void)cols;
+    size_t head = (sizeof(PanelScratch) + 255) & ~size_t(255);
+    return head + 2 * size_t(rows) * sizeof(int) + 256;
+}
+
+cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int mode,
+                            int32_t* perm, double* L, int64_t ldL, int l_trans,
+                            double* U, int64_t ldU, int u_trans, int32_t* info,
+                            void* scratch, int* dev_status, int64_t spin_budget,
+                            int num_sms, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (cols > kMaxCols) return cudaErrorInvalidValue;
+    PanelScratch* ps = static_cast<PanelScratch*>(scratch);
+    const size_t head = (sizeof(PanelScratch) + 255) & ~size_t(255);
+    int* pos = reinterpret_cast<int*>(static_cast<char*>(scratch) + head);
+    int* pivstep = pos + rows;
+    cudaError_t e = cudaMemsetAsync(ps, 0, sizeof(PanelScratch), s);
+    if (e != cudaSuccess) return e;
+    // grid: at most one CTA per SM, at least ~32 rows per CTA
+    int64_t nb = (rows + 31) / 32;
+    if (nb > num_sms) nb = num_sms;
+    if (nb > kMaxGrid) nb = kMaxGrid;
+    if (nb < 1) nb = 1;
+    const size_t smem = size_t(cols) * sizeof(double);
+    int64_t rows_ = rows;
+    int cols_ = cols;
+    int64_t ldx_ = ldx;
+    int64_t budget = spin_budget;
+    void* args[] = {&rows_, &cols_, &X, &ldx_, &ps, &pos, &pivstep, &dev_status, &budget};
+    count_launch();
+    e = cudaLaunchCooperativeKernel((const void*)k_panel_lu, dim3(unsigned(nb)), dim3(NT), args,
+                                    smem, s);
+    if (e != cudaSuccess) return e;
+    int64_t fb = (rows + 255) / 256;
+    if (fb > int64_t(num_sms) * 8) fb = int64_t(num_sms) * 8;
+    count_launch();
+    k_panel_finalize<<<unsigned(fb), 256, 0, s>>>(rows, cols, X, ldx, mode, pos, pivstep, perm,
+                                                  L, ldL, l_trans, U, ldU, u_trans, ps, info,
+                                                  dev_status);
+    return cudaGetLastError();
+}
+
+}  // namespace plu

@@ -1,0 +1,156 @@
+// a5: the orthonormal basis [V, ~] = qr(A^T V) that closes Alg. gpowerlu.
+//
+// FP64 CholeskyQR2 (Fukaya, Nakatsukasa, Yanagisawa, Yamamoto 2014):
+//   W = X^T X, W = R1^T R1 (Cholesky), Q1 = X R1^{-1};
+//   W = Q1^T Q1, W = R2^T R2,           Q  = Q1 R2^{-1};  R = R2 R1.
+// Q equals the Q of the Householder QR with R_ii > 0 up to rounding for
+// condition numbers below ~1e7 (the sketches here stay far below that); the
+// Gram matrices and the products with R^{-1} are the skinny FP64 GEMMs of
+// plu_gemm.cu.  If the first Cholesky meets a non-positive pivot it restarts
+// with the shift 11 (rows*cols + cols*(cols+1)) u tr(W) of shifted
+// CholeskyQR (Fukaya et al. 2020) and the second pass restores orthogonality;
+// a breakdown of the second pass sets the numeric error word.
+#include "plu_internal.h"
+
+namespace plu {
+namespace {
+
+constexpr int CT = 1024;
+
+// In-place upper Cholesky W = R^T R of the n x n SPD matrix W (ld n),
+// one CTA.  The strictly lower triangle is zeroed.  shift_mode 1: on a
+// non-positive pivot restart from Wsave with the CholeskyQR shift.
+__global__ void __launch_bounds__(CT)
+k_cholesky(int n, double* __restrict__ W, const double* __restrict__ Wsave, int64_t rows,
+           int shift_mode, int* __restrict__ status) {
+    __shared__ int broke;
+    __shared__ double rjj;
+    const int t = threadIdx.x;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (attempt == 1) {
+            // tr(W) bounds ||X||_2^2; shift = 11 (rows n + n(n+1)) u tr(W)
+            __shared__ double tr;
+            if (t == 0) {
+                double s = 0.0;
+                for (int i = 0; i < n; ++i) s += Wsave[i + int64_t(i) * n];
+                tr = s;
+            }
+            __syncthreads();
+            const double shift = 11.0 * (double(rows) * n + double(n) * (n + 1)) * 1.1102230246251565e-16 * tr;
+            for (int64_t e = t; e < int64_t(n) * n; e += CT) {
+                const int a = int(e % n), c = int(e / n);
+                W[e] = Wsave[e] + (a == c ? shift : 0.0);
+            }
+            __syncthreads();
+        }
+        if (t == 0) broke = 0;
+        __syncthreads();
+        for (int j = 0; j < n; ++j) {
+            if (t == 0) {
+                const double d = W[j + int64_t(j) * n];
+                if (!(d > 0.0)) broke = 1;
+                rjj = (d > 0.0) ? sqrt(d) : 1.0;
+                W[j + int64_t(j) * n] = rjj;
+            }
+            __syncthreads();
+            if (broke) break;
+            const double inv = 1.0 / rjj;
+            for (int c = j + 1 + t; c < n; c += CT) W[j + int64_t(c) * n] *= inv;
+            __syncthreads();
+            const int m = n - j - 1;
+            for (int64_t e = t; e < int64_t(m) * m; e += CT) {
+                const int a = j + 1 + int(e % m), c = j + 1 + int(e / m);
+                if (a <= c) W[a + int64_t(c) * n] -= W[j + int64_t(a) * n] * W[j + int64_t(c) * n];
+            }
+            __syncthreads();
+        }
+        if (!broke) break;
+        if (!shift_mode || attempt == 1) {
+            if (t == 0) atomicCAS(status, DEV_OK, DEV_NUMERIC);
+            break;
+        }
+    }
+    __syncthreads();
+    for (int64_t e = t; e < int64_t(n) * n; e += CT) {
+        const int a = int(e % n), c = int(e / n);
+        if (a > c) W[e] = 0.0;
+    }
+}
+
+// Rinv(:, j) = R^{-1} e_j for upper triangular R (n x n, ld n); CTA j.
+__global__ void k_trinv_upper(int n, const double* __restrict__ R, double* __restrict__ Rinv) {
+    extern __shared__ double x[];
+    const int j = blockIdx.x;
+    const int t = threadIdx.x;
+    for (int i = t; i < n; i += blockDim.x) x[i] = (i == j) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int i = j; i >= 0; --i) {
+        const double xi = x[i] / R[i + int64_t(i) * n];
+        __syncthreads();
+        if (t == 0) x[i] = xi;
+        for (int k = t; k < i; k += blockDim.x) x[k] -= xi * R[k + int64_t(i) * n];
+        __syncthreads();
+    }
+    for (int i = t; i < n; i += blockDim.x) Rinv[i + int64_t(j) * n] = x[i];
+}
+
+}  // namespace
+
+size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms) {
+    const size_t sq = size_t(cols) * cols * sizeof(double);
+    const size_t p1 = gemm_f64_partials_bytes(cols, cols, rows, num_sms);
+    const size_t p2 = gemm_f64_partials_bytes(rows, cols, cols, num_sms);
+    return 5 * sq + (p1 > p2 ? p1 : p2) + 6 * 256;
+}
+
+cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, double* R,
+                           int64_t ldR, void* scratch, int* dev_status, int num_sms,
+                           cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    Workspace ws;
+    ws.base = static_cast<char*>(scratch);
+    ws.cap = qr_scratch_bytes(rows, cols, num_sms);
+    const size_t sq = size_t(cols) * cols * sizeof(double);
+    double* W = static_cast<double*>(ws.take(sq));
+    double* Wsave = static_cast<double*>(ws.take(sq));
+    double* Rinv = static_cast<double*>(ws.take(sq));
+    double* R1 = static_cast<double*>(ws.take(sq));
+    double* Rtmp = static_cast<double*>(ws.take(sq));
+    const size_t p1 = gemm_f64_partials_bytes(cols, cols, rows, num_sms);
+    const size_t p2 = gemm_f64_partials_bytes(rows, cols, cols, num_sms);
+    void* part = ws.take(p1 > p2 ? p1 : p2);
+    if (!W || !Wsave || !Rinv || !R1 || !Rtmp || !part) return cudaErrorInvalidValue;
+    cudaError_t e;
+    for (int pass = 0; pass < 2; ++pass) {
+        e = launch_gemm_f64(1, 0, cols, cols, rows, X, ldx, X, ldx, W, cols, part, num_sms, s);
+        if (e != cudaSuccess) return e;
+        if (pass == 0) {
+            e = cudaMemcpyAsync(Wsave, W, sq, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+        }
+        count_launch();
+        k_cholesky<<<1, CT, 0, s>>>(cols, W, Wsave, rows, pass == 0 ? 1 : 0, dev_status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int tt = cols < 256 ? 128 : 256;
+        count_launch();
+        k_trinv_upper<<<cols, tt, size_t(cols) * sizeof(double), s>>>(cols, W, Rinv);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // X <- X Rinv (the reduction of the partial sums writes X after the product)
+        e = launch_gemm_f64(0, 0, rows, cols, cols, X, ldx, Rinv, cols, X, ldx, part, num_sms, s);
+        if (e != cudaSuccess) return e;
+        if (pass == 0) {
+            e = cudaMemcpyAsync(R1, W, sq, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    if (R) {
+        // R = R2 R1 (both upper triangular)
+        e = launch_gemm_f64(0, 0, cols, cols, cols, W, cols, R1, cols, Rtmp, cols, part, num_sms, s);
+        if (e != cudaSuccess) return e;
+        e = launch_copy_cols(cols, cols, Rtmp, cols, R, ldR, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace plu

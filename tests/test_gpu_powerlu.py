@@ -1,0 +1,127 @@
+"""GPU parity of the whole algorithms (PowerLU fixed rank, PowerLU_FP fixed
+precision) against the FP64 oracle on the same seeded inputs and the same
+Philox sketch: FP64 path -> identical p and q, L and U within 1e-10
+relative (Frobenius, per factor); FP32 passes -> error within 1.1x of FP64."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2002_07138_gb300 as plu
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(X, dtype=torch.float64):
+    X = np.asarray(X)
+    out = plu.colmajor_empty(X.shape[0], X.shape[1], dtype=dtype)
+    out.copy_(torch.from_numpy(np.ascontiguousarray(X)))
+    return out
+
+
+def host(T):
+    return T.double().cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def check_parity(A, got, ref, tol=1e-10):
+    gp, gq, gL, gU = got
+    p, q, L, U = ref
+    assert np.array_equal(gp.cpu().numpy().astype(np.int64), np.asarray(p))
+    assert np.array_equal(gq.cpu().numpy().astype(np.int64), np.asarray(q))
+    assert rel(host(gL), L) < tol
+    assert rel(host(gU), U) < tol
+
+
+@pytest.fixture(scope="module")
+def plain_case():
+    w = synth.PLAIN_2000x1500
+    return w, w.build("cpu")
+
+
+@pytest.mark.parametrize("v", [2, 3, 4, 5])
+def test_powerlu_fp64_plain_config(ctx, plain_case, v):
+    """2000 x 1500, sigma_i = 1/i^2, k = 20, l = 25, seed 0."""
+    w, A = plain_case
+    ref = oracle.powerlu(A, w.k, w.l, v, seed=0)
+    gp, gq, gL, gU, rep = plu.plu_powerlu(ctx, dev(A), w.k, w.l, v, seed=0, prec="fp64")
+    check_parity(A, (gp, gq, gL, gU), ref)
+    assert rep["passes"] == v
+    err = oracle.rel_lu_error(A, gp.cpu().numpy(), gq.cpu().numpy(), host(gL), host(gU))
+    assert err >= oracle.eckart_young_error(w.sigma_values(), w.k) * (1 - 1e-9)
+
+
+@pytest.mark.parametrize("m,n,k,l,v", [(1000, 700, 13, 20, 3), (700, 1000, 31, 40, 4),
+                                       (517, 517, 64, 70, 2), (3000, 257, 5, 6, 5)])
+def test_powerlu_fp64_ragged_shapes(ctx, m, n, k, l, v):
+    sig = synth.sigma_profile("type2", min(m, n))
+    A = synth.svd_matrix_np(m, n, sig, seed=m + n)
+    ref = oracle.powerlu(A, k, l, v, seed=3)
+    gp, gq, gL, gU, rep = plu.plu_powerlu(ctx, dev(A), k, l, v, seed=3, prec="fp64")
+    check_parity(A, (gp, gq, gL, gU), ref)
+
+
+def test_powerlu_exact_rank_k(ctx):
+    A = synth.rank_k_matrix_np(2000, 1500, 20, seed=4)
+    for v in (2, 3):
+        gp, gq, gL, gU, _ = plu.plu_powerlu(ctx, dev(A), 20, 25, v, seed=0)
+        err = oracle.rel_lu_error(A, gp.cpu().numpy(), gq.cpu().numpy(), host(gL), host(gU))
+        assert err <= 1e-13
+
+
+def test_powerlu_fp32_passes_error_within_1p1_of_fp64(ctx):
+    sig = synth.sigma_profile("exp20", 2048)
+    A = synth.svd_matrix_np(2048, 2048, sig, seed=1, noise=1e-6 / math.sqrt(2048))
+    A32 = dev(A.astype(np.float32), torch.float32)
+    A64h = A.astype(np.float32).astype(np.float64)
+    errs = {}
+    for prec, Ad in (("fp64", dev(A64h)), ("fp32", A32)):
+        gp, gq, gL, gU, _ = plu.plu_powerlu(ctx, Ad, 100, 110, 3, seed=0, prec=prec)
+        errs[prec] = oracle.rel_lu_error(A64h, gp.cpu().numpy(), gq.cpu().numpy(), host(gL), host(gU))
+    assert errs["fp32"] <= 1.1 * errs["fp64"]
+
+
+@pytest.mark.parametrize("precise", [False, True])
+def test_powerlu_fp_parity(ctx, precise):
+    sig = synth.sigma_profile("type2", 800)
+    A = synth.svd_matrix_np(1000, 800, sig, seed=12)
+    eps, b, l, v = 1e-4, 10, 120, 4
+    k, p, q, L, U, E, met = oracle.powerlu_fp(A, eps, b, l, v, seed=2, precise=precise)
+    gk, gp, gq, gL, gU, gmet, rep = plu.plu_powerlu_fp(ctx, dev(A), eps, b, l, v, seed=2,
+                                                       prec="fp64", precise=precise)
+    assert (gk, gmet) == (k, met)
+    check_parity(A, (gp, gq, gL, gU), (p, q, L, U))
+    nA2 = float(np.sum(A * A))
+    assert abs(rep["normA2"] - nA2) <= 1e-12 * nA2
+    assert abs(rep["indicator"] - math.sqrt(max(E, 0) / nA2)) <= 1e-8
+    assert rep["passes"] == v + 1
+
+
+def test_powerlu_fp_tolerance_not_met(ctx):
+    sig = synth.sigma_profile("type1", 300)
+    A = synth.svd_matrix_np(400, 300, sig, seed=3)
+    k, p, q, L, U, E, met = oracle.powerlu_fp(A, 1e-9, 7, 30, 3, seed=2)
+    gk, gp, gq, gL, gU, gmet, rep = plu.plu_powerlu_fp(ctx, dev(A), 1e-9, 7, 30, 3, seed=2)
+    assert not met and not gmet and gk == k == 30
+    check_parity(A, (gp, gq, gL, gU), (p, q, L, U))
+
+
+def test_fixed_rank_8192_fp64_full_parity(ctx):
+    """The 8192 x 8192 fixed-rank workload (sigma_i = exp(-i/20) plus a
+    1e-6 N(0,1)/sqrt(n) floor, k = 100, l = 110) in FP64 at v = 3."""
+    w = synth.FIXED_RANK_8192
+    Ad = w.build("cuda").double()
+    Ad = synth.colmajor(Ad)
+    A = Ad.cpu().numpy()
+    ref = oracle.powerlu(A, w.k, w.l, 3, seed=0)
+    gp, gq, gL, gU, rep = plu.plu_powerlu(ctx, Ad, w.k, w.l, 3, seed=0, prec="fp64")
+    check_parity(A, (gp, gq, gL, gU), ref)
+    err = oracle.rel_lu_error(A, ref[0], ref[1], ref[2], ref[3])
+    opt = oracle.eckart_young_error(w.sigma_values(), w.k)
+    assert opt * (1 - 1e-9) <= err < 2.0 * opt

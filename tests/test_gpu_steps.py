@@ -1,0 +1,200 @@
+"""GPU parity of each step of the hot path against the FP64 oracle, through
+the C ABI (libpowerlu.so).  Sizes span several 64-row tiles and ragged
+tails; FP64 steps are compared at ~1e-12 relative, integer outputs
+(permutations) bit for bit, the Gaussian sketch bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2002_07138_gb300 as plu
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(X, dtype=torch.float64):
+    """Column-major CUDA copy of a numpy matrix."""
+    X = np.asarray(X)
+    out = plu.colmajor_empty(X.shape[0], X.shape[1], dtype=dtype)
+    out.copy_(torch.from_numpy(np.ascontiguousarray(X)))
+    return out
+
+
+def host(T):
+    return T.double().cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# ------------------------------------------------------------------- a1
+@pytest.mark.parametrize("rows,cols,seed,sid", [(2000, 25, 0, 1), (1500, 25, 0, 2), (7, 5, 3, 2),
+                                                 (1001, 33, (1 << 40) + 5, 3), (1, 1, 9, 1)])
+def test_gaussian_bit_identical(ctx, rows, cols, seed, sid):
+    ref = oracle.gaussian_matrix(rows, cols, seed, sid)
+    got = plu.plu_gaussian(ctx, rows, cols, seed, sid)
+    assert np.array_equal(host(got), ref)
+
+
+def test_gaussian_with_leading_dimension(ctx):
+    buf = plu.colmajor_empty(40, 6)
+    buf.fill_(7.0)
+    view = buf[:33, :]
+    plu.plu_gaussian(ctx, 33, 6, 11, 1, out=view)
+    assert np.array_equal(host(buf[:33]), oracle.gaussian_matrix(33, 6, 11, 1))
+    assert torch.all(buf[33:] == 7.0)
+
+
+# --------------------------------------------------------------- a2/a4/a6
+@pytest.mark.parametrize("m,n,cols", [(1000, 777, 25), (333, 1201, 70), (64, 64, 64), (2000, 1500, 1)])
+@pytest.mark.parametrize("trans", [0, 1])
+def test_pass_fp64(ctx, m, n, cols, trans):
+    A = synth.gaussian_np(m, n, 1)
+    X = synth.gaussian_np(n if trans == 0 else m, cols, 2)
+    ref = A @ X if trans == 0 else A.T @ X
+    got = host(plu.plu_pass(ctx, dev(A), trans, dev(X), "fp64"))
+    assert rel(got, ref) < 1e-13
+
+
+@pytest.mark.parametrize("trans", [0, 1])
+def test_pass_fp64_with_f32_matrix_and_ld(ctx, trans):
+    m, n, cols = 517, 300, 19
+    big = plu.colmajor_empty(600, n, dtype=torch.float32)
+    big.copy_(torch.from_numpy(synth.gaussian_np(600, n, 3).astype(np.float32)))
+    A = big[:m, :]
+    X = synth.gaussian_np(n if trans == 0 else m, cols, 4)
+    A64 = host(A)
+    ref = A64 @ X if trans == 0 else A64.T @ X
+    got = host(plu.plu_pass(ctx, A, trans, dev(X), "fp64"))
+    assert rel(got, ref) < 1e-13
+
+
+@pytest.mark.parametrize("trans", [0, 1])
+def test_pass_fp32(ctx, trans):
+    m, n, cols = 1500, 1100, 40
+    A32 = synth.gaussian_np(m, n, 5).astype(np.float32)
+    X = synth.gaussian_np(n if trans == 0 else m, cols, 6)
+    Xr = X.astype(np.float32).astype(np.float64)
+    A64 = A32.astype(np.float64)
+    ref = A64 @ Xr if trans == 0 else A64.T @ Xr
+    got = host(plu.plu_pass(ctx, dev(A32, torch.float32), trans, dev(X), "fp32"))
+    assert rel(got, ref) < 2e-6
+
+
+# ------------------------------------------------------------------- a3
+@pytest.mark.parametrize("rows,cols", [(2000, 25), (1500, 110), (777, 64), (300, 300), (65, 3)])
+def test_lu_reorth(ctx, rows, cols):
+    X = synth.gaussian_np(rows, cols, rows + cols)
+    ref = oracle.lu_permuted_L(X)
+    got = host(plu.plu_lu_reorth(ctx, dev(X)))
+    assert rel(got, ref) < 1e-12
+
+
+# ------------------------------------------------------------------- a8
+@pytest.mark.parametrize("rows,cols", [(2000, 20), (1500, 100), (513, 64), (64, 64), (10000, 7)])
+def test_getrf(ctx, rows, cols):
+    X = synth.gaussian_np(rows, cols, 7 * rows + cols)
+    perm, L, U, info = oracle.getrf(X)
+    gp, gL, gU, ginfo = plu.plu_getrf(ctx, dev(X))
+    assert np.array_equal(gp.cpu().numpy().astype(np.int64), perm)
+    assert rel(host(gL), L) < 1e-12
+    assert rel(host(gU), U) < 1e-12
+    assert ginfo == info == 0
+
+
+def test_getrf_tie_rule_matches_lapack_order(ctx):
+    """Exact-arithmetic integer panels with tied pivot magnitudes: the GPU's
+    virtual pivoting must pick the same rows as the oracle's row swaps."""
+    rng = np.random.default_rng(5)
+    checked = 0
+    while checked < 20:
+        X = rng.integers(-1, 2, size=(12, 5)).astype(np.float64)
+        X[:, 0] = rng.choice([-2.0, 2.0], size=12)          # every row ties in column 0
+        perm, L, U, info = oracle.getrf(X)
+        # keep panels whose elimination is exact (dyadic pivots only)
+        piv = np.abs(np.diag(U))
+        if not np.all((piv == 0) | (np.log2(np.where(piv == 0, 1, piv)) % 1 == 0)):
+            continue
+        if not np.array_equal(X[perm], L @ U):
+            continue
+        gp, gL, gU, ginfo = plu.plu_getrf(ctx, dev(X))
+        assert np.array_equal(gp.cpu().numpy().astype(np.int64), perm)
+        assert np.array_equal(host(gL), L) and np.array_equal(host(gU), U)
+        assert ginfo == info
+        checked += 1
+
+
+def test_getrf_zero_column(ctx):
+    X = synth.gaussian_np(300, 8, 1)
+    X[:, 3] = 0.0
+    perm, L, U, info = oracle.getrf(X)
+    gp, gL, gU, ginfo = plu.plu_getrf(ctx, dev(X))
+    assert info == 4 and ginfo == 4
+    assert np.array_equal(gp.cpu().numpy().astype(np.int64), perm)
+    assert rel(host(gL), L) < 1e-12 and rel(host(gU), U) < 1e-12
+
+
+# ------------------------------------------------------------------- a5
+@pytest.mark.parametrize("rows,cols", [(1500, 25), (8192, 110), (700, 64), (333, 333)])
+def test_qr(ctx, rows, cols):
+    X = synth.gaussian_np(rows, cols, rows) * np.logspace(0, -3, cols)[None, :]
+    Q, R = oracle.qr_economy(X)
+    gQ, gR = plu.plu_qr(ctx, dev(X), want_r=True)
+    gQ, gR = host(gQ), host(gR)
+    assert np.max(np.abs(gQ.T @ gQ - np.eye(cols))) < 1e-13
+    assert rel(gQ, Q) < 1e-11
+    assert rel(gR, R) < 1e-11
+
+
+# ------------------------------------------------------------------- a7
+@pytest.mark.parametrize("precise", [False, True])
+def test_rank_scan(ctx, precise):
+    sig = synth.sigma_profile("type2", 400)
+    A = synth.svd_matrix_np(500, 400, sig, seed=6)
+    V = oracle.gpowerlu(A, 200, 4, seed=1)
+    G = A @ V
+    nA2 = float(np.sum(A * A))
+    for eps in (1e-2, 1e-4, 1e-6):
+        k, E, met = oracle.rank_scan(G, nA2, eps, 10, precise)
+        gk, gE, gmet = plu.plu_rank(ctx, dev(G), nA2, eps, 10, precise)
+        assert (gk, gmet) == (k, met)
+        assert abs(gE - E) <= 1e-12 * nA2
+
+
+def test_norm2(ctx):
+    A = synth.gaussian_np(1234, 567, 8)
+    assert abs(plu.plu_norm2(ctx, dev(A)) - float(np.sum(A * A))) <= 1e-12 * np.sum(A * A)
+    A32 = A.astype(np.float32)
+    ref = float(np.sum(A32.astype(np.float64) ** 2))
+    assert abs(plu.plu_norm2(ctx, dev(A32, torch.float32)) - ref) <= 1e-12 * ref
+
+
+# --------------------------------------------------- failure detection
+def test_barrier_timeout_is_reported_and_context_survives(ctx):
+    """A zero wait budget makes the grid barriers of the panel LU give up:
+    the call returns PLU_ETIMEOUT and the next call on the context works."""
+    X = dev(synth.gaussian_np(20000, 16, 3))
+    ctx.set_wait_budget(0)
+    try:
+        with pytest.raises(plu.PLUError) as ei:
+            plu.plu_lu_reorth(ctx, X)
+        assert ei.value.name == "PLU_ETIMEOUT"
+    finally:
+        ctx.set_wait_budget(-1)
+    Y = synth.gaussian_np(2000, 16, 4)
+    assert rel(host(plu.plu_lu_reorth(ctx, dev(Y))), oracle.lu_permuted_L(Y)) < 1e-12
+
+
+def test_invalid_arguments_launch_nothing(ctx):
+    A = dev(synth.gaussian_np(50, 40, 1))
+    with pytest.raises(plu.PLUError) as ei:
+        plu.plu_powerlu(ctx, A, 10, 9, 2)            # l < k
+    assert ei.value.name == "PLU_EINVAL"
+    with pytest.raises(plu.PLUError) as ei:
+        plu.plu_powerlu(ctx, A, 5, 10, 1)            # v < 2
+    assert ei.value.name == "PLU_EINVAL"
+    with pytest.raises(plu.PLUError) as ei:
+        plu.plu_powerlu(ctx, A, 5, 40, 2)            # l >= min(m, n)
+    assert ei.value.name == "PLU_EINVAL"
