@@ -106,9 +106,14 @@ plu_status check_matrix(plu_ctx* c, const plu_matrix* A) {
     return PLU_OK;
 }
 
-plu_status check_prec(plu_ctx* c, int prec) {
+plu_status check_prec(plu_ctx* c, int prec, const plu_matrix* A) {
     if (prec == PLU_FP64 || prec == PLU_FP32) return PLU_OK;
-    if (prec == PLU_TF32 || prec == PLU_BF16 || prec == PLU_FP8_E4M3)
+    if (prec == PLU_TF32) {
+        if (A && A->dtype != PLU_F32)
+            return fail(c, PLU_EUNSUPPORTED, "TF32 passes need A stored in FP32");
+        return PLU_OK;
+    }
+    if (prec == PLU_BF16 || prec == PLU_FP8_E4M3)
         return fail(c, PLU_EUNSUPPORTED, "precision %d is not built in this library", prec);
     return fail(c, PLU_EINVAL, "bad precision %d", prec);
 }
@@ -127,8 +132,13 @@ plu_status dev_status_to_plu(plu_ctx* c, int st) {
 
 // ---- workspace needs of the steps
 size_t pass_ws(int64_t M, int64_t N, int64_t K, int prec, int sms) {
-    size_t b = gemm_partials_bytes(M, N, K, prec, sms) + 256;
-    if (prec == PLU_FP32) b += size_t(K) * N * sizeof(float) + 256;
+    const int sprec = (prec == PLU_TF32) ? PLU_FP32 : prec;
+    size_t b = gemm_partials_bytes(M, N, K, sprec, sms) + 256;
+    if (sprec == PLU_FP32) b += size_t(K) * N * sizeof(float) + 256;
+    if (prec == PLU_TF32) {
+        const size_t t = tc_scratch_bytes(M, K, int(N), sms);
+        if (t > b) b = t;
+    }
     return b;
 }
 
@@ -136,6 +146,12 @@ plu_status do_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X, 
                    int cols, int prec, double* Y, int64_t ldy, char* ws) {
     const int64_t M = trans ? A->n : A->m;
     const int64_t K = trans ? A->m : A->n;
+    if (prec == PLU_TF32 && A->dtype == PLU_F32 && tc_supported(M, K, cols, A->data, A->ld, trans)) {
+        PLU_CUDA(c, launch_tc_pass(trans, A->m, A->n, static_cast<const float*>(A->data), A->ld, X,
+                                   ldx, cols, Y, ldy, ws, c->d_status, c->num_sms, c->stream));
+        return PLU_OK;
+    }
+    if (prec == PLU_TF32) prec = PLU_FP32;     // shapes the tensor-core kernel does not take
     Workspace w;
     w.base = ws;
     w.cap = pass_ws(M, cols, K, prec, c->num_sms);
@@ -384,7 +400,7 @@ plu_status plu_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X,
                     int cols, plu_prec prec, double* Y, int64_t ldy) {
     PLU_TRY(bind(c));
     PLU_TRY(check_matrix(c, A));
-    PLU_TRY(check_prec(c, prec));
+    PLU_TRY(check_prec(c, prec, A));
     const int64_t M = trans ? A->n : A->m;
     const int64_t K = trans ? A->m : A->n;
     if (cols < 1 || !X || !Y || ldx < K || ldy < M) return fail(c, PLU_EINVAL, "bad pass operands");
@@ -463,7 +479,7 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
                        int64_t ldU, plu_report* rep) {
     PLU_TRY(bind(c));
     PLU_TRY(check_matrix(c, A));
-    PLU_TRY(check_prec(c, prec));
+    PLU_TRY(check_prec(c, prec, A));
     const int64_t m = A->m, n = A->n;
     const int64_t mn = m < n ? m : n;
     if (k < 1 || l < k || l >= mn) return fail(c, PLU_EINVAL, "need 1 <= k <= l < min(m, n)");
@@ -516,7 +532,7 @@ plu_status plu_powerlu_fp(plu_ctx* c, const plu_matrix* A, double eps, int b, in
                           plu_report* rep) {
     PLU_TRY(bind(c));
     PLU_TRY(check_matrix(c, A));
-    PLU_TRY(check_prec(c, prec));
+    PLU_TRY(check_prec(c, prec, A));
     const int64_t m = A->m, n = A->n;
     const int64_t mn = m < n ? m : n;
     if (!(eps > 0.0 && eps < 1.0)) return fail(c, PLU_EINVAL, "need 0 < eps < 1");

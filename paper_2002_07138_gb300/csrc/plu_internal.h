@@ -59,6 +59,17 @@ cudaError_t launch_gemm_f64(int transA, int transB, int64_t M, int64_t N, int64_
                             cudaStream_t s);
 size_t gemm_f64_partials_bytes(int64_t M, int64_t N, int64_t K, int num_sms);
 
+// ----------------------------------------------- tensor-core passes (TF32)
+// Y (FP64) = A X (trans 0) or A^T X (trans 1) with FP32 A (m x n, lda) on
+// tcgen05 tensor cores; X is FP64 (K x cols).  tc_supported() tells whether
+// the shape / alignment is handled (cols <= 512, lda % 4 == 0, A 16-byte
+// aligned).
+bool tc_supported(int64_t M, int64_t K, int cols, const void* A, int64_t lda, int trans);
+size_t tc_scratch_bytes(int64_t M, int64_t K, int cols, int num_sms);
+cudaError_t launch_tc_pass(int trans, int64_t m, int64_t n, const float* A, int64_t lda,
+                           const double* X, int64_t ldx, int cols, double* Y, int64_t ldy,
+                           void* scratch, int* dev_status, int num_sms, cudaStream_t s);
+
 // ------------------------------------------------------- panel LU (a3, a8)
 struct PanelScratch;   // defined in plu_panel.cu
 size_t panel_scratch_bytes(int64_t rows, int cols);

@@ -22,6 +22,17 @@
 // After the sweep each row holds its multipliers left of its pivot step and,
 // for pivot rows, the U row from the pivot step on.  A finalising kernel
 // writes either P^T L in place (a3) or perm, L (pivoted order) and U (a8).
+//
+// Blocked variant (used whenever a CTA's rows fit in shared memory): the
+// columns are taken NB = 32 at a time.  Each CTA keeps its rows of the
+// current NB-column block in shared memory, so a column step touches no
+// global memory except the candidate slots: the winning candidate publishes
+// its whole NB-wide block row with its slot, every CTA copies it after the
+// barrier and eliminates in shared memory.  After the block, every CTA forms
+// U12 = L11^{-1} A12 for the block's pivot rows (forward substitution) and
+// applies the FP64 trailing update X(:, J2) -= L(:, J1) U12 to its own rows.
+// The U rows go to a separate buffer, so no CTA overwrites data that
+// another one still reads.
 #include "plu_internal.h"
 
 #include <climits>
@@ -214,14 +225,193 @@ k_panel_lu(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
     }
 }
 
+constexpr int NB = 32;      // columns per block
+constexpr int UC = 128;     // trailing columns per U12 chunk
+
+__device__ __forceinline__ bool panel_barrier(PanelScratch* ps, unsigned target, int* status,
+                                              int64_t budget) {
+    return grid_barrier(&ps->barrier, target, status, budget);
+}
+
+// smem: P[NB][per] | U12[NB][UC] | PR[NB][NB] | pos_s[per] | piv_s[per] | prow_id[NB]
+__global__ void __launch_bounds__(NT)
+k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
+                   PanelScratch* __restrict__ ps, double* __restrict__ slots,
+                   double* __restrict__ Ubuf, int* __restrict__ pos_g, int* __restrict__ piv_g,
+                   int* __restrict__ status, int64_t budget, int per) {
+    extern __shared__ double dsm[];
+    double* P = dsm;
+    double* U12 = P + NB * per;
+    double* PR = U12 + NB * UC;
+    int* pos_s = reinterpret_cast<int*>(PR + NB * NB);
+    int* piv_s = pos_s + per;
+    int* prow_id = piv_s + per;
+    __shared__ Cand red[NT / 32];
+    __shared__ Cand piv;
+    __shared__ int win_slot;
+    __shared__ int nan_seen;
+
+    const int nb = gridDim.x;
+    const int t = threadIdx.x;
+    const int64_t r0 = int64_t(blockIdx.x) * per;
+    const int64_t r1 = min(rows, r0 + per);
+    const int R = int(r1 > r0 ? r1 - r0 : 0);
+    const int steps = int(rows < int64_t(cols) ? rows : int64_t(cols));
+    const int slot_w = NB + 2;
+
+    for (int r = t; r < R; r += NT) {
+        pos_s[r] = int(r0 + r);
+        piv_s[r] = -1;
+    }
+    if (t == 0) nan_seen = 0;
+    __syncthreads();
+
+    for (int j0 = 0; j0 < steps; j0 += NB) {
+        const int nbk = min(NB, steps - j0);
+        for (int e = t; e < nbk * R; e += NT) {
+            const int r = e % R, c = e / R;
+            P[c * per + r] = X[(r0 + r) + int64_t(j0 + c) * ldx];
+        }
+        __syncthreads();
+        for (int sc = 0; sc < nbk; ++sc) {
+            const int j = j0 + sc;
+            Cand best{-1.0, INT_MAX, -1};
+            for (int r = t; r < R; r += NT) {
+                if (piv_s[r] >= 0) continue;
+                const double a = fabs(P[sc * per + r]);
+                if (a != a) nan_seen = 1;
+                const Cand c{a, pos_s[r], int(r0 + r)};
+                if (better(c, best)) best = c;
+            }
+            const Cand cb = block_best(best, red);
+            double* myslot = slots + (int64_t(j & 1) * nb + blockIdx.x) * slot_w;
+            if (t == 0) {
+                myslot[0] = cb.v;
+                int2 pr;
+                pr.x = cb.pos;
+                pr.y = cb.row;
+                reinterpret_cast<int2*>(myslot + 1)[0] = pr;
+            }
+            if (t < nbk && cb.row >= 0) myslot[2 + t] = P[t * per + int(cb.row - r0)];
+            if (!panel_barrier(ps, unsigned(j + 1) * unsigned(nb), status, budget)) return;
+            if (t < 32) {
+                Cand g{-1.0, INT_MAX, -1};
+                int gs = -1;
+                for (int b = t; b < nb; b += 32) {
+                    const double* src = slots + (int64_t(j & 1) * nb + b) * slot_w;
+                    Cand c;
+                    c.v = __ldcg(src);
+                    const int2 pr = __ldcg(reinterpret_cast<const int2*>(src + 1));
+                    c.pos = pr.x;
+                    c.row = pr.y;
+                    if (better(c, g)) { g = c; gs = b; }
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const Cand o = shfl_cand(g, off);
+                    const int os = __shfl_xor_sync(0xffffffffu, gs, off);
+                    if (better(o, g)) { g = o; gs = os; }
+                }
+                if (t == 0) {
+                    piv = g;
+                    win_slot = gs;
+                }
+            }
+            __syncthreads();
+            const Cand pv = piv;
+            if (pv.row < 0) {
+                if (blockIdx.x == 0 && t == 0) atomicCAS(status, DEV_OK, DEV_NUMERIC);
+                return;
+            }
+            const double* wsrc = slots + (int64_t(j & 1) * nb + win_slot) * slot_w;
+            if (t < nbk) PR[sc * NB + t] = __ldcg(wsrc + 2 + t);
+            if (t == 0) prow_id[sc] = pv.row;
+            for (int r = t; r < R; r += NT) {
+                if (r0 + r == pv.row) {
+                    pos_s[r] = j;
+                    piv_s[r] = j;
+                } else if (pos_s[r] == j) {
+                    pos_s[r] = pv.pos;
+                }
+            }
+            if (blockIdx.x == 0 && t == 0) {
+                if (pv.v == 0.0 && ps->info == 0) ps->info = j + 1;
+                if (!(pv.v <= 1.7976931348623157e308)) ps->any_nan = 1;
+            }
+            __syncthreads();
+            const double ujj = PR[sc * NB + sc];
+            if (ujj != 0.0) {
+                for (int r = t; r < R; r += NT) {
+                    if (piv_s[r] >= 0) continue;
+                    const double l = P[sc * per + r] / ujj;
+                    P[sc * per + r] = l;
+                    for (int u = sc + 1; u < nbk; ++u)
+                        P[u * per + r] = fma(-l, PR[sc * NB + u], P[u * per + r]);
+                }
+            }
+            __syncthreads();
+        }
+        // block columns of own rows back to X (multipliers; pivot rows keep U11)
+        for (int e = t; e < nbk * R; e += NT) {
+            const int r = e % R, c = e / R;
+            X[(r0 + r) + int64_t(j0 + c) * ldx] = P[c * per + r];
+        }
+        // U11 rows to the U buffer (CTA 0)
+        if (blockIdx.x == 0) {
+            for (int e = t; e < nbk * nbk; e += NT) {
+                const int sr = e % nbk, c = e / nbk;
+                if (c >= sr) Ubuf[(j0 + sr) + int64_t(j0 + c) * steps] = PR[sr * NB + c];
+            }
+        }
+        // trailing columns, UC at a time
+        for (int c0 = j0 + nbk; c0 < cols; c0 += UC) {
+            const int cw = min(UC, cols - c0);
+            __syncthreads();
+            // U12 = L11^{-1} A12 over this chunk (every CTA, redundantly)
+            for (int c = t; c < cw; c += NT) {
+                for (int sr = 0; sr < nbk; ++sr) {
+                    double acc = __ldcg(&X[prow_id[sr] + int64_t(c0 + c) * ldx]);
+                    for (int u = 0; u < sr; ++u) acc = fma(-PR[sr * NB + u], U12[u * UC + c], acc);
+                    U12[sr * UC + c] = acc;
+                }
+            }
+            __syncthreads();
+            if (blockIdx.x == 0) {
+                for (int e = t; e < nbk * cw; e += NT) {
+                    const int sr = e % nbk, c = e / nbk;
+                    Ubuf[(j0 + sr) + int64_t(c0 + c) * steps] = U12[sr * UC + c];
+                }
+            }
+            // X(own active rows, chunk) -= L(:, block) U12
+            for (int e = t; e < R * cw; e += NT) {
+                const int r = e % R, c = e / R;
+                if (piv_s[r] >= 0) continue;
+                double acc = 0.0;
+                for (int u = 0; u < nbk; ++u) acc = fma(P[u * per + r], U12[u * UC + c], acc);
+                double* xp = &X[(r0 + r) + int64_t(c0 + c) * ldx];
+                *xp -= acc;
+            }
+        }
+        __syncthreads();
+    }
+    for (int r = t; r < R; r += NT) {
+        pos_g[r0 + r] = pos_s[r];
+        piv_g[r0 + r] = piv_s[r];
+    }
+    if (nan_seen) atomicExch(&ps->any_nan, 1);
+}
+
 __global__ void k_panel_finalize(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
                                  int mode, const int* __restrict__ pos,
                                  const int* __restrict__ pivstep, int32_t* __restrict__ perm,
                                  double* __restrict__ L, int64_t ldL, int l_trans,
                                  double* __restrict__ U, int64_t ldU, int u_trans,
                                  const PanelScratch* __restrict__ ps, int32_t* __restrict__ info,
-                                 int* __restrict__ status) {
+                                 int* __restrict__ status, const double* __restrict__ Ubuf) {
     const int r = int(rows < int64_t(cols) ? rows : int64_t(cols));
+    // after a failed factorisation (barrier timeout, NaN panel) the row state
+    // is incomplete: write nothing
+    if (*reinterpret_cast<volatile int*>(status) != DEV_OK) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (info) *info = ps->info;
         if (ps->any_nan) atomicCAS(status, DEV_OK, DEV_NUMERIC);
@@ -229,6 +419,8 @@ __global__ void k_panel_finalize(int64_t rows, int cols, double* __restrict__ X,
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < rows;
          i += int64_t(gridDim.x) * blockDim.x) {
         const int s = pivstep[i];
+        if (s < -1 || s >= r) continue;                    // defensive: never index with junk
+        if (mode != 0 && (pos[i] < 0 || int64_t(pos[i]) >= rows)) continue;
         if (mode == 0) {
             if (s >= 0) {
                 X[i + int64_t(s) * ldx] = 1.0;
@@ -248,7 +440,8 @@ __global__ void k_panel_finalize(int64_t rows, int cols, double* __restrict__ X,
         }
         if (s >= 0) {
             for (int c = 0; c < cols; ++c) {
-                const double v = (c >= s) ? X[i + int64_t(c) * ldx] : 0.0;
+                const double v = (c < s) ? 0.0
+                                         : (Ubuf ? Ubuf[s + int64_t(c) * r] : X[i + int64_t(c) * ldx]);
                 if (u_trans) U[c + int64_t(s) * ldU] = v;
                 else U[s + int64_t(c) * ldU] = v;
             }
@@ -259,9 +452,11 @@ __global__ void k_panel_finalize(int64_t rows, int cols, double* __restrict__ X,
 }  // namespace
 
 size_t panel_scratch_bytes(int64_t rows, int cols) {
-    (void)cols;
-    size_t head = (sizeof(PanelScratch) + 255) & ~size_t(255);
-    return head + 2 * size_t(rows) * sizeof(int) + 256;
+    const size_t head = (sizeof(PanelScratch) + 255) & ~size_t(255);
+    const size_t slots = size_t(2) * kMaxGrid * (NB + 2) * sizeof(double);
+    const int64_t steps = rows < cols ? rows : cols;
+    const size_t ubuf = size_t(steps) * size_t(cols) * sizeof(double);
+    return head + slots + 256 + ubuf + 256 + 2 * size_t(rows) * sizeof(int) + 256;
 }
 
 cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int mode,
@@ -271,9 +466,15 @@ cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int 
                             int num_sms, cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     if (cols > kMaxCols) return cudaErrorInvalidValue;
-    PanelScratch* ps = static_cast<PanelScratch*>(scratch);
-    const size_t head = (sizeof(PanelScratch) + 255) & ~size_t(255);
-    int* pos = reinterpret_cast<int*>(static_cast<char*>(scratch) + head);
+    char* base = static_cast<char*>(scratch);
+    PanelScratch* ps = reinterpret_cast<PanelScratch*>(base);
+    size_t off = (sizeof(PanelScratch) + 255) & ~size_t(255);
+    double* slots = reinterpret_cast<double*>(base + off);
+    off += (size_t(2) * kMaxGrid * (NB + 2) * sizeof(double) + 255) & ~size_t(255);
+    double* Ubuf = reinterpret_cast<double*>(base + off);
+    const int64_t steps = rows < cols ? rows : cols;
+    off += (size_t(steps) * size_t(cols) * sizeof(double) + 255) & ~size_t(255);
+    int* pos = reinterpret_cast<int*>(base + off);
     int* pivstep = pos + rows;
     cudaError_t e = cudaMemsetAsync(ps, 0, sizeof(PanelScratch), s);
     if (e != cudaSuccess) return e;
@@ -282,22 +483,39 @@ cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int 
     if (nb > num_sms) nb = num_sms;
     if (nb > kMaxGrid) nb = kMaxGrid;
     if (nb < 1) nb = 1;
-    const size_t smem = size_t(cols) * sizeof(double);
+    int64_t per = (rows + nb - 1) / nb;
+    nb = (rows + per - 1) / per;
     int64_t rows_ = rows;
     int cols_ = cols;
     int64_t ldx_ = ldx;
     int64_t budget = spin_budget;
-    void* args[] = {&rows_, &cols_, &X, &ldx_, &ps, &pos, &pivstep, &dev_status, &budget};
-    count_launch();
-    e = cudaLaunchCooperativeKernel((const void*)k_panel_lu, dim3(unsigned(nb)), dim3(NT), args,
-                                    smem, s);
+    const size_t smem_blk = size_t(NB) * per * 8 + size_t(NB) * UC * 8 + size_t(NB) * NB * 8 +
+                            size_t(2) * per * 4 + NB * 4 + 64;
+    const bool blocked = smem_blk <= 200 * 1024;
+    if (blocked) {
+        e = cudaFuncSetAttribute(k_panel_lu_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(smem_blk));
+        if (e != cudaSuccess) return e;
+        int per_ = int(per);
+        void* args[] = {&rows_, &cols_, &X, &ldx_, &ps, &slots, &Ubuf, &pos, &pivstep,
+                        &dev_status, &budget, &per_};
+        count_launch();
+        e = cudaLaunchCooperativeKernel((const void*)k_panel_lu_blocked, dim3(unsigned(nb)),
+                                        dim3(NT), args, smem_blk, s);
+    } else {
+        const size_t smem = size_t(cols) * sizeof(double);
+        void* args[] = {&rows_, &cols_, &X, &ldx_, &ps, &pos, &pivstep, &dev_status, &budget};
+        count_launch();
+        e = cudaLaunchCooperativeKernel((const void*)k_panel_lu, dim3(unsigned(nb)), dim3(NT),
+                                        args, smem, s);
+    }
     if (e != cudaSuccess) return e;
     int64_t fb = (rows + 255) / 256;
     if (fb > int64_t(num_sms) * 8) fb = int64_t(num_sms) * 8;
     count_launch();
     k_panel_finalize<<<unsigned(fb), 256, 0, s>>>(rows, cols, X, ldx, mode, pos, pivstep, perm,
                                                   L, ldL, l_trans, U, ldU, u_trans, ps, info,
-                                                  dev_status);
+                                                  dev_status, blocked ? Ubuf : nullptr);
     return cudaGetLastError();
 }
 

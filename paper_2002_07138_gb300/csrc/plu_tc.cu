@@ -1,0 +1,579 @@
+// Tensor-core passes over A on sm_103a: tcgen05.mma (kind::tf32, FP32
+// accumulation in TMEM) fed by TMA, for the products Y = A X and Y = A^T X
+// of Alg. gpowerlu / Alg. bpowerlu when A is stored in FP32.
+//
+// Shape of the problem: A is m x n (large), the other operand is K x l with
+// l <= 512 (the sketch width).  One CTA per SM walks an equal share of the
+// (128-row output block, 32-wide K step) iteration space ("stream-K"): each
+// CTA's output rows x all l columns live in TMEM (<= 512 FP32 columns), so
+// every byte of A is read from HBM exactly once, and the small operand is
+// re-read from L2.  A CTA ends at most a few output blocks ("segments");
+// their partial sums go to a scratch buffer and a second kernel adds the
+// contributions of each block in CTA order in FP64 (deterministic).
+//
+// Operand layouts in shared memory are the canonical 128-byte-swizzled
+// layouts written by TMA (SWIZZLE_128B) and read by the MMA through shared
+// memory descriptors:
+//   * Y = A^T X: the MMA's A operand is A^T, contiguous along K (= rows of
+//     A): K-major, 128 rows x 128 bytes per 32-wide K step;
+//   * Y = A X:   the MMA's A operand is A itself, contiguous along M (= rows
+//     of A): four 32-row x 32-column TMA boxes per K step land in a staging
+//     buffer and four transposer warps rewrite the 128 x 32 tile into the
+//     same K-major swizzled layout (float4 stores, conflict-free), then
+//     fence the generic-proxy writes for the tensor core;
+//   * the small operand (converted to FP32, zero-padded to Npad columns) is
+//     K-major in both cases.
+// Warp roles: warp 0 issues TMA, warp 1 issues the MMAs (one thread), warps
+// 2-5 drain TMEM to the partial buffer, warps 6-9 transpose (Y = A X only).  Every wait on an
+// mbarrier is bounded; on timeout the CTA raises the device error word,
+// lets its in-flight copies land, frees its TMEM and returns.
+#include "plu_internal.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+namespace plu {
+namespace {
+
+constexpr int TC_THREADS = 192;   // Y = A^T X
+constexpr int TC_THREADS_X = 320; // Y = A X (with transposer warps)
+constexpr int BM = 128;           // rows of an output block (MMA M)
+constexpr int BKB = 128;          // bytes of K per stage (one swizzle row)
+constexpr int A_TILE = BM * BKB;  // 16 KB
+constexpr uint32_t kWaitIters = 1u << 26;
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with parity `parity`; false on timeout or when
+// another role of the CTA has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    for (uint32_t i = 0; i < kWaitIters; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u && *abort) return false;
+    }
+    return false;
+}
+
+// Bounded wait that ignores the abort flag (used while draining).
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kWaitIters; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit TMEM columns -> 32 registers per thread.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared memory matrix descriptor (tcgen05): start address, leading and
+// stride byte offsets (all >> 4), descriptor version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= uint64_t((saddr >> 4) & 0x3FFF);
+    d |= uint64_t((lbo >> 4) & 0x3FFF) << 16;
+    d |= uint64_t((sbo >> 4) & 0x3FFF) << 32;
+    d |= uint64_t(1) << 46;                    // version
+    d |= uint64_t(2) << 61;                    // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, dense.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N, bool a_mn_major) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(a_mn_major) << 15) |
+           (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+struct TcParams {
+    int64_t M;          // output rows
+    int64_t K;          // reduction length
+    int npad;           // padded output columns (multiple of 16, <= 512)
+    int nchunk;         // columns per MMA (npad or npad / 2, <= 256)
+    int ksteps;         // K steps (of 32) per output block
+    int64_t total;      // blocks * ksteps
+    int64_t per;        // steps per CTA
+    int max_segs;       // partial tiles per CTA
+    int stages;
+    int b_bytes;        // npad * 128
+    uint32_t tmem_cols;
+    float* part;        // [grid][max_segs][npad][128]
+    int* status;
+};
+
+template <bool XPOSE>
+__global__ void __launch_bounds__(XPOSE ? TC_THREADS_X : TC_THREADS, 1)
+k_tc_pass(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+          const TcParams P) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[8];
+    __shared__ __align__(8) uint64_t empty_bar[8];
+    __shared__ __align__(8) uint64_t kmaj_bar[8];      // transposed tile ready (XPOSE)
+    __shared__ __align__(8) uint64_t acc_full;
+    __shared__ __align__(8) uint64_t acc_empty;
+    __shared__ __align__(8) uint64_t drain_bar;
+    __shared__ uint32_t tmem_holder;
+    __shared__ volatile int abort_flag;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // stage: [A tile, K-major][B tile][A staging, MN-major (XPOSE only)]
+    const int stage_bytes = A_TILE + P.b_bytes + (XPOSE ? A_TILE : 0);
+
+    const int64_t s0 = int64_t(blockIdx.x) * P.per;
+    const int64_t s1 = min(P.total, s0 + P.per);
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < P.stages; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+            mbar_init(&kmaj_bar[s], 4);                 // one arrival per transposer warp
+        }
+        mbar_init(&acc_full, 1);
+        mbar_init(&acc_empty, 4);                       // one arrival per epilogue warp
+        mbar_init(&drain_bar, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_holder)),
+                     "r"(P.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_holder;
+
+    int issued = 0;          // TMA stages issued (producer)
+    if (s0 < s1) {
+        if (warp == 0) {
+            // ---------------------------------------------------- producer
+            if (lane == 0) {
+                for (int64_t s = s0; s < s1; ++s, ++issued) {
+                    const int st = issued % P.stages;
+                    const uint32_t round = uint32_t(issued / P.stages);
+                    if (round > 0 && !mbar_wait(&empty_bar[st], (round - 1) & 1u, &abort_flag)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    const int64_t blk = s / P.ksteps;
+                    const int kk = int(s % P.ksteps) * 32;
+                    unsigned char* a_dst = smem + st * stage_bytes;
+                    unsigned char* b_dst = a_dst + A_TILE;
+                    mbar_arrive_expect_tx(&full_bar[st], uint32_t(A_TILE + P.b_bytes));
+                    if (XPOSE) {
+                        unsigned char* raw = b_dst + P.b_bytes;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            tma_load_2d(raw + q * 4096, &mapA, &full_bar[st],
+                                        int(blk * BM + 32 * q), kk);
+                    } else {
+                        tma_load_2d(a_dst, &mapA, &full_bar[st], kk, int(blk * BM));
+                    }
+                    for (int c = 0; c * P.nchunk < P.npad; ++c)
+                        tma_load_2d(b_dst + c * P.nchunk * 128, &mapB, &full_bar[st], kk,
+                                    c * P.nchunk);
+                }
+            }
+        } else if (warp == 1) {
+            // ------------------------------------------------------- MMA
+            if (lane == 0) {
+                const uint32_t idesc = idesc_tf32(BM, P.nchunk, false);
+                int it = 0, seg = 0;
+                for (int64_t s = s0; s < s1; ++s, ++it) {
+                    const bool seg_first = (s == s0) || (s % P.ksteps == 0);
+                    const bool seg_last = (s + 1 == s1) || ((s + 1) % P.ksteps == 0);
+                    if (seg_first && seg > 0) {
+                        if (!mbar_wait(&acc_empty, (seg - 1) & 1u, &abort_flag)) {
+                            abort_flag = 1;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    const int st = it % P.stages;
+                    if (!mbar_wait(XPOSE ? &kmaj_bar[st] : &full_bar[st],
+                                   uint32_t(it / P.stages) & 1u, &abort_flag)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_base = smem_u32(smem + st * stage_bytes);
+                    const uint32_t b_base = a_base + A_TILE;
+#pragma unroll
+                    for (int sub = 0; sub < 4; ++sub) {
+                        const uint64_t ad = smem_desc(a_base + sub * 32, 16, 1024);
+                        for (int c = 0; c * P.nchunk < P.npad; ++c) {
+                            const uint64_t bd =
+                                smem_desc(b_base + c * P.nchunk * 128 + sub * 32, 16, 1024);
+                            umma_tf32(tmem + uint32_t(c * P.nchunk), ad, bd, idesc,
+                                      (seg_first && sub == 0) ? 0u : 1u);
+                        }
+                    }
+                    tc_commit(&empty_bar[st]);
+                    if (seg_last) {
+                        tc_commit(&acc_full);
+                        ++seg;
+                    }
+                }
+            }
+        } else if (XPOSE && warp >= 6) {
+            // ------------------------------------------------ transposer
+            // thread t owns row m = t of the 128-row tile; staging box q = m/32
+            // holds A(32q.., k) as 32 K-rows of 128 bytes (128-byte swizzle);
+            // the K-major tile holds row m as 128 bytes, 16-byte chunk c of
+            // K = 4c..4c+3 stored at chunk c ^ (m % 8).
+            const int m = threadIdx.x - 192;
+            const int q = m >> 5, mm = m & 31;
+            int it = 0;
+            for (int64_t s = s0; s < s1; ++s, ++it) {
+                const int st = it % P.stages;
+                if (!mbar_wait(&full_bar[st], uint32_t(it / P.stages) & 1u, &abort_flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                unsigned char* kt = smem + st * stage_bytes;
+                const unsigned char* raw = kt + A_TILE + P.b_bytes + q * 4096;
+#pragma unroll
+                for (int k4 = 0; k4 < 8; ++k4) {
+                    float v[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int kr = 4 * k4 + e;
+                        v[e] = *reinterpret_cast<const float*>(
+                            raw + kr * 128 + (((mm >> 2) ^ (kr & 7)) << 4) + ((mm & 3) << 2));
+                    }
+                    *reinterpret_cast<float4*>(kt + m * 128 + ((k4 ^ (m & 7)) << 4)) =
+                        make_float4(v[0], v[1], v[2], v[3]);
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&kmaj_bar[st]);
+            }
+        } else {
+            // -------------------------------------------------- epilogue
+            const int quarter = warp & 3;                 // TMEM lanes 32*quarter..
+            const int row = quarter * 32 + lane;
+            int seg = 0;
+            for (int64_t s = s0; s < s1;) {
+                const int64_t blk = s / P.ksteps;
+                const int64_t next = min(s1, (blk + 1) * int64_t(P.ksteps));
+                if (!mbar_wait(&acc_full, uint32_t(seg) & 1u, &abort_flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                float* dst = P.part + (int64_t(blockIdx.x) * P.max_segs + seg) *
+                                          int64_t(P.npad) * BM;
+                for (int c0 = 0; c0 < P.npad; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(c0), r);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (c0 + j < P.npad) dst[int64_t(c0 + j) * BM + row] = __uint_as_float(r[j]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty);
+                ++seg;
+                s = next;
+            }
+        }
+    }
+    __syncthreads();
+    if (abort_flag) {
+        if (threadIdx.x == 0) atomicCAS(P.status, DEV_OK, DEV_TIMEOUT);
+        if (warp == 0 && lane == 0) {
+            // let the copies already issued land before shared memory goes away
+            for (int i = 0; i < issued && i < P.stages; ++i) {
+                const int idx = issued - 1 - i;
+                mbar_wait_drain(&full_bar[idx % P.stages], uint32_t(idx / P.stages) & 1u);
+            }
+        }
+        if (warp == 1 && lane == 0) {
+            // wait for every MMA this thread issued before TMEM is freed
+            tc_commit(&drain_bar);
+            mbar_wait_drain(&drain_bar, 0);
+        }
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(P.tmem_cols)
+                     : "memory");
+    }
+}
+
+// Y(i, j) = sum over the CTAs whose share touches block i/128 of their partial
+// tile, in CTA order, in FP64.
+__global__ void k_tc_reduce(const float* __restrict__ part, int64_t M, int l, int npad,
+                            int ksteps, int64_t total, int64_t per, int max_segs, int grid,
+                            double* __restrict__ Y, int64_t ldy) {
+    const int64_t count = M * l;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < count;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = e % M, j = e / M;
+        const int64_t blk = i / BM;
+        const int r = int(i % BM);
+        const int64_t first = blk * ksteps, last = min(total, first + ksteps) - 1;
+        int64_t c_lo = first / per, c_hi = last / per;
+        if (c_hi >= grid) c_hi = grid - 1;
+        double acc = 0.0;
+        for (int64_t c = c_lo; c <= c_hi; ++c) {
+            const int64_t cblk0 = (c * per) / ksteps;
+            const int64_t seg = blk - cblk0;
+            acc += double(part[((c * max_segs + seg) * npad + j) * BM + r]);
+        }
+        Y[i + j * ldy] = acc;
+    }
+}
+
+// X (FP64, K x cols, ldx) -> X32 (FP32, K x npad, ld ldo), zero columns beyond cols,
+// rounded to TF32 (round to nearest, ties away) so the MMA sees rounded values.
+__global__ void k_to_tf32(int64_t K, int cols, int npad, const double* __restrict__ X,
+                          int64_t ldx, float* __restrict__ out, int64_t ldo) {
+    const int64_t total = K * npad;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = e % K, j = e / K;
+        float v = 0.f;
+        if (j < cols) {
+            const float f = float(X[i + j * ldx]);
+            uint32_t t;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(f));
+            v = __uint_as_float(t);
+        }
+        out[i + j * ldo] = v;
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool make_map_2d(CUtensorMap* map, const void* base, uint64_t dim0, uint64_t dim1,
+                 uint64_t stride1_bytes, uint32_t box0, uint32_t box1) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {dim0, dim1};
+    cuuint64_t strides[1] = {stride1_bytes};
+    cuuint32_t box[2] = {box0, box1};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+struct TcPlan {
+    int npad, nchunk, ksteps, stages, max_segs, grid;
+    int64_t blocks, total, per;
+    uint32_t tmem_cols;
+    size_t smem;
+    int64_t ldx32;
+};
+
+TcPlan plan_tc(int64_t M, int64_t K, int cols, int num_sms, bool xpose) {
+    TcPlan p{};
+    p.npad = cols <= 256 ? (cols + 15) / 16 * 16 : (cols + 31) / 32 * 32;
+    p.nchunk = p.npad <= 256 ? p.npad : p.npad / 2;
+    p.ksteps = int((K + 31) / 32);
+    p.blocks = (M + BM - 1) / BM;
+    p.total = p.blocks * p.ksteps;
+    p.grid = num_sms;
+    if (p.grid > p.total) p.grid = int(p.total);
+    p.per = (p.total + p.grid - 1) / p.grid;
+    p.grid = int((p.total + p.per - 1) / p.per);
+    p.max_segs = int((p.per + p.ksteps - 1) / p.ksteps) + 1;
+    const int stage_bytes = A_TILE + p.npad * 128 + (xpose ? A_TILE : 0);
+    int st = int((220 * 1024 - 2048) / stage_bytes);
+    if (st > 8) st = 8;
+    p.stages = st;
+    p.smem = size_t(st) * stage_bytes + 1024;
+    uint32_t tc = 32;
+    while (tc < uint32_t(p.npad)) tc <<= 1;
+    p.tmem_cols = tc;
+    p.ldx32 = (K + 3) / 4 * 4;
+    return p;
+}
+
+}  // namespace
+
+bool tc_supported(int64_t M, int64_t K, int cols, const void* A, int64_t lda, int trans) {
+    if (cols < 1 || cols > 512 || M < 1 || K < 1) return false;
+    if ((reinterpret_cast<uintptr_t>(A) & 15) != 0 || (lda % 4) != 0) return false;
+    if (M > (int64_t(1) << 31) - 256 || K > (int64_t(1) << 31) - 256) return false;
+    const TcPlan p = plan_tc(M, K, cols, 152, trans == 0);
+    return p.stages >= 2 && get_encode() != nullptr;
+}
+
+size_t tc_scratch_bytes(int64_t M, int64_t K, int cols, int num_sms) {
+    const TcPlan p = plan_tc(M, K, cols, num_sms, false);
+    return size_t(p.grid) * p.max_segs * p.npad * BM * sizeof(float) + 256 +
+           size_t(p.ldx32) * p.npad * sizeof(float) + 256;
+}
+
+cudaError_t launch_tc_pass(int trans, int64_t m, int64_t n, const float* A, int64_t lda,
+                           const double* X, int64_t ldx, int cols, double* Y, int64_t ldy,
+                           void* scratch, int* dev_status, int num_sms, cudaStream_t s) {
+    const int64_t M = trans ? n : m;
+    const int64_t K = trans ? m : n;
+    const TcPlan p = plan_tc(M, K, cols, num_sms, trans == 0);
+    Workspace w;
+    w.base = static_cast<char*>(scratch);
+    w.cap = tc_scratch_bytes(M, K, cols, num_sms);
+    float* part = static_cast<float*>(w.take(size_t(p.grid) * p.max_segs * p.npad * BM * sizeof(float)));
+    float* x32 = static_cast<float*>(w.take(size_t(p.ldx32) * p.npad * sizeof(float)));
+    if (!part || !x32) return cudaErrorInvalidValue;
+    // small operand -> TF32, K x npad, ld multiple of 4 (16-byte TMA strides)
+    {
+        int64_t b = (K * p.npad + 255) / 256;
+        if (b > int64_t(num_sms) * 16) b = int64_t(num_sms) * 16;
+        count_launch();
+        k_to_tf32<<<unsigned(b), 256, 0, s>>>(K, cols, p.npad, X, ldx, x32, p.ldx32);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    CUtensorMap mapA, mapB;
+    // A as stored: dim0 = rows (m, contiguous), dim1 = columns (n)
+    const uint32_t a_box0 = 32, a_box1 = trans ? 128 : 32;
+    if (!make_map_2d(&mapA, A, uint64_t(m), uint64_t(n), uint64_t(lda) * 4, a_box0, a_box1))
+        return cudaErrorInvalidValue;
+    if (!make_map_2d(&mapB, x32, uint64_t(K), uint64_t(p.npad), uint64_t(p.ldx32) * 4, 32,
+                     uint32_t(p.nchunk)))
+        return cudaErrorInvalidValue;
+    TcParams P;
+    P.M = M;
+    P.K = K;
+    P.npad = p.npad;
+    P.nchunk = p.nchunk;
+    P.ksteps = p.ksteps;
+    P.total = p.total;
+    P.per = p.per;
+    P.max_segs = p.max_segs;
+    P.stages = p.stages;
+    P.b_bytes = p.npad * 128;
+    P.tmem_cols = p.tmem_cols;
+    P.part = part;
+    P.status = dev_status;
+    cudaError_t e;
+    if (trans) {
+        e = cudaFuncSetAttribute(k_tc_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(p.smem));
+        if (e != cudaSuccess) return e;
+        count_launch();
+        k_tc_pass<false><<<p.grid, TC_THREADS, p.smem, s>>>(mapA, mapB, P);
+    } else {
+        e = cudaFuncSetAttribute(k_tc_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(p.smem));
+        if (e != cudaSuccess) return e;
+        count_launch();
+        k_tc_pass<true><<<p.grid, TC_THREADS_X, p.smem, s>>>(mapA, mapB, P);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int64_t rb = (M * cols + 255) / 256;
+    if (rb > int64_t(num_sms) * 16) rb = int64_t(num_sms) * 16;
+    count_launch();
+    k_tc_reduce<<<unsigned(rb), 256, 0, s>>>(part, M, cols, p.npad, p.ksteps, p.total, p.per,
+                                              p.max_segs, p.grid, Y, ldy);
+    return cudaGetLastError();
+}
+
+}  // namespace plu

@@ -125,3 +125,17 @@ def test_fixed_rank_8192_fp64_full_parity(ctx):
     err = oracle.rel_lu_error(A, ref[0], ref[1], ref[2], ref[3])
     opt = oracle.eckart_young_error(w.sigma_values(), w.k)
     assert opt * (1 - 1e-9) <= err < 2.0 * opt
+
+
+def test_powerlu_tf32_error_within_1p1_of_fp64(ctx):
+    """Mixed precision: TF32 tensor-core passes, FP64 everything else."""
+    sig = synth.sigma_profile("pow15", 4096)
+    A = synth.svd_matrix_np(4096, 4096, sig, seed=2)
+    A32 = A.astype(np.float32)
+    A64h = A32.astype(np.float64)
+    errs = {}
+    for prec, Ad in (("fp64", dev(A64h)), ("tf32", dev(A32, torch.float32))):
+        gp, gq, gL, gU, rep = plu.plu_powerlu(ctx, Ad, 64, 74, 3, seed=0, prec=prec)
+        errs[prec] = oracle.rel_lu_error(A64h, gp.cpu().numpy(), gq.cpu().numpy(), host(gL), host(gU))
+        assert rep["passes"] == 3
+    assert errs["tf32"] <= 1.1 * errs["fp64"], errs

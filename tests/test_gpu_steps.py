@@ -173,10 +173,10 @@ def test_norm2(ctx):
 
 # --------------------------------------------------- failure detection
 def test_barrier_timeout_is_reported_and_context_survives(ctx):
-    """A zero wait budget makes the grid barriers of the panel LU give up:
+    """A one-spin wait budget makes the grid barriers of the panel LU give up:
     the call returns PLU_ETIMEOUT and the next call on the context works."""
     X = dev(synth.gaussian_np(20000, 16, 3))
-    ctx.set_wait_budget(0)
+    ctx.set_wait_budget(1)
     try:
         with pytest.raises(plu.PLUError) as ei:
             plu.plu_lu_reorth(ctx, X)
@@ -198,3 +198,62 @@ def test_invalid_arguments_launch_nothing(ctx):
     with pytest.raises(plu.PLUError) as ei:
         plu.plu_powerlu(ctx, A, 5, 40, 2)            # l >= min(m, n)
     assert ei.value.name == "PLU_EINVAL"
+
+
+# ------------------------------------------- a2/a4/a6 on tensor cores (TF32)
+def tf32_trunc(a):
+    """float32 -> TF32 by dropping the 13 low mantissa bits (what the MMA reads)."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32) & np.uint32(0xFFFFE000)
+    return b.view(np.float32)
+
+
+def tf32_rna(a):
+    """float32 -> TF32, round to nearest, ties away from zero."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+    b = (b + np.uint32(0x1000)) & np.uint32(0xFFFFE000)
+    return b.view(np.float32)
+
+
+@pytest.mark.parametrize("m,n,cols", [(1000, 777, 25), (2048, 1536, 276), (300, 257, 1),
+                                      (512, 8192, 110), (4096, 1024, 512), (132, 4100, 48)])
+@pytest.mark.parametrize("trans", [0, 1])
+def test_pass_tf32_matches_tf32_operands(ctx, m, n, cols, trans):
+    """The tensor-core pass equals the FP64 product of the TF32 operands the
+    MMA consumes (A truncated, X rounded) up to FP32 accumulation error."""
+    A32 = synth.gaussian_np(m, n, 11).astype(np.float32)
+    X = synth.gaussian_np(n if trans == 0 else m, cols, 12)
+    At = tf32_trunc(A32).astype(np.float64)
+    Xr = tf32_rna(X.astype(np.float32)).astype(np.float64)
+    ref = At @ Xr if trans == 0 else At.T @ Xr
+    got = host(plu.plu_pass(ctx, dev(A32, torch.float32), trans, dev(X), "tf32"))
+    K = n if trans == 0 else m
+    assert rel(got, ref) < 4e-7 * np.sqrt(K / 32.0) + 1e-6
+
+
+@pytest.mark.parametrize("trans", [0, 1])
+def test_pass_tf32_leading_dimension_and_fallback(ctx, trans):
+    m, n, cols = 600, 500, 40
+    X = synth.gaussian_np(n if trans == 0 else m, cols, 14)
+    Xr = tf32_rna(X.astype(np.float32)).astype(np.float64)
+    for ld in (604, 601):                    # 601: not a multiple of 4 -> SIMT FP32 kernel
+        big = plu.colmajor_empty(ld, n, dtype=torch.float32)
+        big.copy_(torch.from_numpy(synth.gaussian_np(ld, n, 13).astype(np.float32)))
+        A = big[:m, :]
+        A32 = host(A).astype(np.float32)
+        got = host(plu.plu_pass(ctx, A, trans, dev(X), "tf32"))
+        if ld % 4 == 0:
+            At = tf32_trunc(A32).astype(np.float64)
+            ref = At @ Xr if trans == 0 else At.T @ Xr
+            assert rel(got, ref) < 2e-6
+        else:
+            A64 = A32.astype(np.float64)
+            Xf = X.astype(np.float32).astype(np.float64)
+            ref = A64 @ Xf if trans == 0 else A64.T @ Xf
+            assert rel(got, ref) < 2e-6
+
+
+def test_pass_tf32_rejects_fp64_matrix(ctx):
+    A = dev(synth.gaussian_np(100, 80, 1))
+    with pytest.raises(plu.PLUError) as ei:
+        plu.plu_pass(ctx, A, 0, dev(synth.gaussian_np(80, 4, 2)), "tf32")
+    assert ei.value.name == "PLU_EUNSUPPORTED"
