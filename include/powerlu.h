@@ -189,6 +189,29 @@ plu_status plu_singlepass(plu_ctx* ctx, const plu_matrix* A, int k, uint64_t see
                           plu_prec prec, int32_t* p, int32_t* q, double* L, int64_t ldL,
                           double* U, int64_t ldU, plu_report* rep);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free variant (the paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory, such as code running
+ * under a framework that owns all GPU memory through its own pool, plug-ins
+ * that may not allocate, and latency-critical loops that cannot afford
+ * cudaMalloc's device-wide synchronisation).
+ *
+ * Same result as plu_lu_reorth (X overwritten by P^T L, in place), with no
+ * context and no allocation: the kernels' scratch is a fixed 2 MiB device
+ * array inside the library, held by every GPU that loads the library until
+ * the process exits.  Limits: rows <= 65536, cols <= 256; larger panels are
+ * rejected with PLU_EINVAL and a message.  The work is enqueued on
+ * `cuda_stream` (a cudaStream_t, NULL = legacy default stream) of the current
+ * device; the call then synchronises that stream and returns the device
+ * status (PLU_ETIMEOUT, PLU_ENUMERIC).  The first call on a device looks up
+ * the array's device address: make it before any stream capture.  All calls
+ * share the array, so calls whose GPU work overlaps race; each call clears
+ * what must start at zero.  err (host buffer of err_len bytes, nullable)
+ * receives a message on failure.
+ * ------------------------------------------------------------------- */
+plu_status plu_lu_reorth_static(void* cuda_stream, int64_t rows, int cols, double* X,
+                                int64_t ldx, char* err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

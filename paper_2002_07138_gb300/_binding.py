@@ -66,6 +66,8 @@ SIGNATURES = {
                                c_i64, ctypes.POINTER(plu_report)]),
     "plu_singlepass": (c_int, [c_vp, ctypes.POINTER(plu_matrix), c_int, c_u64, c_int, c_vp, c_vp,
                                c_vp, c_i64, c_vp, c_i64, ctypes.POINTER(plu_report)]),
+    "plu_lu_reorth_static": (c_int, [c_vp, c_i64, c_int, c_vp, c_i64, ctypes.c_char_p,
+                                     ctypes.c_size_t]),
 }
 
 _lib = None

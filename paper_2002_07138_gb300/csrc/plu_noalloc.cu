@@ -1,0 +1,113 @@
+// plu_lu_reorth_static: the re-orthogonalising panel LU (the same kernels as
+// plu_lu_reorth) for callers that cannot allocate device memory.
+//
+// Who needs it: every other entry point works through a plu_ctx, and creating
+// a context (and growing its workspace) calls cudaMalloc.  Some callers cannot
+// do that: a host framework that has handed all of the GPU's memory to its own
+// pool allocator (a raw cudaMalloc then fails or fragments the pool), plug-ins
+// and embedded runtimes whose rules forbid allocating, and latency-critical
+// loops that cannot pay for cudaMalloc / cudaFree, which may synchronise the
+// whole device.  This entry point allocates nothing: its scratch memory (grid
+// barrier word, per-CTA pivot candidates, U rows, row positions and the status
+// word) lives in one file-scope device array of fixed size, kStaticBytes
+// (2 MiB), which every GPU that loads the library holds until the process
+// exits.  Hence the size limits: rows <= 65536 and cols <= 256.
+//
+// Set-up: the first call on a device, with that device current, looks up the
+// device address of the array (cudaGetSymbolAddress) and the SM count; make
+// that first call before any stream capture.  Every call shares the array and
+// finds the previous call's contents there; the call clears what must start
+// at zero (the status word and the barrier header).  Calls whose work overlaps
+// on the GPU (on different streams, or from several host threads without
+// ordering) race on the array and must not be issued.
+#include "plu_internal.h"
+
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+
+namespace {
+
+constexpr size_t kStaticBytes = size_t(2) << 20;     // 2 MiB
+constexpr int64_t kStaticMaxRows = 65536;
+constexpr int kStaticMaxCols = 256;
+constexpr size_t kStatusBytes = 256;                  // status word, then the panel scratch
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_plu_static_scratch[kStaticBytes];
+
+struct DeviceSlot {
+    bool ready = false;
+    char* base = nullptr;      // device address of g_plu_static_scratch on that device
+    int num_sms = 0;
+};
+DeviceSlot g_slots[kMaxDevices];
+std::mutex g_mutex;
+
+plu_status say(char* err, size_t err_len, plu_status st, const char* fmt, ...) {
+    if (err && err_len > 0) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(err, err_len, fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+}  // namespace
+
+extern "C" plu_status plu_lu_reorth_static(void* cuda_stream, int64_t rows, int cols, double* X,
+                                           int64_t ldx, char* err, size_t err_len) {
+    if (err && err_len > 0) err[0] = '\0';
+    if (!X || cols < 1 || rows < cols || ldx < rows)
+        return say(err, err_len, PLU_EINVAL,
+                   "plu_lu_reorth_static needs X != NULL, rows >= cols >= 1, ldx >= rows");
+    if (rows > kStaticMaxRows || cols > kStaticMaxCols)
+        return say(err, err_len, PLU_EINVAL,
+                   "plu_lu_reorth_static takes at most %lld rows and %d columns (got %lld x %d): "
+                   "its scratch is a fixed %zu-byte device array",
+                   (long long)kStaticMaxRows, kStaticMaxCols, (long long)rows, cols, kStaticBytes);
+    const size_t need = kStatusBytes + plu::panel_scratch_bytes(rows, cols);
+    if (need > kStaticBytes)
+        return say(err, err_len, PLU_EINVAL, "panel needs %zu bytes of scratch, the array has %zu",
+                   need, kStaticBytes);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return say(err, err_len, PLU_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return say(err, err_len, PLU_EINVAL, "device %d out of range", dev);
+    DeviceSlot slot;
+    {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        if (!g_slots[dev].ready) {
+            void* ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_plu_static_scratch);
+            if (e != cudaSuccess)
+                return say(err, err_len, PLU_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            int sms = 0;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess)
+                return say(err, err_len, PLU_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+            g_slots[dev].base = static_cast<char*>(ptr);
+            g_slots[dev].num_sms = sms;
+            g_slots[dev].ready = true;
+        }
+        slot = g_slots[dev];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int* status = reinterpret_cast<int*>(slot.base);
+    void* scratch = slot.base + kStatusBytes;
+    e = cudaMemsetAsync(status, 0, sizeof(int), s);
+    if (e == cudaSuccess)
+        e = plu::launch_panel_lu(rows, cols, X, ldx, 0, nullptr, nullptr, 0, 0, nullptr, 0, 0,
+                                 nullptr, scratch, status, 16LL << 20, slot.num_sms, s);
+    if (e != cudaSuccess) return say(err, err_len, PLU_ECUDA, "launch: %s", cudaGetErrorString(e));
+    int h_status = 0;
+    e = cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return say(err, err_len, PLU_ECUDA, "sync: %s", cudaGetErrorString(e));
+    if (h_status == plu::DEV_TIMEOUT)
+        return say(err, err_len, PLU_ETIMEOUT, "a device-side wait ran out of its budget");
+    if (h_status != plu::DEV_OK)
+        return say(err, err_len, PLU_ENUMERIC, "non-finite value in the panel");
+    return PLU_OK;
+}
