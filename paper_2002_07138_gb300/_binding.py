@@ -259,3 +259,18 @@ def plu_powerlu_fp(ctx, A, eps, b, l, v, seed=0, prec="fp64", precise=False):
                                         ctypes.byref(rep)), allow=(6,))
     kk = k.value
     return kk, p, q, L[:, :kk], U[:kk, :], st == 0, rep.as_dict()
+
+
+def plu_singlepass(ctx, A, k, seed=0, prec="fp64"):
+    """Single pass (Alg. singlepasslu).  Returns (p, q, L, U, report dict)."""
+    torch = _torch()
+    m, n = A.shape
+    p = torch.empty(m, dtype=torch.int32, device=A.device)
+    q = torch.empty(n, dtype=torch.int32, device=A.device)
+    L = colmajor_empty(m, k, device=A.device)
+    U = colmajor_empty(k, n, device=A.device)
+    rep = plu_report()
+    Am = as_plu_matrix(A)
+    ctx.check(lib().plu_singlepass(ctx.handle, ctypes.byref(Am), k, seed, PREC[prec], _ptr(p),
+                                   _ptr(q), _ptr(L), _ld(L), _ptr(U), _ld(U), ctypes.byref(rep)))
+    return p, q, L, U, rep.as_dict()

@@ -108,13 +108,11 @@ plu_status check_matrix(plu_ctx* c, const plu_matrix* A) {
 
 plu_status check_prec(plu_ctx* c, int prec, const plu_matrix* A) {
     if (prec == PLU_FP64 || prec == PLU_FP32) return PLU_OK;
-    if (prec == PLU_TF32) {
+    if (prec == PLU_TF32 || prec == PLU_BF16 || prec == PLU_FP8_E4M3) {
         if (A && A->dtype != PLU_F32)
-            return fail(c, PLU_EUNSUPPORTED, "TF32 passes need A stored in FP32");
+            return fail(c, PLU_EUNSUPPORTED, "tensor-core passes need A stored in FP32");
         return PLU_OK;
     }
-    if (prec == PLU_BF16 || prec == PLU_FP8_E4M3)
-        return fail(c, PLU_EUNSUPPORTED, "precision %d is not built in this library", prec);
     return fail(c, PLU_EINVAL, "bad precision %d", prec);
 }
 
@@ -131,27 +129,39 @@ plu_status dev_status_to_plu(plu_ctx* c, int st) {
 }
 
 // ---- workspace needs of the steps
+bool is_tc(int prec) { return prec == PLU_TF32 || prec == PLU_BF16 || prec == PLU_FP8_E4M3; }
+
 size_t pass_ws(int64_t M, int64_t N, int64_t K, int prec, int sms) {
-    const int sprec = (prec == PLU_TF32) ? PLU_FP32 : prec;
+    const int sprec = is_tc(prec) ? PLU_FP32 : prec;
     size_t b = gemm_partials_bytes(M, N, K, sprec, sms) + 256;
     if (sprec == PLU_FP32) b += size_t(K) * N * sizeof(float) + 256;
-    if (prec == PLU_TF32) {
+    if (is_tc(prec)) {
         const size_t t = tc_scratch_bytes(M, K, int(N), sms);
         if (t > b) b = t;
     }
     return b;
 }
 
+// One pass over A.  BF16 / FP8 passes read the quantized copy q (made once
+// per call); TF32 reads the FP32 A directly; shapes the tensor-core kernel
+// does not take (more than 512 columns, unaligned A) use the FP32 SIMT kernel.
 plu_status do_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X, int64_t ldx,
-                   int cols, int prec, double* Y, int64_t ldy, char* ws) {
+                   int cols, int prec, double* Y, int64_t ldy, char* ws,
+                   const QuantA* q = nullptr, int accum = 0) {
     const int64_t M = trans ? A->n : A->m;
     const int64_t K = trans ? A->m : A->n;
-    if (prec == PLU_TF32 && A->dtype == PLU_F32 && tc_supported(M, K, cols, A->data, A->ld, trans)) {
-        PLU_CUDA(c, launch_tc_pass(trans, A->m, A->n, static_cast<const float*>(A->data), A->ld, X,
-                                   ldx, cols, Y, ldy, ws, c->d_status, c->num_sms, c->stream));
+    if ((prec == PLU_BF16 || prec == PLU_FP8_E4M3) && q && cols <= 512) {
+        PLU_CUDA(c, launch_tc_pass_q(trans, *q, X, ldx, cols, Y, ldy, ws, c->d_status, c->num_sms,
+                                     c->stream, accum));
         return PLU_OK;
     }
-    if (prec == PLU_TF32) prec = PLU_FP32;     // shapes the tensor-core kernel does not take
+    if (is_tc(prec) && A->dtype == PLU_F32 && tc_supported(M, K, cols, A->data, A->ld, trans)) {
+        PLU_CUDA(c, launch_tc_pass(trans, A->m, A->n, static_cast<const float*>(A->data), A->ld, X,
+                                   ldx, cols, Y, ldy, ws, c->d_status, c->num_sms, c->stream,
+                                   accum));
+        return PLU_OK;
+    }
+    if (is_tc(prec)) prec = PLU_FP32;
     Workspace w;
     w.base = ws;
     w.cap = pass_ws(M, cols, K, prec, c->num_sms);
@@ -159,13 +169,13 @@ plu_status do_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X, 
     float* b32 = nullptr;
     if (prec == PLU_FP32) b32 = static_cast<float*>(w.take(size_t(K) * cols * sizeof(float)));
     PLU_CUDA(c, launch_gemm_simt(trans, M, cols, K, A->data, A->dtype, A->ld, X, ldx, Y, ldy, prec,
-                                 part, b32, c->num_sms, c->stream));
+                                 part, b32, c->num_sms, c->stream, accum));
     return PLU_OK;
 }
 
 struct PowerLUPlan {
     // offsets into the workspace
-    size_t V, Z, step, L1, U1T, BT, U2T, tailpart, cn, total;
+    size_t V, Z, step, L1, U1T, BT, U2T, tailpart, cn, quant, total;
 };
 
 // Shared by the fixed-rank and fixed-precision drivers: workspace for
@@ -193,6 +203,7 @@ PowerLUPlan plan_powerlu(int64_t m, int64_t n, int l, int kmax, int prec, int sm
     if (t > tp) tp = t;
     p.tailpart = lay.add(tp);
     p.cn = lay.add(size_t(l) * sizeof(double) + norm2_scratch_bytes(sms));
+    p.quant = (prec == PLU_BF16 || prec == PLU_FP8_E4M3) ? lay.add(tc_quant_bytes(m, n, prec)) : 0;
     p.total = lay.total + 256;
     return p;
 }
@@ -225,13 +236,14 @@ struct PassTimer {
 
 // Alg. gpowerlu into V (n x l).  Returns the number of passes launched.
 plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t seed, int prec,
-                        double* V, double* Z, char* step, PassTimer& pt, int* passes) {
+                        double* V, double* Z, char* step, PassTimer& pt, int* passes,
+                        const QuantA* q) {
     const int64_t m = A->m, n = A->n;
     const int p = (v - 1) / 2;
     int np = 0;
     auto pass = [&](int trans, const double* X, int64_t ldx, double* Y, int64_t ldy) -> plu_status {
         pt.mark();
-        PLU_TRY(do_pass(c, A, trans, X, ldx, l, prec, Y, ldy, step));
+        PLU_TRY(do_pass(c, A, trans, X, ldx, l, prec, Y, ldy, step, q));
         pt.mark();
         ++np;
         return PLU_OK;
@@ -404,8 +416,14 @@ plu_status plu_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X,
     const int64_t M = trans ? A->n : A->m;
     const int64_t K = trans ? A->m : A->n;
     if (cols < 1 || !X || !Y || ldx < K || ldy < M) return fail(c, PLU_EINVAL, "bad pass operands");
-    PLU_TRY(ensure_ws(c, pass_ws(M, cols, K, prec, c->num_sms)));
-    PLU_TRY(do_pass(c, A, trans, X, ldx, cols, prec, Y, ldy, c->ws));
+    const bool quant = (prec == PLU_BF16 || prec == PLU_FP8_E4M3) && cols <= 512;
+    const size_t qb = quant ? ((tc_quant_bytes(A->m, A->n, prec) + 255) & ~size_t(255)) : 0;
+    PLU_TRY(ensure_ws(c, qb + pass_ws(M, cols, K, prec, c->num_sms)));
+    QuantA q;
+    if (quant)
+        PLU_CUDA(c, launch_tc_quantize(prec, static_cast<const float*>(A->data), A->m, A->n, A->ld,
+                                       c->ws, &q, c->num_sms, c->stream));
+    PLU_TRY(do_pass(c, A, trans, X, ldx, cols, prec, Y, ldy, c->ws + qb, quant ? &q : nullptr));
     return finish(c);
 }
 
@@ -496,10 +514,16 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
     const long long launches0 = g_launches;
     if (rep) PLU_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
     int np = 0;
-    PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pt, &np));
-    // Y = A V(:, 1:k) (Alg. bpowerlu step 3), the v-th pass
+    QuantA qa;
+    const bool quant = prec == PLU_BF16 || prec == PLU_FP8_E4M3;
+    if (quant)
+        PLU_CUDA(c, launch_tc_quantize(prec, static_cast<const float*>(A->data), m, n, A->ld,
+                                       ws + pl.quant, &qa, c->num_sms, c->stream));
+    PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pt, &np, quant ? &qa : nullptr));
+    // Y = A V(:, 1:k) (Alg. bpowerlu step 3), the v-th pass; in the mixed
+    // modes it reads the FP32 A through TF32 (it enters the result to first order)
     pt.mark();
-    PLU_TRY(do_pass(c, A, 0, V, n, k, prec, Z, m, step));
+    PLU_TRY(do_pass(c, A, 0, V, n, k, is_tc(prec) ? int(PLU_TF32) : int(prec), Z, m, step));
     pt.mark();
     ++np;
     int32_t* info = reinterpret_cast<int32_t*>(ws + pl.cn);
@@ -556,10 +580,15 @@ plu_status plu_powerlu_fp(plu_ctx* c, const plu_matrix* A, double eps, int b, in
     PLU_CUDA(c, launch_norm2(A->data, A->dtype, m, n, A->ld, c->d_scal, nscr, c->num_sms, c->stream));
     pt.mark();
     int np = 0;
-    PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pt, &np));
-    // G = A V (step 3), the v-th pass
+    QuantA qa;
+    const bool quant = prec == PLU_BF16 || prec == PLU_FP8_E4M3;
+    if (quant)
+        PLU_CUDA(c, launch_tc_quantize(prec, static_cast<const float*>(A->data), m, n, A->ld,
+                                       ws + pl.quant, &qa, c->num_sms, c->stream));
+    PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pt, &np, quant ? &qa : nullptr));
+    // G = A V (step 3), the v-th pass (FP32 A through TF32 in the mixed modes)
     pt.mark();
-    PLU_TRY(do_pass(c, A, 0, V, n, l, prec, Z, m, step));
+    PLU_TRY(do_pass(c, A, 0, V, n, l, is_tc(prec) ? int(PLU_TF32) : int(prec), Z, m, step));
     pt.mark();
     ++np;
     PLU_CUDA(c, launch_colnorm2(m, l, Z, m, cn, c->stream));
@@ -601,10 +630,111 @@ plu_status plu_powerlu_fp(plu_ctx* c, const plu_matrix* A, double eps, int b, in
 plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed, plu_prec prec,
                           int32_t* p, int32_t* q, double* L, int64_t ldL, double* U, int64_t ldU,
                           plu_report* rep) {
-    (void)A; (void)k; (void)seed; (void)prec; (void)p; (void)q; (void)L; (void)ldL; (void)U;
-    (void)ldU; (void)rep;
     PLU_TRY(bind(c));
-    return fail(c, PLU_EUNSUPPORTED, "single-pass LU is not built yet");
+    PLU_TRY(check_matrix(c, A));
+    PLU_TRY(check_prec(c, prec, A));
+    if (prec == PLU_BF16 || prec == PLU_FP8_E4M3)
+        return fail(c, PLU_EUNSUPPORTED,
+                    "single pass: a quantized copy would need its own read of A; use TF32");
+    const int64_t m = A->m, n = A->n;
+    const int64_t mn = m < n ? m : n;
+    if (k < 1 || k >= mn) return fail(c, PLU_EINVAL, "need 1 <= k < min(m, n)");
+    if (k > 2048) return fail(c, PLU_EINVAL, "k > 2048 is not supported");
+    if (!p || !q || !L || !U || ldL < m || ldU < k) return fail(c, PLU_EINVAL, "bad outputs");
+    const int64_t es = A->dtype == PLU_F32 ? 4 : 8;
+    // column panels small enough to stay in L2 between their two products
+    int64_t wc = (int64_t(48) << 20) / (m * es) / 128 * 128;
+    if (wc < 128) wc = 128;
+    if (wc > n) wc = n;
+    const size_t dk = size_t(k) * sizeof(double);
+    Layout lay;
+    const size_t oOm = lay.add(size_t(m) * dk), oH = lay.add(size_t(m) * dk);
+    const size_t oG = lay.add(size_t(n) * dk), oQ = lay.add(size_t(n) * dk);
+    const size_t oW = lay.add(size_t(n) * dk), oL1 = lay.add(size_t(m) * dk);
+    const size_t oR = lay.add(size_t(k) * dk), oRi = lay.add(size_t(k) * dk);
+    const size_t oU1T = lay.add(size_t(k) * dk), oU2T = lay.add(size_t(k) * dk);
+    size_t step = pass_ws(wc, k, m, prec, c->num_sms);
+    size_t t = pass_ws(m, k, wc, prec, c->num_sms);
+    if (t > step) step = t;
+    t = panel_scratch_bytes(m > n ? m : n, k);
+    if (t > step) step = t;
+    t = qr_scratch_bytes(n, k, c->num_sms);
+    if (t > step) step = t;
+    const size_t oStep = lay.add(step);
+    size_t tp = gemm_f64_partials_bytes(n, k, k, c->num_sms);
+    t = gemm_f64_partials_bytes(m, k, k, c->num_sms);
+    if (t > tp) tp = t;
+    const size_t oTp = lay.add(tp);
+    const size_t oInfo = lay.add(2 * sizeof(int32_t));
+    PLU_TRY(ensure_ws(c, lay.total + 256));
+    char* ws = c->ws;
+    double* Om = reinterpret_cast<double*>(ws + oOm);
+    double* H = reinterpret_cast<double*>(ws + oH);
+    double* G = reinterpret_cast<double*>(ws + oG);
+    double* Qb = reinterpret_cast<double*>(ws + oQ);
+    double* Wb = reinterpret_cast<double*>(ws + oW);
+    double* L1 = reinterpret_cast<double*>(ws + oL1);
+    double* R = reinterpret_cast<double*>(ws + oR);
+    double* Rinv = reinterpret_cast<double*>(ws + oRi);
+    double* U1T = reinterpret_cast<double*>(ws + oU1T);
+    double* U2T = reinterpret_cast<double*>(ws + oU2T);
+    char* stepp = ws + oStep;
+    void* tpp = ws + oTp;
+    int32_t* info = reinterpret_cast<int32_t*>(ws + oInfo);
+    const long long launches0 = g_launches;
+    PassTimer pt(c, rep != nullptr);
+    if (rep) PLU_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+    // Omega (m x k), Alg. singlepasslu step 1
+    PLU_CUDA(c, launch_gaussian(m, k, seed, kStreamOmegaSP, Om, m, c->stream));
+    // G = A^T Omega and H = A G in one sweep over the columns of A (Sec. 5
+    // remark): per column panel, G(panel, :) = A(:, panel)^T Omega, then
+    // H += A(:, panel) G(panel, :) while the panel is still in L2
+    pt.mark();
+    for (int64_t j0 = 0; j0 < n; j0 += wc) {
+        const int64_t w = (n - j0) < wc ? (n - j0) : wc;
+        plu_matrix Ap = *A;
+        Ap.n = w;
+        Ap.data = static_cast<const char*>(A->data) + size_t(j0) * size_t(A->ld) * size_t(es);
+        PLU_TRY(do_pass(c, &Ap, 1, Om, m, k, prec, G + j0, n, stepp));
+        PLU_TRY(do_pass(c, &Ap, 0, G + j0, n, k, prec, H, m, stepp, nullptr, j0 > 0 ? 1 : 0));
+    }
+    pt.mark();
+    // [L1, U1, P] = lu(H)
+    PLU_CUDA(c, launch_panel_lu(m, k, H, m, 1, p, L1, m, 0, U1T, k, 1, info, stepp, c->d_status,
+                                c->spin_budget, c->num_sms, c->stream));
+    // G^{dagger T} = G (G^T G)^{-1} = Q R^{-T} with G = Q R (CholeskyQR2)
+    PLU_CUDA(c, cudaMemcpyAsync(Qb, G, size_t(n) * dk, cudaMemcpyDeviceToDevice, c->stream));
+    PLU_CUDA(c, launch_cholqr2(n, k, Qb, n, R, k, stepp, c->d_status, c->num_sms, c->stream));
+    PLU_CUDA(c, launch_trinv_upper(k, R, Rinv, c->stream));
+    PLU_CUDA(c, launch_gemm_f64(0, 1, n, k, k, Qb, n, Rinv, k, Wb, n, tpp, c->num_sms, c->stream));
+    // M = G^{dagger T} U1^T, [L2, U2, Q] = lu(M), U = L2^T
+    PLU_CUDA(c, launch_gemm_f64(0, 0, n, k, k, Wb, n, U1T, k, G, n, tpp, c->num_sms, c->stream));
+    PLU_CUDA(c, launch_panel_lu(n, k, G, n, 1, q, U, ldU, 1, U2T, k, 1, info + 1, stepp,
+                                c->d_status, c->spin_budget, c->num_sms, c->stream));
+    // L = L1 U2^T
+    PLU_CUDA(c, launch_gemm_f64(0, 0, m, k, k, L1, m, U2T, k, L, ldL, tpp, c->num_sms, c->stream));
+    if (rep) {
+        PLU_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+        int32_t hinfo[2] = {0, 0};
+        PLU_CUDA(c, cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, c->stream));
+        PLU_CUDA(c, cudaStreamSynchronize(c->stream));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+        memset(rep, 0, sizeof(*rep));
+        rep->ms_total = ms;
+        rep->ms_passes = pt.pairs_ms();
+        rep->passes = 1;
+        rep->rank = k;
+        rep->indicator = -1.0;
+        rep->normA2 = -1.0;
+        rep->info1 = hinfo[0];
+        rep->info2 = hinfo[1];
+        const double mnd = double(m) * double(n);
+        rep->flops_passes = 4.0 * mnd * k;
+        rep->bytes_passes = mnd * double(es) + double(m + n) * k * 8.0;
+        rep->launches = int32_t(g_launches - launches0);
+    }
+    return finish(c);
 }
 
 }  // extern "C"

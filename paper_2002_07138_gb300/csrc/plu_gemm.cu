@@ -24,7 +24,7 @@ template <typename T> __device__ __forceinline__ T to_acc(float x) { return T(x)
 template <typename TA, typename TB, typename TC, bool TRANSA, bool TRANSB>
 __global__ void __launch_bounds__(NT)
 k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t lda,
-            const TB* __restrict__ B, int64_t ldb, TC* __restrict__ P, int64_t kchunk) {
+            const TB* __restrict__ B, int64_t ldb, TC* __restrict__ P, int64_t kchunk, int tri) {
     __shared__ TC As[2][BK][BM + 1];
     __shared__ TC Bs[2][BK][BN + 1];
     const int t = threadIdx.x;
@@ -32,7 +32,12 @@ k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t l
     const int64_t i0 = int64_t(blockIdx.x) * BM;
     const int64_t j0 = int64_t(blockIdx.y) * BN;
     const int64_t kbeg = int64_t(blockIdx.z) * kchunk;
-    const int64_t kend = min(K, kbeg + kchunk);
+    int64_t kend = min(K, kbeg + kchunk);
+    // tri 1: only the upper triangle of C is wanted (tiles wholly below the
+    // diagonal write zeros); tri 2: op(B) is upper triangular (rows k > j of
+    // column j are zero, so the reduction stops at the tile's last column)
+    if (tri == 1 && i0 >= j0 + BN) kend = kbeg;
+    if (tri == 2 && kend > j0 + BN) kend = j0 + BN;
 
     TC ra[4], rb[4];
     auto load_a = [&](int64_t k0) {
@@ -124,14 +129,14 @@ k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t l
 // C(i, j) = sum_z P[z](i, j), z in increasing order, in FP64.
 template <typename TC>
 __global__ void k_reduce_splits(int64_t M, int64_t N, int splits, const TC* __restrict__ P,
-                                double* __restrict__ C, int64_t ldc) {
+                                double* __restrict__ C, int64_t ldc, int accum) {
     const int64_t total = M * N;
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
         double sum = 0.0;
         for (int z = 0; z < splits; ++z) sum += double(P[int64_t(z) * total + e]);
         const int64_t i = e % M, j = e / M;
-        C[i + j * ldc] = sum;
+        C[i + j * ldc] = accum ? C[i + j * ldc] + sum : sum;
     }
 }
 
@@ -167,18 +172,19 @@ int grid_1d(int64_t work, int num_sms) {
 template <typename TA, typename TB, typename TC, bool TA_T, bool TB_T>
 cudaError_t run(int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda, const TB* B,
                 int64_t ldb, double* C, int64_t ldc, void* partials, int num_sms,
-                cudaStream_t s) {
+                cudaStream_t s, int tri = 0, int accum = 0) {
     const int splits = choose_splits(M, N, K, num_sms);
     int64_t kchunk = (K + splits - 1) / splits;
     kchunk = (kchunk + BK - 1) / BK * BK;
     dim3 grid(unsigned((M + BM - 1) / BM), unsigned((N + BN - 1) / BN), unsigned(splits));
     TC* P = static_cast<TC*>(partials);
     count_launch();
-    k_gemm_simt<TA, TB, TC, TA_T, TB_T><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, P, kchunk);
+    k_gemm_simt<TA, TB, TC, TA_T, TB_T><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, P, kchunk,
+                                                           tri);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     count_launch();
-    k_reduce_splits<TC><<<grid_1d(M * N, num_sms), 256, 0, s>>>(M, N, splits, P, C, ldc);
+    k_reduce_splits<TC><<<grid_1d(M * N, num_sms), 256, 0, s>>>(M, N, splits, P, C, ldc, accum);
     return cudaGetLastError();
 }
 
@@ -197,7 +203,7 @@ size_t gemm_f64_partials_bytes(int64_t M, int64_t N, int64_t K, int num_sms) {
 cudaError_t launch_gemm_simt(int trans, int64_t M, int64_t N, int64_t K, const void* A,
                              int dtype, int64_t lda, const double* B, int64_t ldb,
                              double* C, int64_t ldc, int prec, void* partials,
-                             float* b32_scratch, int num_sms, cudaStream_t s) {
+                             float* b32_scratch, int num_sms, cudaStream_t s, int accum) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (prec == PLU_FP32) {
         count_launch();
@@ -206,21 +212,21 @@ cudaError_t launch_gemm_simt(int trans, int64_t M, int64_t N, int64_t K, const v
         if (e != cudaSuccess) return e;
         if (dtype == PLU_F32) {
             const float* Af = static_cast<const float*>(A);
-            return trans ? run<float, float, float, true, false>(M, N, K, Af, lda, b32_scratch, K, C, ldc, partials, num_sms, s)
-                         : run<float, float, float, false, false>(M, N, K, Af, lda, b32_scratch, K, C, ldc, partials, num_sms, s);
+            return trans ? run<float, float, float, true, false>(M, N, K, Af, lda, b32_scratch, K, C, ldc, partials, num_sms, s, 0, accum)
+                         : run<float, float, float, false, false>(M, N, K, Af, lda, b32_scratch, K, C, ldc, partials, num_sms, s, 0, accum);
         }
         const double* Ad = static_cast<const double*>(A);
-        return trans ? run<double, float, float, true, false>(M, N, K, Ad, lda, b32_scratch, K, C, ldc, partials, num_sms, s)
-                     : run<double, float, float, false, false>(M, N, K, Ad, lda, b32_scratch, K, C, ldc, partials, num_sms, s);
+        return trans ? run<double, float, float, true, false>(M, N, K, Ad, lda, b32_scratch, K, C, ldc, partials, num_sms, s, 0, accum)
+                     : run<double, float, float, false, false>(M, N, K, Ad, lda, b32_scratch, K, C, ldc, partials, num_sms, s, 0, accum);
     }
     if (dtype == PLU_F32) {
         const float* Af = static_cast<const float*>(A);
-        return trans ? run<float, double, double, true, false>(M, N, K, Af, lda, B, ldb, C, ldc, partials, num_sms, s)
-                     : run<float, double, double, false, false>(M, N, K, Af, lda, B, ldb, C, ldc, partials, num_sms, s);
+        return trans ? run<float, double, double, true, false>(M, N, K, Af, lda, B, ldb, C, ldc, partials, num_sms, s, 0, accum)
+                     : run<float, double, double, false, false>(M, N, K, Af, lda, B, ldb, C, ldc, partials, num_sms, s, 0, accum);
     }
     const double* Ad = static_cast<const double*>(A);
-    return trans ? run<double, double, double, true, false>(M, N, K, Ad, lda, B, ldb, C, ldc, partials, num_sms, s)
-                 : run<double, double, double, false, false>(M, N, K, Ad, lda, B, ldb, C, ldc, partials, num_sms, s);
+    return trans ? run<double, double, double, true, false>(M, N, K, Ad, lda, B, ldb, C, ldc, partials, num_sms, s, 0, accum)
+                 : run<double, double, double, false, false>(M, N, K, Ad, lda, B, ldb, C, ldc, partials, num_sms, s, 0, accum);
 }
 
 cudaError_t launch_gemm_f64(int transA, int transB, int64_t M, int64_t N, int64_t K,
@@ -234,6 +240,17 @@ cudaError_t launch_gemm_f64(int transA, int transB, int64_t M, int64_t N, int64_
     }
     return transB ? run<double, double, double, false, true>(M, N, K, A, lda, B, ldb, C, ldc, partials, num_sms, s)
                   : run<double, double, double, false, false>(M, N, K, A, lda, B, ldb, C, ldc, partials, num_sms, s);
+}
+
+cudaError_t launch_gemm_f64_tri(int transA, int tri, int64_t M, int64_t N, int64_t K,
+                                const double* A, int64_t lda, const double* B, int64_t ldb,
+                                double* C, int64_t ldc, void* partials, int num_sms,
+                                cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    return transA ? run<double, double, double, true, false>(M, N, K, A, lda, B, ldb, C, ldc,
+                                                             partials, num_sms, s, tri)
+                  : run<double, double, double, false, false>(M, N, K, A, lda, B, ldb, C, ldc,
+                                                              partials, num_sms, s, tri);
 }
 
 }  // namespace plu

@@ -24,6 +24,54 @@ inline void count_launch(long long n = 1) { g_launches += n; }
 // Largest grid of the cooperative kernels (one candidate slot per CTA).
 constexpr int kMaxGrid = 1024;
 
+// ------------------------------------------------ device-side sync helpers
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+    return *reinterpret_cast<const volatile int*>(p);
+}
+
+// Grid-wide barrier over co-resident CTAs (cooperative launch) on a counter
+// that only grows: the k-th barrier of a launch waits for k * gridDim.x
+// arrivals.  The spin is bounded by `budget` polls; returns false in every
+// thread of the CTA when this CTA gave up (it then sets *status) or another
+// CTA reported an error.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int* status,
+                                             int64_t budget) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int good = 1;
+        int64_t spins = 0;
+        while (ld_acquire_u32(bar) < target) {
+            if (ld_volatile_i32(status) != DEV_OK) { good = 0; break; }
+            if (++spins > budget) {
+                atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+                good = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+#endif
+
+
 // Workspace carved out of the context's device buffer.
 struct Workspace {
     char* base = nullptr;
@@ -50,7 +98,8 @@ size_t gemm_partials_bytes(int64_t M, int64_t N, int64_t K, int prec, int num_sm
 cudaError_t launch_gemm_simt(int trans, int64_t M, int64_t N, int64_t K, const void* A,
                              int dtype, int64_t lda, const double* B, int64_t ldb,
                              double* C, int64_t ldc, int prec, void* partials,
-                             float* b32_scratch, int num_sms, cudaStream_t s);
+                             float* b32_scratch, int num_sms, cudaStream_t s, int accum = 0);
+// accum != 0: C += op(A) B instead of C = op(A) B.
 // FP64 GEMM with transposed-B option for the small products of the tail:
 // C = A * op(B), op(B) = B (K x N) or B^T (B is N x K).
 cudaError_t launch_gemm_f64(int transA, int transB, int64_t M, int64_t N, int64_t K,
@@ -58,6 +107,13 @@ cudaError_t launch_gemm_f64(int transA, int transB, int64_t M, int64_t N, int64_
                             double* C, int64_t ldc, void* partials, int num_sms,
                             cudaStream_t s);
 size_t gemm_f64_partials_bytes(int64_t M, int64_t N, int64_t K, int num_sms);
+// As launch_gemm_f64 (no B transpose) with a triangular shortcut: tri 1 computes
+// only the upper triangle of C (the rest is zero), tri 2 takes op(B) upper
+// triangular.
+cudaError_t launch_gemm_f64_tri(int transA, int tri, int64_t M, int64_t N, int64_t K,
+                                const double* A, int64_t lda, const double* B, int64_t ldb,
+                                double* C, int64_t ldc, void* partials, int num_sms,
+                                cudaStream_t s);
 
 // ----------------------------------------------- tensor-core passes (TF32)
 // Y (FP64) = A X (trans 0) or A^T X (trans 1) with FP32 A (m x n, lda) on
@@ -68,7 +124,24 @@ bool tc_supported(int64_t M, int64_t K, int cols, const void* A, int64_t lda, in
 size_t tc_scratch_bytes(int64_t M, int64_t K, int cols, int num_sms);
 cudaError_t launch_tc_pass(int trans, int64_t m, int64_t n, const float* A, int64_t lda,
                            const double* X, int64_t ldx, int cols, double* Y, int64_t ldy,
-                           void* scratch, int* dev_status, int num_sms, cudaStream_t s);
+                           void* scratch, int* dev_status, int num_sms, cudaStream_t s,
+                           int accum = 0);
+// Quantized copy of A for the BF16 / FP8-E4M3 passes: column-major, ld a
+// multiple of 16 elements; FP8 carries rank-1 tile scales s_r (per 128 rows)
+// and s_c (per 128 columns) with A(i, j) ~= Aq(i, j) s_r[i/128] s_c[j/128].
+struct QuantA {
+    const void* data = nullptr;
+    int64_t ld = 0, m = 0, n = 0;
+    int prec = 0;
+    const float* s_r = nullptr;
+    const float* s_c = nullptr;
+};
+size_t tc_quant_bytes(int64_t m, int64_t n, int prec);
+cudaError_t launch_tc_quantize(int prec, const float* A, int64_t m, int64_t n, int64_t lda,
+                               void* qbuf, QuantA* out, int num_sms, cudaStream_t s);
+cudaError_t launch_tc_pass_q(int trans, const QuantA& q, const double* X, int64_t ldx, int cols,
+                             double* Y, int64_t ldy, void* scratch, int* dev_status, int num_sms,
+                             cudaStream_t s, int accum = 0);
 
 // ------------------------------------------------------- panel LU (a3, a8)
 struct PanelScratch;   // defined in plu_panel.cu
@@ -88,6 +161,9 @@ size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms);
 cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, double* R,
                            int64_t ldR, void* scratch, int* dev_status, int num_sms,
                            cudaStream_t s);
+
+// Rinv = R^{-1} for an upper triangular n x n R (ld n); Rinv is upper triangular.
+cudaError_t launch_trinv_upper(int n, const double* R, double* Rinv, cudaStream_t s);
 
 // -------------------------------------------------------- rank and norms
 size_t norm2_scratch_bytes(int num_sms);

@@ -26,9 +26,11 @@
 // Blocked variant (used whenever a CTA's rows fit in shared memory): the
 // columns are taken NB = 32 at a time.  Each CTA keeps its rows of the
 // current NB-column block in shared memory, so a column step touches no
-// global memory except the candidate slots: the winning candidate publishes
-// its whole NB-wide block row with its slot, every CTA copies it after the
-// barrier and eliminates in shared memory.  After the block, every CTA forms
+// global memory except the candidate slots: each CTA publishes its candidate
+// with its whole NB-wide block row and a step tag written last (release);
+// every CTA acquire-polls all tags of the step (bounded), picks the winner and
+// copies its block row, then eliminates in shared memory.  The tags replace
+// the grid barrier: a CTA tags step j only after all its earlier writes.  After the block, every CTA forms
 // U12 = L11^{-1} A12 for the block's pivot rows (forward substitution) and
 // applies the FP64 trailing update X(:, J2) -= L(:, J1) U12 to its own rows.
 // The U rows go to a separate buffer, so no CTA overwrites data that
@@ -85,43 +87,6 @@ __device__ __forceinline__ Cand warp_best(Cand c) {
         if (better(o, c)) c = o;
     }
     return c;
-}
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ int ld_volatile_i32(const int* p) {
-    return *reinterpret_cast<const volatile int*>(p);
-}
-
-// Grid-wide barrier over co-resident CTAs with a bounded spin.  Returns false
-// (in every thread of the CTA) when the barrier failed: this CTA ran out of
-// budget (and set *status) or another CTA reported an error.
-__device__ bool grid_barrier(unsigned* bar, unsigned target, int* status, int64_t budget) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bar, 1u);
-        int good = 1;
-        int64_t spins = 0;
-        while (ld_acquire_u32(bar) < target) {
-            if (ld_volatile_i32(status) != DEV_OK) { good = 0; break; }
-            if (++spins > budget) {
-                atomicCAS(status, DEV_OK, DEV_TIMEOUT);
-                good = 0;
-                break;
-            }
-            __nanosleep(64);
-        }
-        __threadfence();
-        ok = good;
-    }
-    __syncthreads();
-    return ok != 0;
 }
 
 __device__ Cand block_best(Cand c, Cand* red) {
@@ -228,11 +193,6 @@ k_panel_lu(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
 constexpr int NB = 32;      // columns per block
 constexpr int UC = 128;     // trailing columns per U12 chunk
 
-__device__ __forceinline__ bool panel_barrier(PanelScratch* ps, unsigned target, int* status,
-                                              int64_t budget) {
-    return grid_barrier(&ps->barrier, target, status, budget);
-}
-
 // smem: P[NB][per] | U12[NB][UC] | PR[NB][NB] | pos_s[per] | piv_s[per] | prow_id[NB]
 __global__ void __launch_bounds__(NT)
 k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
@@ -250,6 +210,8 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
     __shared__ Cand piv;
     __shared__ int win_slot;
     __shared__ int nan_seen;
+    __shared__ int poll_ok;
+    __shared__ int red_slot[NT / 32];
 
     const int nb = gridDim.x;
     const int t = threadIdx.x;
@@ -257,7 +219,8 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
     const int64_t r1 = min(rows, r0 + per);
     const int R = int(r1 > r0 ? r1 - r0 : 0);
     const int steps = int(rows < int64_t(cols) ? rows : int64_t(cols));
-    const int slot_w = NB + 2;
+    // slot: [0] |x|, [1] (pos, row), [2] step tag (written last), [3..] block row
+    const int slot_w = NB + 3;
 
     for (int r = t; r < R; r += NT) {
         pos_s[r] = int(r0 + r);
@@ -292,13 +255,33 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
                 pr.y = cb.row;
                 reinterpret_cast<int2*>(myslot + 1)[0] = pr;
             }
-            if (t < nbk && cb.row >= 0) myslot[2 + t] = P[t * per + int(cb.row - r0)];
-            if (!panel_barrier(ps, unsigned(j + 1) * unsigned(nb), status, budget)) return;
-            if (t < 32) {
+            if (t < nbk && cb.row >= 0) myslot[3 + t] = P[t * per + int(cb.row - r0)];
+            // publish: every write of this CTA so far (slot, X, trailing update)
+            // happens before the tag
+            __syncthreads();
+            if (t == 0) {
+                __threadfence();
+                st_release_u32(reinterpret_cast<unsigned*>(myslot + 2), unsigned(j + 1));
+            }
+            {
+                // every thread polls its own slots, so all tags are read at once
                 Cand g{-1.0, INT_MAX, -1};
                 int gs = -1;
-                for (int b = t; b < nb; b += 32) {
+                int ok = 1;
+                for (int b = t; b < nb; b += NT) {
                     const double* src = slots + (int64_t(j & 1) * nb + b) * slot_w;
+                    const unsigned* tag = reinterpret_cast<const unsigned*>(src + 2);
+                    int64_t spins = 0;
+                    while (ld_acquire_u32(tag) != unsigned(j + 1)) {
+                        if (ld_volatile_i32(status) != DEV_OK) { ok = 0; break; }
+                        if (++spins > budget) {
+                            atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                    if (!ok) break;
                     Cand c;
                     c.v = __ldcg(src);
                     const int2 pr = __ldcg(reinterpret_cast<const int2*>(src + 1));
@@ -306,25 +289,44 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
                     c.row = pr.y;
                     if (better(c, g)) { g = c; gs = b; }
                 }
+                // block reduction of (candidate, slot) under the pivot order
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) {
                     const Cand o = shfl_cand(g, off);
                     const int os = __shfl_xor_sync(0xffffffffu, gs, off);
                     if (better(o, g)) { g = o; gs = os; }
                 }
-                if (t == 0) {
-                    piv = g;
-                    win_slot = gs;
+                const int lane = t & 31, wid = t >> 5;
+                if (lane == 0) {
+                    red[wid] = g;
+                    red_slot[wid] = gs;
+                }
+                ok = __syncthreads_and(ok);
+                if (wid == 0) {
+                    Cand x = (lane < NT / 32) ? red[lane] : Cand{-1.0, INT_MAX, -1};
+                    int xs = (lane < NT / 32) ? red_slot[lane] : -1;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const Cand o = shfl_cand(x, off);
+                        const int os = __shfl_xor_sync(0xffffffffu, xs, off);
+                        if (better(o, x)) { x = o; xs = os; }
+                    }
+                    if (lane == 0) {
+                        piv = x;
+                        win_slot = xs;
+                        poll_ok = ok;
+                    }
                 }
             }
             __syncthreads();
+            if (!poll_ok) return;
             const Cand pv = piv;
             if (pv.row < 0) {
                 if (blockIdx.x == 0 && t == 0) atomicCAS(status, DEV_OK, DEV_NUMERIC);
                 return;
             }
             const double* wsrc = slots + (int64_t(j & 1) * nb + win_slot) * slot_w;
-            if (t < nbk) PR[sc * NB + t] = __ldcg(wsrc + 2 + t);
+            if (t < nbk) PR[sc * NB + t] = __ldcg(wsrc + 3 + t);
             if (t == 0) prow_id[sc] = pv.row;
             for (int r = t; r < R; r += NT) {
                 if (r0 + r == pv.row) {
@@ -453,7 +455,7 @@ __global__ void k_panel_finalize(int64_t rows, int cols, double* __restrict__ X,
 
 size_t panel_scratch_bytes(int64_t rows, int cols) {
     const size_t head = (sizeof(PanelScratch) + 255) & ~size_t(255);
-    const size_t slots = size_t(2) * kMaxGrid * (NB + 2) * sizeof(double);
+    const size_t slots = size_t(2) * kMaxGrid * (NB + 3) * sizeof(double);
     const int64_t steps = rows < cols ? rows : cols;
     const size_t ubuf = size_t(steps) * size_t(cols) * sizeof(double);
     return head + slots + 256 + ubuf + 256 + 2 * size_t(rows) * sizeof(int) + 256;
@@ -470,7 +472,7 @@ cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int 
     PanelScratch* ps = reinterpret_cast<PanelScratch*>(base);
     size_t off = (sizeof(PanelScratch) + 255) & ~size_t(255);
     double* slots = reinterpret_cast<double*>(base + off);
-    off += (size_t(2) * kMaxGrid * (NB + 2) * sizeof(double) + 255) & ~size_t(255);
+    off += (size_t(2) * kMaxGrid * (NB + 3) * sizeof(double) + 255) & ~size_t(255);
     double* Ubuf = reinterpret_cast<double*>(base + off);
     const int64_t steps = rows < cols ? rows : cols;
     off += (size_t(steps) * size_t(cols) * sizeof(double) + 255) & ~size_t(255);
@@ -485,6 +487,9 @@ cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int 
     if (nb < 1) nb = 1;
     int64_t per = (rows + nb - 1) / nb;
     nb = (rows + per - 1) / per;
+    // step tags of the candidate slots start below every step number
+    e = cudaMemsetAsync(slots, 0, size_t(2) * nb * (NB + 3) * sizeof(double), s);
+    if (e != cudaSuccess) return e;
     int64_t rows_ = rows;
     int cols_ = cols;
     int64_t ldx_ = ldx;

@@ -77,6 +77,121 @@ k_cholesky(int n, double* __restrict__ W, const double* __restrict__ Wsave, int6
     }
 }
 
+// Blocked upper Cholesky W = R^T R over a cooperative grid (n x n, ld n,
+// upper triangle read, R written over it, strictly lower part zeroed).
+// Per block of CB columns: CTA 0 factors the diagonal block in shared memory,
+// grid barrier; every thread of the grid solves R11^T R12 = W12 for some
+// trailing columns, barrier; the grid applies W22 -= R12^T R12 (upper part),
+// barrier.  On a non-positive pivot in the first attempt (shift_mode 1) all
+// CTAs restart from Wsave with the shifted-CholeskyQR diagonal shift.
+constexpr int CB = 32;
+constexpr int CBT = 256;
+
+struct CholCtl {
+    unsigned barrier;
+    int broke;
+};
+
+__global__ void __launch_bounds__(CBT)
+k_cholesky_coop(int n, double* __restrict__ W, const double* __restrict__ Wsave, int64_t rows,
+                int shift_mode, CholCtl* __restrict__ ctl, int* __restrict__ status,
+                int64_t budget) {
+    __shared__ double D[CB][CB + 1];
+    __shared__ double rjj;
+    const int t = threadIdx.x;
+    const int nb = gridDim.x;
+    const int gtid = blockIdx.x * CBT + t;
+    const int gthreads = nb * CBT;
+    unsigned nbar = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (attempt == 1) {
+            double tr = 0.0;
+            for (int i = 0; i < n; ++i) tr += Wsave[i + int64_t(i) * n];
+            const double shift = 11.0 * (double(rows) * n + double(n) * (n + 1)) *
+                                 1.1102230246251565e-16 * tr;
+            for (int64_t e = gtid; e < int64_t(n) * n; e += gthreads) {
+                const int a = int(e % n), c = int(e / n);
+                W[e] = Wsave[e] + (a == c ? shift : 0.0);
+            }
+            if (!grid_barrier(&ctl->barrier, ++nbar * nb, status, budget)) return;
+        }
+        bool broke = false;
+        for (int kb = 0; kb < n; kb += CB) {
+            const int b = min(CB, n - kb);
+            if (blockIdx.x == 0) {
+                for (int e = t; e < b * b; e += CBT) {
+                    const int a = e % b, c = e / b;
+                    D[a][c] = __ldcg(&W[(kb + a) + int64_t(kb + c) * n]);
+                }
+                __syncthreads();
+                int bad = 0;
+                for (int j = 0; j < b; ++j) {
+                    if (t == 0) {
+                        const double d = D[j][j];
+                        rjj = d > 0.0 ? sqrt(d) : 0.0;
+                        D[j][j] = rjj;
+                    }
+                    __syncthreads();
+                    if (rjj == 0.0) { bad = 1; break; }
+                    if (t > j && t < b) D[j][t] /= rjj;
+                    __syncthreads();
+                    for (int e = t; e < b * b; e += CBT) {
+                        const int a = e % b, c = e / b;
+                        if (a > j && a <= c) D[a][c] -= D[j][a] * D[j][c];
+                    }
+                    __syncthreads();
+                }
+                for (int e = t; e < b * b; e += CBT) {
+                    const int a = e % b, c = e / b;
+                    if (a <= c) W[(kb + a) + int64_t(kb + c) * n] = D[a][c];
+                }
+                if (t == 0) ctl->broke = bad;
+            }
+            if (!grid_barrier(&ctl->barrier, ++nbar * nb, status, budget)) return;
+            if (ld_volatile_i32(&ctl->broke)) { broke = true; break; }
+            // R12(:, c) = R11^{-T} W12(:, c), one column per thread
+            for (int c = kb + b + gtid; c < n; c += gthreads) {
+                double x[CB];
+#pragma unroll
+                for (int i = 0; i < CB; ++i) {
+                    if (i < b) {
+                        double acc = __ldcg(&W[(kb + i) + int64_t(c) * n]);
+                        for (int u = 0; u < i; ++u)
+                            acc = fma(-__ldcg(&W[(kb + u) + int64_t(kb + i) * n]), x[u], acc);
+                        x[i] = acc / __ldcg(&W[(kb + i) + int64_t(kb + i) * n]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < CB; ++i)
+                    if (i < b) W[(kb + i) + int64_t(c) * n] = x[i];
+            }
+            if (!grid_barrier(&ctl->barrier, ++nbar * nb, status, budget)) return;
+            // W22 -= R12^T R12 (upper triangle)
+            const int m = n - kb - b;
+            for (int64_t e = gtid; e < int64_t(m) * m; e += gthreads) {
+                const int a = kb + b + int(e % m), c = kb + b + int(e / m);
+                if (a > c) continue;
+                double acc = 0.0;
+                for (int u = 0; u < b; ++u)
+                    acc = fma(__ldcg(&W[(kb + u) + int64_t(a) * n]),
+                              __ldcg(&W[(kb + u) + int64_t(c) * n]), acc);
+                W[a + int64_t(c) * n] -= acc;
+            }
+            if (!grid_barrier(&ctl->barrier, ++nbar * nb, status, budget)) return;
+        }
+        if (!broke) break;
+        if (!shift_mode || attempt == 1) {
+            if (gtid == 0) atomicCAS(status, DEV_OK, DEV_NUMERIC);
+            break;
+        }
+        if (!grid_barrier(&ctl->barrier, ++nbar * nb, status, budget)) return;
+    }
+    for (int64_t e = gtid; e < int64_t(n) * n; e += gthreads) {
+        const int a = int(e % n), c = int(e / n);
+        if (a > c) W[e] = 0.0;
+    }
+}
+
 // Rinv(:, j) = R^{-1} e_j for upper triangular R (n x n, ld n); CTA j.
 __global__ void k_trinv_upper(int n, const double* __restrict__ R, double* __restrict__ Rinv) {
     extern __shared__ double x[];
@@ -95,6 +210,14 @@ __global__ void k_trinv_upper(int n, const double* __restrict__ R, double* __res
 }
 
 }  // namespace
+
+cudaError_t launch_trinv_upper(int n, const double* R, double* Rinv, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int tt = n < 256 ? 128 : 256;
+    count_launch();
+    k_trinv_upper<<<n, tt, size_t(n) * sizeof(double), s>>>(n, R, Rinv);
+    return cudaGetLastError();
+}
 
 size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms) {
     const size_t sq = size_t(cols) * cols * sizeof(double);
@@ -119,24 +242,44 @@ cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, doubl
     const size_t p1 = gemm_f64_partials_bytes(cols, cols, rows, num_sms);
     const size_t p2 = gemm_f64_partials_bytes(rows, cols, cols, num_sms);
     void* part = ws.take(p1 > p2 ? p1 : p2);
-    if (!W || !Wsave || !Rinv || !R1 || !Rtmp || !part) return cudaErrorInvalidValue;
+    CholCtl* ctl = static_cast<CholCtl*>(ws.take(sizeof(CholCtl)));
+    if (!W || !Wsave || !Rinv || !R1 || !Rtmp || !part || !ctl) return cudaErrorInvalidValue;
     cudaError_t e;
     for (int pass = 0; pass < 2; ++pass) {
-        e = launch_gemm_f64(1, 0, cols, cols, rows, X, ldx, X, ldx, W, cols, part, num_sms, s);
+        // W = X^T X, upper triangle only (the Cholesky reads nothing else)
+        e = launch_gemm_f64_tri(1, 1, cols, cols, rows, X, ldx, X, ldx, W, cols, part, num_sms, s);
         if (e != cudaSuccess) return e;
         if (pass == 0) {
             e = cudaMemcpyAsync(Wsave, W, sq, cudaMemcpyDeviceToDevice, s);
             if (e != cudaSuccess) return e;
         }
-        count_launch();
-        k_cholesky<<<1, CT, 0, s>>>(cols, W, Wsave, rows, pass == 0 ? 1 : 0, dev_status);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (cols <= 128) {
+            count_launch();
+            k_cholesky<<<1, CT, 0, s>>>(cols, W, Wsave, rows, pass == 0 ? 1 : 0, dev_status);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        } else {
+            e = cudaMemsetAsync(ctl, 0, sizeof(CholCtl), s);
+            if (e != cudaSuccess) return e;
+            int grid = (cols - CB + CBT - 1) / CBT * 4;     // a few CTAs per 256 trailing columns
+            if (grid < 8) grid = 8;
+            if (grid > num_sms) grid = num_sms;
+            int n_ = cols;
+            int shift = pass == 0 ? 1 : 0;
+            int64_t rows_ = rows;
+            int64_t budget = 16LL << 20;
+            void* args[] = {&n_, &W, &Wsave, &rows_, &shift, &ctl, &dev_status, &budget};
+            count_launch();
+            e = cudaLaunchCooperativeKernel((const void*)k_cholesky_coop, dim3(grid), dim3(CBT),
+                                            args, 0, s);
+            if (e != cudaSuccess) return e;
+        }
         const int tt = cols < 256 ? 128 : 256;
         count_launch();
         k_trinv_upper<<<cols, tt, size_t(cols) * sizeof(double), s>>>(cols, W, Rinv);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // X <- X Rinv (the reduction of the partial sums writes X after the product)
-        e = launch_gemm_f64(0, 0, rows, cols, cols, X, ldx, Rinv, cols, X, ldx, part, num_sms, s);
+        e = launch_gemm_f64_tri(0, 2, rows, cols, cols, X, ldx, Rinv, cols, X, ldx, part, num_sms,
+                                s);
         if (e != cudaSuccess) return e;
         if (pass == 0) {
             e = cudaMemcpyAsync(R1, W, sq, cudaMemcpyDeviceToDevice, s);

@@ -53,9 +53,14 @@ __device__ __forceinline__ double ln_unit(double u) {
     }
     const double s = __ddiv_rn(__dsub_rn(f, 1.0), __dadd_rn(f, 1.0));
     const double w = __dmul_rn(s, s);
-    double t = __ddiv_rn(1.0, 25.0);
+    // 1/(2k+1), k = 0..12, as correctly rounded constants (the same values the
+    // division would give)
+    constexpr double inv_odd[13] = {1.0 / 1.0,  1.0 / 3.0,  1.0 / 5.0,  1.0 / 7.0,  1.0 / 9.0,
+                                    1.0 / 11.0, 1.0 / 13.0, 1.0 / 15.0, 1.0 / 17.0, 1.0 / 19.0,
+                                    1.0 / 21.0, 1.0 / 23.0, 1.0 / 25.0};
+    double t = inv_odd[12];
 #pragma unroll
-    for (int k = 11; k >= 0; --k) t = __dadd_rn(__dmul_rn(t, w), __ddiv_rn(1.0, double(2 * k + 1)));
+    for (int k = 11; k >= 0; --k) t = __dadd_rn(__dmul_rn(t, w), inv_odd[k]);
     const double ln2 = 0.69314718055994530942;
     return __dadd_rn(__dmul_rn(double(e), ln2), __dmul_rn(__dmul_rn(2.0, s), t));
 }

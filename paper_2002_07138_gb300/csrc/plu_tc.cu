@@ -31,6 +31,8 @@
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 namespace plu {
 namespace {
@@ -103,6 +105,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// One contiguous global -> shared copy (sizes multiple of 16 bytes).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -121,14 +132,39 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
         : "memory");
 }
 
-__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
+// Operand kinds of the passes: element bytes E, K elements per 128-byte
+// swizzle row = 128 / E, one MMA consumes 32 bytes of K (8, 16, 32 elements).
+enum TcKind { KIND_TF32 = 0, KIND_BF16 = 1, KIND_FP8 = 2 };
+template <int KIND> struct Kind;
+template <> struct Kind<KIND_TF32> { static constexpr int E = 4; static constexpr uint32_t fmt = 2; };
+template <> struct Kind<KIND_BF16> { static constexpr int E = 2; static constexpr uint32_t fmt = 1; };
+template <> struct Kind<KIND_FP8>  { static constexpr int E = 1; static constexpr uint32_t fmt = 0; };
+
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                     uint32_t idesc, uint32_t accumulate) {
+    if constexpr (KIND == KIND_TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else if constexpr (KIND == KIND_BF16) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
 }
 
 // 32 lanes x 32 consecutive 32-bit TMEM columns -> 32 registers per thread.
@@ -159,10 +195,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
-// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, dense.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N, bool a_mn_major) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(a_mn_major) << 15) |
-           (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+// Instruction descriptor: D = F32, A and B of format `fmt` (kind::tf32: TF32 = 2;
+// kind::f16: BF16 = 1; kind::f8f6f4: E4M3 = 0), dense, both K-major, N and M.
+__host__ __device__ constexpr uint32_t idesc_make(uint32_t fmt, int M, int N) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | (uint32_t(N >> 3) << 17) |
+           (uint32_t(M >> 4) << 24);
 }
 
 struct TcParams {
@@ -181,9 +218,9 @@ struct TcParams {
     int* status;
 };
 
-template <bool XPOSE>
+template <bool XPOSE, int KIND>
 __global__ void __launch_bounds__(XPOSE ? TC_THREADS_X : TC_THREADS, 1)
-k_tc_pass(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restrict__ Bt,
           const TcParams P) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[8];
@@ -195,6 +232,9 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     __shared__ uint32_t tmem_holder;
     __shared__ volatile int abort_flag;
 
+    constexpr int E = Kind<KIND>::E;
+    constexpr int BKE = 128 / E;                  // K elements per stage
+    constexpr int MB = 128 / E;                   // M elements per staging box (A X)
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -242,28 +282,28 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                         break;
                     }
                     const int64_t blk = s / P.ksteps;
-                    const int kk = int(s % P.ksteps) * 32;
+                    const int kk = int(s % P.ksteps) * BKE;
                     unsigned char* a_dst = smem + st * stage_bytes;
                     unsigned char* b_dst = a_dst + A_TILE;
                     mbar_arrive_expect_tx(&full_bar[st], uint32_t(A_TILE + P.b_bytes));
                     if (XPOSE) {
                         unsigned char* raw = b_dst + P.b_bytes;
 #pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            tma_load_2d(raw + q * 4096, &mapA, &full_bar[st],
-                                        int(blk * BM + 32 * q), kk);
+                        for (int q = 0; q < E; ++q)
+                            tma_load_2d(raw + q * (128 * BKE), &mapA, &full_bar[st],
+                                        int(blk * BM + MB * q), kk);
                     } else {
                         tma_load_2d(a_dst, &mapA, &full_bar[st], kk, int(blk * BM));
                     }
-                    for (int c = 0; c * P.nchunk < P.npad; ++c)
-                        tma_load_2d(b_dst + c * P.nchunk * 128, &mapB, &full_bar[st], kk,
-                                    c * P.nchunk);
+                    // the small operand's K step, pre-tiled in its shared-memory image
+                    bulk_load(b_dst, Bt + (s % P.ksteps) * int64_t(P.b_bytes), uint32_t(P.b_bytes),
+                              &full_bar[st]);
                 }
             }
         } else if (warp == 1) {
             // ------------------------------------------------------- MMA
             if (lane == 0) {
-                const uint32_t idesc = idesc_tf32(BM, P.nchunk, false);
+                const uint32_t idesc = idesc_make(Kind<KIND>::fmt, BM, P.nchunk);
                 int it = 0, seg = 0;
                 for (int64_t s = s0; s < s1; ++s, ++it) {
                     const bool seg_first = (s == s0) || (s % P.ksteps == 0);
@@ -290,8 +330,8 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                         for (int c = 0; c * P.nchunk < P.npad; ++c) {
                             const uint64_t bd =
                                 smem_desc(b_base + c * P.nchunk * 128 + sub * 32, 16, 1024);
-                            umma_tf32(tmem + uint32_t(c * P.nchunk), ad, bd, idesc,
-                                      (seg_first && sub == 0) ? 0u : 1u);
+                            umma<KIND>(tmem + uint32_t(c * P.nchunk), ad, bd, idesc,
+                                       (seg_first && sub == 0) ? 0u : 1u);
                         }
                     }
                     tc_commit(&empty_bar[st]);
@@ -303,12 +343,13 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             }
         } else if (XPOSE && warp >= 6) {
             // ------------------------------------------------ transposer
-            // thread t owns row m = t of the 128-row tile; staging box q = m/32
-            // holds A(32q.., k) as 32 K-rows of 128 bytes (128-byte swizzle);
+            // thread t owns row m = t of the 128-row tile; staging box q = m / MB
+            // holds A(MB q.., k) as BKE K-rows of 128 bytes (128-byte swizzle);
             // the K-major tile holds row m as 128 bytes, 16-byte chunk c of
-            // K = 4c..4c+3 stored at chunk c ^ (m % 8).
+            // K = c T .. c T + T - 1 (T = 16 / E elements) at chunk c ^ (m % 8).
+            constexpr int T = 16 / E;
             const int m = threadIdx.x - 192;
-            const int q = m >> 5, mm = m & 31;
+            const int q = m / MB, mm = m % MB;
             int it = 0;
             for (int64_t s = s0; s < s1; ++s, ++it) {
                 const int st = it % P.stages;
@@ -317,18 +358,24 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                     break;
                 }
                 unsigned char* kt = smem + st * stage_bytes;
-                const unsigned char* raw = kt + A_TILE + P.b_bytes + q * 4096;
+                const unsigned char* raw = kt + A_TILE + P.b_bytes + q * (128 * BKE);
+                const int src_in_chunk = (mm % T) * E;
 #pragma unroll
-                for (int k4 = 0; k4 < 8; ++k4) {
-                    float v[4];
+                for (int c = 0; c < 8; ++c) {
+                    uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int kr = 4 * k4 + e;
-                        v[e] = *reinterpret_cast<const float*>(
-                            raw + kr * 128 + (((mm >> 2) ^ (kr & 7)) << 4) + ((mm & 3) << 2));
+                    for (int e = 0; e < T; ++e) {
+                        const int kr = c * T + e;
+                        const unsigned char* src =
+                            raw + kr * 128 + (((mm / T) ^ (kr & 7)) << 4) + src_in_chunk;
+                        uint32_t v;
+                        if constexpr (E == 4) v = *reinterpret_cast<const uint32_t*>(src);
+                        else if constexpr (E == 2) v = *reinterpret_cast<const uint16_t*>(src);
+                        else v = *src;
+                        w[(e * E) >> 2] |= v << (((e * E) & 3) * 8);
                     }
-                    *reinterpret_cast<float4*>(kt + m * 128 + ((k4 ^ (m & 7)) << 4)) =
-                        make_float4(v[0], v[1], v[2], v[3]);
+                    *reinterpret_cast<uint4*>(kt + m * 128 + ((c ^ (m & 7)) << 4)) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
@@ -395,7 +442,9 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 // tile, in CTA order, in FP64.
 __global__ void k_tc_reduce(const float* __restrict__ part, int64_t M, int l, int npad,
                             int ksteps, int64_t total, int64_t per, int max_segs, int grid,
-                            double* __restrict__ Y, int64_t ldy) {
+                            double* __restrict__ Y, int64_t ldy,
+                            const float* __restrict__ rowblk_scale,
+                            const float* __restrict__ col_scale, int accum) {
     const int64_t count = M * l;
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < count;
          e += int64_t(gridDim.x) * blockDim.x) {
@@ -411,26 +460,124 @@ __global__ void k_tc_reduce(const float* __restrict__ part, int64_t M, int l, in
             const int64_t seg = blk - cblk0;
             acc += double(part[((c * max_segs + seg) * npad + j) * BM + r]);
         }
-        Y[i + j * ldy] = acc;
+        if (rowblk_scale) acc *= double(rowblk_scale[blk]);
+        if (col_scale) acc *= double(col_scale[j]);
+        Y[i + j * ldy] = accum ? Y[i + j * ldy] + acc : acc;
     }
 }
 
-// X (FP64, K x cols, ldx) -> X32 (FP32, K x npad, ld ldo), zero columns beyond cols,
-// rounded to TF32 (round to nearest, ties away) so the MMA sees rounded values.
-__global__ void k_to_tf32(int64_t K, int cols, int npad, const double* __restrict__ X,
-                          int64_t ldx, float* __restrict__ out, int64_t ldo) {
-    const int64_t total = K * npad;
+// Small operand X (FP64, K x cols, ldx) -> operand type, written as the
+// shared-memory image of each K step: step t holds rows j < npad of 128 bytes
+// (K = t BKE .. t BKE + BKE - 1), 16-byte chunk c of row j stored at chunk
+// c ^ (j % 8) (the 128-byte swizzle), so one bulk copy moves a whole step.
+// Entries beyond cols or K are zero.  TF32: rounded to nearest (ties away),
+// as FP32 bits; BF16: rounded to nearest even; FP8-E4M3: X(k, j) *
+// fold[k / 128] / col_scale[j], saturated.
+template <int KIND>
+__global__ void k_to_operand(int64_t K, int cols, int npad, int ksteps, const double* __restrict__ X,
+                             int64_t ldx, const float* __restrict__ fold,
+                             const float* __restrict__ col_scale, unsigned char* __restrict__ out) {
+    constexpr int E = Kind<KIND>::E;
+    constexpr int BKE = 128 / E;
+    constexpr int T = 16 / E;
+    const int64_t total = int64_t(ksteps) * BKE * npad;
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t i = e % K, j = e / K;
-        float v = 0.f;
-        if (j < cols) {
-            const float f = float(X[i + j * ldx]);
-            uint32_t t;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(f));
-            v = __uint_as_float(t);
+        const int64_t k = e % (int64_t(ksteps) * BKE);
+        const int j = int(e / (int64_t(ksteps) * BKE));
+        const int64_t t = k / BKE;
+        const int kk = int(k % BKE);
+        unsigned char* dst = out + t * int64_t(npad) * 128 + j * 128 +
+                             (((kk / T) ^ (j & 7)) << 4) + (kk % T) * E;
+        const bool live = j < cols && k < K;
+        const double x = live ? X[k + int64_t(j) * ldx] : 0.0;
+        if constexpr (KIND == KIND_TF32) {
+            uint32_t u;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(float(x)));
+            *reinterpret_cast<uint32_t*>(dst) = u;
+        } else if constexpr (KIND == KIND_BF16) {
+            *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(float(x));
+        } else {
+            float v = 0.f;
+            if (live) v = float(x * double(fold[k / 128]) / double(col_scale[j]));
+            *reinterpret_cast<__nv_fp8_storage_t*>(dst) =
+                __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
         }
-        out[i + j * ldo] = v;
+    }
+}
+
+// col_scale[j] = max_k |X(k, j) fold[k/128]| / 448 (1 when the column is zero).
+__global__ void k_fp8_colscale(int64_t K, int cols, const double* __restrict__ X, int64_t ldx,
+                               const float* __restrict__ fold, float* __restrict__ col_scale) {
+    __shared__ double red[256];
+    const int j = blockIdx.x;
+    double mx = 0.0;
+    for (int64_t i = threadIdx.x; i < K; i += 256)
+        mx = fmax(mx, fabs(X[i + int64_t(j) * ldx] * double(fold[i / 128])));
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s2 = 128; s2 > 0; s2 >>= 1) {
+        if (threadIdx.x < s2) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s2]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) col_scale[j] = red[0] > 0.0 ? float(red[0] / 448.0) : 1.f;
+}
+
+// FP32 A -> BF16 copy (column-major, ld ldq), round to nearest even.
+__global__ void k_quant_bf16(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+                             __nv_bfloat16* __restrict__ Aq, int64_t ldq) {
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y)
+        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m;
+             i += int64_t(gridDim.x) * blockDim.x)
+            Aq[i + j * ldq] = __float2bfloat16_rn(A[i + j * lda]);
+}
+
+// amax of every 128 x 128 tile of A (tile (rb, cb) at amax[rb + cb * RB]).
+__global__ void k_tile_amax(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+                            int RB, float* __restrict__ amax) {
+    __shared__ float red[256];
+    const int64_t rb = blockIdx.x, cb = blockIdx.y;
+    float mx = 0.f;
+    for (int e = threadIdx.x; e < 128 * 128; e += 256) {
+        const int64_t i = rb * 128 + (e & 127), j = cb * 128 + (e >> 7);
+        if (i < m && j < n) mx = fmaxf(mx, fabsf(A[i + j * lda]));
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s2 = 128; s2 > 0; s2 >>= 1) {
+        if (threadIdx.x < s2) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + s2]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) amax[rb + cb * RB] = red[0];
+}
+
+// Rank-1 tile scales: s_r[rb] = max_cb amax, s_c[cb] = max_rb amax / s_r[rb] / 448,
+// so |A(i, j)| / (s_r[rb] s_c[cb]) <= 448 in every tile.
+__global__ void k_tile_scales(const float* __restrict__ amax, int RB, int CB,
+                              float* __restrict__ s_r, float* __restrict__ s_c) {
+    for (int rb = threadIdx.x; rb < RB; rb += blockDim.x) {
+        float mx = 0.f;
+        for (int cb = 0; cb < CB; ++cb) mx = fmaxf(mx, amax[rb + cb * RB]);
+        s_r[rb] = mx > 0.f ? mx : 1.f;
+    }
+    __syncthreads();
+    for (int cb = threadIdx.x; cb < CB; cb += blockDim.x) {
+        float mx = 0.f;
+        for (int rb = 0; rb < RB; ++rb) mx = fmaxf(mx, amax[rb + cb * RB] / s_r[rb]);
+        s_c[cb] = mx > 0.f ? mx / 448.f : 1.f;
+    }
+}
+
+// FP32 A -> FP8-E4M3 copy A(i, j) / (s_r[i/128] s_c[j/128]), saturated.
+__global__ void k_quant_fp8(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+                            const float* __restrict__ s_r, const float* __restrict__ s_c,
+                            __nv_fp8_storage_t* __restrict__ Aq, int64_t ldq) {
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
+        const float cs = s_c[j / 128];
+        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m;
+             i += int64_t(gridDim.x) * blockDim.x)
+            Aq[i + j * ldq] = __nv_cvt_float_to_fp8(A[i + j * lda] / (s_r[i / 128] * cs),
+                                                    __NV_SATFINITE, __NV_E4M3);
     }
 }
 
@@ -447,15 +594,15 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-bool make_map_2d(CUtensorMap* map, const void* base, uint64_t dim0, uint64_t dim1,
-                 uint64_t stride1_bytes, uint32_t box0, uint32_t box1) {
+bool make_map_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t dim0,
+                 uint64_t dim1, uint64_t stride1_bytes, uint32_t box0, uint32_t box1) {
     auto enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[2] = {dim0, dim1};
     cuuint64_t strides[1] = {stride1_bytes};
     cuuint32_t box[2] = {box0, box1};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims,
+    CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims,
                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -469,11 +616,12 @@ struct TcPlan {
     int64_t ldx32;
 };
 
-TcPlan plan_tc(int64_t M, int64_t K, int cols, int num_sms, bool xpose) {
+TcPlan plan_tc(int64_t M, int64_t K, int cols, int num_sms, bool xpose, int E = 4) {
     TcPlan p{};
     p.npad = cols <= 256 ? (cols + 15) / 16 * 16 : (cols + 31) / 32 * 32;
     p.nchunk = p.npad <= 256 ? p.npad : p.npad / 2;
-    p.ksteps = int((K + 31) / 32);
+    const int bke = 128 / E;
+    p.ksteps = int((K + bke - 1) / bke);
     p.blocks = (M + BM - 1) / BM;
     p.total = p.blocks * p.ksteps;
     p.grid = num_sms;
@@ -489,7 +637,7 @@ TcPlan plan_tc(int64_t M, int64_t K, int cols, int num_sms, bool xpose) {
     uint32_t tc = 32;
     while (tc < uint32_t(p.npad)) tc <<= 1;
     p.tmem_cols = tc;
-    p.ldx32 = (K + 3) / 4 * 4;
+    p.ldx32 = (K + 15) / 16 * 16;                 // 16-byte strides for every element size
     return p;
 }
 
@@ -499,44 +647,124 @@ bool tc_supported(int64_t M, int64_t K, int cols, const void* A, int64_t lda, in
     if (cols < 1 || cols > 512 || M < 1 || K < 1) return false;
     if ((reinterpret_cast<uintptr_t>(A) & 15) != 0 || (lda % 4) != 0) return false;
     if (M > (int64_t(1) << 31) - 256 || K > (int64_t(1) << 31) - 256) return false;
-    const TcPlan p = plan_tc(M, K, cols, 152, trans == 0);
+    const TcPlan p = plan_tc(M, K, cols, 152, trans == 0, 4);
     return p.stages >= 2 && get_encode() != nullptr;
 }
 
 size_t tc_scratch_bytes(int64_t M, int64_t K, int cols, int num_sms) {
-    const TcPlan p = plan_tc(M, K, cols, num_sms, false);
-    return size_t(p.grid) * p.max_segs * p.npad * BM * sizeof(float) + 256 +
-           size_t(p.ldx32) * p.npad * sizeof(float) + 256;
+    size_t part = 0;
+    for (int E = 1; E <= 4; E *= 2) {                  // the largest over the element sizes
+        const TcPlan p = plan_tc(M, K, cols, num_sms, false, E);
+        const size_t b = size_t(p.grid) * p.max_segs * p.npad * BM * sizeof(float);
+        if (b > part) part = b;
+    }
+    size_t bt = 0;
+    for (int E = 1; E <= 4; E *= 2) {
+        const TcPlan p = plan_tc(M, K, cols, num_sms, false, E);
+        const size_t b = size_t(p.ksteps) * p.npad * 128;
+        if (b > bt) bt = b;
+    }
+    const TcPlan p = plan_tc(M, K, cols, num_sms, false, 4);
+    return part + 256 + bt + 256 + size_t(p.npad) * sizeof(float) + 256;
 }
 
-cudaError_t launch_tc_pass(int trans, int64_t m, int64_t n, const float* A, int64_t lda,
-                           const double* X, int64_t ldx, int cols, double* Y, int64_t ldy,
-                           void* scratch, int* dev_status, int num_sms, cudaStream_t s) {
+size_t tc_quant_bytes(int64_t m, int64_t n, int prec) {
+    const int E = prec == PLU_BF16 ? 2 : 1;
+    const int64_t ldq = (m + 15) / 16 * 16;
+    const int64_t RB = (m + 127) / 128, CB = (n + 127) / 128;
+    return size_t(ldq) * size_t(n) * E + 256 + size_t(RB * CB + RB + CB) * sizeof(float) + 768;
+}
+
+cudaError_t launch_tc_quantize(int prec, const float* A, int64_t m, int64_t n, int64_t lda,
+                               void* qbuf, QuantA* out, int num_sms, cudaStream_t s) {
+    const int E = prec == PLU_BF16 ? 2 : 1;
+    const int64_t ldq = (m + 15) / 16 * 16;
+    const int64_t RB = (m + 127) / 128, CB = (n + 127) / 128;
+    Workspace w;
+    w.base = static_cast<char*>(qbuf);
+    w.cap = tc_quant_bytes(m, n, prec);
+    void* Aq = w.take(size_t(ldq) * size_t(n) * E);
+    float* amax = static_cast<float*>(w.take(size_t(RB * CB) * sizeof(float)));
+    float* s_r = static_cast<float*>(w.take(size_t(RB) * sizeof(float)));
+    float* s_c = static_cast<float*>(w.take(size_t(CB) * sizeof(float)));
+    if (!Aq || !amax || !s_r || !s_c) return cudaErrorInvalidValue;
+    const unsigned gy = unsigned(n < 65535 ? n : 65535);
+    const unsigned gx = unsigned((m + 255) / 256 < 64 ? (m + 255) / 256 : 64);
+    cudaError_t e;
+    if (prec == PLU_BF16) {
+        count_launch();
+        k_quant_bf16<<<dim3(gx, gy), 256, 0, s>>>(A, m, n, lda, static_cast<__nv_bfloat16*>(Aq), ldq);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        out->s_r = nullptr;
+        out->s_c = nullptr;
+    } else {
+        count_launch();
+        k_tile_amax<<<dim3(unsigned(RB), unsigned(CB)), 256, 0, s>>>(A, m, n, lda, int(RB), amax);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        count_launch();
+        k_tile_scales<<<1, 256, 0, s>>>(amax, int(RB), int(CB), s_r, s_c);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        count_launch();
+        k_quant_fp8<<<dim3(gx, gy), 256, 0, s>>>(A, m, n, lda, s_r, s_c,
+                                                 static_cast<__nv_fp8_storage_t*>(Aq), ldq);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        out->s_r = s_r;
+        out->s_c = s_c;
+    }
+    out->data = Aq;
+    out->ld = ldq;
+    out->prec = prec;
+    out->m = m;
+    out->n = n;
+    return cudaSuccess;
+}
+
+namespace {
+
+template <int KIND>
+cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t lda,
+                         const float* s_r, const float* s_c, const double* X, int64_t ldx,
+                         int cols, double* Y, int64_t ldy, void* scratch, int* dev_status,
+                         int num_sms, cudaStream_t s, int accum) {
+    constexpr int E = Kind<KIND>::E;
+    constexpr int BKE = 128 / E;
     const int64_t M = trans ? n : m;
     const int64_t K = trans ? m : n;
-    const TcPlan p = plan_tc(M, K, cols, num_sms, trans == 0);
+    const TcPlan p = plan_tc(M, K, cols, num_sms, trans == 0, E);
+    if (p.stages < 2) return cudaErrorInvalidValue;
     Workspace w;
     w.base = static_cast<char*>(scratch);
     w.cap = tc_scratch_bytes(M, K, cols, num_sms);
     float* part = static_cast<float*>(w.take(size_t(p.grid) * p.max_segs * p.npad * BM * sizeof(float)));
-    float* x32 = static_cast<float*>(w.take(size_t(p.ldx32) * p.npad * sizeof(float)));
-    if (!part || !x32) return cudaErrorInvalidValue;
-    // small operand -> TF32, K x npad, ld multiple of 4 (16-byte TMA strides)
+    unsigned char* xq = static_cast<unsigned char*>(w.take(size_t(p.ksteps) * p.npad * 128));
+    float* colsc = static_cast<float*>(w.take(size_t(p.npad) * sizeof(float)));
+    if (!part || !xq || !colsc) return cudaErrorInvalidValue;
+    // fold: scales of A along the reduction index (A X: s_c by column block of
+    // A; A^T X: s_r by row block); rowblk: scales along the output rows
+    const float* fold = trans ? s_r : s_c;
+    const float* rowblk = trans ? s_c : s_r;
+    cudaError_t e;
     {
-        int64_t b = (K * p.npad + 255) / 256;
+        int64_t b = (int64_t(p.ksteps) * BKE * p.npad + 255) / 256;
         if (b > int64_t(num_sms) * 16) b = int64_t(num_sms) * 16;
+        if (KIND == KIND_FP8) {
+            count_launch();
+            k_fp8_colscale<<<cols, 256, 0, s>>>(K, cols, X, ldx, fold, colsc);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         count_launch();
-        k_to_tf32<<<unsigned(b), 256, 0, s>>>(K, cols, p.npad, X, ldx, x32, p.ldx32);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        k_to_operand<KIND><<<unsigned(b), 256, 0, s>>>(K, cols, p.npad, p.ksteps, X, ldx, fold,
+                                                        colsc, xq);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    CUtensorMap mapA, mapB;
+    const CUtensorMapDataType dt = KIND == KIND_TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                  : KIND == KIND_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    CUtensorMap mapA;
     // A as stored: dim0 = rows (m, contiguous), dim1 = columns (n)
-    const uint32_t a_box0 = 32, a_box1 = trans ? 128 : 32;
-    if (!make_map_2d(&mapA, A, uint64_t(m), uint64_t(n), uint64_t(lda) * 4, a_box0, a_box1))
-        return cudaErrorInvalidValue;
-    if (!make_map_2d(&mapB, x32, uint64_t(K), uint64_t(p.npad), uint64_t(p.ldx32) * 4, 32,
-                     uint32_t(p.nchunk)))
+    if (!make_map_2d(&mapA, dt, A, uint64_t(m), uint64_t(n), uint64_t(lda) * E, BKE,
+                     trans ? 128 : BKE))
         return cudaErrorInvalidValue;
     TcParams P;
     P.M = M;
@@ -552,19 +780,18 @@ cudaError_t launch_tc_pass(int trans, int64_t m, int64_t n, const float* A, int6
     P.tmem_cols = p.tmem_cols;
     P.part = part;
     P.status = dev_status;
-    cudaError_t e;
     if (trans) {
-        e = cudaFuncSetAttribute(k_tc_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_tc_pass<false, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(p.smem));
         if (e != cudaSuccess) return e;
         count_launch();
-        k_tc_pass<false><<<p.grid, TC_THREADS, p.smem, s>>>(mapA, mapB, P);
+        k_tc_pass<false, KIND><<<p.grid, TC_THREADS, p.smem, s>>>(mapA, xq, P);
     } else {
-        e = cudaFuncSetAttribute(k_tc_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_tc_pass<true, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(p.smem));
         if (e != cudaSuccess) return e;
         count_launch();
-        k_tc_pass<true><<<p.grid, TC_THREADS_X, p.smem, s>>>(mapA, mapB, P);
+        k_tc_pass<true, KIND><<<p.grid, TC_THREADS_X, p.smem, s>>>(mapA, xq, P);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -572,8 +799,29 @@ cudaError_t launch_tc_pass(int trans, int64_t m, int64_t n, const float* A, int6
     if (rb > int64_t(num_sms) * 16) rb = int64_t(num_sms) * 16;
     count_launch();
     k_tc_reduce<<<unsigned(rb), 256, 0, s>>>(part, M, cols, p.npad, p.ksteps, p.total, p.per,
-                                              p.max_segs, p.grid, Y, ldy);
+                                              p.max_segs, p.grid, Y, ldy, rowblk,
+                                              KIND == KIND_FP8 ? colsc : nullptr, accum);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tc_pass(int trans, int64_t m, int64_t n, const float* A, int64_t lda,
+                           const double* X, int64_t ldx, int cols, double* Y, int64_t ldy,
+                           void* scratch, int* dev_status, int num_sms, cudaStream_t s,
+                           int accum) {
+    return tc_pass_kind<KIND_TF32>(trans, m, n, A, lda, nullptr, nullptr, X, ldx, cols, Y, ldy,
+                                   scratch, dev_status, num_sms, s, accum);
+}
+
+cudaError_t launch_tc_pass_q(int trans, const QuantA& q, const double* X, int64_t ldx, int cols,
+                             double* Y, int64_t ldy, void* scratch, int* dev_status, int num_sms,
+                             cudaStream_t s, int accum) {
+    if (q.prec == PLU_BF16)
+        return tc_pass_kind<KIND_BF16>(trans, q.m, q.n, q.data, q.ld, nullptr, nullptr, X, ldx,
+                                       cols, Y, ldy, scratch, dev_status, num_sms, s, accum);
+    return tc_pass_kind<KIND_FP8>(trans, q.m, q.n, q.data, q.ld, q.s_r, q.s_c, X, ldx, cols, Y,
+                                  ldy, scratch, dev_status, num_sms, s, accum);
 }
 
 }  // namespace plu

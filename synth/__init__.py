@@ -91,11 +91,27 @@ def colmajor(t):
     return t.t().contiguous().t()
 
 
+def _preload_torch_linalg():
+    """Load torch's CUDA linear-algebra library by absolute path (its lazy
+    load by name fails under some profilers' injected environments)."""
+    import ctypes
+    import os
+    import torch
+    path = os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so")
+    if os.path.exists(path):
+        try:
+            ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+        except OSError:
+            pass
+
+
 def svd_matrix_torch(m, n, sigma, seed, device="cuda", dtype=None, noise=0.0,
                      work_dtype=None):
     """A = U diag(sigma) V^T built with torch (QR of seeded Gaussians) on
     ``device``; returned column-major in ``dtype``."""
     import torch
+    if str(device).startswith("cuda"):
+        _preload_torch_linalg()
     dtype = dtype or torch.float32
     work_dtype = work_dtype or (torch.float64 if max(m, n) <= 4096 else torch.float32)
     g = torch.Generator(device=device)

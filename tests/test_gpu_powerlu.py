@@ -139,3 +139,49 @@ def test_powerlu_tf32_error_within_1p1_of_fp64(ctx):
         errs[prec] = oracle.rel_lu_error(A64h, gp.cpu().numpy(), gq.cpu().numpy(), host(gL), host(gU))
         assert rep["passes"] == 3
     assert errs["tf32"] <= 1.1 * errs["fp64"], errs
+
+
+@pytest.mark.parametrize("prec,limit", [("bf16", 1.5), ("fp8", 6.0)])
+def test_powerlu_quantized_passes_run_and_report_error(ctx, prec, limit):
+    """BF16 / FP8-E4M3 power passes over a quantized copy of A, final pass on
+    the FP32 A: v passes, valid factors, error bounded against FP64."""
+    sig = synth.sigma_profile("pow15", 2048)
+    A = synth.svd_matrix_np(2048, 2048, sig, seed=3)
+    A32 = A.astype(np.float32)
+    A64h = A32.astype(np.float64)
+    gp, gq, gL, gU, rep = plu.plu_powerlu(ctx, dev(A64h), 64, 74, 3, seed=0, prec="fp64")
+    e64 = oracle.rel_lu_error(A64h, gp.cpu().numpy(), gq.cpu().numpy(), host(gL), host(gU))
+    gp, gq, gL, gU, rep = plu.plu_powerlu(ctx, dev(A32, torch.float32), 64, 74, 3, seed=0, prec=prec)
+    assert rep["passes"] == 3
+    p, q = gp.cpu().numpy(), gq.cpu().numpy()
+    assert sorted(p.tolist()) == list(range(2048)) and sorted(q.tolist()) == list(range(2048))
+    e = oracle.rel_lu_error(A64h, p, q, host(gL), host(gU))
+    assert e <= limit * e64, (e, e64)
+
+
+@pytest.mark.parametrize("m,n,k", [(1000, 800, 12), (3000, 2500, 40)])
+def test_singlepass_fp64_parity(ctx, m, n, k):
+    """Alg. singlepasslu on the same Omega: identical p, q; L, U to 1e-9
+    (G^{dagger T} goes through CholeskyQR2 of G instead of (G^T G)^{-1})."""
+    sig = synth.sigma_profile("type2", min(m, n))
+    A = synth.svd_matrix_np(m, n, sig, seed=m)
+    ref = oracle.singlepass(A, k, seed=5)
+    gp, gq, gL, gU, rep = plu.plu_singlepass(ctx, dev(A), k, seed=5, prec="fp64")
+    assert rep["passes"] == 1
+    check_parity(A, (gp, gq, gL, gU), ref, tol=1e-9)
+
+
+def test_singlepass_streams_column_panels_and_tf32(ctx):
+    """Wide enough that the column sweep takes several L2-sized panels; TF32
+    error within 1.1x of the FP64 single pass."""
+    sig = synth.sigma_profile("type1", 3000)
+    A = synth.svd_matrix_np(6000, 3000, sig, seed=7)      # 6000 x 8 B x 1024 cols = 49 MB
+    A32 = A.astype(np.float32)
+    A64h = A32.astype(np.float64)
+    ref = oracle.singlepass(A64h, 30, seed=1)
+    gp, gq, gL, gU, _ = plu.plu_singlepass(ctx, dev(A64h), 30, seed=1, prec="fp64")
+    check_parity(A64h, (gp, gq, gL, gU), ref, tol=1e-9)
+    e64 = oracle.rel_lu_error(A64h, gp.cpu().numpy(), gq.cpu().numpy(), host(gL), host(gU))
+    gp, gq, gL, gU, _ = plu.plu_singlepass(ctx, dev(A32, torch.float32), 30, seed=1, prec="tf32")
+    e32 = oracle.rel_lu_error(A64h, gp.cpu().numpy(), gq.cpu().numpy(), host(gL), host(gU))
+    assert e32 <= 1.1 * e64, (e32, e64)

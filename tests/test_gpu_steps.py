@@ -257,3 +257,97 @@ def test_pass_tf32_rejects_fp64_matrix(ctx):
     with pytest.raises(plu.PLUError) as ei:
         plu.plu_pass(ctx, A, 0, dev(synth.gaussian_np(80, 4, 2)), "tf32")
     assert ei.value.name == "PLU_EUNSUPPORTED"
+
+
+@pytest.mark.parametrize("rows,cols", [(4096, 512), (2000, 276)])
+def test_qr_wide_sketch_cooperative_cholesky(ctx, rows, cols):
+    """Sketch widths of the mixed and fixed-precision workloads go through the
+    multi-CTA blocked Cholesky."""
+    X = synth.gaussian_np(rows, cols, cols) * np.logspace(0, -2, cols)[None, :]
+    Q, R = oracle.qr_economy(X)
+    gQ, gR = plu.plu_qr(ctx, dev(X), want_r=True)
+    gQ, gR = host(gQ), host(gR)
+    assert np.max(np.abs(gQ.T @ gQ - np.eye(cols))) < 1e-13
+    assert rel(gQ, Q) < 1e-11
+    assert rel(gR, R) < 1e-11
+
+
+@pytest.mark.parametrize("rows,cols", [(32768, 276), (20000, 512)])
+def test_lu_reorth_full_size_panels(ctx, rows, cols):
+    """Panels of the 32768^2 mixed and 20000 x 10000 fixed-precision workloads."""
+    X = synth.gaussian_np(rows, cols, rows + cols)
+    perm, L, U, info = oracle.getrf(X)
+    gp, gL, gU, ginfo = plu.plu_getrf(ctx, dev(X))
+    assert np.array_equal(gp.cpu().numpy().astype(np.int64), perm)
+    assert rel(host(gL), L) < 1e-12
+    assert rel(host(gU), U) < 1e-12
+
+
+# ------------------------------------- a2/a4 on tensor cores (BF16, FP8-E4M3)
+def bf16_rne(a):
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32)
+
+
+def e4m3_rne(x):
+    """Round float64 values to FP8-E4M3 (round to nearest even, saturate at 448)."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.minimum(np.abs(x), 448.0)
+    e = np.floor(np.log2(np.where(a > 0, a, 1.0)))
+    e = np.maximum(e, -6.0)                       # subnormal spacing 2^-9 below 2^-6
+    sp = 2.0 ** (e - 3)
+    q = np.round(a / sp) * sp                     # numpy rounds half to even
+    return np.sign(x) * np.minimum(q, 448.0)
+
+
+def fp8_reference(A32, X, trans):
+    """The FP8 pass as the library defines it: rank-1 128x128 tile scales
+    s_r (rows) and s_c (columns), A/(s_r s_c) and the scaled small operand
+    rounded to E4M3, FP32 scales applied in FP64."""
+    m, n = A32.shape
+    RB, CB = (m + 127) // 128, (n + 127) // 128
+    amax = np.zeros((RB, CB), dtype=np.float32)
+    for rb in range(RB):
+        for cb in range(CB):
+            amax[rb, cb] = np.max(np.abs(A32[rb * 128:(rb + 1) * 128, cb * 128:(cb + 1) * 128]))
+    s_r = np.max(amax, axis=1).astype(np.float32)
+    s_r[s_r == 0] = 1
+    s_c = (np.max(amax / s_r[:, None], axis=0) / np.float32(448)).astype(np.float32)
+    s_c[s_c == 0] = 1
+    rows_s = np.repeat(s_r, 128)[:m]
+    cols_s = np.repeat(s_c, 128)[:n]
+    Aq = e4m3_rne((A32 / (rows_s[:, None] * cols_s[None, :]).astype(np.float32)).astype(np.float32))
+    fold = (cols_s if trans == 0 else rows_s).astype(np.float64)
+    outs = (rows_s if trans == 0 else cols_s).astype(np.float64)
+    Z = X * fold[:, None]
+    cs = (np.max(np.abs(Z), axis=0) / 448.0).astype(np.float32).astype(np.float64)
+    cs[cs == 0] = 1
+    Zq = e4m3_rne((Z / cs[None, :]).astype(np.float32).astype(np.float64))
+    Y = (Aq @ Zq if trans == 0 else Aq.T @ Zq) * outs[:, None] * cs[None, :]
+    return Y
+
+
+@pytest.mark.parametrize("m,n,cols", [(1000, 777, 25), (2048, 1536, 276), (300, 4100, 48)])
+@pytest.mark.parametrize("trans", [0, 1])
+def test_pass_bf16_matches_bf16_operands(ctx, m, n, cols, trans):
+    A32 = synth.gaussian_np(m, n, 21).astype(np.float32)
+    X = synth.gaussian_np(n if trans == 0 else m, cols, 22)
+    Ab = bf16_rne(A32).astype(np.float64)
+    Xb = bf16_rne(X.astype(np.float32)).astype(np.float64)
+    ref = Ab @ Xb if trans == 0 else Ab.T @ Xb
+    got = host(plu.plu_pass(ctx, dev(A32, torch.float32), trans, dev(X), "bf16"))
+    assert rel(got, ref) < 2e-6
+
+
+@pytest.mark.parametrize("m,n,cols", [(1000, 777, 25), (2048, 1536, 276), (300, 4100, 48)])
+@pytest.mark.parametrize("trans", [0, 1])
+def test_pass_fp8_matches_fp8_operands(ctx, m, n, cols, trans):
+    rng = np.random.default_rng(23)
+    A32 = (synth.gaussian_np(m, n, 23) * rng.uniform(0.1, 10.0, size=(1, n))).astype(np.float32)
+    X = synth.gaussian_np(n if trans == 0 else m, cols, 24)
+    ref = fp8_reference(A32, X, trans)
+    got = host(plu.plu_pass(ctx, dev(A32, torch.float32), trans, dev(X), "fp8"))
+    assert rel(got, ref) < 2e-5
+    exact = A32.astype(np.float64) @ X if trans == 0 else A32.astype(np.float64).T @ X
+    assert rel(got, exact) < 0.1
