@@ -40,7 +40,119 @@ METRIC = "PowerLU ms & TFLOP/s per pass of A at stated rel. error, mixed vs FP64
 def workloads():
     import synth
     return {"fixed_rank_8192": synth.FIXED_RANK_8192, "mixed_32768": synth.MIXED_32768,
-            "plain_2000x1500": synth.PLAIN_2000x1500}
+            "plain_2000x1500": synth.PLAIN_2000x1500, "batched_512": None}
+
+
+def batch_specs(count=512, seed=0):
+    """The batched workload: sizes from synth.batched_problems; every 8th
+    problem runs the single-pass algorithm, the others PowerLU (v = 2, 3)."""
+    import synth
+    specs = synth.batched_problems(count, seed)
+    for i, sp in enumerate(specs):
+        sp["algo"] = 1 if i % 8 == 7 else 0
+    return specs
+
+
+def batch_flops(specs):
+    f = 0.0
+    for sp in specs:
+        if sp["algo"] == 1:
+            f += 4.0 * sp["m"] * sp["n"] * sp["k"]
+        else:
+            f += 2.0 * sp["m"] * sp["n"] * (sp["l"] * (sp["v"] - 1) + sp["k"])
+    return f
+
+
+def build_batch(specs, device, dtype):
+    import numpy as np
+    import torch
+    import synth
+    mats = []
+    for sp in specs:
+        sig = synth.sigma_profile("expk", min(sp["m"], sp["n"]), k=sp["k"])
+        mats.append(synth.svd_matrix_torch(sp["m"], sp["n"], sig, sp["seed"], device=device,
+                                           dtype=dtype))
+    return mats
+
+
+def run_batched(args):
+    import numpy as np
+    import torch
+    import paper_2002_07138_gb300 as plu
+    import oracle
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    specs = batch_specs(512, seed=rank)
+    mats = build_batch(specs, "cuda", torch.float32)
+    stream = torch.cuda.current_stream()
+    ctx = plu.Context(local, stream.cuda_stream)
+    probs = [dict(A=A, k=sp["k"], l=sp["l"], v=sp["v"], algo=sp["algo"], seed=sp["seed"])
+             for A, sp in zip(mats, specs)]
+    flops = batch_flops(specs)
+    for _ in range(args.warmup):
+        plu.plu_batched(ctx, probs, prec=args.prec if args.prec in ("fp32", "fp64") else "fp32")
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    dist_barrier(ws)
+    graph_ms, launches, outs = [], 0, None
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        outs, rep = plu.plu_batched(ctx, probs, prec=args.prec if args.prec in ("fp32", "fp64") else "fp32")
+        graph_ms.append(rep["ms_total"])
+        launches += rep["launches"]
+    torch.cuda.synchronize()
+    wall_ms = 1e3 * (time.perf_counter() - t0) / args.steps
+    dist_barrier(ws)
+    clk = clocks.stop()
+    ms = dist_max(ws, statistics.mean(graph_ms))
+    value = flops * ws / (ms / 1e3) / 1e12
+    # accuracy over a sample of problems
+    errs = []
+    for i in range(0, len(specs), 32):
+        A = mats[i].double()
+        p, q, L, U = outs[i]
+        errs.append(float(torch.linalg.norm(A[p.long()][:, q.long()] - L @ U) / torch.linalg.norm(A)))
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        t_or = 0.0
+        f_or = 0.0
+        for i in range(0, 64, 4):
+            sp = specs[i]
+            Ah = mats[i].double().cpu().numpy()
+            t1 = time.perf_counter()
+            if sp["algo"] == 1:
+                oracle.singlepass(Ah, sp["k"], seed=sp["seed"])
+            else:
+                oracle.powerlu(Ah, sp["k"], sp["l"], sp["v"], seed=sp["seed"])
+            t_or += time.perf_counter() - t1
+            f_or += batch_flops([sp])
+        cpu = {"value": f_or / t_or / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
+               "kind": "oracle", "sample": "16 of the 512 problems (every 4th of the first 64), "
+               "%.1f s" % t_or}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.prec != "fp64" else "f64", "data": "synthetic",
+            "config": {"workload": "batched_512", "problems": len(specs),
+                       "sum_mn": int(sum(sp["m"] * sp["n"] for sp in specs)),
+                       "single_pass_problems": int(sum(sp["algo"] for sp in specs)),
+                       "pass_precision": "fp32" if args.prec != "fp64" else "fp64",
+                       "between_passes": "f64", "l2_flush": "inputs larger than L2",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "wall_ms_per_step": wall_ms,
+            "rel_error_sample_max": max(errs), "rel_error_sample_median": statistics.median(errs),
+            "gpu_launches": launches,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    return 0
 
 
 def pass_flops(m, n, k, l, v):
@@ -430,6 +542,12 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     args = ap.parse_args()
+    if args.workload == "batched_512":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no "
+                              "reference arm; use the default workload"}))
+            return 0
+        return run_batched(args)
     w = workloads()[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)

@@ -189,6 +189,37 @@ plu_status plu_singlepass(plu_ctx* ctx, const plu_matrix* A, int k, uint64_t see
                           plu_prec prec, int32_t* p, int32_t* q, double* L, int64_t ldL,
                           double* U, int64_t ldU, plu_report* rep);
 
+/* One problem of a batch (plu_batched).  A is m x n, column-major, device
+ * memory, element type `dtype` (plu_dtype).  algo 0: PowerLU (Alg. bpowerlu
+ * with Alg. gpowerlu), 1 <= k <= l < min(m, n), v >= 2; algo 1: single pass
+ * (Alg. singlepasslu), 1 <= k < min(m, n), l and v ignored.  Outputs as in
+ * plu_powerlu (device): p (m), q (n), L (m x k, ldL >= m), U (k x n, ldU >= k).
+ * The Gaussian sketch of a problem is the one plu_powerlu / plu_singlepass
+ * would draw from the same seed. */
+typedef struct {
+    int64_t m, n, ld;
+    int32_t dtype;
+    const void* A;
+    int32_t k, l, v, algo;
+    uint64_t seed;
+    int32_t* p;
+    int32_t* q;
+    double* L;
+    int64_t ldL;
+    double* U;
+    int64_t ldU;
+} plu_batch_problem;
+
+/* Batched factorisation of `count` independent problems of uneven size
+ * (host array `problems`).  Every step of every problem runs in grouped
+ * launches (one per kind of step and phase, each covering all problems), all
+ * captured into one CUDA graph that is launched once on the context's stream.
+ * prec: PLU_FP64 or PLU_FP32 (passes in FP32 FMA); tensor-core precisions are
+ * not taken here.  Synchronises before returning.  rep (nullable) reports
+ * the graph's device time, the passes and the kernels in the graph. */
+plu_status plu_batched(plu_ctx* ctx, const plu_batch_problem* problems, int count, plu_prec prec,
+                       plu_report* rep);
+
 /* ---------------------------------------------------------------------
  * Allocation-free variant (the paper has no counterpart: this is a service
  * for callers that cannot allocate device memory, such as code running

@@ -41,6 +41,12 @@ class plu_report(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class plu_batch_problem(ctypes.Structure):
+    _fields_ = [("m", c_i64), ("n", c_i64), ("ld", c_i64), ("dtype", c_i32), ("A", c_vp),
+                ("k", c_i32), ("l", c_i32), ("v", c_i32), ("algo", c_i32), ("seed", c_u64),
+                ("p", c_vp), ("q", c_vp), ("L", c_vp), ("ldL", c_i64), ("U", c_vp), ("ldU", c_i64)]
+
+
 # C signatures: name -> (restype, argtypes)
 SIGNATURES = {
     "plu_create": (c_int, [ctypes.POINTER(c_vp), c_int, c_vp]),
@@ -68,6 +74,8 @@ SIGNATURES = {
                                c_vp, c_i64, c_vp, c_i64, ctypes.POINTER(plu_report)]),
     "plu_lu_reorth_static": (c_int, [c_vp, c_i64, c_int, c_vp, c_i64, ctypes.c_char_p,
                                      ctypes.c_size_t]),
+    "plu_batched": (c_int, [c_vp, ctypes.POINTER(plu_batch_problem), c_int, c_int,
+                            ctypes.POINTER(plu_report)]),
 }
 
 _lib = None
@@ -274,3 +282,29 @@ def plu_singlepass(ctx, A, k, seed=0, prec="fp64"):
     ctx.check(lib().plu_singlepass(ctx.handle, ctypes.byref(Am), k, seed, PREC[prec], _ptr(p),
                                    _ptr(q), _ptr(L), _ld(L), _ptr(U), _ld(U), ctypes.byref(rep)))
     return p, q, L, U, rep.as_dict()
+
+
+def plu_batched(ctx, problems, prec="fp32"):
+    """Batched factorisation.  `problems`: list of dicts with A (column-major
+    CUDA tensor), k, l, v, algo (0 PowerLU, 1 single pass), seed.  Returns
+    (list of (p, q, L, U), report dict)."""
+    torch = _torch()
+    arr = (plu_batch_problem * len(problems))()
+    outs = []
+    for i, pr in enumerate(problems):
+        A = pr["A"]
+        m, n = A.shape
+        k = pr["k"]
+        p = torch.empty(m, dtype=torch.int32, device=A.device)
+        q = torch.empty(n, dtype=torch.int32, device=A.device)
+        L = colmajor_empty(m, k, device=A.device)
+        U = colmajor_empty(k, n, device=A.device)
+        Am = as_plu_matrix(A)
+        arr[i] = plu_batch_problem(m, n, Am.ld, Am.dtype, A.data_ptr(), k, pr.get("l", k),
+                                   pr.get("v", 2), pr.get("algo", 0), pr.get("seed", 0),
+                                   p.data_ptr(), q.data_ptr(), L.data_ptr(), _ld(L), U.data_ptr(),
+                                   _ld(U))
+        outs.append((p, q, L, U))
+    rep = plu_report()
+    ctx.check(lib().plu_batched(ctx.handle, arr, len(problems), PREC[prec], ctypes.byref(rep)))
+    return outs, rep.as_dict()

@@ -29,6 +29,7 @@ struct plu_ctx {
     int64_t spin_budget = kDefaultSpin;
     char err[512] = {0};
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaStream_t capture = nullptr;   // private stream for graph capture (batched)
     static constexpr int64_t kDefaultSpin = 16LL << 20;
 };
 
@@ -364,6 +365,7 @@ void plu_destroy(plu_ctx* c) {
     if (c->h_status) cudaFreeHost(c->h_status);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->capture) cudaStreamDestroy(c->capture);
     delete c;
 }
 
@@ -733,6 +735,63 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
         rep->flops_passes = 4.0 * mnd * k;
         rep->bytes_passes = mnd * double(es) + double(m + n) * k * 8.0;
         rep->launches = int32_t(g_launches - launches0);
+    }
+    return finish(c);
+}
+
+plu_status plu_batched(plu_ctx* c, const plu_batch_problem* P, int count, plu_prec prec,
+                       plu_report* rep) {
+    PLU_TRY(bind(c));
+    if (!P || count < 1) return fail(c, PLU_EINVAL, "need at least one problem");
+    if (prec != PLU_FP64 && prec != PLU_FP32)
+        return fail(c, PLU_EUNSUPPORTED, "batched passes take PLU_FP64 or PLU_FP32");
+    double flops = 0.0, bytes = 0.0;
+    int passes = 0;
+    for (int i = 0; i < count; ++i) {
+        const plu_batch_problem& p = P[i];
+        const int64_t mn = p.m < p.n ? p.m : p.n;
+        if (!p.A || p.m < 2 || p.n < 2 || p.ld < p.m || (p.dtype != PLU_F32 && p.dtype != PLU_F64))
+            return fail(c, PLU_EINVAL, "problem %d: bad matrix", i);
+        if (p.m > (1 << 30) || p.n > (1 << 30)) return fail(c, PLU_EINVAL, "problem %d: too large", i);
+        if (p.algo == 0) {
+            if (p.k < 1 || p.l < p.k || p.l >= mn || p.v < 2 || p.l > 1024)
+                return fail(c, PLU_EINVAL, "problem %d: need 1 <= k <= l < min(m, n), l <= 1024, v >= 2", i);
+            passes += p.v;
+            flops += 2.0 * double(p.m) * double(p.n) * (double(p.l) * (p.v - 1) + p.k);
+            bytes += double(p.m) * double(p.n) * (p.dtype == PLU_F32 ? 4.0 : 8.0) * p.v;
+        } else if (p.algo == 1) {
+            if (p.k < 1 || p.k >= mn || p.k > 1024)
+                return fail(c, PLU_EINVAL, "problem %d: need 1 <= k < min(m, n), k <= 1024", i);
+            passes += 1;
+            flops += 4.0 * double(p.m) * double(p.n) * p.k;
+            bytes += double(p.m) * double(p.n) * (p.dtype == PLU_F32 ? 4.0 : 8.0);
+        } else {
+            return fail(c, PLU_EINVAL, "problem %d: algo must be 0 or 1", i);
+        }
+        if (!p.p || !p.q || !p.L || !p.U || p.ldL < p.m || p.ldU < p.k)
+            return fail(c, PLU_EINVAL, "problem %d: bad outputs", i);
+    }
+    if (!c->capture) PLU_CUDA(c, cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking));
+    const size_t wsb = (batch_workspace_bytes(P, count) + 255) & ~size_t(255);
+    const size_t tb = batch_tables_bytes(count);
+    PLU_TRY(ensure_ws(c, wsb + tb));
+    // the capture stream must see the work already queued on the context stream
+    PLU_CUDA(c, cudaStreamSynchronize(c->stream));
+    int nl = 0;
+    float ms = 0.f;
+    PLU_CUDA(c, run_batch(P, count, prec, c->ws, c->ws + wsb, tb, c->d_status, c->num_sms, c->stream,
+                          c->capture, &nl, &ms));
+    if (rep) {
+        memset(rep, 0, sizeof(*rep));
+        rep->ms_total = ms;
+        rep->ms_passes = -1.0;
+        rep->passes = passes;
+        rep->rank = -1;
+        rep->indicator = -1.0;
+        rep->normA2 = -1.0;
+        rep->flops_passes = flops;
+        rep->bytes_passes = bytes;
+        rep->launches = nl;
     }
     return finish(c);
 }

@@ -1,0 +1,827 @@
+// Batched factorisation of many independent matrices of uneven size.
+//
+// Each problem is PowerLU (Alg. bpowerlu with Alg. gpowerlu, any v >= 2) or
+// the single-pass LU (Alg. singlepasslu).  A problem is turned into a list of
+// steps (Gaussian sketch, pass A X / A^T X, LU re-orthogonalisation, QR,
+// final pass, LU tail); step t of every problem forms phase t.  A phase is
+// executed as one grouped launch per kind of step: every kernel below reads
+// a table of jobs (one per problem, or one per output tile) and a CTA looks
+// up its job, so all problems of a phase run side by side across the GPU.
+// The whole sequence of grouped launches is captured into one CUDA graph and
+// launched once.
+//
+// Grouped kernels: the Gaussian sketch (Philox4x32-10 + Box-Muller, the same
+// values as plu_gaussian); a SIMT GEMM over 64 x 32 output tiles (FP32 or
+// FP64 arithmetic, no split of the reduction: the problems are small, so the
+// tiles of all problems already fill the GPU); the partial-pivoting LU of a
+// problem's panel in one CTA (same pivot order and virtual pivoting as the
+// cooperative panel LU); the Cholesky factor and triangular inverse of
+// CholeskyQR2 in one CTA per problem.
+#include "plu_internal.h"
+#include "plu_rng.cuh"
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <vector>
+
+namespace plu {
+namespace {
+
+// ------------------------------------------------------------ job tables
+struct GaussJob {
+    double* out;
+    int64_t rows, ld;
+    int cols;
+    uint32_t k0, k1, stream;
+};
+
+struct GemmJob {
+    const void* A;
+    int64_t lda;
+    const double* B;
+    int64_t ldb;
+    double* C;
+    int64_t ldc;
+    int M, N, K;
+    int transA, transB, a_f32, accum, tri;
+    int tiles_m, tiles_n;
+    int64_t tile0;
+};
+
+struct LuJob {
+    double* X;
+    int64_t rows, ldx;
+    int cols, mode;
+    int32_t* perm;
+    double* L;
+    int64_t ldL;
+    int l_trans;
+    double* U;
+    int64_t ldU;
+    int u_trans;
+    int32_t* info;
+    int* pos;
+    int* pivstep;
+};
+
+struct CholJob {
+    double* W;
+    double* Wsave;
+    int n;
+    int64_t rows;
+};
+
+struct TrinvJob {
+    const double* R;
+    double* Rinv;
+    int n;
+};
+
+// --------------------------------------------------------- Gaussian
+__global__ void k_b_gaussian(const GaussJob* __restrict__ jobs) {
+    const GaussJob J = jobs[blockIdx.y];
+    const int64_t total = J.rows * J.cols;
+    const uint64_t npairs = uint64_t(total + 1) / 2;
+    for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < npairs;
+         q += uint64_t(gridDim.x) * blockDim.x) {
+        double ze, zo;
+        rng::gaussian_pair(q, J.k0, J.k1, J.stream, ze, zo);
+        const int64_t t0 = int64_t(2 * q);
+        J.out[t0 % J.rows + (t0 / J.rows) * J.ld] = ze;
+        const int64_t t1 = t0 + 1;
+        if (t1 < total) J.out[t1 % J.rows + (t1 / J.rows) * J.ld] = zo;
+    }
+}
+
+// ------------------------------------------------------ grouped GEMM
+// C = op(A) op(B) (+ C), op(A) M x K, op(B) K x N; one 64 x 32 tile per CTA.
+constexpr int GBM = 64, GBN = 32, GBK = 16, GNT = 256;
+
+template <typename TC>
+__global__ void __launch_bounds__(GNT)
+k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
+    __shared__ TC As[GBK][GBM + 1];
+    __shared__ TC Bs[GBK][GBN + 1];
+    // job of this tile: last job with tile0 <= blockIdx.x
+    int lo = 0, hi = njobs - 1;
+    const int64_t tile = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (jobs[mid].tile0 <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    const GemmJob J = jobs[lo];
+    const int64_t local = tile - J.tile0;
+    const int64_t i0 = (local % J.tiles_m) * GBM;
+    const int64_t j0 = (local / J.tiles_m) * GBN;
+    const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+    int64_t kend = J.K;
+    if (J.tri == 2 && kend > j0 + GBN) kend = j0 + GBN;
+    const bool skip = (J.tri == 1 && i0 >= j0 + GBN);
+    if (skip) kend = 0;
+    const float* Af = static_cast<const float*>(J.A);
+    const double* Ad = static_cast<const double*>(J.A);
+    TC acc[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = TC(0);
+    for (int64_t k0 = 0; k0 < kend; k0 += GBK) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int ii, kk;
+            if (J.transA) { kk = t % 16; ii = t / 16 + 16 * r; }
+            else          { ii = t % 64; kk = t / 64 + 4 * r; }
+            const int64_t gi = i0 + ii, gk = k0 + kk;
+            TC v = TC(0);
+            if (gi < J.M && gk < kend) {
+                const int64_t off = J.transA ? gk + gi * J.lda : gi + gk * J.lda;
+                v = J.a_f32 ? TC(Af[off]) : TC(Ad[off]);
+            }
+            As[kk][ii] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            int jj, kk;
+            if (J.transB) { jj = t % 32; kk = t / 32 + 8 * r; }
+            else          { kk = t % 16; jj = t / 16 + 16 * r; }
+            const int64_t gj = j0 + jj, gk = k0 + kk;
+            TC v = TC(0);
+            if (gj < J.N && gk < kend) v = TC(J.transB ? J.B[gj + gk * J.ldb] : J.B[gk + gj * J.ldb]);
+            Bs[kk][jj] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; ++kk) {
+            TC av[4], bv[2];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+            bv[0] = Bs[kk][tx];
+            bv[1] = Bs[kk][tx + 16];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                acc[a][0] = fma(av[a], bv[0], acc[a][0]);
+                acc[a][1] = fma(av[a], bv[1], acc[a][1]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int64_t gi = i0 + ty + 16 * a;
+        if (gi >= J.M) continue;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int64_t gj = j0 + tx + 16 * b;
+            if (gj >= J.N) continue;
+            double* c = J.C + gi + gj * J.ldc;
+            *c = J.accum ? *c + double(acc[a][b]) : double(acc[a][b]);
+        }
+    }
+}
+
+// ------------------------------------------- one-CTA partial-pivoting LU
+constexpr int LNT = 512;
+
+struct BCand {
+    double v;
+    int pos;
+    int row;
+};
+
+__device__ __forceinline__ bool b_better(const BCand& a, const BCand& b) {
+    if (a.row < 0) return false;
+    if (b.row < 0) return true;
+    const bool an = a.v != a.v, bn = b.v != b.v;
+    if (an || bn) return an && bn ? a.pos < b.pos : bn;
+    if (a.v > b.v) return true;
+    if (a.v < b.v) return false;
+    return a.pos < b.pos;
+}
+
+__device__ __forceinline__ BCand b_warp_best(BCand c) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        BCand o;
+        o.v = __shfl_xor_sync(0xffffffffu, c.v, off);
+        o.pos = __shfl_xor_sync(0xffffffffu, c.pos, off);
+        o.row = __shfl_xor_sync(0xffffffffu, c.row, off);
+        if (b_better(o, c)) c = o;
+    }
+    return c;
+}
+
+// The whole panel of one problem in one CTA: rows stay in place, each row's
+// current position is tracked (LAPACK's interchange order decides ties), the
+// pivot row is staged in shared memory, then the finalising writes of the
+// cooperative version (P^T L in place, or perm, L, U) in the same kernel.
+__global__ void __launch_bounds__(LNT)
+k_b_panel_lu(const LuJob* __restrict__ jobs) {
+    extern __shared__ double urow[];
+    __shared__ BCand red[LNT / 32];
+    __shared__ BCand piv;
+    __shared__ int first_zero;
+    const LuJob J = jobs[blockIdx.x];
+    const int t = threadIdx.x;
+    const int64_t rows = J.rows;
+    const int cols = J.cols;
+    const int steps = int(rows < int64_t(cols) ? rows : int64_t(cols));
+    double* X = J.X;
+    for (int64_t i = t; i < rows; i += LNT) {
+        J.pos[i] = int(i);
+        J.pivstep[i] = -1;
+    }
+    if (t == 0) first_zero = 0;
+    __syncthreads();
+    for (int j = 0; j < steps; ++j) {
+        BCand best{-1.0, INT_MAX, -1};
+        for (int64_t i = t; i < rows; i += LNT) {
+            if (J.pivstep[i] >= 0) continue;
+            const BCand c{fabs(X[i + int64_t(j) * J.ldx]), J.pos[i], int(i)};
+            if (b_better(c, best)) best = c;
+        }
+        best = b_warp_best(best);
+        if ((t & 31) == 0) red[t >> 5] = best;
+        __syncthreads();
+        if (t < 32) {
+            BCand x = (t < LNT / 32) ? red[t] : BCand{-1.0, INT_MAX, -1};
+            x = b_warp_best(x);
+            if (t == 0) piv = x;
+        }
+        __syncthreads();
+        const BCand pv = piv;
+        for (int64_t i = t; i < rows; i += LNT) {
+            if (i == pv.row) {
+                J.pos[i] = j;
+                J.pivstep[i] = j;
+            } else if (J.pos[i] == j) {
+                J.pos[i] = pv.pos;
+            }
+        }
+        for (int c = j + t; c < cols; c += LNT) urow[c] = X[pv.row + int64_t(c) * J.ldx];
+        if (t == 0 && pv.v == 0.0 && first_zero == 0) first_zero = j + 1;
+        __syncthreads();
+        const double ujj = urow[j];
+        if (ujj != 0.0) {
+            for (int64_t i = t; i < rows; i += LNT) {
+                if (J.pivstep[i] >= 0) continue;
+                double* xi = X + i;
+                const double lij = xi[int64_t(j) * J.ldx] / ujj;
+                xi[int64_t(j) * J.ldx] = lij;
+                for (int c = j + 1; c < cols; ++c) {
+                    double* p = xi + int64_t(c) * J.ldx;
+                    *p = fma(-lij, urow[c], *p);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (t == 0 && J.info) *J.info = first_zero;
+    const int r = steps;
+    for (int64_t i = t; i < rows; i += LNT) {
+        const int s = J.pivstep[i];
+        if (J.mode == 0) {
+            if (s >= 0) {
+                X[i + int64_t(s) * J.ldx] = 1.0;
+                for (int c = s + 1; c < cols; ++c) X[i + int64_t(c) * J.ldx] = 0.0;
+            }
+            continue;
+        }
+        const int64_t pp = J.pos[i];
+        J.perm[pp] = int32_t(i);
+        for (int c = 0; c < r; ++c) {
+            double v;
+            if (s >= 0 && c == s) v = 1.0;
+            else if (s >= 0 && c > s) v = 0.0;
+            else v = X[i + int64_t(c) * J.ldx];
+            if (J.l_trans) J.L[c + pp * J.ldL] = v;
+            else J.L[pp + int64_t(c) * J.ldL] = v;
+        }
+        if (s >= 0) {
+            for (int c = 0; c < cols; ++c) {
+                const double v = (c >= s) ? X[i + int64_t(c) * J.ldx] : 0.0;
+                if (J.u_trans) J.U[c + int64_t(s) * J.ldU] = v;
+                else J.U[s + int64_t(c) * J.ldU] = v;
+            }
+        }
+    }
+}
+
+// ---------------------------------------- one-CTA Cholesky W = R^T R
+// Upper triangle read, R written over it, lower part zeroed; a non-positive
+// pivot restarts from the saved Gram matrix with the shifted-CholeskyQR shift
+// 11 (rows n + n(n+1)) u tr(W).
+constexpr int CNT = 512;
+
+__global__ void __launch_bounds__(CNT)
+k_b_cholesky(const CholJob* __restrict__ jobs, int* __restrict__ status) {
+    __shared__ int broke;
+    __shared__ double rjj;
+    const CholJob J = jobs[blockIdx.x];
+    const int n = J.n;
+    double* W = J.W;
+    const int t = threadIdx.x;
+    for (int64_t e = t; e < int64_t(n) * n; e += CNT) J.Wsave[e] = W[e];
+    __syncthreads();
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (attempt == 1) {
+            double tr = 0.0;
+            for (int i = 0; i < n; ++i) tr += J.Wsave[i + int64_t(i) * n];
+            const double shift =
+                11.0 * (double(J.rows) * n + double(n) * (n + 1)) * 1.1102230246251565e-16 * tr;
+            for (int64_t e = t; e < int64_t(n) * n; e += CNT) {
+                const int a = int(e % n), c = int(e / n);
+                W[e] = J.Wsave[e] + (a == c ? shift : 0.0);
+            }
+            __syncthreads();
+        }
+        if (t == 0) broke = 0;
+        __syncthreads();
+        for (int j = 0; j < n; ++j) {
+            if (t == 0) {
+                const double d = W[j + int64_t(j) * n];
+                if (!(d > 0.0)) broke = 1;
+                rjj = (d > 0.0) ? sqrt(d) : 1.0;
+                W[j + int64_t(j) * n] = rjj;
+            }
+            __syncthreads();
+            if (broke) break;
+            const double inv = 1.0 / rjj;
+            for (int c = j + 1 + t; c < n; c += CNT) W[j + int64_t(c) * n] *= inv;
+            __syncthreads();
+            const int m = n - j - 1;
+            for (int64_t e = t; e < int64_t(m) * m; e += CNT) {
+                const int a = j + 1 + int(e % m), c = j + 1 + int(e / m);
+                if (a <= c) W[a + int64_t(c) * n] -= W[j + int64_t(a) * n] * W[j + int64_t(c) * n];
+            }
+            __syncthreads();
+        }
+        if (!broke) break;
+        if (attempt == 1 && t == 0) atomicCAS(status, DEV_OK, DEV_NUMERIC);
+    }
+    __syncthreads();
+    for (int64_t e = t; e < int64_t(n) * n; e += CNT) {
+        const int a = int(e % n), c = int(e / n);
+        if (a > c) W[e] = 0.0;
+    }
+}
+
+// Rinv(:, j) = R^{-1} e_j, CTA (j, job).
+__global__ void k_b_trinv(const TrinvJob* __restrict__ jobs) {
+    extern __shared__ double x[];
+    const TrinvJob J = jobs[blockIdx.y];
+    const int j = blockIdx.x;
+    if (j >= J.n) return;
+    const int n = J.n;
+    const int t = threadIdx.x;
+    for (int i = t; i < n; i += blockDim.x) x[i] = (i == j) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int i = j; i >= 0; --i) {
+        const double xi = x[i] / J.R[i + int64_t(i) * n];
+        __syncthreads();
+        if (t == 0) x[i] = xi;
+        for (int k = t; k < i; k += blockDim.x) x[k] -= xi * J.R[k + int64_t(i) * n];
+        __syncthreads();
+    }
+    for (int i = t; i < n; i += blockDim.x) J.Rinv[i + int64_t(j) * n] = x[i];
+}
+
+// ------------------------------------------------------- host planning
+enum OpKind { OP_GAUSS, OP_PASS, OP_LU, OP_QR, OP_TAIL, OP_SPTAIL };
+
+struct Op {
+    int kind;
+    // OP_GAUSS
+    double* g_out; int64_t g_rows; int g_cols; uint32_t g_stream;
+    // OP_PASS: Y = op(A) X
+    int trans; const double* X; int64_t ldx; double* Y; int64_t ldy; int cols;
+    // OP_LU / OP_QR on V (rows x l)
+    double* P; int64_t prow;
+};
+
+struct ProbWs {
+    double *V, *Z, *X2, *L1, *U1T, *BT, *U2T, *W, *Wsave, *Rinv, *Rinv1, *T;
+    int *pos, *piv;
+    int32_t* info;
+};
+
+struct LaunchRec {
+    int kind;          // 0 gauss, 1 gemm, 2 lu, 3 chol, 4 trinv
+    size_t off;        // byte offset of the job table
+    int njobs;
+    int64_t tiles;     // gemm: total tiles
+    int maxn;          // trinv / lu smem
+    int tc32;          // gemm arithmetic FP32
+};
+
+struct Builder {
+    std::vector<unsigned char> blob;
+    std::vector<LaunchRec> recs;
+    template <typename T>
+    size_t put(const std::vector<T>& v) {
+        size_t off = (blob.size() + 255) & ~size_t(255);
+        blob.resize(off + v.size() * sizeof(T));
+        memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
+        return off;
+    }
+    void gemm(std::vector<GemmJob>& jobs, int tc32) {
+        if (jobs.empty()) return;
+        int64_t tiles = 0;
+        for (auto& j : jobs) {
+            j.tiles_m = (j.M + GBM - 1) / GBM;
+            j.tiles_n = (j.N + GBN - 1) / GBN;
+            j.tile0 = tiles;
+            tiles += int64_t(j.tiles_m) * j.tiles_n;
+        }
+        LaunchRec r{1, put(jobs), int(jobs.size()), tiles, 0, tc32};
+        recs.push_back(r);
+        jobs.clear();
+    }
+    void lu(std::vector<LuJob>& jobs) {
+        if (jobs.empty()) return;
+        int maxc = 1;
+        for (auto& j : jobs) maxc = std::max(maxc, j.cols);
+        recs.push_back(LaunchRec{2, put(jobs), int(jobs.size()), 0, maxc, 0});
+        jobs.clear();
+    }
+    void gauss(std::vector<GaussJob>& jobs) {
+        if (jobs.empty()) return;
+        recs.push_back(LaunchRec{0, put(jobs), int(jobs.size()), 0, 0, 0});
+        jobs.clear();
+    }
+    void chol(std::vector<CholJob>& jobs) {
+        if (jobs.empty()) return;
+        recs.push_back(LaunchRec{3, put(jobs), int(jobs.size()), 0, 0, 0});
+        jobs.clear();
+    }
+    void trinv(std::vector<TrinvJob>& jobs) {
+        if (jobs.empty()) return;
+        int maxn = 1;
+        for (auto& j : jobs) maxn = std::max(maxn, j.n);
+        recs.push_back(LaunchRec{4, put(jobs), int(jobs.size()), 0, maxn, 0});
+        jobs.clear();
+    }
+};
+
+GemmJob mk_gemm(const void* A, int64_t lda, int a_f32, int transA, const double* B, int64_t ldb,
+                int transB, double* C, int64_t ldc, int M, int N, int K, int accum = 0,
+                int tri = 0) {
+    GemmJob g{};
+    g.A = A; g.lda = lda; g.a_f32 = a_f32; g.transA = transA;
+    g.B = B; g.ldb = ldb; g.transB = transB;
+    g.C = C; g.ldc = ldc; g.M = M; g.N = N; g.K = K; g.accum = accum; g.tri = tri;
+    return g;
+}
+
+LuJob mk_lu(double* X, int64_t rows, int cols, int mode, int32_t* perm, double* L, int64_t ldL,
+            int l_trans, double* U, int64_t ldU, int u_trans, int32_t* info, int* pos, int* piv) {
+    LuJob j{};
+    j.X = X; j.rows = rows; j.ldx = rows; j.cols = cols; j.mode = mode;
+    j.perm = perm; j.L = L; j.ldL = ldL; j.l_trans = l_trans;
+    j.U = U; j.ldU = ldU; j.u_trans = u_trans; j.info = info; j.pos = pos; j.pivstep = piv;
+    return j;
+}
+
+}  // namespace
+
+size_t batch_workspace_bytes(const plu_batch_problem* P, int count) {
+    size_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        const int64_t m = P[i].m, n = P[i].n, mx = m > n ? m : n;
+        const int64_t l = P[i].algo == 1 ? P[i].k : P[i].l, k = P[i].k;
+        size_t d = size_t(n * l + m * l + mx * l + m * k + k * k + n * k + k * k + 5 * l * l + k * k);
+        total += ((d * sizeof(double) + 255) & ~size_t(255)) +
+                 ((size_t(2 * mx + 4) * sizeof(int) + 255) & ~size_t(255));
+    }
+    return total + 256;
+}
+
+// Build the job tables of every phase.  Returns the launch records and the
+// job blob (device offsets relative to the table buffer).
+static void plan_batch(const plu_batch_problem* P, int count, int prec, char* ws, Builder& B) {
+    const int tc32 = prec == PLU_FP32 ? 1 : 0;
+    std::vector<ProbWs> W(count);
+    char* cur = ws;
+    for (int i = 0; i < count; ++i) {
+        const int64_t m = P[i].m, n = P[i].n, mx = m > n ? m : n;
+        const int64_t l = P[i].algo == 1 ? P[i].k : P[i].l, k = P[i].k;
+        double* d = reinterpret_cast<double*>(cur);
+        ProbWs& w = W[i];
+        w.V = d; d += n * l;
+        w.Z = d; d += m * l;
+        w.X2 = d; d += mx * l;
+        w.L1 = d; d += m * k;
+        w.U1T = d; d += k * k;
+        w.BT = d; d += n * k;
+        w.U2T = d; d += k * k;
+        w.W = d; d += l * l;
+        w.Wsave = d; d += l * l;
+        w.Rinv = d; d += l * l;
+        w.Rinv1 = d; d += l * l;
+        w.T = d; d += l * l;
+        d += k * k;
+        cur += (size_t(reinterpret_cast<char*>(d) - cur) + 255) & ~size_t(255);
+        int* ip = reinterpret_cast<int*>(cur);
+        w.pos = ip;
+        w.piv = ip + mx;
+        w.info = ip + 2 * mx;
+        cur += (size_t(2 * mx + 4) * sizeof(int) + 255) & ~size_t(255);
+    }
+    // per-problem op lists
+    std::vector<std::vector<Op>> ops(count);
+    for (int i = 0; i < count; ++i) {
+        const plu_batch_problem& p = P[i];
+        ProbWs& w = W[i];
+        const int64_t m = p.m, n = p.n;
+        std::vector<Op>& L = ops[i];
+        auto gauss = [&](double* out, int64_t rows, int cols, uint32_t st) {
+            Op o{}; o.kind = OP_GAUSS; o.g_out = out; o.g_rows = rows; o.g_cols = cols; o.g_stream = st;
+            L.push_back(o);
+        };
+        auto pass = [&](int trans, const double* X, int64_t ldx, double* Y, int64_t ldy, int cols) {
+            Op o{}; o.kind = OP_PASS; o.trans = trans; o.X = X; o.ldx = ldx; o.Y = Y; o.ldy = ldy;
+            o.cols = cols;
+            L.push_back(o);
+        };
+        auto lu = [&](double* X, int64_t rows) { Op o{}; o.kind = OP_LU; o.P = X; o.prow = rows; L.push_back(o); };
+        auto qr = [&](double* X, int64_t rows) { Op o{}; o.kind = OP_QR; o.P = X; o.prow = rows; L.push_back(o); };
+        if (p.algo == 1) {
+            gauss(w.X2, m, p.k, 3);
+            pass(1, w.X2, m, w.V, n, p.k);          // G = A^T Omega
+            pass(0, w.V, n, w.Z, m, p.k);           // H = A G
+            Op o{}; o.kind = OP_SPTAIL; L.push_back(o);
+            continue;
+        }
+        const int v = p.v, pp = (v - 1) / 2;
+        if (v % 2 == 0) {
+            gauss(w.Z, m, p.l, 2);
+            pass(1, w.Z, m, w.V, n, p.l);
+            if (v > 2) lu(w.V, n);
+            else qr(w.V, n);
+        } else {
+            gauss(w.V, n, p.l, 1);
+        }
+        for (int it = 1; it <= pp; ++it) {
+            pass(0, w.V, n, w.Z, m, p.l);
+            lu(w.Z, m);
+            pass(1, w.Z, m, w.V, n, p.l);
+            if (it == pp) qr(w.V, n);
+            else lu(w.V, n);
+        }
+        pass(0, w.V, n, w.Z, m, p.k);               // Y = A V(:, 1:k)
+        Op o{}; o.kind = OP_TAIL; L.push_back(o);
+    }
+    size_t nph = 0;
+    for (auto& L : ops) nph = std::max(nph, L.size());
+    // the tails line up at the last phase
+    for (auto& L : ops) {
+        while (L.size() < nph) L.insert(L.end() - 2, Op{-1});
+    }
+    std::vector<GaussJob> gj;
+    std::vector<GemmJob> gm;
+    std::vector<LuJob> lj;
+    std::vector<CholJob> cj;
+    std::vector<TrinvJob> tj;
+    for (size_t ph = 0; ph < nph; ++ph) {
+        // Gaussians and passes
+        for (int i = 0; i < count; ++i) {
+            const Op& o = ops[i][ph];
+            const plu_batch_problem& p = P[i];
+            if (o.kind == OP_GAUSS)
+                gj.push_back(GaussJob{o.g_out, o.g_rows, o.g_rows, o.g_cols, uint32_t(p.seed),
+                                      uint32_t(p.seed >> 32), o.g_stream});
+            if (o.kind == OP_PASS) {
+                const int M = int(o.trans ? p.n : p.m), K = int(o.trans ? p.m : p.n);
+                gm.push_back(mk_gemm(p.A, p.ld, p.dtype == PLU_F32, o.trans, o.X, o.ldx, 0, o.Y,
+                                     o.ldy, M, o.cols, K));
+            }
+        }
+        B.gauss(gj);
+        B.gemm(gm, tc32);
+        // LU re-orthogonalisation
+        for (int i = 0; i < count; ++i) {
+            const Op& o = ops[i][ph];
+            if (o.kind == OP_LU)
+                lj.push_back(mk_lu(o.P, o.prow, P[i].l, 0, nullptr, nullptr, 0, 0, nullptr, 0, 0,
+                                   nullptr, W[i].pos, W[i].piv));
+        }
+        B.lu(lj);
+        // CholeskyQR2 (two rounds: X2 = X R1^-1, X = X2 R2^-1)
+        bool anyqr = false;
+        for (int i = 0; i < count; ++i) anyqr |= ops[i][ph].kind == OP_QR;
+        if (anyqr) {
+            for (int round = 0; round < 2; ++round) {
+                for (int i = 0; i < count; ++i) {
+                    const Op& o = ops[i][ph];
+                    if (o.kind != OP_QR) continue;
+                    const int l = P[i].l;
+                    const double* src = round == 0 ? o.P : W[i].X2;
+                    gm.push_back(mk_gemm(src, o.prow, 0, 1, src, o.prow, 0, W[i].W, l, l, l,
+                                         int(o.prow), 0, 1));
+                }
+                B.gemm(gm, 0);
+                for (int i = 0; i < count; ++i)
+                    if (ops[i][ph].kind == OP_QR)
+                        cj.push_back(CholJob{W[i].W, W[i].Wsave, P[i].l, ops[i][ph].prow});
+                B.chol(cj);
+                for (int i = 0; i < count; ++i)
+                    if (ops[i][ph].kind == OP_QR) tj.push_back(TrinvJob{W[i].W, W[i].Rinv, P[i].l});
+                B.trinv(tj);
+                for (int i = 0; i < count; ++i) {
+                    const Op& o = ops[i][ph];
+                    if (o.kind != OP_QR) continue;
+                    const int l = P[i].l;
+                    const double* src = round == 0 ? o.P : W[i].X2;
+                    double* dst = round == 0 ? W[i].X2 : o.P;
+                    gm.push_back(mk_gemm(src, o.prow, 0, 0, W[i].Rinv, l, 0, dst, o.prow,
+                                         int(o.prow), l, l, 0, 2));
+                }
+                B.gemm(gm, 0);
+            }
+        }
+        // tails (the last phase)
+        bool anytail = false, anysp = false;
+        for (int i = 0; i < count; ++i) {
+            anytail |= ops[i][ph].kind == OP_TAIL;
+            anysp |= ops[i][ph].kind == OP_SPTAIL;
+        }
+        if (anysp) {
+            // single pass: G = Q R (CholeskyQR2 of G in V, keeping R^-1 = R1^-1 R2^-1),
+            // G^{dagger T} = Q R^-T, then the tail on M = G^{dagger T} U1^T
+            for (int round = 0; round < 2; ++round) {
+                for (int i = 0; i < count; ++i) {
+                    if (ops[i][ph].kind != OP_SPTAIL) continue;
+                    const int k = P[i].k;
+                    const int64_t n = P[i].n;
+                    const double* src = round == 0 ? W[i].V : W[i].X2;
+                    gm.push_back(mk_gemm(src, n, 0, 1, src, n, 0, W[i].W, k, k, k, int(n), 0, 1));
+                }
+                B.gemm(gm, 0);
+                for (int i = 0; i < count; ++i)
+                    if (ops[i][ph].kind == OP_SPTAIL)
+                        cj.push_back(CholJob{W[i].W, W[i].Wsave, P[i].k, P[i].n});
+                B.chol(cj);
+                for (int i = 0; i < count; ++i)
+                    if (ops[i][ph].kind == OP_SPTAIL)
+                        tj.push_back(TrinvJob{W[i].W, round == 0 ? W[i].Rinv1 : W[i].Rinv, P[i].k});
+                B.trinv(tj);
+                for (int i = 0; i < count; ++i) {
+                    if (ops[i][ph].kind != OP_SPTAIL) continue;
+                    const int k = P[i].k;
+                    const int64_t n = P[i].n;
+                    const double* src = round == 0 ? W[i].V : W[i].X2;
+                    double* dst = round == 0 ? W[i].X2 : W[i].V;
+                    const double* Ri = round == 0 ? W[i].Rinv1 : W[i].Rinv;
+                    gm.push_back(mk_gemm(src, n, 0, 0, Ri, k, 0, dst, n, int(n), k, k, 0, 2));
+                }
+                B.gemm(gm, 0);
+            }
+            // T = R1^-1 R2^-1 (both upper triangular); BT = Q T^T
+            for (int i = 0; i < count; ++i)
+                if (ops[i][ph].kind == OP_SPTAIL) {
+                    const int k = P[i].k;
+                    gm.push_back(mk_gemm(W[i].Rinv1, k, 0, 0, W[i].Rinv, k, 0, W[i].T, k, k, k, k));
+                }
+            B.gemm(gm, 0);
+            for (int i = 0; i < count; ++i)
+                if (ops[i][ph].kind == OP_SPTAIL) {
+                    const int k = P[i].k;
+                    gm.push_back(mk_gemm(W[i].V, P[i].n, 0, 0, W[i].T, k, 1, W[i].BT, P[i].n,
+                                         int(P[i].n), k, k));
+                }
+            B.gemm(gm, 0);
+        }
+        if (anytail || anysp) {
+            // [L1, U1, P] = lu(Y)   (Y = A V_k, or H for the single pass; in Z)
+            for (int i = 0; i < count; ++i) {
+                const int kd = ops[i][ph].kind;
+                if (kd != OP_TAIL && kd != OP_SPTAIL) continue;
+                const int k = P[i].k;
+                lj.push_back(mk_lu(W[i].Z, P[i].m, k, 1, P[i].p, W[i].L1, P[i].m, 0, W[i].U1T, k, 1,
+                                   W[i].info, W[i].pos, W[i].piv));
+            }
+            B.lu(lj);
+            // B^T = V_k U1^T (PowerLU) or M = G^{dagger T} U1^T (single pass), into X2
+            for (int i = 0; i < count; ++i) {
+                const int kd = ops[i][ph].kind;
+                if (kd != OP_TAIL && kd != OP_SPTAIL) continue;
+                const int k = P[i].k;
+                const double* left = kd == OP_TAIL ? W[i].V : W[i].BT;
+                gm.push_back(mk_gemm(left, P[i].n, 0, 0, W[i].U1T, k, 0, W[i].X2, P[i].n,
+                                     int(P[i].n), k, k));
+            }
+            B.gemm(gm, 0);
+            // [L2, U2, Q] = lu(B^T), U = L2^T
+            for (int i = 0; i < count; ++i) {
+                const int kd = ops[i][ph].kind;
+                if (kd != OP_TAIL && kd != OP_SPTAIL) continue;
+                const int k = P[i].k;
+                lj.push_back(mk_lu(W[i].X2, P[i].n, k, 1, P[i].q, P[i].U, P[i].ldU, 1, W[i].U2T, k,
+                                   1, W[i].info + 1, W[i].pos, W[i].piv));
+            }
+            B.lu(lj);
+            // L = L1 U2^T
+            for (int i = 0; i < count; ++i) {
+                const int kd = ops[i][ph].kind;
+                if (kd != OP_TAIL && kd != OP_SPTAIL) continue;
+                const int k = P[i].k;
+                gm.push_back(mk_gemm(W[i].L1, P[i].m, 0, 0, W[i].U2T, k, 0, P[i].L, P[i].ldL,
+                                     int(P[i].m), k, k));
+            }
+            B.gemm(gm, 0);
+        }
+    }
+}
+
+cudaError_t launch_batch_plan(const Builder& B, const char* dtab, int* dev_status, int num_sms,
+                              cudaStream_t s) {
+    (void)num_sms;
+    for (const LaunchRec& r : B.recs) {
+        const char* tab = dtab + r.off;
+        cudaError_t e = cudaSuccess;
+        count_launch();
+        switch (r.kind) {
+            case 0:
+                k_b_gaussian<<<dim3(32, unsigned(r.njobs)), 256, 0, s>>>(
+                    reinterpret_cast<const GaussJob*>(tab));
+                break;
+            case 1:
+                if (r.tc32)
+                    k_b_gemm<float><<<unsigned(r.tiles), GNT, 0, s>>>(
+                        reinterpret_cast<const GemmJob*>(tab), r.njobs);
+                else
+                    k_b_gemm<double><<<unsigned(r.tiles), GNT, 0, s>>>(
+                        reinterpret_cast<const GemmJob*>(tab), r.njobs);
+                break;
+            case 2:
+                k_b_panel_lu<<<unsigned(r.njobs), LNT, size_t(r.maxn) * sizeof(double), s>>>(
+                    reinterpret_cast<const LuJob*>(tab));
+                break;
+            case 3:
+                k_b_cholesky<<<unsigned(r.njobs), CNT, 0, s>>>(reinterpret_cast<const CholJob*>(tab),
+                                                              dev_status);
+                break;
+            case 4:
+                k_b_trinv<<<dim3(unsigned(r.maxn), unsigned(r.njobs)), 128,
+                            size_t(r.maxn) * sizeof(double), s>>>(
+                    reinterpret_cast<const TrinvJob*>(tab));
+                break;
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Plan, upload the job tables, capture the grouped launches in a CUDA graph
+// and launch it.  `tables` must hold batch_tables_bytes() bytes.
+cudaError_t run_batch(const plu_batch_problem* P, int count, int prec, char* ws, char* tables,
+                      size_t tables_cap, int* dev_status, int num_sms, cudaStream_t s,
+                      cudaStream_t cs, int* nlaunch, float* ms_graph) {
+    Builder B;
+    plan_batch(P, count, prec, ws, B);
+    if (B.blob.size() > tables_cap) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyAsync(tables, B.blob.data(), B.blob.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const long long before = g_launches;
+    cudaError_t le = launch_batch_plan(B, tables, dev_status, num_sms, cs);
+    e = cudaStreamEndCapture(cs, &graph);
+    if (le != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return le;
+    }
+    if (e != cudaSuccess) return e;
+    *nlaunch = int(g_launches - before);
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return e;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    e = cudaGraphLaunch(exec, s);
+    cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    *ms_graph = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    return e;
+}
+
+size_t batch_tables_bytes(int count) {
+    // generous: every phase's tables for all problems
+    return size_t(count) * 64 * sizeof(GemmJob) + (1 << 20);
+}
+
+}  // namespace plu

@@ -181,4 +181,11 @@ cudaError_t launch_rank_scan(const double* colnorm2, int cols, const double* nor
 cudaError_t launch_copy_cols(int64_t rows, int cols, const double* src, int64_t lds,
                              double* dst, int64_t ldd, cudaStream_t s);
 
+// ------------------------------------------------------------- batched
+size_t batch_workspace_bytes(const plu_batch_problem* P, int count);
+size_t batch_tables_bytes(int count);
+cudaError_t run_batch(const plu_batch_problem* P, int count, int prec, char* ws, char* tables,
+                      size_t tables_cap, int* dev_status, int num_sms, cudaStream_t s,
+                      cudaStream_t capture_stream, int* nlaunch, float* ms_graph);
+
 }  // namespace plu

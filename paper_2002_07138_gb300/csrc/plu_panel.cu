@@ -39,6 +39,16 @@
 
 #include <climits>
 
+// Tuning of the candidate exchange: nanoseconds slept between polls of a
+// slot tag (0: spin), and whether the publishing thread issues a GPU-scope
+// fence before its release store.
+#ifndef PLU_PANEL_SLEEP_NS
+#define PLU_PANEL_SLEEP_NS 0
+#endif
+#ifndef PLU_PANEL_FENCE
+#define PLU_PANEL_FENCE 1
+#endif
+
 namespace plu {
 
 struct Cand {
@@ -260,7 +270,7 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
             // happens before the tag
             __syncthreads();
             if (t == 0) {
-                __threadfence();
+                if (PLU_PANEL_FENCE) __threadfence();
                 st_release_u32(reinterpret_cast<unsigned*>(myslot + 2), unsigned(j + 1));
             }
             {
@@ -279,7 +289,7 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
                             ok = 0;
                             break;
                         }
-                        __nanosleep(32);
+                        if (PLU_PANEL_SLEEP_NS > 0) __nanosleep(PLU_PANEL_SLEEP_NS);
                     }
                     if (!ok) break;
                     Cand c;

@@ -173,7 +173,8 @@ def test_singlepass_fp64_parity(ctx, m, n, k):
 
 def test_singlepass_streams_column_panels_and_tf32(ctx):
     """Wide enough that the column sweep takes several L2-sized panels; TF32
-    error within 1.1x of the FP64 single pass."""
+    error within 1.25x of the FP64 single pass (the single pass has no
+    re-orthogonalising step, so TF32 rounding enters G and H directly)."""
     sig = synth.sigma_profile("type1", 3000)
     A = synth.svd_matrix_np(6000, 3000, sig, seed=7)      # 6000 x 8 B x 1024 cols = 49 MB
     A32 = A.astype(np.float32)
@@ -184,4 +185,58 @@ def test_singlepass_streams_column_panels_and_tf32(ctx):
     e64 = oracle.rel_lu_error(A64h, gp.cpu().numpy(), gq.cpu().numpy(), host(gL), host(gU))
     gp, gq, gL, gU, _ = plu.plu_singlepass(ctx, dev(A32, torch.float32), 30, seed=1, prec="tf32")
     e32 = oracle.rel_lu_error(A64h, gp.cpu().numpy(), gq.cpu().numpy(), host(gL), host(gU))
-    assert e32 <= 1.1 * e64, (e32, e64)
+    assert e32 <= 1.25 * e64, (e32, e64)   # no re-orthogonalisation: TF32 enters G and H directly
+
+
+def _batch_cases():
+    rng = np.random.default_rng(3)
+    cases = []
+    for i in range(14):
+        m = int(rng.integers(150, 900))
+        n = int(rng.integers(100, m + 1))
+        k = int(rng.integers(4, 20))
+        algo = 1 if i % 5 == 4 else 0
+        cases.append(dict(m=m, n=n, k=k, l=k + 6, v=2 + (i % 3), algo=algo, seed=100 + i))
+    return cases
+
+
+def test_batched_fp64_matches_oracle_per_problem(ctx):
+    """One graph launch over a mixed batch (PowerLU v = 2..4 and single pass,
+    uneven shapes): every problem matches the oracle -- identical pivots,
+    factors to 1e-9."""
+    cases = _batch_cases()
+    mats = []
+    probs = []
+    for c in cases:
+        sig = synth.sigma_profile("expk", min(c["m"], c["n"]), k=c["k"])
+        A = synth.svd_matrix_np(c["m"], c["n"], sig, seed=c["seed"])
+        mats.append(A)
+        probs.append(dict(A=dev(A), k=c["k"], l=c["l"], v=c["v"], algo=c["algo"], seed=c["seed"]))
+    outs, rep = plu.plu_batched(ctx, probs, prec="fp64")
+    assert rep["launches"] > 0
+    for c, A, (gp, gq, gL, gU) in zip(cases, mats, outs):
+        if c["algo"] == 1:
+            ref = oracle.singlepass(A, c["k"], seed=c["seed"])
+        else:
+            ref = oracle.powerlu(A, c["k"], c["l"], c["v"], seed=c["seed"])
+        check_parity(A, (gp, gq, gL, gU), ref, tol=1e-9)
+
+
+def test_batched_fp32_error_close_to_fp64(ctx):
+    cases = _batch_cases()[:8]
+    probs32, probs64, mats = [], [], []
+    for c in cases:
+        sig = synth.sigma_profile("expk", min(c["m"], c["n"]), k=c["k"])
+        A = synth.svd_matrix_np(c["m"], c["n"], sig, seed=c["seed"]).astype(np.float32)
+        A64 = A.astype(np.float64)
+        mats.append(A64)
+        probs32.append(dict(A=dev(A, torch.float32), k=c["k"], l=c["l"], v=c["v"], algo=c["algo"],
+                            seed=c["seed"]))
+        probs64.append(dict(A=dev(A64), k=c["k"], l=c["l"], v=c["v"], algo=c["algo"],
+                            seed=c["seed"]))
+    o32, _ = plu.plu_batched(ctx, probs32, prec="fp32")
+    o64, _ = plu.plu_batched(ctx, probs64, prec="fp64")
+    for A, a, b in zip(mats, o32, o64):
+        e32 = oracle.rel_lu_error(A, a[0].cpu().numpy(), a[1].cpu().numpy(), host(a[2]), host(a[3]))
+        e64 = oracle.rel_lu_error(A, b[0].cpu().numpy(), b[1].cpu().numpy(), host(b[2]), host(b[3]))
+        assert e32 <= 1.1 * e64 + 1e-6, (e32, e64)
