@@ -4,9 +4,12 @@
 One step = one fixed-rank PowerLU call (Alg. bpowerlu with Alg. gpowerlu:
 Gaussian sketch, v passes over A, LU re-orthogonalisation, QR, final pass,
 two LUs and the tail products) through the C ABI, on a seeded synthetic A
-already resident in HBM.  Default workload: m = n = 8192, sigma_i = exp(-i/20)
-plus a 1e-6 N(0,1)/sqrt(n) floor, k = 100, l = 110, v = 3, A stored in FP32
-(larger than L2, so no flush is needed between steps).
+already resident in HBM.  Default workload: the mixed-precision one, m = n =
+32768, A stored in FP32 (4.3 GB, larger than L2, so no flush is needed
+between steps), sigma_i = i^-1.5, k = 256, l = 276, v = 3, passes on TF32
+tensor cores; the BF16 and FP8-E4M3 passes are reported beside it.
+--workload fixed_rank_8192 runs the 8192^2 FP32 workload, batched_512 the
+batch of 512 problems.
 
 value = algorithmic pass flops (2 m n l per power pass + 2 m n k for the
 last pass) over the whole call time, in TFLOP/s, summed over ranks.
@@ -40,6 +43,7 @@ METRIC = "PowerLU ms & TFLOP/s per pass of A at stated rel. error, mixed vs FP64
 def workloads():
     import synth
     return {"fixed_rank_8192": synth.FIXED_RANK_8192, "mixed_32768": synth.MIXED_32768,
+            "mixed_16384": synth.MIXED_16384,
             "plain_2000x1500": synth.PLAIN_2000x1500, "batched_512": None}
 
 
@@ -252,6 +256,32 @@ def oracle_call(A, w, seed):
     return time.perf_counter() - t0, (p, q, L, U)
 
 
+FULL_ORACLE_MAX_MN = 1 << 27          # larger workloads time a bounded sample
+
+
+def oracle_sample(A, w, seed):
+    """Time the oracle on a bounded sample of the workload: the whole call
+    when A is small, otherwise the first pass of Alg. gpowerlu (A^T Omega or
+    A Omega) and the LU re-orthogonalisation of its result.  Returns
+    (seconds, pass flops of the sample, description)."""
+    import oracle
+    m, n = A.shape
+    if m * n <= FULL_ORACLE_MAX_MN:
+        dt, _ = oracle_call(A, w, seed)
+        return dt, pass_flops(m, n, w.k, w.l, w.v), "one full oracle PowerLU call"
+    t0 = time.perf_counter()
+    if w.v % 2 == 0:
+        Om = oracle.gaussian_matrix(m, w.l, seed, oracle.STREAM_OMEGA_M)
+        Y = A.T @ Om
+    else:
+        Om = oracle.gaussian_matrix(n, w.l, seed, oracle.STREAM_OMEGA_N)
+        Y = A @ Om
+    oracle.lu_permuted_L(Y)
+    dt = time.perf_counter() - t0
+    return dt, 2.0 * m * n * w.l, ("the oracle's first pass of Alg. gpowerlu (one FP64 product "
+                                   "with A) and its LU re-orthogonalisation")
+
+
 def build_host_matrix(w, seed_offset=0):
     """The workload's A as a float64 numpy array (built on the GPU when one is
     present, then copied; otherwise with numpy)."""
@@ -277,12 +307,11 @@ def run_reference(args, w):
     if rank != 0:
         return 0
     A = build_host_matrix(w)
-    flops = pass_flops(w.m, w.n, w.k, w.l, w.v)
     for i in range(args.warmup):
-        oracle_call(A, w, seed=i)
+        oracle_sample(A, w, seed=i)
     times = []
     for i in range(args.steps):
-        dt, _ = oracle_call(A, w, seed=i)
+        dt, flops, desc = oracle_sample(A, w, seed=i)
         times.append(dt)
     total = sum(times)
     value = flops * args.steps / total / 1e12
@@ -295,7 +324,7 @@ def run_reference(args, w):
         "config": {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "l": w.l, "v": w.v,
                    "storage": "f64 (host)", "l2_flush": "inputs larger than L2"},
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                         "sample": "one full oracle PowerLU call per step on the same matrix"},
+                         "sample": desc + " per step, on the same matrix"},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -359,7 +388,9 @@ def kernel_rooflines(torch, plu, ctx, Ad, w, prec, stream, peaks):
     ms = time_calls(torch, lambda: (Xc.copy_(X), plu.plu_qr(ctx, Xc)), 3, stream)
     ms_copy = time_calls(torch, lambda: Xc.copy_(X), 3, stream)
     ms = max(ms - ms_copy, 1e-6)
-    fl = 2 * (2.0 * n * l * l + 2.0 * n * l * l + l ** 3 / 3.0 + l ** 3 / 3.0)
+    # CholeskyQR2: per round, the symmetric Gram n l^2, the triangular product
+    # X R^-1 n l^2, the Cholesky l^3/3 and the triangular inverse l^3/3 flops
+    fl = 2 * (2.0 * n * l * l + 2.0 * l ** 3 / 3.0)
     out["qr"] = (ms, 1, {"bound": "alu", "achieved": fl / ms / 1e9, "peak": fp64_peak,
                          "unit": "TFLOP/s", "peak_source": "nominal FP64 1.25 TFLOP/s"},
                  "cholqr2")
@@ -427,9 +458,9 @@ def run_ours(args, w):
     opt = float(np.sqrt(np.sum(w.sigma_values()[w.k:] ** 2) / np.sum(w.sigma_values() ** 2)))
 
     # FP64 plain: the same workload with every step in FP64
-    A64 = synth_colmajor(Ad.double())
     fp64 = {}
     if not args.skip_fp64:
+        A64 = synth_colmajor(Ad.double())
         call(0, A64, "fp64")
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
@@ -445,7 +476,7 @@ def run_ours(args, w):
                 "rel_error": rel_error(call(7, A64, "fp64"), Ad),
                 "tflops_per_pass": (flops / w.v) / (statistics.mean(
                     r["ms_passes"] / r["passes"] for r in r64) / 1e3) / 1e12}
-    del A64
+        del A64
 
     # end to end through host buffers: H2D of A, the call, D2H of p, q, L, U
     Ah = torch.empty(Ad.shape[1], Ad.shape[0], dtype=Ad.dtype, pin_memory=True).t()
@@ -490,10 +521,29 @@ def run_ours(args, w):
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
         Ahost = Ad.double().cpu().numpy()
-        dt, _ = oracle_call(Ahost, w, seed=0)
-        cpu = {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
-               "kind": "oracle", "sample": "one full oracle PowerLU call (FP64, numpy BLAS) on "
-               "the same %dx%d matrix, %.1f s" % (w.m, w.n, dt)}
+        dt, sfl, desc = oracle_sample(Ahost, w, seed=0)
+        del Ahost
+        cpu = {"value": sfl / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
+               "kind": "oracle", "sample": "%s (FP64, numpy BLAS) on the same %dx%d matrix, "
+               "%.1f s" % (desc, w.m, w.n, dt)}
+
+    # the other mixed precisions on the same matrix (one call each)
+    by_prec = {}
+    if not args.skip_fp64 and Ad.dtype == torch.float32:
+        for pr in ("tf32", "bf16", "fp8"):
+            if pr == prec:
+                continue
+            call(0, Ad, pr)
+            torch.cuda.synchronize()
+            t0e = torch.cuda.Event(enable_timing=True)
+            t1e = torch.cuda.Event(enable_timing=True)
+            t0e.record(stream)
+            res = call(4000, Ad, pr)
+            t1e.record(stream)
+            torch.cuda.synchronize()
+            by_prec[pr] = {"ms_per_step": t0e.elapsed_time(t1e),
+                           "ms_per_pass": res[4]["ms_passes"] / res[4]["passes"],
+                           "rel_error": rel_error(res, Ad)}
 
     if rank == 0:
         line = {
@@ -511,6 +561,7 @@ def run_ours(args, w):
             "tflops_per_pass": (flops / w.v) / (ms_pass / 1e3) / 1e12,
             "rel_error": err, "eckart_young_optimum": opt,
             "fp64_plain": fp64,
+            "other_precisions": by_prec,
             "speedup_vs_fp64_plain": (fp64["ms_per_step"] / (ms_max / args.steps)) if fp64 else None,
             "e2e": {"value": flops * ws / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s",
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -537,8 +588,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fixed_rank_8192", choices=sorted(workloads()))
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "tf32", "bf16", "fp8"])
+    ap.add_argument("--workload", default="mixed_32768", choices=sorted(workloads()))
+    ap.add_argument("--prec", default="tf32", choices=["fp64", "fp32", "tf32", "bf16", "fp8"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     args = ap.parse_args()

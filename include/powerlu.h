@@ -37,9 +37,12 @@ extern "C" {
 /* Arithmetic of the passes over A (Sec. 3.3 counts them; v passes).
  * PLU_FP64: FP64 FMA.  PLU_FP32: FP32 FMA, FP32 accumulation.
  * PLU_TF32, PLU_BF16, PLU_FP8_E4M3: tensor-core products with FP32
- * accumulation (A converted to the operand type); the last pass Y = A V_k
- * (and G = A V) is then taken in split precision.  Everything between the
- * passes (LU, QR, rank, tail) is FP64 in every mode. */
+ * accumulation.  TF32 reads the FP32 A directly; BF16 and FP8 read a
+ * quantised copy made once per call (FP8 with per-tile scales).  In these
+ * modes the last pass Y = A V_k reads the FP32 A through TF32, and the
+ * fixed-precision pass G = A V (whose column norms decide the rank) runs in
+ * FP32 arithmetic.  Everything between the passes (LU, QR, rank, tail) is
+ * FP64 in every mode. */
 typedef enum {
     PLU_FP64 = 0,
     PLU_TF32 = 1,

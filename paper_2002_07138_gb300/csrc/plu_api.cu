@@ -146,37 +146,45 @@ size_t pass_ws(int64_t M, int64_t N, int64_t K, int prec, int sms) {
 // One pass over A.  BF16 / FP8 passes read the quantized copy q (made once
 // per call); TF32 reads the FP32 A directly; shapes the tensor-core kernel
 // does not take (more than 512 columns, unaligned A) use the FP32 SIMT kernel.
+// ws holds ws_cap bytes; a shape that needs more is an error, never an overrun.
 plu_status do_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X, int64_t ldx,
-                   int cols, int prec, double* Y, int64_t ldy, char* ws,
+                   int cols, int prec, double* Y, int64_t ldy, char* ws, size_t ws_cap,
                    const QuantA* q = nullptr, int accum = 0) {
     const int64_t M = trans ? A->n : A->m;
     const int64_t K = trans ? A->m : A->n;
     if ((prec == PLU_BF16 || prec == PLU_FP8_E4M3) && q && cols <= 512) {
-        PLU_CUDA(c, launch_tc_pass_q(trans, *q, X, ldx, cols, Y, ldy, ws, c->d_status, c->num_sms,
-                                     c->stream, accum));
+        PLU_CUDA(c, launch_tc_pass_q(trans, *q, X, ldx, cols, Y, ldy, ws, ws_cap, c->d_status,
+                                     c->num_sms, c->stream, accum));
         return PLU_OK;
     }
     if (is_tc(prec) && A->dtype == PLU_F32 && tc_supported(M, K, cols, A->data, A->ld, trans)) {
         PLU_CUDA(c, launch_tc_pass(trans, A->m, A->n, static_cast<const float*>(A->data), A->ld, X,
-                                   ldx, cols, Y, ldy, ws, c->d_status, c->num_sms, c->stream,
-                                   accum));
+                                   ldx, cols, Y, ldy, ws, ws_cap, c->d_status, c->num_sms,
+                                   c->stream, accum));
         return PLU_OK;
     }
     if (is_tc(prec)) prec = PLU_FP32;
     Workspace w;
     w.base = ws;
-    w.cap = pass_ws(M, cols, K, prec, c->num_sms);
-    void* part = w.take(gemm_partials_bytes(M, cols, K, prec, c->num_sms));
+    w.cap = ws_cap;
     float* b32 = nullptr;
-    if (prec == PLU_FP32) b32 = static_cast<float*>(w.take(size_t(K) * cols * sizeof(float)));
+    if (prec == PLU_FP32) {
+        b32 = static_cast<float*>(w.take(size_t(K) * cols * sizeof(float)));
+        if (!b32) return fail(c, PLU_ENOMEM, "pass scratch too small");
+    }
+    // the rest holds the split-K partial sums
+    const size_t off = (w.used + 255) & ~size_t(255);
+    const size_t part_cap = ws_cap > off ? ws_cap - off : 0;
+    void* part = w.take(part_cap);
     PLU_CUDA(c, launch_gemm_simt(trans, M, cols, K, A->data, A->dtype, A->ld, X, ldx, Y, ldy, prec,
-                                 part, b32, c->num_sms, c->stream, accum));
+                                 part, part_cap, b32, c->num_sms, c->stream, accum));
     return PLU_OK;
 }
 
 struct PowerLUPlan {
     // offsets into the workspace
     size_t V, Z, step, L1, U1T, BT, U2T, tailpart, cn, quant, total;
+    size_t step_bytes, tailpart_bytes;
 };
 
 // Shared by the fixed-rank and fixed-precision drivers: workspace for
@@ -195,14 +203,22 @@ PowerLUPlan plan_powerlu(int64_t m, int64_t n, int l, int kmax, int prec, int sm
     t = qr_scratch_bytes(n, l, sms);
     if (t > step) step = t;
     p.step = lay.add(step);
+    p.step_bytes = step;
     p.L1 = lay.add(size_t(m) * kmax * sizeof(double));
     p.U1T = lay.add(size_t(kmax) * kmax * sizeof(double));
     p.BT = lay.add(size_t(n) * kmax * sizeof(double));
     p.U2T = lay.add(size_t(kmax) * kmax * sizeof(double));
-    size_t tp = gemm_f64_partials_bytes(n, kmax, kmax, sms);
-    t = gemm_f64_partials_bytes(m, kmax, kmax, sms);
-    if (t > tp) tp = t;
+    // the tail runs at any rank k <= kmax (fixed precision): the largest
+    // preferred partial-sum size over those ranks
+    size_t tp = 0;
+    for (int kk = 1; kk <= kmax; ++kk) {
+        t = gemm_f64_partials_bytes(n, kk, kk, sms);
+        if (t > tp) tp = t;
+        t = gemm_f64_partials_bytes(m, kk, kk, sms);
+        if (t > tp) tp = t;
+    }
     p.tailpart = lay.add(tp);
+    p.tailpart_bytes = tp;
     p.cn = lay.add(size_t(l) * sizeof(double) + norm2_scratch_bytes(sms));
     p.quant = (prec == PLU_BF16 || prec == PLU_FP8_E4M3) ? lay.add(tc_quant_bytes(m, n, prec)) : 0;
     p.total = lay.total + 256;
@@ -236,15 +252,18 @@ struct PassTimer {
 };
 
 // Alg. gpowerlu into V (n x l).  Returns the number of passes launched.
+// The final QR orthonormalises only the leading qr_cols columns of the
+// n x l product: Q(:, 1:j) depends on X(:, 1:j) alone, and the fixed-rank
+// path reads only V(:, 1:k) (Alg. bpowerlu step 3 and the tail).
 plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t seed, int prec,
-                        double* V, double* Z, char* step, PassTimer& pt, int* passes,
-                        const QuantA* q) {
+                        double* V, double* Z, char* step, size_t step_cap, PassTimer& pt,
+                        int* passes, const QuantA* q, int qr_cols) {
     const int64_t m = A->m, n = A->n;
     const int p = (v - 1) / 2;
     int np = 0;
     auto pass = [&](int trans, const double* X, int64_t ldx, double* Y, int64_t ldy) -> plu_status {
         pt.mark();
-        PLU_TRY(do_pass(c, A, trans, X, ldx, l, prec, Y, ldy, step, q));
+        PLU_TRY(do_pass(c, A, trans, X, ldx, l, prec, Y, ldy, step, step_cap, q));
         pt.mark();
         ++np;
         return PLU_OK;
@@ -256,7 +275,8 @@ plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t 
         return PLU_OK;
     };
     auto qr = [&](double* X) -> plu_status {
-        PLU_CUDA(c, launch_cholqr2(n, l, X, n, nullptr, 0, step, c->d_status, c->num_sms, c->stream));
+        PLU_CUDA(c, launch_cholqr2(n, qr_cols, X, n, nullptr, 0, step, step_cap, c->d_status,
+                                   c->num_sms, c->stream));
         return PLU_OK;
     };
     if (v % 2 == 0) {
@@ -290,13 +310,15 @@ plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const do
     // [L1, U1, P] = lu(Y)
     PLU_CUDA(c, launch_panel_lu(m, k, Y, m, 1, p, L1, m, 0, U1T, k, 1, info2dev, step, c->d_status,
                                 c->spin_budget, c->num_sms, c->stream));
-    // B^T = Vk U1^T
-    PLU_CUDA(c, launch_gemm_f64(0, 0, n, k, k, Vk, n, U1T, k, BT, n, tp, c->num_sms, c->stream));
+    // B^T = Vk U1^T (U1^T lower triangular)
+    PLU_CUDA(c, launch_gemm_f64_tri(0, 3, n, k, k, Vk, n, U1T, k, BT, n, tp, pl.tailpart_bytes,
+                                    c->num_sms, c->stream));
     // [L2, U2, Q] = lu(B^T); U = L2^T written straight into U
     PLU_CUDA(c, launch_panel_lu(n, k, BT, n, 1, q, U, ldU, 1, U2T, k, 1, info2dev + 1, step,
                                 c->d_status, c->spin_budget, c->num_sms, c->stream));
-    // L = L1 U2^T
-    PLU_CUDA(c, launch_gemm_f64(0, 0, m, k, k, L1, m, U2T, k, L, ldL, tp, c->num_sms, c->stream));
+    // L = L1 U2^T (U2^T lower triangular)
+    PLU_CUDA(c, launch_gemm_f64_tri(0, 3, m, k, k, L1, m, U2T, k, L, ldL, tp, pl.tailpart_bytes,
+                                    c->num_sms, c->stream));
     return PLU_OK;
 }
 
@@ -420,12 +442,13 @@ plu_status plu_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X,
     if (cols < 1 || !X || !Y || ldx < K || ldy < M) return fail(c, PLU_EINVAL, "bad pass operands");
     const bool quant = (prec == PLU_BF16 || prec == PLU_FP8_E4M3) && cols <= 512;
     const size_t qb = quant ? ((tc_quant_bytes(A->m, A->n, prec) + 255) & ~size_t(255)) : 0;
-    PLU_TRY(ensure_ws(c, qb + pass_ws(M, cols, K, prec, c->num_sms)));
+    const size_t pw = pass_ws(M, cols, K, prec, c->num_sms);
+    PLU_TRY(ensure_ws(c, qb + pw));
     QuantA q;
     if (quant)
         PLU_CUDA(c, launch_tc_quantize(prec, static_cast<const float*>(A->data), A->m, A->n, A->ld,
                                        c->ws, &q, c->num_sms, c->stream));
-    PLU_TRY(do_pass(c, A, trans, X, ldx, cols, prec, Y, ldy, c->ws + qb, quant ? &q : nullptr));
+    PLU_TRY(do_pass(c, A, trans, X, ldx, cols, prec, Y, ldy, c->ws + qb, pw, quant ? &q : nullptr));
     return finish(c);
 }
 
@@ -455,8 +478,10 @@ plu_status plu_qr(plu_ctx* c, int64_t rows, int cols, double* X, int64_t ldx, do
     PLU_TRY(bind(c));
     if (cols < 1 || rows < cols || !X || ldx < rows || (R && ldR < cols))
         return fail(c, PLU_EINVAL, "qr needs rows >= cols >= 1");
-    PLU_TRY(ensure_ws(c, qr_scratch_bytes(rows, cols, c->num_sms)));
-    PLU_CUDA(c, launch_cholqr2(rows, cols, X, ldx, R, ldR, c->ws, c->d_status, c->num_sms, c->stream));
+    const size_t qw = qr_scratch_bytes(rows, cols, c->num_sms);
+    PLU_TRY(ensure_ws(c, qw));
+    PLU_CUDA(c, launch_cholqr2(rows, cols, X, ldx, R, ldR, c->ws, qw, c->d_status, c->num_sms,
+                               c->stream));
     return finish(c);
 }
 
@@ -521,11 +546,13 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
     if (quant)
         PLU_CUDA(c, launch_tc_quantize(prec, static_cast<const float*>(A->data), m, n, A->ld,
                                        ws + pl.quant, &qa, c->num_sms, c->stream));
-    PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pt, &np, quant ? &qa : nullptr));
+    PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pl.step_bytes, pt, &np,
+                         quant ? &qa : nullptr, k));
     // Y = A V(:, 1:k) (Alg. bpowerlu step 3), the v-th pass; in the mixed
     // modes it reads the FP32 A through TF32 (it enters the result to first order)
     pt.mark();
-    PLU_TRY(do_pass(c, A, 0, V, n, k, is_tc(prec) ? int(PLU_TF32) : int(prec), Z, m, step));
+    PLU_TRY(do_pass(c, A, 0, V, n, k, is_tc(prec) ? int(PLU_TF32) : int(prec), Z, m, step,
+                    pl.step_bytes));
     pt.mark();
     ++np;
     int32_t* info = reinterpret_cast<int32_t*>(ws + pl.cn);
@@ -587,10 +614,15 @@ plu_status plu_powerlu_fp(plu_ctx* c, const plu_matrix* A, double eps, int b, in
     if (quant)
         PLU_CUDA(c, launch_tc_quantize(prec, static_cast<const float*>(A->data), m, n, A->ld,
                                        ws + pl.quant, &qa, c->num_sms, c->stream));
-    PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pt, &np, quant ? &qa : nullptr));
-    // G = A V (step 3), the v-th pass (FP32 A through TF32 in the mixed modes)
+    PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pl.step_bytes, pt, &np,
+                         quant ? &qa : nullptr, l));
+    // G = A V (step 3), the v-th pass.  Its column norms decide the rank:
+    // E = ||A||_F^2 - sum ||G(:, j)||^2 must resolve eps^2 ||A||_F^2, which
+    // TF32 rounding (relative bias ~1e-3) cannot, so the mixed modes take this
+    // pass in FP32 arithmetic on the FP32 A.
     pt.mark();
-    PLU_TRY(do_pass(c, A, 0, V, n, l, is_tc(prec) ? int(PLU_TF32) : int(prec), Z, m, step));
+    PLU_TRY(do_pass(c, A, 0, V, n, l, is_tc(prec) ? int(PLU_FP32) : int(prec), Z, m, step,
+                    pl.step_bytes));
     pt.mark();
     ++np;
     PLU_CUDA(c, launch_colnorm2(m, l, Z, m, cn, c->stream));
@@ -655,9 +687,14 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
     const size_t oW = lay.add(size_t(n) * dk), oL1 = lay.add(size_t(m) * dk);
     const size_t oR = lay.add(size_t(k) * dk), oRi = lay.add(size_t(k) * dk);
     const size_t oU1T = lay.add(size_t(k) * dk), oU2T = lay.add(size_t(k) * dk);
-    size_t step = pass_ws(wc, k, m, prec, c->num_sms);
-    size_t t = pass_ws(m, k, wc, prec, c->num_sms);
-    if (t > step) step = t;
+    size_t step = 0, t = 0;
+    for (int64_t w : {wc, n % wc}) {                // full panels and the last one
+        if (w == 0) continue;
+        t = pass_ws(w, k, m, prec, c->num_sms);
+        if (t > step) step = t;
+        t = pass_ws(m, k, w, prec, c->num_sms);
+        if (t > step) step = t;
+    }
     t = panel_scratch_bytes(m > n ? m : n, k);
     if (t > step) step = t;
     t = qr_scratch_bytes(n, k, c->num_sms);
@@ -697,8 +734,9 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
         plu_matrix Ap = *A;
         Ap.n = w;
         Ap.data = static_cast<const char*>(A->data) + size_t(j0) * size_t(A->ld) * size_t(es);
-        PLU_TRY(do_pass(c, &Ap, 1, Om, m, k, prec, G + j0, n, stepp));
-        PLU_TRY(do_pass(c, &Ap, 0, G + j0, n, k, prec, H, m, stepp, nullptr, j0 > 0 ? 1 : 0));
+        PLU_TRY(do_pass(c, &Ap, 1, Om, m, k, prec, G + j0, n, stepp, step));
+        PLU_TRY(do_pass(c, &Ap, 0, G + j0, n, k, prec, H, m, stepp, step, nullptr,
+                        j0 > 0 ? 1 : 0));
     }
     pt.mark();
     // [L1, U1, P] = lu(H)
@@ -706,15 +744,18 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
                                 c->spin_budget, c->num_sms, c->stream));
     // G^{dagger T} = G (G^T G)^{-1} = Q R^{-T} with G = Q R (CholeskyQR2)
     PLU_CUDA(c, cudaMemcpyAsync(Qb, G, size_t(n) * dk, cudaMemcpyDeviceToDevice, c->stream));
-    PLU_CUDA(c, launch_cholqr2(n, k, Qb, n, R, k, stepp, c->d_status, c->num_sms, c->stream));
+    PLU_CUDA(c, launch_cholqr2(n, k, Qb, n, R, k, stepp, step, c->d_status, c->num_sms, c->stream));
     PLU_CUDA(c, launch_trinv_upper(k, R, Rinv, c->stream));
-    PLU_CUDA(c, launch_gemm_f64(0, 1, n, k, k, Qb, n, Rinv, k, Wb, n, tpp, c->num_sms, c->stream));
+    PLU_CUDA(c, launch_gemm_f64(0, 1, n, k, k, Qb, n, Rinv, k, Wb, n, tpp, tp, c->num_sms,
+                                c->stream));
     // M = G^{dagger T} U1^T, [L2, U2, Q] = lu(M), U = L2^T
-    PLU_CUDA(c, launch_gemm_f64(0, 0, n, k, k, Wb, n, U1T, k, G, n, tpp, c->num_sms, c->stream));
+    PLU_CUDA(c, launch_gemm_f64(0, 0, n, k, k, Wb, n, U1T, k, G, n, tpp, tp, c->num_sms,
+                                c->stream));
     PLU_CUDA(c, launch_panel_lu(n, k, G, n, 1, q, U, ldU, 1, U2T, k, 1, info + 1, stepp,
                                 c->d_status, c->spin_budget, c->num_sms, c->stream));
     // L = L1 U2^T
-    PLU_CUDA(c, launch_gemm_f64(0, 0, m, k, k, L1, m, U2T, k, L, ldL, tpp, c->num_sms, c->stream));
+    PLU_CUDA(c, launch_gemm_f64(0, 0, m, k, k, L1, m, U2T, k, L, ldL, tpp, tp, c->num_sms,
+                                c->stream));
     if (rep) {
         PLU_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
         int32_t hinfo[2] = {0, 0};

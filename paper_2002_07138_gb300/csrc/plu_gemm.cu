@@ -5,11 +5,16 @@
 // Y = A^T X (n x m by m x l) with column-major A.  On GB300 FP64 FMA runs at
 // about 1/64 of the FP32 rate (~1 TFLOP/s), so the FP64 products are bound by
 // the FP64 pipe, not by HBM: a 64x64x16 register-tiled kernel (4x4 outputs per
-// thread, operands staged through padded shared memory) saturates it.  When
+// thread, operands staged through padded shared memory) saturates it.  Each
+// warp owns an 8-column strip of the tile, so the triangular products skip
+// the FMAs of known-zero terms warp by warp (16 x 8 granularity), not only
+// whole tiles: with the FP64 pipe as the bound, skipped FMAs are saved time.  When
 // the output has too few 64x64 tiles to fill 152 SMs the reduction dimension
 // is split; each split writes its partial tile and a second kernel sums the
 // splits in a fixed order, so results do not depend on scheduling.
 #include "plu_internal.h"
+
+#include <climits>
 
 namespace plu {
 namespace {
@@ -28,16 +33,24 @@ k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t l
     __shared__ TC As[2][BK][BM + 1];
     __shared__ TC Bs[2][BK][BN + 1];
     const int t = threadIdx.x;
-    const int tx = t % 16, ty = t / 16;
+    // warp w computes columns 8w .. 8w+7 of the tile: lane -> rows
+    // (lane % 16) + 16a and columns 8w + lane / 16 + 2b, a, b = 0..3
+    const int warp = t >> 5, lane = t & 31;
+    const int ty = lane & 15, tx = 8 * warp + (lane >> 4);
     const int64_t i0 = int64_t(blockIdx.x) * BM;
     const int64_t j0 = int64_t(blockIdx.y) * BN;
     const int64_t kbeg = int64_t(blockIdx.z) * kchunk;
     int64_t kend = min(K, kbeg + kchunk);
     // tri 1: only the upper triangle of C is wanted (tiles wholly below the
     // diagonal write zeros); tri 2: op(B) is upper triangular (rows k > j of
-    // column j are zero, so the reduction stops at the tile's last column)
+    // column j are zero, so the reduction stops at the tile's last column);
+    // tri 3: op(B) is lower triangular (rows k < j are zero, so the reduction
+    // starts at the tile's first column)
     if (tri == 1 && i0 >= j0 + BN) kend = kbeg;
     if (tri == 2 && kend > j0 + BN) kend = j0 + BN;
+    int64_t kstart = kbeg;
+    if (tri == 3 && kstart < j0) kstart = j0 / BK * BK;
+    if (kstart > kend) kstart = kend;
 
     TC ra[4], rb[4];
     auto load_a = [&](int64_t k0) {
@@ -83,15 +96,23 @@ k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t l
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = TC(0);
+    // the warp's useful reduction range [wlo, whi] (tri 2, 3) and row groups
+    // (tri 1: group a holds rows i0+16a.., wanted while i <= the strip's last column)
+    const int64_t wc0 = j0 + 8 * warp, wc1 = wc0 + 7;
+    const int64_t wlo = tri == 3 ? wc0 : INT64_MIN;
+    const int64_t whi = tri == 2 ? wc1 : INT64_MAX;
+    bool rowgrp[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) rowgrp[a] = tri != 1 || i0 + 16 * a <= wc1;
 
     int buf = 0;
-    if (kbeg < kend) {
-        load_a(kbeg);
-        load_b(kbeg);
+    if (kstart < kend) {
+        load_a(kstart);
+        load_b(kstart);
         store(0);
     }
     __syncthreads();
-    for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+    for (int64_t k0 = kstart; k0 < kend; k0 += BK) {
         const bool more = k0 + BK < kend;
         if (more) {
             load_a(k0 + BK);
@@ -99,15 +120,18 @@ k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t l
         }
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
+            if (k0 + kk < wlo || k0 + kk > whi) continue;   // warp-uniform
             TC av[4], bv[4];
 #pragma unroll
             for (int a = 0; a < 4; ++a) av[a] = As[buf][kk][ty + 16 * a];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) bv[b] = Bs[buf][kk][tx + 16 * b];
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[buf][kk][tx + 2 * b];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 4; ++a) {
+                if (!rowgrp[a]) continue;                     // warp-uniform
 #pragma unroll
                 for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+            }
         }
         if (more) store(buf ^ 1);
         __syncthreads();
@@ -120,7 +144,7 @@ k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t l
         if (gi >= M) continue;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const int64_t gj = j0 + tx + 16 * b;
+            const int64_t gj = j0 + tx + 2 * b;
             if (gj < N) Pz[gi + gj * M] = acc[a][b];
         }
     }
@@ -152,7 +176,8 @@ __global__ void k_f64_to_f32(int64_t rows, int64_t cols, const double* __restric
 
 int choose_splits(int64_t M, int64_t N, int64_t K, int num_sms) {
     const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-    const int64_t target = 4LL * num_sms;
+    // many CTAs per SM so that uneven tiles (triangular shortcuts) balance
+    const int64_t target = 16LL * num_sms;
     int64_t splits = (target + tiles - 1) / tiles;
     const int64_t max_by_k = (K + 8 * BK - 1) / (8 * BK);     // >= 8 k-steps per split
     if (splits > max_by_k) splits = max_by_k;
@@ -169,11 +194,17 @@ int grid_1d(int64_t work, int num_sms) {
     return int(b);
 }
 
+// The split count is the preferred one, lowered to what the partial-sum
+// buffer (part_cap bytes) holds; a buffer without room for one split is an
+// error, never an overrun.
 template <typename TA, typename TB, typename TC, bool TA_T, bool TB_T>
 cudaError_t run(int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda, const TB* B,
-                int64_t ldb, double* C, int64_t ldc, void* partials, int num_sms,
-                cudaStream_t s, int tri = 0, int accum = 0) {
-    const int splits = choose_splits(M, N, K, num_sms);
+                int64_t ldb, double* C, int64_t ldc, void* partials, size_t part_cap,
+                int num_sms, cudaStream_t s, int tri = 0, int accum = 0) {
+    int splits = choose_splits(M, N, K, num_sms);
+    const size_t one = size_t(M) * size_t(N) * sizeof(TC);
+    if (!partials || part_cap < one) return cudaErrorInvalidValue;
+    if (size_t(splits) * one > part_cap) splits = int(part_cap / one);
     int64_t kchunk = (K + splits - 1) / splits;
     kchunk = (kchunk + BK - 1) / BK * BK;
     dim3 grid(unsigned((M + BM - 1) / BM), unsigned((N + BN - 1) / BN), unsigned(splits));
@@ -203,7 +234,8 @@ size_t gemm_f64_partials_bytes(int64_t M, int64_t N, int64_t K, int num_sms) {
 cudaError_t launch_gemm_simt(int trans, int64_t M, int64_t N, int64_t K, const void* A,
                              int dtype, int64_t lda, const double* B, int64_t ldb,
                              double* C, int64_t ldc, int prec, void* partials,
-                             float* b32_scratch, int num_sms, cudaStream_t s, int accum) {
+                             size_t part_cap, float* b32_scratch, int num_sms, cudaStream_t s,
+                             int accum) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (prec == PLU_FP32) {
         count_launch();
@@ -212,45 +244,45 @@ cudaError_t launch_gemm_simt(int trans, int64_t M, int64_t N, int64_t K, const v
         if (e != cudaSuccess) return e;
         if (dtype == PLU_F32) {
             const float* Af = static_cast<const float*>(A);
-            return trans ? run<float, float, float, true, false>(M, N, K, Af, lda, b32_scratch, K, C, ldc, partials, num_sms, s, 0, accum)
-                         : run<float, float, float, false, false>(M, N, K, Af, lda, b32_scratch, K, C, ldc, partials, num_sms, s, 0, accum);
+            return trans ? run<float, float, float, true, false>(M, N, K, Af, lda, b32_scratch, K, C, ldc, partials, part_cap, num_sms, s, 0, accum)
+                         : run<float, float, float, false, false>(M, N, K, Af, lda, b32_scratch, K, C, ldc, partials, part_cap, num_sms, s, 0, accum);
         }
         const double* Ad = static_cast<const double*>(A);
-        return trans ? run<double, float, float, true, false>(M, N, K, Ad, lda, b32_scratch, K, C, ldc, partials, num_sms, s, 0, accum)
-                     : run<double, float, float, false, false>(M, N, K, Ad, lda, b32_scratch, K, C, ldc, partials, num_sms, s, 0, accum);
+        return trans ? run<double, float, float, true, false>(M, N, K, Ad, lda, b32_scratch, K, C, ldc, partials, part_cap, num_sms, s, 0, accum)
+                     : run<double, float, float, false, false>(M, N, K, Ad, lda, b32_scratch, K, C, ldc, partials, part_cap, num_sms, s, 0, accum);
     }
     if (dtype == PLU_F32) {
         const float* Af = static_cast<const float*>(A);
-        return trans ? run<float, double, double, true, false>(M, N, K, Af, lda, B, ldb, C, ldc, partials, num_sms, s, 0, accum)
-                     : run<float, double, double, false, false>(M, N, K, Af, lda, B, ldb, C, ldc, partials, num_sms, s, 0, accum);
+        return trans ? run<float, double, double, true, false>(M, N, K, Af, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s, 0, accum)
+                     : run<float, double, double, false, false>(M, N, K, Af, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s, 0, accum);
     }
     const double* Ad = static_cast<const double*>(A);
-    return trans ? run<double, double, double, true, false>(M, N, K, Ad, lda, B, ldb, C, ldc, partials, num_sms, s, 0, accum)
-                 : run<double, double, double, false, false>(M, N, K, Ad, lda, B, ldb, C, ldc, partials, num_sms, s, 0, accum);
+    return trans ? run<double, double, double, true, false>(M, N, K, Ad, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s, 0, accum)
+                 : run<double, double, double, false, false>(M, N, K, Ad, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s, 0, accum);
 }
 
 cudaError_t launch_gemm_f64(int transA, int transB, int64_t M, int64_t N, int64_t K,
                             const double* A, int64_t lda, const double* B, int64_t ldb,
-                            double* C, int64_t ldc, void* partials, int num_sms,
-                            cudaStream_t s) {
+                            double* C, int64_t ldc, void* partials, size_t part_cap,
+                            int num_sms, cudaStream_t s) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (transA) {
-        return transB ? run<double, double, double, true, true>(M, N, K, A, lda, B, ldb, C, ldc, partials, num_sms, s)
-                      : run<double, double, double, true, false>(M, N, K, A, lda, B, ldb, C, ldc, partials, num_sms, s);
+        return transB ? run<double, double, double, true, true>(M, N, K, A, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s)
+                      : run<double, double, double, true, false>(M, N, K, A, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s);
     }
-    return transB ? run<double, double, double, false, true>(M, N, K, A, lda, B, ldb, C, ldc, partials, num_sms, s)
-                  : run<double, double, double, false, false>(M, N, K, A, lda, B, ldb, C, ldc, partials, num_sms, s);
+    return transB ? run<double, double, double, false, true>(M, N, K, A, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s)
+                  : run<double, double, double, false, false>(M, N, K, A, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s);
 }
 
 cudaError_t launch_gemm_f64_tri(int transA, int tri, int64_t M, int64_t N, int64_t K,
                                 const double* A, int64_t lda, const double* B, int64_t ldb,
-                                double* C, int64_t ldc, void* partials, int num_sms,
-                                cudaStream_t s) {
+                                double* C, int64_t ldc, void* partials, size_t part_cap,
+                                int num_sms, cudaStream_t s) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     return transA ? run<double, double, double, true, false>(M, N, K, A, lda, B, ldb, C, ldc,
-                                                             partials, num_sms, s, tri)
+                                                             partials, part_cap, num_sms, s, tri)
                   : run<double, double, double, false, false>(M, N, K, A, lda, B, ldb, C, ldc,
-                                                              partials, num_sms, s, tri);
+                                                              partials, part_cap, num_sms, s, tri);
 }
 
 }  // namespace plu

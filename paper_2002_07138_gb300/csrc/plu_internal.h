@@ -61,7 +61,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int
                 good = 0;
                 break;
             }
-            __nanosleep(64);
         }
         __threadfence();
         ok = good;
@@ -92,40 +91,44 @@ cudaError_t launch_gaussian(int64_t rows, int64_t cols, uint64_t seed, uint32_t 
 // ----------------------------------------------------------- SIMT passes
 // C (M x N, FP64, ldc) = op(A) * B with op(A) = A (trans = 0, A is M x K) or
 // A^T (trans = 1, A is K x M); A of element type dtype (lda), B FP64 (K x N).
-// prec selects FP64 FMA or FP32 FMA (B converted to FP32).  `partials` must
-// hold gemm_partials_bytes(...) bytes (split-K partial sums).
+// prec selects FP64 FMA or FP32 FMA (B converted to FP32).  `partials`
+// (part_cap bytes) receives the split-K partial sums: gemm_partials_bytes(...)
+// is the size for the preferred split count; a smaller buffer lowers the
+// split count, one without room for a single M x N partial is an error.
 size_t gemm_partials_bytes(int64_t M, int64_t N, int64_t K, int prec, int num_sms);
 cudaError_t launch_gemm_simt(int trans, int64_t M, int64_t N, int64_t K, const void* A,
                              int dtype, int64_t lda, const double* B, int64_t ldb,
                              double* C, int64_t ldc, int prec, void* partials,
-                             float* b32_scratch, int num_sms, cudaStream_t s, int accum = 0);
+                             size_t part_cap, float* b32_scratch, int num_sms, cudaStream_t s,
+                             int accum = 0);
 // accum != 0: C += op(A) B instead of C = op(A) B.
 // FP64 GEMM with transposed-B option for the small products of the tail:
 // C = A * op(B), op(B) = B (K x N) or B^T (B is N x K).
 cudaError_t launch_gemm_f64(int transA, int transB, int64_t M, int64_t N, int64_t K,
                             const double* A, int64_t lda, const double* B, int64_t ldb,
-                            double* C, int64_t ldc, void* partials, int num_sms,
-                            cudaStream_t s);
+                            double* C, int64_t ldc, void* partials, size_t part_cap,
+                            int num_sms, cudaStream_t s);
 size_t gemm_f64_partials_bytes(int64_t M, int64_t N, int64_t K, int num_sms);
 // As launch_gemm_f64 (no B transpose) with a triangular shortcut: tri 1 computes
 // only the upper triangle of C (the rest is zero), tri 2 takes op(B) upper
-// triangular.
+// triangular, tri 3 lower triangular.
 cudaError_t launch_gemm_f64_tri(int transA, int tri, int64_t M, int64_t N, int64_t K,
                                 const double* A, int64_t lda, const double* B, int64_t ldb,
-                                double* C, int64_t ldc, void* partials, int num_sms,
-                                cudaStream_t s);
+                                double* C, int64_t ldc, void* partials, size_t part_cap,
+                                int num_sms, cudaStream_t s);
 
 // ----------------------------------------------- tensor-core passes (TF32)
 // Y (FP64) = A X (trans 0) or A^T X (trans 1) with FP32 A (m x n, lda) on
 // tcgen05 tensor cores; X is FP64 (K x cols).  tc_supported() tells whether
 // the shape / alignment is handled (cols <= 512, lda % 4 == 0, A 16-byte
-// aligned).
+// aligned).  scratch holds scratch_cap bytes, at least tc_scratch_bytes(M, K,
+// cols, num_sms) (an error otherwise).
 bool tc_supported(int64_t M, int64_t K, int cols, const void* A, int64_t lda, int trans);
 size_t tc_scratch_bytes(int64_t M, int64_t K, int cols, int num_sms);
 cudaError_t launch_tc_pass(int trans, int64_t m, int64_t n, const float* A, int64_t lda,
                            const double* X, int64_t ldx, int cols, double* Y, int64_t ldy,
-                           void* scratch, int* dev_status, int num_sms, cudaStream_t s,
-                           int accum = 0);
+                           void* scratch, size_t scratch_cap, int* dev_status, int num_sms,
+                           cudaStream_t s, int accum = 0);
 // Quantized copy of A for the BF16 / FP8-E4M3 passes: column-major, ld a
 // multiple of 16 elements; FP8 carries rank-1 tile scales s_r (per 128 rows)
 // and s_c (per 128 columns) with A(i, j) ~= Aq(i, j) s_r[i/128] s_c[j/128].
@@ -140,8 +143,8 @@ size_t tc_quant_bytes(int64_t m, int64_t n, int prec);
 cudaError_t launch_tc_quantize(int prec, const float* A, int64_t m, int64_t n, int64_t lda,
                                void* qbuf, QuantA* out, int num_sms, cudaStream_t s);
 cudaError_t launch_tc_pass_q(int trans, const QuantA& q, const double* X, int64_t ldx, int cols,
-                             double* Y, int64_t ldy, void* scratch, int* dev_status, int num_sms,
-                             cudaStream_t s, int accum = 0);
+                             double* Y, int64_t ldy, void* scratch, size_t scratch_cap,
+                             int* dev_status, int num_sms, cudaStream_t s, int accum = 0);
 
 // ------------------------------------------------------- panel LU (a3, a8)
 struct PanelScratch;   // defined in plu_panel.cu
@@ -157,10 +160,12 @@ cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int 
                             int num_sms, cudaStream_t s);
 
 // --------------------------------------------------------------- QR (a5)
+// scratch holds scratch_cap >= qr_scratch_bytes(rows, cols, num_sms) bytes
+// (less works down to one split of each product; too little is an error).
 size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms);
 cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, double* R,
-                           int64_t ldR, void* scratch, int* dev_status, int num_sms,
-                           cudaStream_t s);
+                           int64_t ldR, void* scratch, size_t scratch_cap, int* dev_status,
+                           int num_sms, cudaStream_t s);
 
 // Rinv = R^{-1} for an upper triangular n x n R (ld n); Rinv is upper triangular.
 cudaError_t launch_trinv_upper(int n, const double* R, double* Rinv, cudaStream_t s);

@@ -27,10 +27,9 @@
 // columns are taken NB = 32 at a time.  Each CTA keeps its rows of the
 // current NB-column block in shared memory, so a column step touches no
 // global memory except the candidate slots: each CTA publishes its candidate
-// with its whole NB-wide block row and a step tag written last (release);
-// every CTA acquire-polls all tags of the step (bounded), picks the winner and
-// copies its block row, then eliminates in shared memory.  The tags replace
-// the grid barrier: a CTA tags step j only after all its earlier writes.  After the block, every CTA forms
+// with its whole NB-wide block row;
+// after a grid barrier every CTA reads all candidates at once, picks the
+// winner and copies its block row, then eliminates in shared memory.  After the block, every CTA forms
 // U12 = L11^{-1} A12 for the block's pivot rows (forward substitution) and
 // applies the FP64 trailing update X(:, J2) -= L(:, J1) U12 to its own rows.
 // The U rows go to a separate buffer, so no CTA overwrites data that
@@ -38,16 +37,6 @@
 #include "plu_internal.h"
 
 #include <climits>
-
-// Tuning of the candidate exchange: nanoseconds slept between polls of a
-// slot tag (0: spin), and whether the publishing thread issues a GPU-scope
-// fence before its release store.
-#ifndef PLU_PANEL_SLEEP_NS
-#define PLU_PANEL_SLEEP_NS 0
-#endif
-#ifndef PLU_PANEL_FENCE
-#define PLU_PANEL_FENCE 1
-#endif
 
 namespace plu {
 
@@ -229,7 +218,7 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
     const int64_t r1 = min(rows, r0 + per);
     const int R = int(r1 > r0 ? r1 - r0 : 0);
     const int steps = int(rows < int64_t(cols) ? rows : int64_t(cols));
-    // slot: [0] |x|, [1] (pos, row), [2] step tag (written last), [3..] block row
+    // slot: [0] |x|, [1] (pos, row), [2] unused, [3..] block row
     const int slot_w = NB + 3;
 
     for (int r = t; r < R; r += NT) {
@@ -266,32 +255,16 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
                 reinterpret_cast<int2*>(myslot + 1)[0] = pr;
             }
             if (t < nbk && cb.row >= 0) myslot[3 + t] = P[t * per + int(cb.row - r0)];
-            // publish: every write of this CTA so far (slot, X, trailing update)
-            // happens before the tag
-            __syncthreads();
-            if (t == 0) {
-                if (PLU_PANEL_FENCE) __threadfence();
-                st_release_u32(reinterpret_cast<unsigned*>(myslot + 2), unsigned(j + 1));
-            }
+            // grid barrier (one arrival counter: polled by one thread per CTA,
+            // much cheaper than polling every CTA's slot), then every thread
+            // reads one slot so all candidates arrive in one round trip
+            if (!grid_barrier(&ps->barrier, unsigned(j + 1) * unsigned(nb), status, budget)) return;
             {
-                // every thread polls its own slots, so all tags are read at once
                 Cand g{-1.0, INT_MAX, -1};
                 int gs = -1;
                 int ok = 1;
                 for (int b = t; b < nb; b += NT) {
                     const double* src = slots + (int64_t(j & 1) * nb + b) * slot_w;
-                    const unsigned* tag = reinterpret_cast<const unsigned*>(src + 2);
-                    int64_t spins = 0;
-                    while (ld_acquire_u32(tag) != unsigned(j + 1)) {
-                        if (ld_volatile_i32(status) != DEV_OK) { ok = 0; break; }
-                        if (++spins > budget) {
-                            atomicCAS(status, DEV_OK, DEV_TIMEOUT);
-                            ok = 0;
-                            break;
-                        }
-                        if (PLU_PANEL_SLEEP_NS > 0) __nanosleep(PLU_PANEL_SLEEP_NS);
-                    }
-                    if (!ok) break;
                     Cand c;
                     c.v = __ldcg(src);
                     const int2 pr = __ldcg(reinterpret_cast<const int2*>(src + 1));

@@ -227,27 +227,29 @@ size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms) {
 }
 
 cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, double* R,
-                           int64_t ldR, void* scratch, int* dev_status, int num_sms,
-                           cudaStream_t s) {
+                           int64_t ldR, void* scratch, size_t scratch_cap, int* dev_status,
+                           int num_sms, cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     Workspace ws;
     ws.base = static_cast<char*>(scratch);
-    ws.cap = qr_scratch_bytes(rows, cols, num_sms);
+    ws.cap = scratch_cap;
     const size_t sq = size_t(cols) * cols * sizeof(double);
     double* W = static_cast<double*>(ws.take(sq));
     double* Wsave = static_cast<double*>(ws.take(sq));
     double* Rinv = static_cast<double*>(ws.take(sq));
     double* R1 = static_cast<double*>(ws.take(sq));
     double* Rtmp = static_cast<double*>(ws.take(sq));
-    const size_t p1 = gemm_f64_partials_bytes(cols, cols, rows, num_sms);
-    const size_t p2 = gemm_f64_partials_bytes(rows, cols, cols, num_sms);
-    void* part = ws.take(p1 > p2 ? p1 : p2);
     CholCtl* ctl = static_cast<CholCtl*>(ws.take(sizeof(CholCtl)));
+    // the rest holds the split-K partial sums of the products
+    const size_t off = (ws.used + 255) & ~size_t(255);
+    const size_t part_cap = scratch_cap > off ? scratch_cap - off : 0;
+    void* part = ws.take(part_cap);
     if (!W || !Wsave || !Rinv || !R1 || !Rtmp || !part || !ctl) return cudaErrorInvalidValue;
     cudaError_t e;
     for (int pass = 0; pass < 2; ++pass) {
         // W = X^T X, upper triangle only (the Cholesky reads nothing else)
-        e = launch_gemm_f64_tri(1, 1, cols, cols, rows, X, ldx, X, ldx, W, cols, part, num_sms, s);
+        e = launch_gemm_f64_tri(1, 1, cols, cols, rows, X, ldx, X, ldx, W, cols, part, part_cap,
+                                num_sms, s);
         if (e != cudaSuccess) return e;
         if (pass == 0) {
             e = cudaMemcpyAsync(Wsave, W, sq, cudaMemcpyDeviceToDevice, s);
@@ -278,8 +280,8 @@ cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, doubl
         k_trinv_upper<<<cols, tt, size_t(cols) * sizeof(double), s>>>(cols, W, Rinv);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // X <- X Rinv (the reduction of the partial sums writes X after the product)
-        e = launch_gemm_f64_tri(0, 2, rows, cols, cols, X, ldx, Rinv, cols, X, ldx, part, num_sms,
-                                s);
+        e = launch_gemm_f64_tri(0, 2, rows, cols, cols, X, ldx, Rinv, cols, X, ldx, part,
+                                part_cap, num_sms, s);
         if (e != cudaSuccess) return e;
         if (pass == 0) {
             e = cudaMemcpyAsync(R1, W, sq, cudaMemcpyDeviceToDevice, s);
@@ -288,7 +290,8 @@ cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, doubl
     }
     if (R) {
         // R = R2 R1 (both upper triangular)
-        e = launch_gemm_f64(0, 0, cols, cols, cols, W, cols, R1, cols, Rtmp, cols, part, num_sms, s);
+        e = launch_gemm_f64(0, 0, cols, cols, cols, W, cols, R1, cols, Rtmp, cols, part, part_cap,
+                            num_sms, s);
         if (e != cudaSuccess) return e;
         e = launch_copy_cols(cols, cols, Rtmp, cols, R, ldR, s);
         if (e != cudaSuccess) return e;

@@ -725,17 +725,18 @@ namespace {
 template <int KIND>
 cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t lda,
                          const float* s_r, const float* s_c, const double* X, int64_t ldx,
-                         int cols, double* Y, int64_t ldy, void* scratch, int* dev_status,
-                         int num_sms, cudaStream_t s, int accum) {
+                         int cols, double* Y, int64_t ldy, void* scratch, size_t scratch_cap,
+                         int* dev_status, int num_sms, cudaStream_t s, int accum) {
     constexpr int E = Kind<KIND>::E;
     constexpr int BKE = 128 / E;
     const int64_t M = trans ? n : m;
     const int64_t K = trans ? m : n;
     const TcPlan p = plan_tc(M, K, cols, num_sms, trans == 0, E);
     if (p.stages < 2) return cudaErrorInvalidValue;
+    if (scratch_cap < tc_scratch_bytes(M, K, cols, num_sms)) return cudaErrorInvalidValue;
     Workspace w;
     w.base = static_cast<char*>(scratch);
-    w.cap = tc_scratch_bytes(M, K, cols, num_sms);
+    w.cap = scratch_cap;
     float* part = static_cast<float*>(w.take(size_t(p.grid) * p.max_segs * p.npad * BM * sizeof(float)));
     unsigned char* xq = static_cast<unsigned char*>(w.take(size_t(p.ksteps) * p.npad * 128));
     float* colsc = static_cast<float*>(w.take(size_t(p.npad) * sizeof(float)));
@@ -808,20 +809,21 @@ cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t
 
 cudaError_t launch_tc_pass(int trans, int64_t m, int64_t n, const float* A, int64_t lda,
                            const double* X, int64_t ldx, int cols, double* Y, int64_t ldy,
-                           void* scratch, int* dev_status, int num_sms, cudaStream_t s,
-                           int accum) {
+                           void* scratch, size_t scratch_cap, int* dev_status, int num_sms,
+                           cudaStream_t s, int accum) {
     return tc_pass_kind<KIND_TF32>(trans, m, n, A, lda, nullptr, nullptr, X, ldx, cols, Y, ldy,
-                                   scratch, dev_status, num_sms, s, accum);
+                                   scratch, scratch_cap, dev_status, num_sms, s, accum);
 }
 
 cudaError_t launch_tc_pass_q(int trans, const QuantA& q, const double* X, int64_t ldx, int cols,
-                             double* Y, int64_t ldy, void* scratch, int* dev_status, int num_sms,
-                             cudaStream_t s, int accum) {
+                             double* Y, int64_t ldy, void* scratch, size_t scratch_cap,
+                             int* dev_status, int num_sms, cudaStream_t s, int accum) {
     if (q.prec == PLU_BF16)
         return tc_pass_kind<KIND_BF16>(trans, q.m, q.n, q.data, q.ld, nullptr, nullptr, X, ldx,
-                                       cols, Y, ldy, scratch, dev_status, num_sms, s, accum);
+                                       cols, Y, ldy, scratch, scratch_cap, dev_status, num_sms, s,
+                                       accum);
     return tc_pass_kind<KIND_FP8>(trans, q.m, q.n, q.data, q.ld, q.s_r, q.s_c, X, ldx, cols, Y,
-                                  ldy, scratch, dev_status, num_sms, s, accum);
+                                  ldy, scratch, scratch_cap, dev_status, num_sms, s, accum);
 }
 
 }  // namespace plu

@@ -183,6 +183,10 @@ FIXED_RANK_8192 = Workload("fixed_rank_8192_k100_l110", 8192, 8192, "exp20",
                            noise=1e-6 / math.sqrt(8192))
 MIXED_32768 = Workload("mixed_32768_k256_l276_v3", 32768, 32768, "pow15",
                        k=256, l=276, v=3, storage="f32")
+# the mixed-precision recipe at a quarter of the size (A is 1.07 GB, still
+# larger than L2): the case the kernel profiles are captured on
+MIXED_16384 = Workload("mixed_16384_k256_l276_v3", 16384, 16384, "pow15",
+                       k=256, l=276, v=3, storage="f32")
 FIXED_PREC_20000x10000 = Workload("fixed_prec_20000x10000_eps1e-3_b32_l512_v4",
                                   20000, 10000, "gap400", l=512, v=4,
                                   storage="f32", eps=1e-3, b=32)

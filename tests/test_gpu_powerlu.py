@@ -240,3 +240,25 @@ def test_batched_fp32_error_close_to_fp64(ctx):
         e32 = oracle.rel_lu_error(A, a[0].cpu().numpy(), a[1].cpu().numpy(), host(a[2]), host(a[3]))
         e64 = oracle.rel_lu_error(A, b[0].cpu().numpy(), b[1].cpu().numpy(), host(b[2]), host(b[3]))
         assert e32 <= 1.1 * e64 + 1e-6, (e32, e64)
+
+
+def test_fixed_precision_20000x10000_full_size(ctx):
+    """The fixed-precision workload at full size: 20000 x 10000 FP32 A,
+    sigma_i = 1/i with a 100x gap at i = 400, b = 32, eps = 1e-3, l = 512,
+    v = 4.  FP64 path: same rank, pivots and factors as the oracle; TF32 path:
+    same rank, error within 1.1x of FP64 and below eps."""
+    w = synth.FIXED_PREC_20000x10000
+    A32 = w.build("cuda")                                   # FP32, column-major
+    A64 = synth.colmajor(A32.double())
+    Ah = A64.cpu().numpy()
+    k, p, q, L, U, E, met = oracle.powerlu_fp(Ah, w.eps, w.b, w.l, w.v, seed=0)
+    gk, gp, gq, gL, gU, gmet, rep = plu.plu_powerlu_fp(ctx, A64, w.eps, w.b, w.l, w.v, seed=0,
+                                                       prec="fp64")
+    assert met and gmet and gk == k
+    check_parity(Ah, (gp, gq, gL, gU), (p, q, L, U), tol=1e-9)
+    e64 = oracle.rel_lu_error(Ah, gp.cpu().numpy(), gq.cpu().numpy(), host(gL), host(gU))
+    tk, tp, tq, tL, tU, tmet, trep = plu.plu_powerlu_fp(ctx, A32, w.eps, w.b, w.l, w.v, seed=0,
+                                                        prec="tf32")
+    assert tmet and tk == k
+    e32 = oracle.rel_lu_error(Ah, tp.cpu().numpy(), tq.cpu().numpy(), host(tL), host(tU))
+    assert e64 <= w.eps and e32 <= 1.1 * e64, (e32, e64)
