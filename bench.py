@@ -39,6 +39,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PowerLU ms & TFLOP/s per pass of A at stated rel. error, mixed vs FP64 plain"
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture of the kernel as it stands, keyed by (kernel, workload,
+# precision); each entry names its summary under profiles/.  Absent: null.
+TRAFFIC = {}
+
 
 def workloads():
     import synth
@@ -347,8 +352,9 @@ def time_calls(torch, fn, reps, stream):
 
 
 def kernel_rooflines(torch, plu, ctx, Ad, w, prec, stream, peaks):
-    """Time each step's kernel(s) alone with CUDA events on the library's
-    stream and return {name: (ms per launch, launches per step, roofline)}."""
+    """Time each step's kernels alone, at the sizes one call uses, with CUDA
+    events on the library's stream.  Returns {name: (ms per launch, launches
+    per call, roofline, kernel)}."""
     m, n, k, l, v = w.m, w.n, w.k, w.l, w.v
     X = plu.colmajor_empty(n, l)
     X.normal_()
@@ -358,42 +364,45 @@ def kernel_rooflines(torch, plu, ctx, Ad, w, prec, stream, peaks):
     sm_clock_ghz = peaks["sm_max_mhz"] / 1e3
     fp32_alu = 152 * 128 * 2 * sm_clock_ghz * 1e9 / 1e12          # TFLOP/s
     fp64_peak = 1.25                                             # nominal, TFLOP/s
+    fp64 = {"bound": "alu", "peak": fp64_peak, "unit": "TFLOP/s",
+            "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)"}
 
-    # pass A X (trans 0) in the workload precision
-    ms = time_calls(torch, lambda: plu.plu_pass(ctx, Ad, 0, X, prec, out=Z), 5, stream)
-    fl = 2.0 * m * n * l
+    # the passes: A X (trans 0) and A^T X (trans 1) over the l-wide basis
     abytes = m * n * Ad.element_size()
+    ms0 = time_calls(torch, lambda: plu.plu_pass(ctx, Ad, 0, X, prec, out=Z), 5, stream)
+    ms1 = time_calls(torch, lambda: plu.plu_pass(ctx, Ad, 1, Z, prec, out=X), 5, stream)
+    ms = 0.5 * (ms0 + ms1)
+    fl = 2.0 * m * n * l
     if prec == "fp64":
-        rf = {"bound": "alu", "achieved": fl / ms / 1e9, "peak": fp64_peak, "unit": "TFLOP/s",
-              "peak_source": "nominal FP64 1.25 TFLOP/s"}
+        rf = dict(fp64, achieved=fl / ms / 1e9)
     elif prec == "fp32":
         rf = {"bound": "alu", "achieved": fl / ms / 1e9, "peak": fp32_alu, "unit": "TFLOP/s",
               "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % peaks["sm_max_mhz"]}
     else:
         rf = {"bound": "hbm", "achieved": abytes / ms / 1e6, "peak": peaks["hbm_gbs"],
-              "unit": "GB/s", "peak_source": "measured"}
-    out["pass"] = (ms, v, rf, "k_gemm (A X)")
-    # re-orthogonalising LU of the m x l panel
+              "unit": "GB/s", "peak_source": "measured copy bandwidth"}
+    rf["ms_trans0"] = ms0
+    rf["ms_trans1"] = ms1
+    kname = "k_tc_pass" if prec in ("tf32", "bf16", "fp8") else "k_gemm_simt"
+    out["pass"] = (ms, v, rf, kname)
+    # re-orthogonalising LU of the m x l panel (the tail's two getrf of m x k
+    # and n x k panels run the same kernel)
     Zc = Z.clone()
     ms = time_calls(torch, lambda: (Zc.copy_(Z), plu.plu_lu_reorth(ctx, Zc)), 3, stream)
     ms_copy = time_calls(torch, lambda: Zc.copy_(Z), 3, stream)
     ms = max(ms - ms_copy, 1e-6)
-    fl = lu_flops(m, l)
-    out["panel_lu"] = (ms, max(v - 2, 0) + 2, {"bound": "alu", "achieved": fl / ms / 1e9,
-                                               "peak": fp64_peak, "unit": "TFLOP/s",
-                                               "peak_source": "nominal FP64 1.25 TFLOP/s"},
-                       "k_panel_lu")
-    # CholeskyQR2 of the n x l basis
-    Xc = X.clone()
-    ms = time_calls(torch, lambda: (Xc.copy_(X), plu.plu_qr(ctx, Xc)), 3, stream)
-    ms_copy = time_calls(torch, lambda: Xc.copy_(X), 3, stream)
+    out["panel_lu"] = (ms, max(v - 2, 0) + 2, dict(fp64, achieved=lu_flops(m, l) / ms / 1e9),
+                       "k_panel_lu_blocked")
+    # CholeskyQR2 of the n x k leading basis columns (all the fixed-rank call needs)
+    Xk = X[:, :k].clone()
+    Xc = Xk.clone()
+    ms = time_calls(torch, lambda: (Xc.copy_(Xk), plu.plu_qr(ctx, Xc)), 3, stream)
+    ms_copy = time_calls(torch, lambda: Xc.copy_(Xk), 3, stream)
     ms = max(ms - ms_copy, 1e-6)
-    # CholeskyQR2: per round, the symmetric Gram n l^2, the triangular product
-    # X R^-1 n l^2, the Cholesky l^3/3 and the triangular inverse l^3/3 flops
-    fl = 2 * (2.0 * n * l * l + 2.0 * l ** 3 / 3.0)
-    out["qr"] = (ms, 1, {"bound": "alu", "achieved": fl / ms / 1e9, "peak": fp64_peak,
-                         "unit": "TFLOP/s", "peak_source": "nominal FP64 1.25 TFLOP/s"},
-                 "cholqr2")
+    # per round: the symmetric Gram n k^2, the triangular product X R^-1 n k^2,
+    # the Cholesky k^3/3 and the triangular inverse k^3/3
+    fl = 2 * (2.0 * n * k * k + 2.0 * k ** 3 / 3.0)
+    out["qr"] = (ms, 1, dict(fp64, achieved=fl / ms / 1e9), "cholqr2 (k_gemm_simt FP64 + Cholesky)")
     return out
 
 
@@ -416,6 +425,7 @@ def run_ours(args, w):
 
     wr = replace(w, seed=w.seed + rank)
     Ad = wr.build("cuda")                                       # column-major FP32 (or FP64)
+    torch.cuda.empty_cache()                                    # drop the generator's temporaries
     stream = torch.cuda.current_stream()
     ctx = plu.Context(device, stream.cuda_stream)
     prec = args.prec
@@ -505,17 +515,23 @@ def run_ours(args, w):
     h2d = w.m * w.n * Ad.element_size()
     d2h = 4 * (w.m + w.n) + 8 * (w.m * w.k + w.k * w.n)
 
-    # roofline of the dominant kernel (timed alone, live)
+    # roofline of the dominant step (timed alone, live), and of the pass
     kr = kernel_rooflines(torch, plu, ctx, Ad, w, prec, stream, peaks)
     share = {name: ms * cnt for name, (ms, cnt, _, _) in kr.items()}
     dom = max(share, key=share.get)
-    ms_dom, cnt_dom, rf, kname = kr[dom]
-    rf = dict(rf)
-    rf["frac"] = rf["achieved"] / rf["peak"]
-    rf["traffic"] = None
-    rf["kernel"] = kname
-    rf["ms_per_launch"] = ms_dom
-    rf["share_of_step"] = share[dom] / (ms_total / args.steps)
+
+    def roofline_of(name):
+        ms_k, cnt_k, rf_k, kname = kr[name]
+        rf_k = dict(rf_k)
+        rf_k["frac"] = rf_k["achieved"] / rf_k["peak"]
+        rf_k["traffic"] = TRAFFIC.get((kname, w.name, prec))
+        rf_k["kernel"] = kname
+        rf_k["ms_per_launch"] = ms_k
+        rf_k["share_of_step"] = share[name] / (ms_total / args.steps)
+        return rf_k
+
+    rf = roofline_of(dom)
+    rf_pass = roofline_of("pass")
 
     # CPU baseline: the FP64 oracle on the host cores, one call on the same A
     cpu = None
@@ -568,6 +584,7 @@ def run_ours(args, w):
             "gpu_launches": launches,
             "clocks": clk,
             "roofline": rf,
+            "roofline_pass": rf_pass,
             "kernel_ms": {name: {"ms_per_launch": ms, "launches_per_step": cnt}
                           for name, (ms, cnt, _, _) in kr.items()},
             "cpu_baseline": cpu,

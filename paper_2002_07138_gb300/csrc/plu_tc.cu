@@ -23,8 +23,9 @@
 //     fence the generic-proxy writes for the tensor core;
 //   * the small operand (converted to FP32, zero-padded to Npad columns) is
 //     K-major in both cases.
-// Warp roles: warp 0 issues TMA, warp 1 issues the MMAs (one thread), warps
-// 2-5 drain TMEM to the partial buffer, warps 6-9 transpose (Y = A X only).  Every wait on an
+// Warp roles: up to four warps issue the copies (A tiles and slices of the
+// small operand), one thread issues the MMAs, four warps drain TMEM to the
+// partial buffer and, for Y = A X, four warps transpose.  Every wait on an
 // mbarrier is bounded; on timeout the CTA raises the device error word,
 // lets its in-flight copies land, frees its TMEM and returns.
 #include "plu_internal.h"
@@ -37,8 +38,9 @@
 namespace plu {
 namespace {
 
-constexpr int TC_THREADS = 192;   // Y = A^T X
-constexpr int TC_THREADS_X = 320; // Y = A X (with transposer warps)
+constexpr int TC_THREADS = 320;   // Y = A^T X
+constexpr int TC_THREADS_X = 448; // Y = A X (with transposer warps)
+constexpr int NPA_MAX = 4;        // warps issuing the TMA loads of A
 constexpr int BM = 128;           // rows of an output block (MMA M)
 constexpr int BKB = 128;          // bytes of K per stage (one swizzle row)
 constexpr int A_TILE = BM * BKB;  // 16 KB
@@ -103,6 +105,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
         : "memory");
+}
+
+// Prefetch of a tensor-map box into L2 (no shared memory, no barrier).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
 }
 
 // One contiguous global -> shared copy (sizes multiple of 16 bytes).
@@ -207,25 +217,55 @@ struct TcParams {
     int64_t K;          // reduction length
     int npad;           // padded output columns (multiple of 16, <= 512)
     int nchunk;         // columns per MMA (npad or npad / 2, <= 256)
-    int ksteps;         // K steps (of 32) per output block
+    int ksteps;         // K steps (of 128 bytes) per output block
     int64_t total;      // blocks * ksteps
     int64_t per;        // steps per CTA
     int max_segs;       // partial tiles per CTA
-    int stages;
+    int sa;             // A ring depth (the MN-major staging ring for Y = A X)
+    int sb;             // small-operand ring depth
+    int sk;             // K-major A ring depth (Y = A X only)
+    int npa;            // A producer warps (sa is a multiple of npa)
     int b_bytes;        // npad * 128
     uint32_t tmem_cols;
     float* part;        // [grid][max_segs][npad][128]
     int* status;
 };
 
+constexpr int MAX_SA = 16, MAX_SK = 4;
+constexpr int PF = 8;             // stages of A prefetched into L2 ahead of the loads
+
+// Ring structure.  Stage g (the g-th K step of this CTA's share) puts its A
+// tile in A-ring slot g % sa and its slice of the small operand in B-ring
+// slot g % sb; both copies complete on a_full[g % sa], so the MMA thread
+// waits once per stage.  The copies of stage g are issued by producer warp
+// g % npa, which owns the A slots congruent to it: one issuing thread
+// sustains only about a third of the HBM bandwidth of an SM, several in
+// parallel reach it.  A B slot is reused once the MMAs of stage g - sb have
+// completed (sb <= sa, and sb <= sk for Y = A X, so a phase waited on
+// cannot be overtaken).  For Y = A X the A tile arrives MN-major; four
+// transposer warps rewrite it into a K-major ring of sk slots and release
+// the staging slot at once, so staging slots recycle without waiting for
+// the MMA.  The small-operand slots are large (npad x 128 bytes), so only two
+// or three fit and the stage ring runs only that far ahead of the MMAs; the
+// producers therefore also prefetch the A tiles of stage g + PF into L2, and
+// the TMA loads of A hit L2.  The MMA thread (one thread issues every MMA of the CTA, so its
+// loop carries no divisions and one commit per stage) releases the stage
+// through a_empty (Y = A^T X) or k_empty (Y = A X).
+//
+// Parity waits on a ring of depth D are exact only while the waiter lags the
+// barrier by less than D phases.  A producer checks the completion of stage
+// g - sb after having checked that of stage g - npa - sb, so it never lags by
+// a full ring: that needs npa <= sa for A^T X (a_empty, depth sa) and
+// npa <= sb = sk for A X (k_empty, depth sk).
 template <bool XPOSE, int KIND>
 __global__ void __launch_bounds__(XPOSE ? TC_THREADS_X : TC_THREADS, 1)
 k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restrict__ Bt,
           const TcParams P) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[8];
-    __shared__ __align__(8) uint64_t empty_bar[8];
-    __shared__ __align__(8) uint64_t kmaj_bar[8];      // transposed tile ready (XPOSE)
+    __shared__ __align__(8) uint64_t a_full[MAX_SA];
+    __shared__ __align__(8) uint64_t a_empty[MAX_SA];
+    __shared__ __align__(8) uint64_t k_full[MAX_SK];       // transposed tile ready (XPOSE)
+    __shared__ __align__(8) uint64_t k_empty[MAX_SK];
     __shared__ __align__(8) uint64_t acc_full;
     __shared__ __align__(8) uint64_t acc_empty;
     __shared__ __align__(8) uint64_t drain_bar;
@@ -235,22 +275,30 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restr
     constexpr int E = Kind<KIND>::E;
     constexpr int BKE = 128 / E;                  // K elements per stage
     constexpr int MB = 128 / E;                   // M elements per staging box (A X)
+    // warps: 0..npa-1 producers, 4-7 epilogue (TMEM lane quarter = warp % 4),
+    // 8 MMA, 10-13 transposer (Y = A X)
+    constexpr int EPI_WARP = 4, MMA_WARP = 8, XP_WARP = 10;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    // stage: [A tile, K-major][B tile][A staging, MN-major (XPOSE only)]
-    const int stage_bytes = A_TILE + P.b_bytes + (XPOSE ? A_TILE : 0);
+    // [A ring: sa x 16 KB][K-major ring: sk x 16 KB][B ring: sb x b_bytes]
+    unsigned char* a_ring = smem;
+    unsigned char* k_ring = a_ring + P.sa * A_TILE;
+    unsigned char* b_ring = k_ring + P.sk * A_TILE;
 
     const int64_t s0 = int64_t(blockIdx.x) * P.per;
     const int64_t s1 = min(P.total, s0 + P.per);
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
-        for (int s = 0; s < P.stages; ++s) {
-            mbar_init(&full_bar[s], 1);
-            mbar_init(&empty_bar[s], 1);
-            mbar_init(&kmaj_bar[s], 4);                 // one arrival per transposer warp
+        for (int i = 0; i < P.sa; ++i) {
+            mbar_init(&a_full[i], 1);
+            mbar_init(&a_empty[i], XPOSE ? 4 : 1);      // transposer warps, or the MMA commit
+        }
+        for (int i = 0; i < P.sk; ++i) {
+            mbar_init(&k_full[i], 4);                   // one arrival per transposer warp
+            mbar_init(&k_empty[i], 1);
         }
         mbar_init(&acc_full, 1);
         mbar_init(&acc_empty, 4);                       // one arrival per epilogue warp
@@ -269,45 +317,97 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restr
     tc_fence_after();
     const uint32_t tmem = tmem_holder;
 
-    int issued = 0;          // TMA stages issued (producer)
+    int issued = 0;          // one past the last stage this producer issued
     if (s0 < s1) {
-        if (warp == 0) {
-            // ---------------------------------------------------- producer
+        if (warp < P.npa) {
+            // ------------------------------------------------------ producers
             if (lane == 0) {
-                for (int64_t s = s0; s < s1; ++s, ++issued) {
-                    const int st = issued % P.stages;
-                    const uint32_t round = uint32_t(issued / P.stages);
-                    if (round > 0 && !mbar_wait(&empty_bar[st], (round - 1) & 1u, &abort_flag)) {
+                // stages warp, warp + npa, ...; slots and rounds kept incrementally
+                int g = warp, st = warp;
+                uint32_t round = 0;
+                int64_t blk = (s0 + warp) / P.ksteps;
+                int kpos = int((s0 + warp) % P.ksteps);
+                // L2 prefetch cursor: stage g + PF
+                int64_t pf_blk = (s0 + warp + PF) / P.ksteps;
+                int pf_kpos = int((s0 + warp + PF) % P.ksteps);
+                auto prefetch = [&](int64_t b, int kp) {
+                    if (XPOSE) {
+#pragma unroll
+                        for (int q = 0; q < E; ++q)
+                            tma_prefetch_2d(&mapA, int(b * BM + MB * q), kp * BKE);
+                    } else {
+                        tma_prefetch_2d(&mapA, kp * BKE, int(b * BM));
+                    }
+                };
+                // this warp's stages before the cursor start (warp + npa, ...)
+                {
+                    int64_t b = blk;
+                    int kp = kpos;
+                    for (int j = warp + P.npa; j < PF && s0 + j < s1; j += P.npa) {
+                        kp += P.npa;
+                        while (kp >= P.ksteps) { kp -= P.ksteps; ++b; }
+                        prefetch(b, kp);
+                    }
+                }
+                for (int64_t s = s0 + warp; s < s1; s += P.npa, g += P.npa) {
+                    // the MMAs of stage g - sb have completed: B slot g % sb is free
+                    // (and, for A^T X, A slot g % sa, since sb <= sa)
+                    if (g >= P.sb) {
+                        const int gp = g - P.sb;
+                        const bool ok =
+                            XPOSE ? mbar_wait(&k_empty[gp % P.sk], uint32_t(gp / P.sk) & 1u,
+                                              &abort_flag)
+                                  : mbar_wait(&a_empty[gp % P.sa], uint32_t(gp / P.sa) & 1u,
+                                              &abort_flag);
+                        if (!ok) {
+                            abort_flag = 1;
+                            break;
+                        }
+                    }
+                    // A X: the transposer has released staging slot g % sa
+                    if (XPOSE && round > 0 &&
+                        !mbar_wait(&a_empty[st], (round - 1) & 1u, &abort_flag)) {
                         abort_flag = 1;
                         break;
                     }
-                    const int64_t blk = s / P.ksteps;
-                    const int kk = int(s % P.ksteps) * BKE;
-                    unsigned char* a_dst = smem + st * stage_bytes;
-                    unsigned char* b_dst = a_dst + A_TILE;
-                    mbar_arrive_expect_tx(&full_bar[st], uint32_t(A_TILE + P.b_bytes));
+                    const int kk = kpos * BKE;
+                    unsigned char* dst = a_ring + st * A_TILE;
+                    mbar_arrive_expect_tx(&a_full[st], uint32_t(A_TILE + P.b_bytes));
                     if (XPOSE) {
-                        unsigned char* raw = b_dst + P.b_bytes;
 #pragma unroll
                         for (int q = 0; q < E; ++q)
-                            tma_load_2d(raw + q * (128 * BKE), &mapA, &full_bar[st],
+                            tma_load_2d(dst + q * (128 * BKE), &mapA, &a_full[st],
                                         int(blk * BM + MB * q), kk);
                     } else {
-                        tma_load_2d(a_dst, &mapA, &full_bar[st], kk, int(blk * BM));
+                        tma_load_2d(dst, &mapA, &a_full[st], kk, int(blk * BM));
                     }
-                    // the small operand's K step, pre-tiled in its shared-memory image
-                    bulk_load(b_dst, Bt + (s % P.ksteps) * int64_t(P.b_bytes), uint32_t(P.b_bytes),
-                              &full_bar[st]);
+                    // the K step's slice of the small operand, pre-tiled as its
+                    // shared-memory image
+                    bulk_load(b_ring + (g % P.sb) * P.b_bytes, Bt + int64_t(kpos) * P.b_bytes,
+                              uint32_t(P.b_bytes), &a_full[st]);
+                    if (s + PF < s1) prefetch(pf_blk, pf_kpos);
+                    pf_kpos += P.npa;
+                    while (pf_kpos >= P.ksteps) { pf_kpos -= P.ksteps; ++pf_blk; }
+                    issued = g + 1;
+                    st += P.npa;
+                    if (st >= P.sa) { st -= P.sa; ++round; }
+                    kpos += P.npa;
+                    while (kpos >= P.ksteps) { kpos -= P.ksteps; ++blk; }
                 }
             }
-        } else if (warp == 1) {
+        } else if (warp == MMA_WARP) {
             // ------------------------------------------------------- MMA
             if (lane == 0) {
                 const uint32_t idesc = idesc_make(Kind<KIND>::fmt, BM, P.nchunk);
-                int it = 0, seg = 0;
-                for (int64_t s = s0; s < s1; ++s, ++it) {
-                    const bool seg_first = (s == s0) || (s % P.ksteps == 0);
-                    const bool seg_last = (s + 1 == s1) || ((s + 1) % P.ksteps == 0);
+                const int ra = XPOSE ? P.sk : P.sa;
+                const int nch = P.npad > P.nchunk ? 2 : 1;
+                const uint64_t chunk_off = uint64_t(P.nchunk * 128 / 16);
+                int slot_a = 0, slot_b = 0, seg = 0;
+                uint32_t ph_a = 0;
+                int kpos = int(s0 % P.ksteps);
+                for (int64_t s = s0; s < s1; ++s) {
+                    const bool seg_first = (s == s0) || (kpos == 0);
+                    const bool seg_last = (s + 1 == s1) || (kpos + 1 == P.ksteps);
                     if (seg_first && seg > 0) {
                         if (!mbar_wait(&acc_empty, (seg - 1) & 1u, &abort_flag)) {
                             abort_flag = 1;
@@ -315,50 +415,57 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restr
                         }
                         tc_fence_after();
                     }
-                    const int st = it % P.stages;
-                    if (!mbar_wait(XPOSE ? &kmaj_bar[st] : &full_bar[st],
-                                   uint32_t(it / P.stages) & 1u, &abort_flag)) {
+                    if (!mbar_wait(XPOSE ? &k_full[slot_a] : &a_full[slot_a], ph_a, &abort_flag)) {
                         abort_flag = 1;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a_base = smem_u32(smem + st * stage_bytes);
-                    const uint32_t b_base = a_base + A_TILE;
+                    // descriptors of the stage's first K slice; the next 32-byte slices
+                    // and the second column chunk only move the start address field
+                    // (16-byte units), which stays below 2^14 in shared memory
+                    const uint64_t ad0 =
+                        smem_desc(smem_u32((XPOSE ? k_ring : a_ring) + slot_a * A_TILE), 16, 1024);
+                    const uint64_t bd0 = smem_desc(smem_u32(b_ring + slot_b * P.b_bytes), 16, 1024);
+                    const uint32_t acc0 = seg_first ? 0u : 1u;
 #pragma unroll
                     for (int sub = 0; sub < 4; ++sub) {
-                        const uint64_t ad = smem_desc(a_base + sub * 32, 16, 1024);
-                        for (int c = 0; c * P.nchunk < P.npad; ++c) {
-                            const uint64_t bd =
-                                smem_desc(b_base + c * P.nchunk * 128 + sub * 32, 16, 1024);
-                            umma<KIND>(tmem + uint32_t(c * P.nchunk), ad, bd, idesc,
-                                       (seg_first && sub == 0) ? 0u : 1u);
-                        }
+                        umma<KIND>(tmem, ad0 + uint64_t(2 * sub), bd0 + uint64_t(2 * sub), idesc,
+                                   sub == 0 ? acc0 : 1u);
+                        if (nch == 2)
+                            umma<KIND>(tmem + uint32_t(P.nchunk), ad0 + uint64_t(2 * sub),
+                                       bd0 + uint64_t(2 * sub) + chunk_off, idesc,
+                                       sub == 0 ? acc0 : 1u);
                     }
-                    tc_commit(&empty_bar[st]);
+                    tc_commit(XPOSE ? &k_empty[slot_a] : &a_empty[slot_a]);
                     if (seg_last) {
                         tc_commit(&acc_full);
                         ++seg;
                     }
+                    if (++slot_a == ra) { slot_a = 0; ph_a ^= 1u; }
+                    if (++slot_b == P.sb) slot_b = 0;
+                    if (++kpos == P.ksteps) kpos = 0;
                 }
             }
-        } else if (XPOSE && warp >= 6) {
+        } else if (XPOSE && warp >= XP_WARP && warp < XP_WARP + 4) {
             // ------------------------------------------------ transposer
             // thread t owns row m = t of the 128-row tile; staging box q = m / MB
             // holds A(MB q.., k) as BKE K-rows of 128 bytes (128-byte swizzle);
             // the K-major tile holds row m as 128 bytes, 16-byte chunk c of
             // K = c T .. c T + T - 1 (T = 16 / E elements) at chunk c ^ (m % 8).
             constexpr int T = 16 / E;
-            const int m = threadIdx.x - 192;
+            const int m = threadIdx.x - 32 * XP_WARP;
             const int q = m / MB, mm = m % MB;
-            int it = 0;
-            for (int64_t s = s0; s < s1; ++s, ++it) {
-                const int st = it % P.stages;
-                if (!mbar_wait(&full_bar[st], uint32_t(it / P.stages) & 1u, &abort_flag)) {
+            int sa_ = 0, sk_ = 0, kround = 0;
+            uint32_t ph_a = 0;
+            for (int64_t it = 0; it < s1 - s0; ++it) {
+                if (!mbar_wait(&a_full[sa_], ph_a, &abort_flag) ||
+                    (kround > 0 &&
+                     !mbar_wait(&k_empty[sk_], uint32_t(kround - 1) & 1u, &abort_flag))) {
                     abort_flag = 1;
                     break;
                 }
-                unsigned char* kt = smem + st * stage_bytes;
-                const unsigned char* raw = kt + A_TILE + P.b_bytes + q * (128 * BKE);
+                unsigned char* kt = k_ring + sk_ * A_TILE;
+                const unsigned char* raw = a_ring + sa_ * A_TILE + q * (128 * BKE);
                 const int src_in_chunk = (mm % T) * E;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
@@ -379,9 +486,14 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restr
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&kmaj_bar[st]);
+                if (lane == 0) {
+                    mbar_arrive(&k_full[sk_]);
+                    mbar_arrive(&a_empty[sa_]);     // the staging slot may be refilled
+                }
+                if (++sa_ == P.sa) { sa_ = 0; ph_a ^= 1u; }
+                if (++sk_ == P.sk) { sk_ = 0; ++kround; }
             }
-        } else {
+        } else if (warp >= EPI_WARP && warp < EPI_WARP + 4) {
             // -------------------------------------------------- epilogue
             const int quarter = warp & 3;                 // TMEM lanes 32*quarter..
             const int row = quarter * 32 + lane;
@@ -414,14 +526,14 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restr
     __syncthreads();
     if (abort_flag) {
         if (threadIdx.x == 0) atomicCAS(P.status, DEV_OK, DEV_TIMEOUT);
-        if (warp == 0 && lane == 0) {
-            // let the copies already issued land before shared memory goes away
-            for (int i = 0; i < issued && i < P.stages; ++i) {
-                const int idx = issued - 1 - i;
-                mbar_wait_drain(&full_bar[idx % P.stages], uint32_t(idx / P.stages) & 1u);
-            }
+        // let the copies already issued land before shared memory goes away:
+        // both copies of a stage complete on its a_full phase
+        if (warp < P.npa && lane == 0) {
+            // this warp's stages among the last sa issued: g = issued-1, issued-1-npa, ...
+            for (int g = issued - 1; g >= 0 && g > issued - 1 - P.sa; g -= P.npa)
+                mbar_wait_drain(&a_full[g % P.sa], uint32_t(g / P.sa) & 1u);
         }
-        if (warp == 1 && lane == 0) {
+        if (warp == MMA_WARP && lane == 0) {
             // wait for every MMA this thread issued before TMEM is freed
             tc_commit(&drain_bar);
             mbar_wait_drain(&drain_bar, 0);
@@ -609,7 +721,8 @@ bool make_map_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uin
 }
 
 struct TcPlan {
-    int npad, nchunk, ksteps, stages, max_segs, grid;
+    int npad, nchunk, ksteps, sa, sb, sk, npa, max_segs, grid;
+    bool ok;
     int64_t blocks, total, per;
     uint32_t tmem_cols;
     size_t smem;
@@ -629,11 +742,25 @@ TcPlan plan_tc(int64_t M, int64_t K, int cols, int num_sms, bool xpose, int E = 
     p.per = (p.total + p.grid - 1) / p.grid;
     p.grid = int((p.total + p.per - 1) / p.per);
     p.max_segs = int((p.per + p.ksteps - 1) / p.ksteps) + 1;
-    const int stage_bytes = A_TILE + p.npad * 128 + (xpose ? A_TILE : 0);
-    int st = int((220 * 1024 - 2048) / stage_bytes);
-    if (st > 8) st = 8;
-    p.stages = st;
-    p.smem = size_t(st) * stage_bytes + 1024;
+    // ring depths within ~224 KB of dynamic shared memory: three small-operand
+    // slots when they fit in 112 KB (two otherwise), as many K-major slots for
+    // Y = A X, and every remaining 16 KB slot for A
+    const int b_bytes = p.npad * 128;
+    const int budget = 224 * 1024 - 1024;
+    p.sb = 3 * b_bytes <= 112 * 1024 ? 3 : 2;
+    p.sk = xpose ? p.sb : 0;                          // sb <= sk (see the kernel)
+    int sa = (budget - p.sb * b_bytes - p.sk * A_TILE) / A_TILE;
+    if (sa > MAX_SA) sa = MAX_SA;
+    // producers: four with at least eight slots, three with six or seven, else
+    // one per slot up to four; every slot belongs to exactly one producer
+    if (sa >= 2 * NPA_MAX) p.npa = NPA_MAX;
+    else if (sa >= 6) p.npa = 3;
+    else p.npa = sa < NPA_MAX ? sa : NPA_MAX;
+    if (xpose && p.npa > p.sb) p.npa = p.sb;          // producers never lag a full k_empty ring
+    if (p.npa > 0) sa = sa / p.npa * p.npa;
+    p.sa = sa;
+    p.ok = p.sa >= 2 && p.npa >= 1 && (xpose || p.sa >= p.sb);
+    p.smem = size_t(p.sa + p.sk) * A_TILE + size_t(p.sb) * b_bytes + 1024;
     uint32_t tc = 32;
     while (tc < uint32_t(p.npad)) tc <<= 1;
     p.tmem_cols = tc;
@@ -648,7 +775,7 @@ bool tc_supported(int64_t M, int64_t K, int cols, const void* A, int64_t lda, in
     if ((reinterpret_cast<uintptr_t>(A) & 15) != 0 || (lda % 4) != 0) return false;
     if (M > (int64_t(1) << 31) - 256 || K > (int64_t(1) << 31) - 256) return false;
     const TcPlan p = plan_tc(M, K, cols, 152, trans == 0, 4);
-    return p.stages >= 2 && get_encode() != nullptr;
+    return p.ok && get_encode() != nullptr;
 }
 
 size_t tc_scratch_bytes(int64_t M, int64_t K, int cols, int num_sms) {
@@ -732,7 +859,7 @@ cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t
     const int64_t M = trans ? n : m;
     const int64_t K = trans ? m : n;
     const TcPlan p = plan_tc(M, K, cols, num_sms, trans == 0, E);
-    if (p.stages < 2) return cudaErrorInvalidValue;
+    if (!p.ok) return cudaErrorInvalidValue;
     if (scratch_cap < tc_scratch_bytes(M, K, cols, num_sms)) return cudaErrorInvalidValue;
     Workspace w;
     w.base = static_cast<char*>(scratch);
@@ -776,7 +903,10 @@ cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t
     P.total = p.total;
     P.per = p.per;
     P.max_segs = p.max_segs;
-    P.stages = p.stages;
+    P.sa = p.sa;
+    P.sb = p.sb;
+    P.sk = p.sk;
+    P.npa = p.npa;
     P.b_bytes = p.npad * 128;
     P.tmem_cols = p.tmem_cols;
     P.part = part;
