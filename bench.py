@@ -226,6 +226,13 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ distributed
+def replica_workload(w, rank):
+    """Replicas only: rank r factors its own matrix, the workload's recipe
+    with seed + r (no data-path collective between ranks)."""
+    from dataclasses import replace
+    return replace(w, seed=w.seed + rank)
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -423,7 +430,7 @@ def run_ours(args, w):
     except OSError:
         peaks["source"] = "fallback"
 
-    wr = replace(w, seed=w.seed + rank)
+    wr = replica_workload(w, rank)
     Ad = wr.build("cuda")                                       # column-major FP32 (or FP64)
     torch.cuda.empty_cache()                                    # drop the generator's temporaries
     stream = torch.cuda.current_stream()

@@ -209,8 +209,6 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
     __shared__ Cand piv;
     __shared__ int win_slot;
     __shared__ int nan_seen;
-    __shared__ int poll_ok;
-    __shared__ int red_slot[NT / 32];
 
     const int nb = gridDim.x;
     const int t = threadIdx.x;
@@ -235,16 +233,18 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
             P[c * per + r] = X[(r0 + r) + int64_t(j0 + c) * ldx];
         }
         __syncthreads();
+        // candidate of the block's first column; later columns get theirs from
+        // the elimination loop of the step before
+        Cand best{-1.0, INT_MAX, -1};
+        for (int r = t; r < R; r += NT) {
+            if (piv_s[r] >= 0) continue;
+            const double a = fabs(P[r]);
+            if (a != a) nan_seen = 1;
+            const Cand c{a, pos_s[r], int(r0 + r)};
+            if (better(c, best)) best = c;
+        }
         for (int sc = 0; sc < nbk; ++sc) {
             const int j = j0 + sc;
-            Cand best{-1.0, INT_MAX, -1};
-            for (int r = t; r < R; r += NT) {
-                if (piv_s[r] >= 0) continue;
-                const double a = fabs(P[sc * per + r]);
-                if (a != a) nan_seen = 1;
-                const Cand c{a, pos_s[r], int(r0 + r)};
-                if (better(c, best)) best = c;
-            }
             const Cand cb = block_best(best, red);
             double* myslot = slots + (int64_t(j & 1) * nb + blockIdx.x) * slot_w;
             if (t == 0) {
@@ -256,53 +256,47 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
             }
             if (t < nbk && cb.row >= 0) myslot[3 + t] = P[t * per + int(cb.row - r0)];
             // grid barrier (one arrival counter: polled by one thread per CTA,
-            // much cheaper than polling every CTA's slot), then every thread
-            // reads one slot so all candidates arrive in one round trip
+            // much cheaper than polling every CTA's slot), then warp 0 reads all
+            // slots (a few per lane, in one round trip) and reduces them
             if (!grid_barrier(&ps->barrier, unsigned(j + 1) * unsigned(nb), status, budget)) return;
-            {
+            if (t < 32) {
                 Cand g{-1.0, INT_MAX, -1};
                 int gs = -1;
-                int ok = 1;
-                for (int b = t; b < nb; b += NT) {
-                    const double* src = slots + (int64_t(j & 1) * nb + b) * slot_w;
-                    Cand c;
-                    c.v = __ldcg(src);
-                    const int2 pr = __ldcg(reinterpret_cast<const int2*>(src + 1));
-                    c.pos = pr.x;
-                    c.row = pr.y;
-                    if (better(c, g)) { g = c; gs = b; }
+                // eight slots per lane per round: all loads first, so they are in
+                // flight together, then the comparisons
+                for (int b0 = 0; b0 < nb; b0 += 256) {
+                    double v[8];
+                    int2 pr[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int b = b0 + t + 32 * k;
+                        if (b < nb) {
+                            const double* src = slots + (int64_t(j & 1) * nb + b) * slot_w;
+                            v[k] = __ldcg(src);
+                            pr[k] = __ldcg(reinterpret_cast<const int2*>(src + 1));
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int b = b0 + t + 32 * k;
+                        if (b < nb) {
+                            const Cand c{v[k], pr[k].x, pr[k].y};
+                            if (better(c, g)) { g = c; gs = b; }
+                        }
+                    }
                 }
-                // block reduction of (candidate, slot) under the pivot order
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) {
                     const Cand o = shfl_cand(g, off);
                     const int os = __shfl_xor_sync(0xffffffffu, gs, off);
                     if (better(o, g)) { g = o; gs = os; }
                 }
-                const int lane = t & 31, wid = t >> 5;
-                if (lane == 0) {
-                    red[wid] = g;
-                    red_slot[wid] = gs;
-                }
-                ok = __syncthreads_and(ok);
-                if (wid == 0) {
-                    Cand x = (lane < NT / 32) ? red[lane] : Cand{-1.0, INT_MAX, -1};
-                    int xs = (lane < NT / 32) ? red_slot[lane] : -1;
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) {
-                        const Cand o = shfl_cand(x, off);
-                        const int os = __shfl_xor_sync(0xffffffffu, xs, off);
-                        if (better(o, x)) { x = o; xs = os; }
-                    }
-                    if (lane == 0) {
-                        piv = x;
-                        win_slot = xs;
-                        poll_ok = ok;
-                    }
+                if (t == 0) {
+                    piv = g;
+                    win_slot = gs;
                 }
             }
             __syncthreads();
-            if (!poll_ok) return;
             const Cand pv = piv;
             if (pv.row < 0) {
                 if (blockIdx.x == 0 && t == 0) atomicCAS(status, DEV_OK, DEV_NUMERIC);
@@ -324,18 +318,28 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
                 if (!(pv.v <= 1.7976931348623157e308)) ps->any_nan = 1;
             }
             __syncthreads();
+            // eliminate column sc from the own active rows of the block and,
+            // in the same sweep, find the candidate for column sc + 1
             const double ujj = PR[sc * NB + sc];
-            if (ujj != 0.0) {
-                for (int r = t; r < R; r += NT) {
-                    if (piv_s[r] >= 0) continue;
+            const bool next = sc + 1 < nbk;
+            best = Cand{-1.0, INT_MAX, -1};
+            for (int r = t; r < R; r += NT) {
+                if (piv_s[r] >= 0) continue;
+                if (ujj != 0.0) {
                     const double l = P[sc * per + r] / ujj;
                     P[sc * per + r] = l;
                     for (int u = sc + 1; u < nbk; ++u)
                         P[u * per + r] = fma(-l, PR[sc * NB + u], P[u * per + r]);
                 }
+                if (next) {
+                    const double a = fabs(P[(sc + 1) * per + r]);
+                    if (a != a) nan_seen = 1;
+                    const Cand c{a, pos_s[r], int(r0 + r)};
+                    if (better(c, best)) best = c;
+                }
             }
-            __syncthreads();
         }
+        __syncthreads();
         // block columns of own rows back to X (multipliers; pivot rows keep U11)
         for (int e = t; e < nbk * R; e += NT) {
             const int r = e % R, c = e / R;
@@ -377,6 +381,291 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
                 *xp -= acc;
             }
         }
+        __syncthreads();
+    }
+    for (int r = t; r < R; r += NT) {
+        pos_g[r0 + r] = pos_s[r];
+        piv_g[r0 + r] = piv_s[r];
+    }
+    if (nan_seen) atomicExch(&ps->any_nan, 1);
+}
+
+// Look-ahead variant of the blocked panel LU.  The column steps of a block
+// are latency-bound (a grid barrier and a candidate exchange each), the
+// trailing update is bound by the FP64 pipe; here they overlap.  Warps 0-3
+// (the panel group) factor block b while warps 4-7 (the update group) apply
+// block b-1's update to the columns beyond block b.  Block b's own columns
+// received block b-1's update first (the catch-up, all warps, before its
+// steps).  After the steps a grid barrier makes every CTA's deferred update
+// visible, then every CTA forms U12 = L11^{-1} A12 of block b for all
+// trailing columns.  Every number is produced by the same FP64 operations in
+// the same order as in the non-overlapped kernel; only their timing moves.
+// Rows pivoted in block b still receive block b-1's update (their pivot step
+// is >= the block's first column), rows pivoted earlier do not.
+//
+// smem: Pa[NB][per] | Pb[NB][per] | U12[NB][cols] | PR[NB][NB] | pos_s[per] |
+//       piv_s[per] | prow_id[NB]
+constexpr int NTP = 128;    // panel group threads (warps 0-3)
+
+__device__ __forceinline__ void panel_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ Cand panel_best(Cand c, Cand* red) {
+    c = warp_best(c);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = c;
+    panel_sync();
+    if (warp == 0) {
+        Cand x = (lane < NTP / 32) ? red[lane] : Cand{-1.0, INT_MAX, -1};
+        x = warp_best(x);
+        if (lane == 0) red[NTP / 32] = x;
+    }
+    panel_sync();
+    return red[NTP / 32];
+}
+
+// grid barrier entered by the panel group only (one poller)
+__device__ __forceinline__ bool panel_grid_barrier(unsigned* bar, unsigned target, int* status,
+                                                   int64_t budget, volatile int* ok_s) {
+    panel_sync();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int good = 1;
+        int64_t spins = 0;
+        while (ld_acquire_u32(bar) < target) {
+            if (ld_volatile_i32(status) != DEV_OK) { good = 0; break; }
+            if (++spins > budget) {
+                atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+                good = 0;
+                break;
+            }
+        }
+        __threadfence();
+        *ok_s = good;
+    }
+    panel_sync();
+    return *ok_s != 0;
+}
+
+__global__ void __launch_bounds__(NT)
+k_panel_lu_la(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
+              PanelScratch* __restrict__ ps, double* __restrict__ slots,
+              double* __restrict__ Ubuf, int* __restrict__ pos_g, int* __restrict__ piv_g,
+              int* __restrict__ status, int64_t budget, int per) {
+    extern __shared__ double dsm[];
+    double* Pa = dsm;
+    double* Pb = Pa + NB * per;
+    double* U12 = Pb + NB * per;
+    double* PR = U12 + int64_t(NB) * cols;
+    int* pos_s = reinterpret_cast<int*>(PR + NB * NB);
+    int* piv_s = pos_s + per;
+    int* prow_id = piv_s + per;
+    __shared__ Cand red[NTP / 32 + 1];
+    __shared__ Cand piv;
+    __shared__ int win_slot;
+    __shared__ int nan_seen;
+    __shared__ volatile int panel_ok;
+    __shared__ int abort_s;
+
+    const int nb = gridDim.x;
+    const int t = threadIdx.x;
+    const bool panel = t < NTP;
+    const int64_t r0 = int64_t(blockIdx.x) * per;
+    const int64_t r1 = min(rows, r0 + per);
+    const int R = int(r1 > r0 ? r1 - r0 : 0);
+    const int steps = int(rows < int64_t(cols) ? rows : int64_t(cols));
+    const int slot_w = NB + 3;
+    unsigned nbar = 0;                        // grid barriers passed (same sequence in every CTA)
+
+    for (int r = t; r < R; r += NT) {
+        pos_s[r] = int(r0 + r);
+        piv_s[r] = -1;
+    }
+    if (t == 0) {
+        nan_seen = 0;
+        abort_s = 0;
+    }
+    __syncthreads();
+
+    double* Pc = Pa;                          // block being factored
+    double* Lp = Pb;                          // previous block's multipliers
+    for (int j0 = 0; j0 < steps; j0 += NB) {
+        const int nbk = min(NB, steps - j0);
+        const bool have_prev = j0 > 0;
+        // ---- catch-up: the block's columns of own rows, minus block b-1's update
+        for (int e = t; e < nbk * R; e += NT) {
+            const int r = e % R, c = e / R;
+            double x = X[(r0 + r) + int64_t(j0 + c) * ldx];
+            const int ps_r = piv_s[r];
+            if (have_prev && (ps_r < 0 || ps_r >= j0)) {
+                double acc = 0.0;
+                for (int u = 0; u < NB; ++u) acc = fma(Lp[u * per + r], U12[u * cols + j0 + c], acc);
+                x -= acc;
+            }
+            Pc[c * per + r] = x;
+        }
+        __syncthreads();
+        if (panel) {
+            // ---------------------------------------------- panel group: steps
+            Cand best{-1.0, INT_MAX, -1};
+            for (int r = t; r < R; r += NTP) {
+                if (piv_s[r] >= 0) continue;
+                const double a = fabs(Pc[r]);
+                if (a != a) nan_seen = 1;
+                const Cand c{a, pos_s[r], int(r0 + r)};
+                if (better(c, best)) best = c;
+            }
+            for (int sc = 0; sc < nbk; ++sc) {
+                const int j = j0 + sc;
+                const Cand cb = panel_best(best, red);
+                double* myslot = slots + (int64_t(j & 1) * nb + blockIdx.x) * slot_w;
+                if (t == 0) {
+                    myslot[0] = cb.v;
+                    int2 pr;
+                    pr.x = cb.pos;
+                    pr.y = cb.row;
+                    reinterpret_cast<int2*>(myslot + 1)[0] = pr;
+                }
+                if (t < nbk && cb.row >= 0) myslot[3 + t] = Pc[t * per + int(cb.row - r0)];
+                ++nbar;
+                if (!panel_grid_barrier(&ps->barrier, nbar * unsigned(nb), status, budget,
+                                        &panel_ok)) {
+                    if (t == 0) abort_s = 1;
+                    break;
+                }
+                if (t < 32) {
+                    Cand g{-1.0, INT_MAX, -1};
+                    int gs = -1;
+                    for (int b0 = 0; b0 < nb; b0 += 256) {
+                        double v[8];
+                        int2 pr[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int b = b0 + t + 32 * k;
+                            if (b < nb) {
+                                const double* src = slots + (int64_t(j & 1) * nb + b) * slot_w;
+                                v[k] = __ldcg(src);
+                                pr[k] = __ldcg(reinterpret_cast<const int2*>(src + 1));
+                            }
+                        }
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int b = b0 + t + 32 * k;
+                            if (b < nb) {
+                                const Cand c{v[k], pr[k].x, pr[k].y};
+                                if (better(c, g)) { g = c; gs = b; }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const Cand o = shfl_cand(g, off);
+                        const int os = __shfl_xor_sync(0xffffffffu, gs, off);
+                        if (better(o, g)) { g = o; gs = os; }
+                    }
+                    if (t == 0) {
+                        piv = g;
+                        win_slot = gs;
+                    }
+                }
+                panel_sync();
+                const Cand pv = piv;
+                if (pv.row < 0) {
+                    if (t == 0) {
+                        if (blockIdx.x == 0) atomicCAS(status, DEV_OK, DEV_NUMERIC);
+                        abort_s = 1;
+                    }
+                    break;
+                }
+                const double* wsrc = slots + (int64_t(j & 1) * nb + win_slot) * slot_w;
+                if (t < nbk) PR[sc * NB + t] = __ldcg(wsrc + 3 + t);
+                if (t == 0) prow_id[sc] = pv.row;
+                for (int r = t; r < R; r += NTP) {
+                    if (r0 + r == pv.row) {
+                        pos_s[r] = j;
+                        piv_s[r] = j;
+                    } else if (pos_s[r] == j) {
+                        pos_s[r] = pv.pos;
+                    }
+                }
+                if (blockIdx.x == 0 && t == 0) {
+                    if (pv.v == 0.0 && ps->info == 0) ps->info = j + 1;
+                    if (!(pv.v <= 1.7976931348623157e308)) ps->any_nan = 1;
+                }
+                panel_sync();
+                const double ujj = PR[sc * NB + sc];
+                const bool next = sc + 1 < nbk;
+                best = Cand{-1.0, INT_MAX, -1};
+                for (int r = t; r < R; r += NTP) {
+                    if (piv_s[r] >= 0) continue;
+                    if (ujj != 0.0) {
+                        const double l = Pc[sc * per + r] / ujj;
+                        Pc[sc * per + r] = l;
+                        for (int u = sc + 1; u < nbk; ++u)
+                            Pc[u * per + r] = fma(-l, PR[sc * NB + u], Pc[u * per + r]);
+                    }
+                    if (next) {
+                        const double a = fabs(Pc[(sc + 1) * per + r]);
+                        if (a != a) nan_seen = 1;
+                        const Cand c{a, pos_s[r], int(r0 + r)};
+                        if (better(c, best)) best = c;
+                    }
+                }
+            }
+        } else {
+            // ------------------------------ update group: block b-1's deferred update
+            // of the columns beyond block b (rows not pivoted before block b; a
+            // row the panel group pivots meanwhile has piv_s >= j0 either way)
+            if (have_prev) {
+                const int tu = t - NTP;
+                const int c0 = j0 + NB;
+                const int ncol = cols - c0;
+                for (int64_t e = tu; e < int64_t(R) * (ncol > 0 ? ncol : 0); e += NT - NTP) {
+                    const int r = int(e % R), c = c0 + int(e / R);
+                    const int ps_r = piv_s[r];
+                    if (ps_r >= 0 && ps_r < j0) continue;
+                    double acc = 0.0;
+                    for (int u = 0; u < NB; ++u)
+                        acc = fma(Lp[u * per + r], U12[u * cols + c], acc);
+                    X[(r0 + r) + int64_t(c) * ldx] -= acc;
+                }
+            }
+            nbar += unsigned(nbk);            // the panel group's step barriers
+        }
+        __syncthreads();
+        if (abort_s) return;
+        // block columns of own rows back to X (multipliers; pivot rows keep U11)
+        for (int e = t; e < nbk * R; e += NT) {
+            const int r = e % R, c = e / R;
+            X[(r0 + r) + int64_t(j0 + c) * ldx] = Pc[c * per + r];
+        }
+        if (blockIdx.x == 0) {
+            for (int e = t; e < nbk * nbk; e += NT) {
+                const int sr = e % nbk, c = e / nbk;
+                if (c >= sr) Ubuf[(j0 + sr) + int64_t(j0 + c) * steps] = PR[sr * NB + c];
+            }
+        }
+        // every CTA's deferred update is visible after this barrier: U12 of block
+        // b over all trailing columns, from the fully updated pivot rows
+        ++nbar;
+        if (!grid_barrier(&ps->barrier, nbar * unsigned(nb), status, budget)) return;
+        for (int c = j0 + nbk + t; c < cols; c += NT) {
+            for (int sr = 0; sr < nbk; ++sr) {
+                double acc = __ldcg(&X[prow_id[sr] + int64_t(c) * ldx]);
+                for (int u = 0; u < sr; ++u) acc = fma(-PR[sr * NB + u], U12[u * cols + c], acc);
+                U12[sr * cols + c] = acc;
+            }
+        }
+        __syncthreads();
+        if (blockIdx.x == 0) {
+            for (int e = t; e < nbk * (cols - j0 - nbk); e += NT) {
+                const int sr = e % nbk, c = j0 + nbk + e / nbk;
+                Ubuf[(j0 + sr) + int64_t(c) * steps] = U12[sr * cols + c];
+            }
+        }
+        double* tmp = Pc;
+        Pc = Lp;
+        Lp = tmp;
         __syncthreads();
     }
     for (int r = t; r < R; r += NT) {
@@ -479,8 +768,21 @@ cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int 
     int64_t budget = spin_budget;
     const size_t smem_blk = size_t(NB) * per * 8 + size_t(NB) * UC * 8 + size_t(NB) * NB * 8 +
                             size_t(2) * per * 4 + NB * 4 + 64;
+    const size_t smem_la = size_t(2) * NB * per * 8 + size_t(NB) * cols * 8 +
+                           size_t(NB) * NB * 8 + size_t(2) * per * 4 + NB * 4 + 64;
     const bool blocked = smem_blk <= 200 * 1024;
-    if (blocked) {
+    const bool lookahead = cols > NB && smem_la <= 210 * 1024;
+    if (lookahead) {
+        e = cudaFuncSetAttribute(k_panel_lu_la, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(smem_la));
+        if (e != cudaSuccess) return e;
+        int per_ = int(per);
+        void* args[] = {&rows_, &cols_, &X, &ldx_, &ps, &slots, &Ubuf, &pos, &pivstep,
+                        &dev_status, &budget, &per_};
+        count_launch();
+        e = cudaLaunchCooperativeKernel((const void*)k_panel_lu_la, dim3(unsigned(nb)),
+                                        dim3(NT), args, smem_la, s);
+    } else if (blocked) {
         e = cudaFuncSetAttribute(k_panel_lu_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(smem_blk));
         if (e != cudaSuccess) return e;
@@ -503,7 +805,7 @@ cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int 
     count_launch();
     k_panel_finalize<<<unsigned(fb), 256, 0, s>>>(rows, cols, X, ldx, mode, pos, pivstep, perm,
                                                   L, ldL, l_trans, U, ldU, u_trans, ps, info,
-                                                  dev_status, blocked ? Ubuf : nullptr);
+                                                  dev_status, (blocked || lookahead) ? Ubuf : nullptr);
     return cudaGetLastError();
 }
 

@@ -80,9 +80,10 @@ k_cholesky(int n, double* __restrict__ W, const double* __restrict__ Wsave, int6
 // Blocked upper Cholesky W = R^T R over a cooperative grid (n x n, ld n,
 // upper triangle read, R written over it, strictly lower part zeroed).
 // Per block of CB columns: CTA 0 factors the diagonal block in shared memory,
-// grid barrier; every thread of the grid solves R11^T R12 = W12 for some
-// trailing columns, barrier; the grid applies W22 -= R12^T R12 (upper part),
-// barrier.  On a non-positive pivot in the first attempt (shift_mode 1) all
+// grid barrier; every CTA copies R11 to shared memory and every thread of the
+// grid solves R11^T R12 = W12 for some trailing columns, barrier; every CTA
+// stages the block rows R12 in shared memory (when they fit, else reads them
+// from W) and the grid applies W22 -= R12^T R12 (upper part), barrier.  On a non-positive pivot in the first attempt (shift_mode 1) all
 // CTAs restart from Wsave with the shifted-CholeskyQR diagonal shift.
 constexpr int CB = 32;
 constexpr int CBT = 256;
@@ -95,7 +96,8 @@ struct CholCtl {
 __global__ void __launch_bounds__(CBT)
 k_cholesky_coop(int n, double* __restrict__ W, const double* __restrict__ Wsave, int64_t rows,
                 int shift_mode, CholCtl* __restrict__ ctl, int* __restrict__ status,
-                int64_t budget) {
+                int64_t budget, int stage_rows) {
+    extern __shared__ double S[];                 // [CB][n - kb - b] block rows of R12
     __shared__ double D[CB][CB + 1];
     __shared__ double rjj;
     const int t = threadIdx.x;
@@ -149,16 +151,21 @@ k_cholesky_coop(int n, double* __restrict__ W, const double* __restrict__ Wsave,
             }
             if (!grid_barrier(&ctl->barrier, ++nbar * nb, status, budget)) return;
             if (ld_volatile_i32(&ctl->broke)) { broke = true; break; }
-            // R12(:, c) = R11^{-T} W12(:, c), one column per thread
+            // R11 to shared memory, then R12(:, c) = R11^{-T} W12(:, c), one
+            // column per thread of the grid
+            for (int e = t; e < b * b; e += CBT) {
+                const int a = e % b, c = e / b;
+                D[a][c] = a <= c ? __ldcg(&W[(kb + a) + int64_t(kb + c) * n]) : 0.0;
+            }
+            __syncthreads();
             for (int c = kb + b + gtid; c < n; c += gthreads) {
                 double x[CB];
 #pragma unroll
                 for (int i = 0; i < CB; ++i) {
                     if (i < b) {
                         double acc = __ldcg(&W[(kb + i) + int64_t(c) * n]);
-                        for (int u = 0; u < i; ++u)
-                            acc = fma(-__ldcg(&W[(kb + u) + int64_t(kb + i) * n]), x[u], acc);
-                        x[i] = acc / __ldcg(&W[(kb + i) + int64_t(kb + i) * n]);
+                        for (int u = 0; u < i; ++u) acc = fma(-D[u][i], x[u], acc);
+                        x[i] = acc / D[i][i];
                     }
                 }
 #pragma unroll
@@ -166,16 +173,28 @@ k_cholesky_coop(int n, double* __restrict__ W, const double* __restrict__ Wsave,
                     if (i < b) W[(kb + i) + int64_t(c) * n] = x[i];
             }
             if (!grid_barrier(&ctl->barrier, ++nbar * nb, status, budget)) return;
-            // W22 -= R12^T R12 (upper triangle)
+            // W22 -= R12^T R12 (upper triangle), R12 staged in shared memory
             const int m = n - kb - b;
+            const int c0 = kb + b;
+            if (stage_rows) {
+                for (int e = t; e < b * m; e += CBT) {
+                    const int u = e % b, c = e / b;
+                    S[u * m + c] = __ldcg(&W[(kb + u) + int64_t(c0 + c) * n]);
+                }
+                __syncthreads();
+            }
             for (int64_t e = gtid; e < int64_t(m) * m; e += gthreads) {
-                const int a = kb + b + int(e % m), c = kb + b + int(e / m);
+                const int a = int(e % m), c = int(e / m);
                 if (a > c) continue;
                 double acc = 0.0;
-                for (int u = 0; u < b; ++u)
-                    acc = fma(__ldcg(&W[(kb + u) + int64_t(a) * n]),
-                              __ldcg(&W[(kb + u) + int64_t(c) * n]), acc);
-                W[a + int64_t(c) * n] -= acc;
+                if (stage_rows) {
+                    for (int u = 0; u < b; ++u) acc = fma(S[u * m + a], S[u * m + c], acc);
+                } else {
+                    for (int u = 0; u < b; ++u)
+                        acc = fma(__ldcg(&W[(kb + u) + int64_t(c0 + a) * n]),
+                                  __ldcg(&W[(kb + u) + int64_t(c0 + c) * n]), acc);
+                }
+                W[(c0 + a) + int64_t(c0 + c) * n] -= acc;
             }
             if (!grid_barrier(&ctl->barrier, ++nbar * nb, status, budget)) return;
         }
@@ -262,17 +281,26 @@ cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, doubl
         } else {
             e = cudaMemsetAsync(ctl, 0, sizeof(CholCtl), s);
             if (e != cudaSuccess) return e;
-            int grid = (cols - CB + CBT - 1) / CBT * 4;     // a few CTAs per 256 trailing columns
+            // about one CTA per 4096 entries of the Gram matrix (the trailing
+            // updates dominate), at least 8, at most one per SM
+            int grid = int(int64_t(cols) * cols / 4096);
             if (grid < 8) grid = 8;
             if (grid > num_sms) grid = num_sms;
+            // the block rows of R12 (CB x (cols - CB) doubles) in shared memory when they fit
+            const size_t stage_bytes = size_t(CB) * size_t(cols - CB) * sizeof(double);
+            int stage = stage_bytes <= 200 * 1024 ? 1 : 0;
+            const size_t dsm = stage ? stage_bytes : 0;
+            e = cudaFuncSetAttribute(k_cholesky_coop, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(dsm));
+            if (e != cudaSuccess) return e;
             int n_ = cols;
             int shift = pass == 0 ? 1 : 0;
             int64_t rows_ = rows;
             int64_t budget = 16LL << 20;
-            void* args[] = {&n_, &W, &Wsave, &rows_, &shift, &ctl, &dev_status, &budget};
+            void* args[] = {&n_, &W, &Wsave, &rows_, &shift, &ctl, &dev_status, &budget, &stage};
             count_launch();
             e = cudaLaunchCooperativeKernel((const void*)k_cholesky_coop, dim3(grid), dim3(CBT),
-                                            args, 0, s);
+                                            args, dsm, s);
             if (e != cudaSuccess) return e;
         }
         const int tt = cols < 256 ? 128 : 256;

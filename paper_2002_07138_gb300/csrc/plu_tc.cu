@@ -98,29 +98,35 @@ __device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) 
     return false;
 }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-        : "memory");
+// L2 eviction policies: A streams through L2 once (evict first), the small
+// operand is re-read by every CTA (evict last).
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 
-// Prefetch of a tensor-map box into L2 (no shared memory, no barrier).
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
-    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(x), "r"(y)
-                 : "memory");
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        ".L2::cache_hint [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "l"(policy)
+        : "memory");
 }
 
 // One contiguous global -> shared copy (sizes multiple of 16 bytes).
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
-                                          uint64_t* bar) {
+                                          uint64_t* bar, uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
 }
 
@@ -232,7 +238,6 @@ struct TcParams {
 };
 
 constexpr int MAX_SA = 16, MAX_SK = 4;
-constexpr int PF = 8;             // stages of A prefetched into L2 ahead of the loads
 
 // Ring structure.  Stage g (the g-th K step of this CTA's share) puts its A
 // tile in A-ring slot g % sa and its slice of the small operand in B-ring
@@ -245,10 +250,7 @@ constexpr int PF = 8;             // stages of A prefetched into L2 ahead of the
 // cannot be overtaken).  For Y = A X the A tile arrives MN-major; four
 // transposer warps rewrite it into a K-major ring of sk slots and release
 // the staging slot at once, so staging slots recycle without waiting for
-// the MMA.  The small-operand slots are large (npad x 128 bytes), so only two
-// or three fit and the stage ring runs only that far ahead of the MMAs; the
-// producers therefore also prefetch the A tiles of stage g + PF into L2, and
-// the TMA loads of A hit L2.  The MMA thread (one thread issues every MMA of the CTA, so its
+// the MMA.  The MMA thread (one thread issues every MMA of the CTA, so its
 // loop carries no divisions and one commit per stage) releases the stage
 // through a_empty (Y = A^T X) or k_empty (Y = A X).
 //
@@ -323,32 +325,11 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restr
             // ------------------------------------------------------ producers
             if (lane == 0) {
                 // stages warp, warp + npa, ...; slots and rounds kept incrementally
+                const uint64_t pol_a = policy_evict_first(), pol_b = policy_evict_last();
                 int g = warp, st = warp;
                 uint32_t round = 0;
                 int64_t blk = (s0 + warp) / P.ksteps;
                 int kpos = int((s0 + warp) % P.ksteps);
-                // L2 prefetch cursor: stage g + PF
-                int64_t pf_blk = (s0 + warp + PF) / P.ksteps;
-                int pf_kpos = int((s0 + warp + PF) % P.ksteps);
-                auto prefetch = [&](int64_t b, int kp) {
-                    if (XPOSE) {
-#pragma unroll
-                        for (int q = 0; q < E; ++q)
-                            tma_prefetch_2d(&mapA, int(b * BM + MB * q), kp * BKE);
-                    } else {
-                        tma_prefetch_2d(&mapA, kp * BKE, int(b * BM));
-                    }
-                };
-                // this warp's stages before the cursor start (warp + npa, ...)
-                {
-                    int64_t b = blk;
-                    int kp = kpos;
-                    for (int j = warp + P.npa; j < PF && s0 + j < s1; j += P.npa) {
-                        kp += P.npa;
-                        while (kp >= P.ksteps) { kp -= P.ksteps; ++b; }
-                        prefetch(b, kp);
-                    }
-                }
                 for (int64_t s = s0 + warp; s < s1; s += P.npa, g += P.npa) {
                     // the MMAs of stage g - sb have completed: B slot g % sb is free
                     // (and, for A^T X, A slot g % sa, since sb <= sa)
@@ -377,17 +358,14 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restr
 #pragma unroll
                         for (int q = 0; q < E; ++q)
                             tma_load_2d(dst + q * (128 * BKE), &mapA, &a_full[st],
-                                        int(blk * BM + MB * q), kk);
+                                        int(blk * BM + MB * q), kk, pol_a);
                     } else {
-                        tma_load_2d(dst, &mapA, &a_full[st], kk, int(blk * BM));
+                        tma_load_2d(dst, &mapA, &a_full[st], kk, int(blk * BM), pol_a);
                     }
                     // the K step's slice of the small operand, pre-tiled as its
                     // shared-memory image
                     bulk_load(b_ring + (g % P.sb) * P.b_bytes, Bt + int64_t(kpos) * P.b_bytes,
-                              uint32_t(P.b_bytes), &a_full[st]);
-                    if (s + PF < s1) prefetch(pf_blk, pf_kpos);
-                    pf_kpos += P.npa;
-                    while (pf_kpos >= P.ksteps) { pf_kpos -= P.ksteps; ++pf_blk; }
+                              uint32_t(P.b_bytes), &a_full[st], pol_b);
                     issued = g + 1;
                     st += P.npa;
                     if (st >= P.sa) { st -= P.sa; ++round; }
