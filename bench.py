@@ -41,8 +41,16 @@ METRIC = "PowerLU ms & TFLOP/s per pass of A at stated rel. error, mixed vs FP64
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the kernel as it stands, keyed by (kernel, workload,
-# precision); each entry names its summary under profiles/.  Absent: null.
-TRAFFIC = {}
+# precision); absent: null.  The 32768^2 entries scale the 16384^2 captures
+# by the bytes the kernel streams (A: x4, the m x l panel: x2).
+TRAFFIC = {
+    # profiles/k_panel_lu_la_mixed_16384.md: 36.25 MB read + 0.08 MB written
+    ("k_panel_lu_la", "mixed_32768_k256_l276_v3", "tf32"): 2 * (36.250e6 + 0.082e6),
+    ("k_panel_lu_la", "mixed_16384_k256_l276_v3", "tf32"): 36.250e6 + 0.082e6,
+    # profiles/k_tc_pass_mixed_16384_tf32.md: mean of the two orientations
+    ("k_tc_pass", "mixed_32768_k256_l276_v3", "tf32"): 4 * (1.0927e9 + 0.0071e9),
+    ("k_tc_pass", "mixed_16384_k256_l276_v3", "tf32"): 1.0927e9 + 0.0071e9,
+}
 
 
 def workloads():
@@ -166,6 +174,15 @@ def run_batched(args):
 
 def pass_flops(m, n, k, l, v):
     return 2.0 * m * n * l * (v - 1) + 2.0 * m * n * k
+
+
+def panel_kernel_name(rows, cols, sms):
+    """The panel LU kernel the library picks for a rows x cols panel (the
+    look-ahead kernel when its shared memory fits, as in launch_panel_lu)."""
+    nb = min(sms, (rows + 31) // 32, 1024)
+    per = -(-rows // nb)
+    smem_la = 2 * 32 * per * 8 + 32 * cols * 8 + 32 * 32 * 8 + 2 * per * 4 + 32 * 4 + 64
+    return "k_panel_lu_la" if cols > 32 and smem_la <= 210 * 1024 else "k_panel_lu_blocked"
 
 
 def lu_flops(rows, cols):
@@ -399,7 +416,7 @@ def kernel_rooflines(torch, plu, ctx, Ad, w, prec, stream, peaks):
     ms_copy = time_calls(torch, lambda: Zc.copy_(Z), 3, stream)
     ms = max(ms - ms_copy, 1e-6)
     out["panel_lu"] = (ms, max(v - 2, 0) + 2, dict(fp64, achieved=lu_flops(m, l) / ms / 1e9),
-                       "k_panel_lu_blocked")
+                       panel_kernel_name(m, l, torch.cuda.get_device_properties(0).multi_processor_count))
     # CholeskyQR2 of the n x k leading basis columns (all the fixed-rank call needs)
     Xk = X[:, :k].clone()
     Xc = Xk.clone()

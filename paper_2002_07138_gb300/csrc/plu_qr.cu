@@ -126,28 +126,32 @@ k_cholesky_coop(int n, double* __restrict__ W, const double* __restrict__ Wsave,
                     D[a][c] = __ldcg(&W[(kb + a) + int64_t(kb + c) * n]);
                 }
                 __syncthreads();
-                int bad = 0;
-                for (int j = 0; j < b; ++j) {
-                    if (t == 0) {
+                // the diagonal block by warp 0 alone (lane c owns column c), so
+                // a column step costs warp syncs, not CTA barriers
+                if (t < 32) {
+                    int bad = 0;
+                    for (int j = 0; j < b; ++j) {
                         const double d = D[j][j];
-                        rjj = d > 0.0 ? sqrt(d) : 0.0;
-                        D[j][j] = rjj;
+                        const double r = d > 0.0 ? sqrt(d) : 0.0;
+                        if (r == 0.0) { bad = 1; break; }      // same value in every lane
+                        __syncwarp();
+                        if (t == j) D[j][j] = r;
+                        if (t > j && t < b) D[j][t] /= r;
+                        __syncwarp();
+                        if (t > j && t < b) {
+                            const double rjc = D[j][t];
+                            for (int a = j + 1; a <= t; ++a) D[a][t] -= D[j][a] * rjc;
+                        }
+                        __syncwarp();
                     }
-                    __syncthreads();
-                    if (rjj == 0.0) { bad = 1; break; }
-                    if (t > j && t < b) D[j][t] /= rjj;
-                    __syncthreads();
-                    for (int e = t; e < b * b; e += CBT) {
-                        const int a = e % b, c = e / b;
-                        if (a > j && a <= c) D[a][c] -= D[j][a] * D[j][c];
-                    }
-                    __syncthreads();
+                    if (t == 0) rjj = bad ? 0.0 : 1.0;
                 }
+                __syncthreads();
                 for (int e = t; e < b * b; e += CBT) {
                     const int a = e % b, c = e / b;
                     if (a <= c) W[(kb + a) + int64_t(kb + c) * n] = D[a][c];
                 }
-                if (t == 0) ctl->broke = bad;
+                if (t == 0) ctl->broke = rjj == 0.0 ? 1 : 0;
             }
             if (!grid_barrier(&ctl->barrier, ++nbar * nb, status, budget)) return;
             if (ld_volatile_i32(&ctl->broke)) { broke = true; break; }
