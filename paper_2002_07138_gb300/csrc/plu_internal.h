@@ -36,6 +36,13 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Release-add on a grid barrier counter: after a CTA barrier, it publishes the
+// CTA's earlier writes (release is cumulative over what the CTA barrier
+// ordered before it) without a full fence.
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ int ld_volatile_i32(const int* p) {
     return *reinterpret_cast<const volatile int*>(p);
 }
@@ -50,10 +57,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bar, 1u);
+        red_release_add_u32(bar, 1u);
         int good = 1;
         int64_t spins = 0;
+        // acquire loads: the other CTAs' writes released before their arrival
+        // are visible to this CTA after the CTA barrier below
         while (ld_acquire_u32(bar) < target) {
             if (ld_volatile_i32(status) != DEV_OK) { good = 0; break; }
             if (++spins > budget) {
@@ -62,7 +70,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int
                 break;
             }
         }
-        __threadfence();
         ok = good;
     }
     __syncthreads();

@@ -428,8 +428,7 @@ __device__ __forceinline__ bool panel_grid_barrier(unsigned* bar, unsigned targe
                                                    int64_t budget, volatile int* ok_s) {
     panel_sync();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bar, 1u);
+        red_release_add_u32(bar, 1u);
         int good = 1;
         int64_t spins = 0;
         while (ld_acquire_u32(bar) < target) {
@@ -440,7 +439,6 @@ __device__ __forceinline__ bool panel_grid_barrier(unsigned* bar, unsigned targe
                 break;
             }
         }
-        __threadfence();
         *ok_s = good;
     }
     panel_sync();

@@ -11,9 +11,11 @@
 //   r = sqrt(-2 ln u), theta = 2 pi w2 / 2^32, entry = r cos / r sin.
 // ln and sin/cos are evaluated from their series (atanh form of ln on
 // [sqrt(1/2), sqrt(2)); Taylor sin/cos on |phi| <= pi/4 after taking the
-// quarter turn from the top bits of w2) with explicitly rounded IEEE
-// operations (no contraction into FMA), so every value is a fixed sequence
-// of correctly rounded +, -, *, /, sqrt and is reproducible bit for bit.
+// quarter turn from the top bits of w2; the series terms multiply by the
+// correctly rounded reciprocals of their denominators) with explicitly
+// rounded IEEE operations (no contraction into FMA), so every value is a
+// fixed sequence of correctly rounded +, -, *, /, sqrt and is reproducible
+// bit for bit.
 #include "plu_internal.h"
 
 #include "plu_rng.cuh"

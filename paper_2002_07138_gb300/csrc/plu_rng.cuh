@@ -64,15 +64,19 @@ __device__ __forceinline__ void sincos_turn(uint32_t x, double& so, double& co) 
     const double pi_over_2_31 = 3.141592653589793116 * (1.0 / 2147483648.0);
     const double phi = __dmul_rn(double(d), pi_over_2_31);
     const double x2 = __dmul_rn(phi, phi);
-    const double sden[9] = {342.0, 272.0, 210.0, 156.0, 110.0, 72.0, 42.0, 20.0, 6.0};
-    const double cden[10] = {380.0, 306.0, 240.0, 182.0, 132.0, 90.0, 56.0, 30.0, 12.0, 2.0};
+    // nested Taylor series; 1/d of the denominators d = (2i)(2i+1), (2i-1)(2i)
+    // as correctly rounded constants (compile-time IEEE divisions)
+    constexpr double sinv[9] = {1.0 / 342.0, 1.0 / 272.0, 1.0 / 210.0, 1.0 / 156.0, 1.0 / 110.0,
+                                1.0 / 72.0,  1.0 / 42.0,  1.0 / 20.0,  1.0 / 6.0};
+    constexpr double cinv[10] = {1.0 / 380.0, 1.0 / 306.0, 1.0 / 240.0, 1.0 / 182.0, 1.0 / 132.0,
+                                 1.0 / 90.0,  1.0 / 56.0,  1.0 / 30.0,  1.0 / 12.0,  1.0 / 2.0};
     double ts = 1.0;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) ts = __dsub_rn(1.0, __dmul_rn(__ddiv_rn(x2, sden[i]), ts));
+    for (int i = 0; i < 9; ++i) ts = __dsub_rn(1.0, __dmul_rn(__dmul_rn(x2, sinv[i]), ts));
     const double s = __dmul_rn(phi, ts);
     double tc = 1.0;
 #pragma unroll
-    for (int i = 0; i < 10; ++i) tc = __dsub_rn(1.0, __dmul_rn(__ddiv_rn(x2, cden[i]), tc));
+    for (int i = 0; i < 10; ++i) tc = __dsub_rn(1.0, __dmul_rn(__dmul_rn(x2, cinv[i]), tc));
     const double c = tc;
     switch (quad) {
         case 0: so = s; co = c; break;

@@ -141,6 +141,24 @@ def test_powerlu_tf32_error_within_1p1_of_fp64(ctx):
     assert errs["tf32"] <= 1.1 * errs["fp64"], errs
 
 
+@pytest.mark.parametrize("v", [2, 4])
+@pytest.mark.parametrize("prec,limit", [("tf32", 1.1), ("bf16", 1.5)])
+def test_powerlu_mixed_even_pass_counts(ctx, v, prec, limit):
+    """Even v (Alg. gpowerlu starts from A^T Omega, Omega m x l): v passes in
+    the mixed modes, error bounded against the FP64 path at the same v."""
+    sig = synth.sigma_profile("pow15", 2048)
+    A = synth.svd_matrix_np(2048, 1536, sig[:1536], seed=8)
+    A32 = A.astype(np.float32)
+    A64h = A32.astype(np.float64)
+    gp, gq, gL, gU, rep = plu.plu_powerlu(ctx, dev(A64h), 48, 58, v, seed=3, prec="fp64")
+    assert rep["passes"] == v
+    e64 = oracle.rel_lu_error(A64h, gp.cpu().numpy(), gq.cpu().numpy(), host(gL), host(gU))
+    gp, gq, gL, gU, rep = plu.plu_powerlu(ctx, dev(A32, torch.float32), 48, 58, v, seed=3, prec=prec)
+    assert rep["passes"] == v
+    e = oracle.rel_lu_error(A64h, gp.cpu().numpy(), gq.cpu().numpy(), host(gL), host(gU))
+    assert e <= limit * e64, (e, e64)
+
+
 @pytest.mark.parametrize("prec,limit", [("bf16", 1.5), ("fp8", 6.0)])
 def test_powerlu_quantized_passes_run_and_report_error(ctx, prec, limit):
     """BF16 / FP8-E4M3 power passes over a quantized copy of A, final pass on
