@@ -57,6 +57,7 @@ def workloads():
     import synth
     return {"fixed_rank_8192": synth.FIXED_RANK_8192, "mixed_32768": synth.MIXED_32768,
             "mixed_16384": synth.MIXED_16384,
+            "fixed_prec_20000x10000": synth.FIXED_PREC_20000x10000,
             "plain_2000x1500": synth.PLAIN_2000x1500, "batched_512": None}
 
 
@@ -618,6 +619,83 @@ def run_ours(args, w):
     return 0
 
 
+def run_fixed_precision(args, w):
+    """PowerLU_FP (Alg. adaptivewithoutupdating + Alg. powerlufp) on the
+    fixed-precision workload: chosen rank, relative error, time per call, in
+    the requested precision and in FP64 plain."""
+    import numpy as np
+    import torch
+    import paper_2002_07138_gb300 as plu
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    Ad = replica_workload(w, rank).build("cuda")
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+    ctx = plu.Context(local, stream.cuda_stream)
+
+    def call(seed, A, pr):
+        return plu.plu_powerlu_fp(ctx, A, w.eps, w.b, w.l, w.v, seed=seed, prec=pr)
+
+    def timed(A, pr, steps, warmup):
+        for i in range(warmup):
+            call(i, A, pr)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            res = call(1000 + i, A, pr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, res
+
+    def rel_error(res, A):
+        k, p, q, L, U = res[:5]
+        Ap = A.double()[p.long()][:, q.long()]
+        return float(torch.linalg.norm(Ap - L @ U) / torch.linalg.norm(A.double()))
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    dist_barrier(ws)
+    ms, res = timed(Ad, args.prec, args.steps, args.warmup)
+    dist_barrier(ws)
+    clk = clocks.stop()
+    ms = dist_max(ws, ms)
+    k, met, rep_ = res[0], res[5], res[6]
+    err = rel_error(res, Ad)
+    flops = 2.0 * w.m * w.n * w.l * w.v            # v passes over A with l columns
+    out = {}
+    if not args.skip_fp64:
+        A64 = synth_colmajor(Ad.double())
+        ms64, r64 = timed(A64, "fp64", 2, 1)
+        out = {"ms_per_step": ms64, "rank": r64[0], "rel_error": rel_error(r64, Ad),
+               "tolerance_met": r64[5]}
+        del A64
+    sig = w.sigma_values()
+    tail = np.sqrt(np.cumsum((sig ** 2)[::-1])[::-1] / np.sum(sig ** 2))
+    svd_rank = int(np.argmax(tail <= w.eps))          # smallest r with ||A - A_r|| <= eps ||A||
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": flops * ws / (ms / 1e3) / 1e12, "unit": "TFLOP/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "bf16": "bf16",
+                      "fp8": "fp8e4m3"}[args.prec], "data": "synthetic",
+            "config": {"workload": w.name, "m": w.m, "n": w.n, "eps": w.eps, "b": w.b, "l": w.l,
+                       "v": w.v, "sigma": w.sigma, "pass_precision": args.prec,
+                       "between_passes": "f64", "parallelism": "replicas" if ws > 1 else "single"},
+            "rank": k, "tolerance_met": met, "rel_error": err, "svd_rank_at_eps": svd_rank,
+            "ms_per_pass": rep_["ms_passes"] / max(rep_["passes"], 1),
+            "fp64_plain": out,
+            "speedup_vs_fp64_plain": (out["ms_per_step"] / ms) if out else None,
+            "gpu_launches": rep_["launches"], "clocks": clk,
+        }))
+    ctx.close()
+    return 0
+
+
 def synth_colmajor(t):
     import synth
     return synth.colmajor(t)
@@ -643,6 +721,8 @@ def main():
     w = workloads()[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
+    if w.eps:
+        return run_fixed_precision(args, w)
     return run_ours(args, w)
 
 
