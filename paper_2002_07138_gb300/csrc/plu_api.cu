@@ -257,7 +257,7 @@ struct PassTimer {
 // path reads only V(:, 1:k) (Alg. bpowerlu step 3 and the tail).
 plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t seed, int prec,
                         double* V, double* Z, char* step, size_t step_cap, PassTimer& pt,
-                        int* passes, const QuantA* q, int qr_cols) {
+                        int* passes, const QuantA* q, int qr_cols, int adaptive_qr) {
     const int64_t m = A->m, n = A->n;
     const int p = (v - 1) / 2;
     int np = 0;
@@ -276,7 +276,7 @@ plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t 
     };
     auto qr = [&](double* X) -> plu_status {
         PLU_CUDA(c, launch_cholqr2(n, qr_cols, X, n, nullptr, 0, step, step_cap, c->d_status,
-                                   c->num_sms, c->stream));
+                                   c->num_sms, c->stream, adaptive_qr));
         return PLU_OK;
     };
     if (v % 2 == 0) {
@@ -546,8 +546,10 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
     if (quant)
         PLU_CUDA(c, launch_tc_quantize(prec, static_cast<const float*>(A->data), m, n, A->ld,
                                        ws + pl.quant, &qa, c->num_sms, c->stream));
+    // mixed modes: one CholeskyQR round when it is orthogonal enough (see
+    // launch_cholqr2); the FP64 path keeps both rounds
     PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pl.step_bytes, pt, &np,
-                         quant ? &qa : nullptr, k));
+                         quant ? &qa : nullptr, k, prec != PLU_FP64 ? 1 : 0));
     // Y = A V(:, 1:k) (Alg. bpowerlu step 3), the v-th pass; in the mixed
     // modes it reads the FP32 A through TF32 (it enters the result to first order)
     pt.mark();
@@ -615,7 +617,7 @@ plu_status plu_powerlu_fp(plu_ctx* c, const plu_matrix* A, double eps, int b, in
         PLU_CUDA(c, launch_tc_quantize(prec, static_cast<const float*>(A->data), m, n, A->ld,
                                        ws + pl.quant, &qa, c->num_sms, c->stream));
     PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pl.step_bytes, pt, &np,
-                         quant ? &qa : nullptr, l));
+                         quant ? &qa : nullptr, l, 0));
     // G = A V (step 3), the v-th pass.  Its column norms decide the rank:
     // E = ||A||_F^2 - sum ||G(:, j)||^2 must resolve eps^2 ||A||_F^2, which
     // TF32 rounding (relative bias ~1e-3) cannot, so the mixed modes take this

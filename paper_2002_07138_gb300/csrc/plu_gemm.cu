@@ -29,7 +29,9 @@ template <typename T> __device__ __forceinline__ T to_acc(float x) { return T(x)
 template <typename TA, typename TB, typename TC, bool TRANSA, bool TRANSB>
 __global__ void __launch_bounds__(NT)
 k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t lda,
-            const TB* __restrict__ B, int64_t ldb, TC* __restrict__ P, int64_t kchunk, int tri) {
+            const TB* __restrict__ B, int64_t ldb, TC* __restrict__ P, int64_t kchunk, int tri,
+            const int* __restrict__ skip) {
+    if (skip && *skip) return;                      // work cancelled on the device
     __shared__ TC As[2][BK][BM + 1];
     __shared__ TC Bs[2][BK][BN + 1];
     const int t = threadIdx.x;
@@ -153,7 +155,9 @@ k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t l
 // C(i, j) = sum_z P[z](i, j), z in increasing order, in FP64.
 template <typename TC>
 __global__ void k_reduce_splits(int64_t M, int64_t N, int splits, const TC* __restrict__ P,
-                                double* __restrict__ C, int64_t ldc, int accum) {
+                                double* __restrict__ C, int64_t ldc, int accum,
+                                const int* __restrict__ skip) {
+    if (skip && *skip) return;
     const int64_t total = M * N;
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
@@ -200,7 +204,8 @@ int grid_1d(int64_t work, int num_sms) {
 template <typename TA, typename TB, typename TC, bool TA_T, bool TB_T>
 cudaError_t run(int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda, const TB* B,
                 int64_t ldb, double* C, int64_t ldc, void* partials, size_t part_cap,
-                int num_sms, cudaStream_t s, int tri = 0, int accum = 0) {
+                int num_sms, cudaStream_t s, int tri = 0, int accum = 0,
+                const int* skip = nullptr) {
     int splits = choose_splits(M, N, K, num_sms);
     const size_t one = size_t(M) * size_t(N) * sizeof(TC);
     if (!partials || part_cap < one) return cudaErrorInvalidValue;
@@ -211,11 +216,12 @@ cudaError_t run(int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda, const
     TC* P = static_cast<TC*>(partials);
     count_launch();
     k_gemm_simt<TA, TB, TC, TA_T, TB_T><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, P, kchunk,
-                                                           tri);
+                                                           tri, skip);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     count_launch();
-    k_reduce_splits<TC><<<grid_1d(M * N, num_sms), 256, 0, s>>>(M, N, splits, P, C, ldc, accum);
+    k_reduce_splits<TC><<<grid_1d(M * N, num_sms), 256, 0, s>>>(M, N, splits, P, C, ldc, accum,
+                                                                skip);
     return cudaGetLastError();
 }
 
@@ -277,12 +283,14 @@ cudaError_t launch_gemm_f64(int transA, int transB, int64_t M, int64_t N, int64_
 cudaError_t launch_gemm_f64_tri(int transA, int tri, int64_t M, int64_t N, int64_t K,
                                 const double* A, int64_t lda, const double* B, int64_t ldb,
                                 double* C, int64_t ldc, void* partials, size_t part_cap,
-                                int num_sms, cudaStream_t s) {
+                                int num_sms, cudaStream_t s, const int* skip) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     return transA ? run<double, double, double, true, false>(M, N, K, A, lda, B, ldb, C, ldc,
-                                                             partials, part_cap, num_sms, s, tri)
+                                                             partials, part_cap, num_sms, s, tri,
+                                                             0, skip)
                   : run<double, double, double, false, false>(M, N, K, A, lda, B, ldb, C, ldc,
-                                                              partials, part_cap, num_sms, s, tri);
+                                                              partials, part_cap, num_sms, s, tri,
+                                                              0, skip);
 }
 
 }  // namespace plu

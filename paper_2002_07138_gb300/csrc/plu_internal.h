@@ -119,10 +119,12 @@ size_t gemm_f64_partials_bytes(int64_t M, int64_t N, int64_t K, int num_sms);
 // As launch_gemm_f64 (no B transpose) with a triangular shortcut: tri 1 computes
 // only the upper triangle of C (the rest is zero), tri 2 takes op(B) upper
 // triangular, tri 3 lower triangular.
+// skip (nullable, device): when *skip != 0 at run time the kernels return
+// without touching C.
 cudaError_t launch_gemm_f64_tri(int transA, int tri, int64_t M, int64_t N, int64_t K,
                                 const double* A, int64_t lda, const double* B, int64_t ldb,
                                 double* C, int64_t ldc, void* partials, size_t part_cap,
-                                int num_sms, cudaStream_t s);
+                                int num_sms, cudaStream_t s, const int* skip = nullptr);
 
 // ----------------------------------------------- tensor-core passes (TF32)
 // Y (FP64) = A X (trans 0) or A^T X (trans 1) with FP32 A (m x n, lda) on
@@ -170,9 +172,13 @@ cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int 
 // scratch holds scratch_cap >= qr_scratch_bytes(rows, cols, num_sms) bytes
 // (less works down to one split of each product; too little is an error).
 size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms);
+// adaptive != 0: the second CholeskyQR round runs only when the first
+// Cholesky factor's diagonal spread max|r_ii| / min|r_ii| exceeds 1e4 (the
+// decision is taken on the device; the second round's kernels return at once
+// otherwise).  R (when requested) is then R1.
 cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, double* R,
                            int64_t ldR, void* scratch, size_t scratch_cap, int* dev_status,
-                           int num_sms, cudaStream_t s);
+                           int num_sms, cudaStream_t s, int adaptive = 0);
 
 // Rinv = R^{-1} for an upper triangular n x n R (ld n); Rinv is upper triangular.
 cudaError_t launch_trinv_upper(int n, const double* R, double* Rinv, cudaStream_t s);

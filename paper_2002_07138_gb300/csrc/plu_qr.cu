@@ -22,7 +22,8 @@ constexpr int CT = 1024;
 // non-positive pivot restart from Wsave with the CholeskyQR shift.
 __global__ void __launch_bounds__(CT)
 k_cholesky(int n, double* __restrict__ W, const double* __restrict__ Wsave, int64_t rows,
-           int shift_mode, int* __restrict__ status) {
+           int shift_mode, int* __restrict__ status, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     __shared__ int broke;
     __shared__ double rjj;
     const int t = threadIdx.x;
@@ -96,7 +97,8 @@ struct CholCtl {
 __global__ void __launch_bounds__(CBT)
 k_cholesky_coop(int n, double* __restrict__ W, const double* __restrict__ Wsave, int64_t rows,
                 int shift_mode, CholCtl* __restrict__ ctl, int* __restrict__ status,
-                int64_t budget, int stage_rows) {
+                int64_t budget, int stage_rows, const int* __restrict__ skip) {
+    if (skip && *skip) return;                      // every CTA reads the same flag
     extern __shared__ double S[];                 // [CB][n - kb - b] block rows of R12
     __shared__ double D[CB][CB + 1];
     __shared__ double rjj;
@@ -216,7 +218,9 @@ k_cholesky_coop(int n, double* __restrict__ W, const double* __restrict__ Wsave,
 }
 
 // Rinv(:, j) = R^{-1} e_j for upper triangular R (n x n, ld n); CTA j.
-__global__ void k_trinv_upper(int n, const double* __restrict__ R, double* __restrict__ Rinv) {
+__global__ void k_trinv_upper(int n, const double* __restrict__ R, double* __restrict__ Rinv,
+                              const int* __restrict__ skip) {
+    if (skip && *skip) return;
     extern __shared__ double x[];
     const int j = blockIdx.x;
     const int t = threadIdx.x;
@@ -232,13 +236,30 @@ __global__ void k_trinv_upper(int n, const double* __restrict__ R, double* __res
     for (int i = t; i < n; i += blockDim.x) Rinv[i + int64_t(j) * n] = x[i];
 }
 
+// skip2 = 1 when the diagonal spread of the first Cholesky factor is at most
+// 1e5 (orthogonality loss of one CholeskyQR round ~ (spread)^2 u <= ~1e-6).
+__global__ void k_qr_decide(int n, const double* __restrict__ R, int* __restrict__ skip2) {
+    double dmax = 0.0, dmin = 1.7976931348623157e308;
+    for (int i = threadIdx.x; i < n; i += 32) {
+        const double d = fabs(R[i + int64_t(i) * n]);
+        dmax = fmax(dmax, d);
+        dmin = fmin(dmin, d);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+        dmin = fmin(dmin, __shfl_xor_sync(0xffffffffu, dmin, off));
+    }
+    if (threadIdx.x == 0) *skip2 = (dmin > 0.0 && dmax <= 1e5 * dmin) ? 1 : 0;
+}
+
 }  // namespace
 
 cudaError_t launch_trinv_upper(int n, const double* R, double* Rinv, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int tt = n < 256 ? 128 : 256;
     count_launch();
-    k_trinv_upper<<<n, tt, size_t(n) * sizeof(double), s>>>(n, R, Rinv);
+    k_trinv_upper<<<n, tt, size_t(n) * sizeof(double), s>>>(n, R, Rinv, nullptr);
     return cudaGetLastError();
 }
 
@@ -246,13 +267,14 @@ size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms) {
     const size_t sq = size_t(cols) * cols * sizeof(double);
     const size_t p1 = gemm_f64_partials_bytes(cols, cols, rows, num_sms);
     const size_t p2 = gemm_f64_partials_bytes(rows, cols, cols, num_sms);
-    return 5 * sq + (p1 > p2 ? p1 : p2) + 6 * 256;
+    return 5 * sq + (p1 > p2 ? p1 : p2) + 8 * 256;
 }
 
 cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, double* R,
                            int64_t ldR, void* scratch, size_t scratch_cap, int* dev_status,
-                           int num_sms, cudaStream_t s) {
+                           int num_sms, cudaStream_t s, int adaptive) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (adaptive && R) return cudaErrorInvalidValue;     // R would be R1 or R2 R1
     Workspace ws;
     ws.base = static_cast<char*>(scratch);
     ws.cap = scratch_cap;
@@ -263,16 +285,19 @@ cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, doubl
     double* R1 = static_cast<double*>(ws.take(sq));
     double* Rtmp = static_cast<double*>(ws.take(sq));
     CholCtl* ctl = static_cast<CholCtl*>(ws.take(sizeof(CholCtl)));
+    int* skip2 = static_cast<int*>(ws.take(sizeof(int)));
     // the rest holds the split-K partial sums of the products
     const size_t off = (ws.used + 255) & ~size_t(255);
     const size_t part_cap = scratch_cap > off ? scratch_cap - off : 0;
     void* part = ws.take(part_cap);
-    if (!W || !Wsave || !Rinv || !R1 || !Rtmp || !part || !ctl) return cudaErrorInvalidValue;
+    if (!W || !Wsave || !Rinv || !R1 || !Rtmp || !part || !ctl || !skip2)
+        return cudaErrorInvalidValue;
     cudaError_t e;
     for (int pass = 0; pass < 2; ++pass) {
+        const int* sk = (pass == 1 && adaptive) ? skip2 : nullptr;
         // W = X^T X, upper triangle only (the Cholesky reads nothing else)
         e = launch_gemm_f64_tri(1, 1, cols, cols, rows, X, ldx, X, ldx, W, cols, part, part_cap,
-                                num_sms, s);
+                                num_sms, s, sk);
         if (e != cudaSuccess) return e;
         if (pass == 0) {
             e = cudaMemcpyAsync(Wsave, W, sq, cudaMemcpyDeviceToDevice, s);
@@ -280,7 +305,7 @@ cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, doubl
         }
         if (cols <= 128) {
             count_launch();
-            k_cholesky<<<1, CT, 0, s>>>(cols, W, Wsave, rows, pass == 0 ? 1 : 0, dev_status);
+            k_cholesky<<<1, CT, 0, s>>>(cols, W, Wsave, rows, pass == 0 ? 1 : 0, dev_status, sk);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         } else {
             e = cudaMemsetAsync(ctl, 0, sizeof(CholCtl), s);
@@ -301,19 +326,26 @@ cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, doubl
             int shift = pass == 0 ? 1 : 0;
             int64_t rows_ = rows;
             int64_t budget = 16LL << 20;
-            void* args[] = {&n_, &W, &Wsave, &rows_, &shift, &ctl, &dev_status, &budget, &stage};
+            const int* skp = sk;
+            void* args[] = {&n_, &W, &Wsave, &rows_, &shift, &ctl, &dev_status, &budget, &stage,
+                            &skp};
             count_launch();
             e = cudaLaunchCooperativeKernel((const void*)k_cholesky_coop, dim3(grid), dim3(CBT),
                                             args, dsm, s);
             if (e != cudaSuccess) return e;
         }
+        if (pass == 0 && adaptive) {
+            count_launch();
+            k_qr_decide<<<1, 32, 0, s>>>(cols, W, skip2);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         const int tt = cols < 256 ? 128 : 256;
         count_launch();
-        k_trinv_upper<<<cols, tt, size_t(cols) * sizeof(double), s>>>(cols, W, Rinv);
+        k_trinv_upper<<<cols, tt, size_t(cols) * sizeof(double), s>>>(cols, W, Rinv, sk);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // X <- X Rinv (the reduction of the partial sums writes X after the product)
         e = launch_gemm_f64_tri(0, 2, rows, cols, cols, X, ldx, Rinv, cols, X, ldx, part,
-                                part_cap, num_sms, s);
+                                part_cap, num_sms, s, sk);
         if (e != cudaSuccess) return e;
         if (pass == 0) {
             e = cudaMemcpyAsync(R1, W, sq, cudaMemcpyDeviceToDevice, s);
