@@ -696,6 +696,74 @@ def run_fixed_precision(args, w):
     return 0
 
 
+def run_singlepass(args, w):
+    """Alg. singlepasslu (Sec. 5) on the workload at rank k: one read of A
+    from HBM (column panels re-read from L2), in the requested precision and
+    in FP64.  value counts the two products G = A^T Omega, H = A G."""
+    import torch
+    import paper_2002_07138_gb300 as plu
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    Ad = replica_workload(w, rank).build("cuda")
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+    ctx = plu.Context(local, stream.cuda_stream)
+    prec = args.prec if args.prec in ("fp64", "fp32", "tf32") else "tf32"
+
+    def timed(A, pr, steps, warmup):
+        for i in range(warmup):
+            plu.plu_singlepass(ctx, A, w.k, seed=i, prec=pr)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            res = plu.plu_singlepass(ctx, A, w.k, seed=1000 + i, prec=pr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, res
+
+    def rel_error(res, A):
+        p, q, L, U = res[:4]
+        Ap = A.double()[p.long()][:, q.long()]
+        return float(torch.linalg.norm(Ap - L @ U) / torch.linalg.norm(A.double()))
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    dist_barrier(ws)
+    ms, res = timed(Ad, prec, args.steps, args.warmup)
+    dist_barrier(ws)
+    clk = clocks.stop()
+    ms = dist_max(ws, ms)
+    err = rel_error(res, Ad)
+    fp64 = {}
+    if not args.skip_fp64:
+        A64 = synth_colmajor(Ad.double())
+        ms64, r64 = timed(A64, "fp64", 2, 1)
+        fp64 = {"ms_per_step": ms64, "rel_error": rel_error(r64, Ad)}
+        del A64
+    flops = 4.0 * w.m * w.n * w.k
+    abytes = w.m * w.n * Ad.element_size()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": flops * ws / (ms / 1e3) / 1e12, "unit": "TFLOP/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32"}[prec], "data": "synthetic",
+            "config": {"workload": w.name, "algo": "singlepass", "m": w.m, "n": w.n, "k": w.k,
+                       "sigma": w.sigma, "pass_precision": prec, "between_passes": "f64",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "rel_error": err, "hbm_gbs_one_read_of_A": abytes / (ms / 1e3) / 1e9,
+            "fp64_plain": fp64,
+            "speedup_vs_fp64_plain": (fp64["ms_per_step"] / ms) if fp64 else None,
+            "gpu_launches": res[4]["launches"], "clocks": clk,
+        }))
+    ctx.close()
+    return 0
+
+
 def synth_colmajor(t):
     import synth
     return synth.colmajor(t)
@@ -711,6 +779,8 @@ def main():
     ap.add_argument("--prec", default="tf32", choices=["fp64", "fp32", "tf32", "bf16", "fp8"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--algo", default="powerlu", choices=["powerlu", "singlepass"],
+                    help="singlepass: Alg. singlepasslu (rank k, one read of A) on the workload")
     args = ap.parse_args()
     if args.workload == "batched_512":
         if args.impl == "reference":
@@ -723,6 +793,8 @@ def main():
         return run_reference(args, w)
     if w.eps:
         return run_fixed_precision(args, w)
+    if args.algo == "singlepass":
+        return run_singlepass(args, w)
     return run_ours(args, w)
 
 

@@ -29,7 +29,8 @@ from .philox import philox4x32_10, STREAM_OMEGA_N, STREAM_OMEGA_M, STREAM_OMEGA_
 from .gaussian import ln_pos, sincos_turn, gaussian_matrix
 from .lu import getrf, lu_permuted_L, lu_full
 from .qr import qr_economy
-from .powerlu import (gpowerlu, powerlu, adaptive_rank, rank_scan, powerlu_fp, randlu,
+from .powerlu import (gpowerlu, powerlu, adaptive_rank, adaptive_rank_restart, Remainder,
+                      RESTART_STREAM_STRIDE, rank_scan, powerlu_fp, randlu,
                       basic_power_iteration_lu, singlepass, PassCounter)
 from .metrics import (rel_lu_error, eckart_young_error, eckart_young_rank,
                       max_principal_sine)
@@ -38,7 +39,8 @@ __all__ = [
     "philox4x32_10", "STREAM_OMEGA_N", "STREAM_OMEGA_M", "STREAM_OMEGA_SP",
     "ln_pos", "sincos_turn", "gaussian_matrix",
     "getrf", "lu_permuted_L", "lu_full", "qr_economy",
-    "gpowerlu", "powerlu", "adaptive_rank", "rank_scan", "powerlu_fp", "randlu",
+    "gpowerlu", "powerlu", "adaptive_rank", "adaptive_rank_restart", "Remainder",
+    "RESTART_STREAM_STRIDE", "rank_scan", "powerlu_fp", "randlu",
     "basic_power_iteration_lu", "singlepass", "PassCounter",
     "rel_lu_error", "eckart_young_error", "eckart_young_rank", "max_principal_sine",
 ]

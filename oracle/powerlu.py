@@ -22,7 +22,17 @@ Readings of silent or garbled points:
 * Alg. singlepasslu: Omega is m x k (its step 1), G^{dagger T} = G (G^T G)^-1,
   U = L2^T (Sec. 5, "U = L_2^T");
 * Alg. rlu: "LU with column pivoting" of the k x n matrix B is lu(B^T):
-  Q B^T = L' U', L_b = U'^T, U_b = L'^T.
+  Q B^T = L' U', L_b = U'^T, U_b = L'^T;
+* the restart of the Remark after Alg. adaptivewithoutupdating: when the l
+  columns of a round leave E > eps^2 ||A||_F^2, the next round reruns the
+  algorithm on the remainder A_r = A - A W W^T (W = every basis column so
+  far) with a fresh Gaussian matrix (Philox streams shifted by 16 per round),
+  the indicator E carrying over; the remainder is applied as
+  A_r X = A X - G (W^T X), A_r^T Z = A^T Z - W (G^T Z) with G = A W the
+  stacked G's of the earlier rounds (equal in exact arithmetic, since each
+  round's basis lies in the row space of its remainder, orthogonal to W);
+  k is the total number of columns consumed and Alg. powerlufp's tail runs
+  on [G] and [W].
 """
 import numpy as np
 
@@ -53,10 +63,41 @@ class PassCounter:
 
 
 def _wrap(A):
-    return A if isinstance(A, PassCounter) else PassCounter(A)
+    return A if isinstance(A, (PassCounter, Remainder)) else PassCounter(A)
 
 
-def gpowerlu(A, l, v, seed):
+class Remainder:
+    """A_r = A - A W W^T applied through G = A W (see the module notes);
+    every product is one pass over A."""
+
+    def __init__(self, Ac, W, G):
+        self.base = Ac
+        self.W = W
+        self.G = G
+
+    @property
+    def A(self):
+        return self.base.A
+
+    @property
+    def shape(self):
+        return self.base.shape
+
+    @property
+    def passes(self):
+        return self.base.passes
+
+    def mul(self, X):           # A_r X
+        return self.base.mul(X) - self.G @ (self.W.T @ X)
+
+    def tmul(self, Z):          # A_r^T Z
+        return self.base.tmul(Z) - self.W @ (self.G.T @ Z)
+
+
+RESTART_STREAM_STRIDE = 16       # Philox stream shift per restart round
+
+
+def gpowerlu(A, l, v, seed, stream_shift=0):
     """Alg. gpowerlu: orthonormal basis V (n x l) of (A^T A)^p A^T Omega
     (v even, Omega m x l) or (A^T A)^p Omega (v odd, Omega n x l),
     p = floor((v-1)/2), with LU re-orthogonalisation between passes and a
@@ -67,13 +108,13 @@ def gpowerlu(A, l, v, seed):
         raise ValueError("v >= 2 required (Alg. gpowerlu)")
     p = (v - 1) // 2
     if v % 2 == 0:
-        Omega = gaussian_matrix(m, l, seed, STREAM_OMEGA_M)
+        Omega = gaussian_matrix(m, l, seed, STREAM_OMEGA_M + stream_shift)
         if v > 2:
             V = lu_permuted_L(Ac.tmul(Omega))
         else:
             V, _ = qr_economy(Ac.tmul(Omega))
     else:
-        V = gaussian_matrix(n, l, seed, STREAM_OMEGA_N)
+        V = gaussian_matrix(n, l, seed, STREAM_OMEGA_N + stream_shift)
     for i in range(1, p + 1):
         V = lu_permuted_L(Ac.mul(V))
         if i == p:
@@ -106,12 +147,13 @@ def powerlu(A, k, l, v, seed, return_basis=False):
     return p, q, L, U
 
 
-def rank_scan(G, normA2, eps, b, precise=False):
+def rank_scan(G, normA2, eps, b, precise=False, E_start=None):
     """The loop of Alg. adaptivewithoutupdating (steps 4-10), or with the
-    per-column refinement of Sec. 6.4, on G = A V and E = ||A||_F^2.
+    per-column refinement of Sec. 6.4, on G = A V and E = ||A||_F^2 (or the
+    indicator E_start carried over from an earlier round).
     Returns (k, E, met)."""
-    E = float(normA2)
-    acc = eps * eps * E
+    E = float(normA2) if E_start is None else float(E_start)
+    acc = eps * eps * float(normA2)
     l = G.shape[1]
     k = 0
     met = False
@@ -150,11 +192,37 @@ def adaptive_rank(A, eps, b, l, v, seed, precise=False):
     return k, V, G, E, met
 
 
-def powerlu_fp(A, eps, b, l, v, seed, precise=False):
-    """Alg. powerlufp.  Returns (k, p, q, L, U, E, met)."""
+def adaptive_rank_restart(A, eps, b, l, v, seed, precise=False, max_rounds=1):
+    """Alg. adaptivewithoutupdating with the restart of its Remark: up to
+    max_rounds rounds, round r on the remainder of the r earlier bases.
+    Returns (k, W, G, E, met, rounds): W n x k, G = A W m x k."""
     Ac = _wrap(A)
-    k, V, G, E, met = adaptive_rank(Ac, eps, b, l, v, seed, precise)
-    p, q, L, U, _ = _lu_tail(G[:, :k], V[:, :k])
+    m, n = Ac.shape
+    nA2 = float(np.sum(Ac.A * Ac.A))
+    W = np.zeros((n, 0))
+    G = np.zeros((m, 0))
+    E = nA2
+    met = False
+    rounds = 0
+    for r in range(max_rounds):
+        Ar = Ac if r == 0 else Remainder(Ac, W, G)
+        V = gpowerlu(Ar, l, v, seed, stream_shift=RESTART_STREAM_STRIDE * r)
+        Gr = Ar.mul(V)
+        kr, E, met = rank_scan(Gr, nA2, eps, b, precise, E_start=E)
+        W = np.hstack([W, V[:, :kr]])
+        G = np.hstack([G, Gr[:, :kr]])
+        rounds = r + 1
+        if met:
+            break
+    return W.shape[1], W, G, E, met, rounds
+
+
+def powerlu_fp(A, eps, b, l, v, seed, precise=False, max_rounds=1):
+    """Alg. powerlufp (with max_rounds > 1: the restart of the Remark after
+    Alg. adaptivewithoutupdating).  Returns (k, p, q, L, U, E, met)."""
+    Ac = _wrap(A)
+    k, W, G, E, met, _ = adaptive_rank_restart(Ac, eps, b, l, v, seed, precise, max_rounds)
+    p, q, L, U, _ = _lu_tail(G, W)
     return k, p, q, L, U, E, met
 
 

@@ -111,3 +111,59 @@ def test_table1_powerlu_fp_rank_type2_n2000():
         kopt = eckart_young_rank(sig, eps)
         k, *_ = adaptive_rank(A, eps, 10, 500, 4, seed=3, precise=True)
         assert kopt <= k <= kopt + 10
+
+
+# ---- the restart of the Remark after Alg. adaptivewithoutupdating
+def _restart_case():
+    sig = 1.0 / np.arange(1, 201)
+    A = synth.svd_matrix_np(300, 200, sig, seed=21)
+    return A, sig
+
+
+def test_remainder_operator_equals_explicit_remainder():
+    """A_r X and A_r^T Z through G = A W equal the explicit A - A W W^T."""
+    from oracle import Remainder, PassCounter
+    A, _ = _restart_case()
+    W = gpowerlu(A, 24, 3, seed=4)                       # orthonormal n x 24
+    Ac = PassCounter(A)
+    R = Remainder(Ac, W, A @ W)
+    Ar = A - A @ W @ W.T
+    X = synth.gaussian_np(200, 7, 5)
+    Z = synth.gaussian_np(300, 7, 6)
+    assert np.abs(R.mul(X) - Ar @ X).max() <= 1e-12 * np.abs(Ar @ X).max()
+    assert np.abs(R.tmul(Z) - Ar.T @ Z).max() <= 1e-12 * np.abs(Ar.T @ Z).max()
+    assert Ac.passes == 2
+
+
+@pytest.mark.parametrize("v", [3, 4])
+def test_restart_reaches_tolerance_with_orthonormal_union(v):
+    """With l too small for eps, later rounds on the remainder reach it: the
+    union of the rounds' bases is orthonormal, the carried-over indicator E
+    equals the explicit residual ||A - A W W^T||_F^2 (Thm. errorindicator),
+    the factors meet eps, and each round reads A v times."""
+    from oracle import adaptive_rank_restart, PassCounter, eckart_young_rank
+    A, sig = _restart_case()
+    eps, b, l = 0.05, 8, 24
+    r_svd = eckart_young_rank(sig, eps)
+    assert r_svd > l                                      # one round cannot succeed
+    Ac = PassCounter(A)
+    k, W, G, E, met, rounds = adaptive_rank_restart(Ac, eps, b, l, v, seed=2, max_rounds=6)
+    assert met and rounds >= 2 and k >= r_svd and k <= rounds * l
+    assert Ac.passes == rounds * v
+    assert np.abs(W.T @ W - np.eye(k)).max() <= 1e-10
+    assert np.abs(G - A @ W).max() <= 1e-10 * np.abs(G).max()
+    resid = np.sum((A - A @ W @ W.T) ** 2)
+    assert abs(E - resid) <= 1e-9 * np.sum(A * A)
+    kk, p, q, L, U, E2, met2 = powerlu_fp(A, eps, b, l, v, seed=2, max_rounds=6)
+    assert kk == k and met2
+    assert rel_lu_error(A, p, q, L, U) <= eps
+
+
+def test_restart_single_round_is_the_plain_algorithm():
+    """max_rounds = 1 is Alg. adaptivewithoutupdating itself: not met, k = l."""
+    from oracle import adaptive_rank_restart
+    A, _ = _restart_case()
+    k, W, G, E, met, rounds = adaptive_rank_restart(A, 0.05, 8, 24, 3, seed=2, max_rounds=1)
+    k1, V1, G1, E1, met1 = adaptive_rank(A, 0.05, 8, 24, 3, seed=2)
+    assert (k, met, rounds) == (24, False, 1) and (k1, met1) == (24, False)
+    assert np.array_equal(W, V1) and np.array_equal(G, G1) and E == E1
