@@ -84,7 +84,7 @@ typedef struct {
     double flops_passes;    /* algorithmic flops of the passes, 2 m n cols each   */
     double bytes_passes;    /* algorithmic bytes of the passes (A + operands)    */
     int32_t launches;       /* library kernels launched by the call              */
-    int32_t reserved;
+    int32_t rounds;         /* fixed precision: rounds of the rank determination */
 } plu_report;
 
 typedef struct plu_ctx plu_ctx;
@@ -184,6 +184,25 @@ plu_status plu_powerlu_fp(plu_ctx* ctx, const plu_matrix* A, double eps, int b, 
                           int v, int precise, uint64_t seed, plu_prec prec, int* k_out,
                           int32_t* p, int32_t* q, double* L, int64_t ldL, double* U,
                           int64_t ldU, plu_report* rep);
+
+/* Fixed precision with the restart of the Remark after Alg.
+ * adaptivewithoutupdating: when the l columns of a round leave
+ * E > eps^2 ||A||_F^2, the next round reruns Alg. adaptivewithoutupdating on
+ * the remainder A - A W W^T (W: every basis column so far, applied as
+ * A X - (A W)(W^T X)) with a fresh Gaussian matrix (the Philox streams of
+ * round r are those of round 0 plus 16 r), the indicator E carrying over; at
+ * most max_rounds rounds (max_rounds * l <= 2048 and < min(m, n)).  The rank k
+ * is the number of columns consumed over all rounds; Alg. powerlufp's tail
+ * runs on the union of the rounds' bases.  L must hold m x (l max_rounds)
+ * (ldL >= m) and U (l max_rounds) x n (ldU >= l max_rounds).  Returns
+ * PLU_TOL_NOT_MET with valid factors of rank l max_rounds when eps is not
+ * reached.  rep->rounds receives the rounds used.  One stream synchronisation
+ * per round; v passes over A per round plus one for ||A||_F.  The paper's
+ * interface is this one with max_rounds = 1 (plu_powerlu_fp). */
+plu_status plu_powerlu_fp_restart(plu_ctx* ctx, const plu_matrix* A, double eps, int b, int l,
+                                  int v, int precise, int max_rounds, uint64_t seed,
+                                  plu_prec prec, int* k_out, int32_t* p, int32_t* q, double* L,
+                                  int64_t ldL, double* U, int64_t ldU, plu_report* rep);
 
 /* Single pass (Alg. singlepasslu, Sec. 5): Omega m x k, G = A^T Omega and
  * H = A G from one read of A, then two LUs.  1 <= k < min(m, n).

@@ -35,7 +35,7 @@ class plu_report(ctypes.Structure):
     _fields_ = [("ms_total", c_dbl), ("ms_passes", c_dbl), ("passes", c_i32), ("rank", c_i32),
                 ("indicator", c_dbl), ("normA2", c_dbl), ("info1", c_i32), ("info2", c_i32),
                 ("flops_passes", c_dbl), ("bytes_passes", c_dbl), ("launches", c_i32),
-                ("reserved", c_i32)]
+                ("rounds", c_i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -70,6 +70,10 @@ SIGNATURES = {
     "plu_powerlu_fp": (c_int, [c_vp, ctypes.POINTER(plu_matrix), c_dbl, c_int, c_int, c_int, c_int,
                                c_u64, c_int, ctypes.POINTER(c_int), c_vp, c_vp, c_vp, c_i64, c_vp,
                                c_i64, ctypes.POINTER(plu_report)]),
+    "plu_powerlu_fp_restart": (c_int, [c_vp, ctypes.POINTER(plu_matrix), c_dbl, c_int, c_int, c_int,
+                                       c_int, c_int, c_u64, c_int, ctypes.POINTER(c_int), c_vp,
+                                       c_vp, c_vp, c_i64, c_vp, c_i64,
+                                       ctypes.POINTER(plu_report)]),
     "plu_singlepass": (c_int, [c_vp, ctypes.POINTER(plu_matrix), c_int, c_u64, c_int, c_vp, c_vp,
                                c_vp, c_i64, c_vp, c_i64, ctypes.POINTER(plu_report)]),
     "plu_lu_reorth_static": (c_int, [c_vp, c_i64, c_int, c_vp, c_i64, ctypes.c_char_p,
@@ -250,21 +254,29 @@ def plu_powerlu(ctx, A, k, l, v, seed=0, prec="fp64"):
     return p, q, L, U, rep.as_dict()
 
 
-def plu_powerlu_fp(ctx, A, eps, b, l, v, seed=0, prec="fp64", precise=False):
-    """Fixed precision.  Returns (k, p, q, L[:, :k], U[:k], met, report dict)."""
+def plu_powerlu_fp(ctx, A, eps, b, l, v, seed=0, prec="fp64", precise=False, max_rounds=1):
+    """Fixed precision (max_rounds > 1: with the restart on the remainder,
+    plu_powerlu_fp_restart).  Returns (k, p, q, L[:, :k], U[:k], met, report dict)."""
     torch = _torch()
     m, n = A.shape
+    K = l * max_rounds
     p = torch.empty(m, dtype=torch.int32, device=A.device)
     q = torch.empty(n, dtype=torch.int32, device=A.device)
-    L = colmajor_empty(m, l, device=A.device)
-    U = colmajor_empty(l, n, device=A.device)
+    L = colmajor_empty(m, K, device=A.device)
+    U = colmajor_empty(K, n, device=A.device)
     rep = plu_report()
     k = c_int()
     Am = as_plu_matrix(A)
-    st = ctx.check(lib().plu_powerlu_fp(ctx.handle, ctypes.byref(Am), float(eps), b, l, v,
-                                        int(bool(precise)), seed, PREC[prec], ctypes.byref(k),
-                                        _ptr(p), _ptr(q), _ptr(L), _ld(L), _ptr(U), _ld(U),
-                                        ctypes.byref(rep)), allow=(6,))
+    if max_rounds == 1:
+        st = ctx.check(lib().plu_powerlu_fp(ctx.handle, ctypes.byref(Am), float(eps), b, l, v,
+                                            int(bool(precise)), seed, PREC[prec], ctypes.byref(k),
+                                            _ptr(p), _ptr(q), _ptr(L), _ld(L), _ptr(U), _ld(U),
+                                            ctypes.byref(rep)), allow=(6,))
+    else:
+        st = ctx.check(lib().plu_powerlu_fp_restart(
+            ctx.handle, ctypes.byref(Am), float(eps), b, l, v, int(bool(precise)), max_rounds,
+            seed, PREC[prec], ctypes.byref(k), _ptr(p), _ptr(q), _ptr(L), _ld(L), _ptr(U), _ld(U),
+            ctypes.byref(rep)), allow=(6,))
     kk = k.value
     return kk, p, q, L[:, :kk], U[:kk, :], st == 0, rep.as_dict()
 

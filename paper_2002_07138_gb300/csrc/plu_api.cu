@@ -38,6 +38,7 @@ namespace {
 constexpr uint32_t kStreamOmegaN = 1;   // n x l (odd v)
 constexpr uint32_t kStreamOmegaM = 2;   // m x l (even v)
 constexpr uint32_t kStreamOmegaSP = 3;  // m x k (single pass)
+constexpr uint32_t kStreamRestartStride = 16;   // restart round r: streams + 16 r
 
 plu_status fail(plu_ctx* c, plu_status st, const char* fmt, ...) {
     if (c) {
@@ -251,20 +252,51 @@ struct PassTimer {
     }
 };
 
+// The remainder A_r = A - A W W^T of a restart round (the Remark after
+// Alg. adaptivewithoutupdating), applied through G = A W:
+// A_r X = A X - G (W^T X), A_r^T Z = A^T Z - W (G^T Z).  W (n x kw) and G
+// (m x kw) are FP64, T (kw x cols) is scratch.
+struct Remainder {
+    const double* W = nullptr;
+    const double* G = nullptr;
+    int kw = 0;
+    double* T = nullptr;
+};
+
+// Y -= the remainder's correction of a pass Y = op(A) X (cols columns).
+plu_status remainder_correct(plu_ctx* c, const plu_matrix* A, const Remainder& r, int trans,
+                             const double* X, int64_t ldx, int cols, double* Y, int64_t ldy,
+                             char* step, size_t step_cap) {
+    if (!r.W || r.kw < 1) return PLU_OK;
+    const int64_t m = A->m, n = A->n;
+    // T = W^T X (A X) or G^T X (A^T X); then Y -= G T or W T, in FP64
+    PLU_CUDA(c, launch_gemm_f64(1, 0, r.kw, cols, trans ? m : n, trans ? r.G : r.W, trans ? m : n,
+                                X, ldx, r.T, r.kw, step, step_cap, c->num_sms, c->stream));
+    PLU_CUDA(c, launch_gemm_simt(0, trans ? n : m, cols, r.kw, trans ? r.W : r.G, PLU_F64,
+                                 trans ? n : m, r.T, r.kw, Y, ldy, PLU_FP64, step, step_cap,
+                                 nullptr, c->num_sms, c->stream, -1));
+    return PLU_OK;
+}
+
 // Alg. gpowerlu into V (n x l).  Returns the number of passes launched.
 // The final QR orthonormalises only the leading qr_cols columns of the
 // n x l product: Q(:, 1:j) depends on X(:, 1:j) alone, and the fixed-rank
-// path reads only V(:, 1:k) (Alg. bpowerlu step 3 and the tail).
+// path reads only V(:, 1:k) (Alg. bpowerlu step 3 and the tail).  With a
+// remainder (restart round r), every pass is over A_r and Omega comes from
+// the streams shifted by 16 r.
 plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t seed, int prec,
                         double* V, double* Z, char* step, size_t step_cap, PassTimer& pt,
-                        int* passes, const QuantA* q, int qr_cols, int adaptive_qr) {
+                        int* passes, const QuantA* q, int qr_cols, int adaptive_qr,
+                        const Remainder& rem = Remainder(), int round = 0) {
     const int64_t m = A->m, n = A->n;
     const int p = (v - 1) / 2;
+    const uint32_t shift = kStreamRestartStride * uint32_t(round);
     int np = 0;
     auto pass = [&](int trans, const double* X, int64_t ldx, double* Y, int64_t ldy) -> plu_status {
         pt.mark();
         PLU_TRY(do_pass(c, A, trans, X, ldx, l, prec, Y, ldy, step, step_cap, q));
         pt.mark();
+        PLU_TRY(remainder_correct(c, A, rem, trans, X, ldx, l, Y, ldy, step, step_cap));
         ++np;
         return PLU_OK;
     };
@@ -280,12 +312,12 @@ plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t 
         return PLU_OK;
     };
     if (v % 2 == 0) {
-        PLU_CUDA(c, launch_gaussian(m, l, seed, kStreamOmegaM, Z, m, c->stream));
+        PLU_CUDA(c, launch_gaussian(m, l, seed, kStreamOmegaM + shift, Z, m, c->stream));
         PLU_TRY(pass(1, Z, m, V, n));                 // A^T Omega
         if (v > 2) PLU_TRY(reorth(n, V));
         else PLU_TRY(qr(V));
     } else {
-        PLU_CUDA(c, launch_gaussian(n, l, seed, kStreamOmegaN, V, n, c->stream));
+        PLU_CUDA(c, launch_gaussian(n, l, seed, kStreamOmegaN + shift, V, n, c->stream));
     }
     for (int i = 1; i <= p; ++i) {
         PLU_TRY(pass(0, V, n, Z, m));                 // A V
@@ -581,10 +613,14 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
     return finish(c);
 }
 
-plu_status plu_powerlu_fp(plu_ctx* c, const plu_matrix* A, double eps, int b, int l, int v,
-                          int precise, uint64_t seed, plu_prec prec, int* k_out, int32_t* p,
-                          int32_t* q, double* L, int64_t ldL, double* U, int64_t ldU,
-                          plu_report* rep) {
+// Alg. powerlufp with up to max_rounds rounds of Alg. adaptivewithoutupdating
+// (the restart of its Remark: round r runs on the remainder A - A W W^T of the
+// earlier rounds' bases W, with Omega from streams shifted by 16 r, and the
+// indicator E carries over).  One round is Alg. powerlufp as printed.
+plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b, int l, int v,
+                             int precise, int max_rounds, uint64_t seed, plu_prec prec,
+                             int* k_out, int32_t* p, int32_t* q, double* L, int64_t ldL,
+                             double* U, int64_t ldU, plu_report* rep) {
     PLU_TRY(bind(c));
     PLU_TRY(check_matrix(c, A));
     PLU_TRY(check_prec(c, prec, A));
@@ -594,12 +630,27 @@ plu_status plu_powerlu_fp(plu_ctx* c, const plu_matrix* A, double eps, int b, in
     if (b < 1 || l < b || l >= mn) return fail(c, PLU_EINVAL, "need 1 <= b <= l < min(m, n)");
     if (v < 2) return fail(c, PLU_EINVAL, "need v >= 2 passes");
     if (l > 2048) return fail(c, PLU_EINVAL, "l > 2048 is not supported");
-    if (!k_out || !p || !q || !L || !U || ldL < m || ldU < l) return fail(c, PLU_EINVAL, "bad outputs");
-    const PowerLUPlan pl = plan_powerlu(m, n, l, l, prec, c->num_sms);
-    PLU_TRY(ensure_ws(c, pl.total));
+    if (max_rounds < 1 || int64_t(max_rounds) * l > 2048 || int64_t(max_rounds) * l >= mn)
+        return fail(c, PLU_EINVAL, "need max_rounds >= 1 and max_rounds * l <= 2048, < min(m, n)");
+    const int K = l * max_rounds;                       // largest possible rank
+    if (!k_out || !p || !q || !L || !U || ldL < m || ldU < K)
+        return fail(c, PLU_EINVAL, "bad outputs (L needs m x %d, U %d x n)", K, K);
+    const PowerLUPlan pl = plan_powerlu(m, n, l, K, prec, c->num_sms);
+    // restart rounds: the union of the bases W (n x K), G = A W (m x K), and
+    // the corrections' scratch T (K x l)
+    Layout lay;
+    lay.total = pl.total;
+    const bool multi = max_rounds > 1;
+    const size_t oW = multi ? lay.add(size_t(n) * K * sizeof(double)) : 0;
+    const size_t oG = multi ? lay.add(size_t(m) * K * sizeof(double)) : 0;
+    const size_t oT = multi ? lay.add(size_t(K) * l * sizeof(double)) : 0;
+    PLU_TRY(ensure_ws(c, lay.total + 256));
     char* ws = c->ws;
     double* V = reinterpret_cast<double*>(ws + pl.V);
     double* Z = reinterpret_cast<double*>(ws + pl.Z);
+    double* Wu = multi ? reinterpret_cast<double*>(ws + oW) : nullptr;
+    double* Gu = multi ? reinterpret_cast<double*>(ws + oG) : nullptr;
+    double* T = multi ? reinterpret_cast<double*>(ws + oT) : nullptr;
     char* step = ws + pl.step;
     double* cn = reinterpret_cast<double*>(ws + pl.cn);
     void* nscr = ws + pl.cn + ((size_t(l) * sizeof(double) + 255) & ~size_t(255));
@@ -616,27 +667,54 @@ plu_status plu_powerlu_fp(plu_ctx* c, const plu_matrix* A, double eps, int b, in
     if (quant)
         PLU_CUDA(c, launch_tc_quantize(prec, static_cast<const float*>(A->data), m, n, A->ld,
                                        ws + pl.quant, &qa, c->num_sms, c->stream));
-    PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pl.step_bytes, pt, &np,
-                         quant ? &qa : nullptr, l, 0));
-    // G = A V (step 3), the v-th pass.  Its column norms decide the rank:
-    // E = ||A||_F^2 - sum ||G(:, j)||^2 must resolve eps^2 ||A||_F^2, which
-    // TF32 rounding (relative bias ~1e-3) cannot, so the mixed modes take this
-    // pass in FP32 arithmetic on the FP32 A.
-    pt.mark();
-    PLU_TRY(do_pass(c, A, 0, V, n, l, is_tc(prec) ? int(PLU_FP32) : int(prec), Z, m, step,
-                    pl.step_bytes));
-    pt.mark();
-    ++np;
-    PLU_CUDA(c, launch_colnorm2(m, l, Z, m, cn, c->stream));
-    PLU_CUDA(c, launch_rank_scan(cn, l, c->d_scal, eps, b, precise, c->d_kmet, c->d_scal + 1, c->stream));
-    PLU_CUDA(c, cudaMemcpyAsync(c->h_kmet, c->d_kmet, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    PLU_CUDA(c, cudaMemcpyAsync(c->h_scal, c->d_scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    PLU_CUDA(c, cudaStreamSynchronize(c->stream));
-    const int k = c->h_kmet[0];
-    const int met = c->h_kmet[1];
-    if (k < 1 || k > l) return fail(c, PLU_ECUDA, "rank scan returned k = %d", k);
+    int kw = 0, met = 0, rounds = 0;
+    for (int r = 0; r < max_rounds; ++r) {
+        Remainder rem;
+        if (r > 0) {
+            rem.W = Wu;
+            rem.G = Gu;
+            rem.kw = kw;
+            rem.T = T;
+        }
+        int npr = 0;
+        PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pl.step_bytes, pt, &npr,
+                             quant ? &qa : nullptr, l, 0, rem, r));
+        np += npr;
+        // G = A V (step 3), the v-th pass.  Its column norms decide the rank:
+        // E = ||A||_F^2 - sum ||G(:, j)||^2 must resolve eps^2 ||A||_F^2, which
+        // TF32 rounding (relative bias ~1e-3) cannot, so the mixed modes take
+        // this pass in FP32 arithmetic on the FP32 A.
+        pt.mark();
+        PLU_TRY(do_pass(c, A, 0, V, n, l, is_tc(prec) ? int(PLU_FP32) : int(prec), Z, m, step,
+                        pl.step_bytes));
+        pt.mark();
+        PLU_TRY(remainder_correct(c, A, rem, 0, V, n, l, Z, m, step, pl.step_bytes));
+        ++np;
+        PLU_CUDA(c, launch_colnorm2(m, l, Z, m, cn, c->stream));
+        PLU_CUDA(c, launch_rank_scan(cn, l, c->d_scal, eps, b, precise, c->d_kmet, c->d_scal + 1,
+                                     c->stream, r > 0 ? c->d_scal + 1 : nullptr));
+        PLU_CUDA(c, cudaMemcpyAsync(c->h_kmet, c->d_kmet, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        PLU_CUDA(c, cudaMemcpyAsync(c->h_scal, c->d_scal, 2 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->stream));
+        PLU_CUDA(c, cudaStreamSynchronize(c->stream));
+        const int kr = c->h_kmet[0];
+        met = c->h_kmet[1];
+        if (kr < 1 || kr > l) return fail(c, PLU_ECUDA, "rank scan returned k = %d", kr);
+        rounds = r + 1;
+        if (!multi) {
+            kw = kr;
+            break;
+        }
+        PLU_CUDA(c, launch_copy_cols(n, kr, V, n, Wu + size_t(kw) * n, n, c->stream));
+        PLU_CUDA(c, launch_copy_cols(m, kr, Z, m, Gu + size_t(kw) * m, m, c->stream));
+        kw += kr;
+        if (met) break;
+    }
+    const int k = kw;
     int32_t* info = reinterpret_cast<int32_t*>(c->d_kmet + 2);
-    PLU_TRY(run_tail(c, m, n, k, Z, V, ws, pl, step, p, q, L, ldL, U, ldU, info));
+    PLU_TRY(run_tail(c, m, n, k, multi ? Gu : Z, multi ? Wu : V, ws, pl, step, p, q, L, ldL, U,
+                     ldU, info));
     *k_out = k;
     if (rep) {
         PLU_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
@@ -655,12 +733,31 @@ plu_status plu_powerlu_fp(plu_ctx* c, const plu_matrix* A, double eps, int b, in
         rep->indicator = nA2 > 0 ? sqrt((E > 0 ? E : 0.0) / nA2) : 0.0;
         rep->info1 = hinfo[0];
         rep->info2 = hinfo[1];
+        rep->rounds = rounds;
         fill_pass_report(rep, A, np, l, 0, prec, false);
         rep->launches = int32_t(g_launches - launches0);
     }
     plu_status st = finish(c);
     if (st != PLU_OK) return st;
-    return met ? PLU_OK : fail(c, PLU_TOL_NOT_MET, "tolerance not met within l = %d columns", l);
+    return met ? PLU_OK
+               : fail(c, PLU_TOL_NOT_MET, "tolerance not met within %d round(s) of l = %d columns",
+                      rounds, l);
+}
+
+plu_status plu_powerlu_fp(plu_ctx* c, const plu_matrix* A, double eps, int b, int l, int v,
+                          int precise, uint64_t seed, plu_prec prec, int* k_out, int32_t* p,
+                          int32_t* q, double* L, int64_t ldL, double* U, int64_t ldU,
+                          plu_report* rep) {
+    return powerlu_fp_rounds(c, A, eps, b, l, v, precise, 1, seed, prec, k_out, p, q, L, ldL, U,
+                             ldU, rep);
+}
+
+plu_status plu_powerlu_fp_restart(plu_ctx* c, const plu_matrix* A, double eps, int b, int l,
+                                  int v, int precise, int max_rounds, uint64_t seed,
+                                  plu_prec prec, int* k_out, int32_t* p, int32_t* q, double* L,
+                                  int64_t ldL, double* U, int64_t ldU, plu_report* rep) {
+    return powerlu_fp_rounds(c, A, eps, b, l, v, precise, max_rounds, seed, prec, k_out, p, q, L,
+                             ldL, U, ldU, rep);
 }
 
 plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed, plu_prec prec,

@@ -152,7 +152,8 @@ k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t l
     }
 }
 
-// C(i, j) = sum_z P[z](i, j), z in increasing order, in FP64.
+// C(i, j) = sum_z P[z](i, j), z in increasing order, in FP64 (accum > 0: added
+// to C, accum < 0: subtracted from C).
 template <typename TC>
 __global__ void k_reduce_splits(int64_t M, int64_t N, int splits, const TC* __restrict__ P,
                                 double* __restrict__ C, int64_t ldc, int accum,
@@ -164,7 +165,7 @@ __global__ void k_reduce_splits(int64_t M, int64_t N, int splits, const TC* __re
         double sum = 0.0;
         for (int z = 0; z < splits; ++z) sum += double(P[int64_t(z) * total + e]);
         const int64_t i = e % M, j = e / M;
-        C[i + j * ldc] = accum ? C[i + j * ldc] + sum : sum;
+        C[i + j * ldc] = accum > 0 ? C[i + j * ldc] + sum : accum < 0 ? C[i + j * ldc] - sum : sum;
     }
 }
 

@@ -108,7 +108,7 @@ cudaError_t launch_gemm_simt(int trans, int64_t M, int64_t N, int64_t K, const v
                              double* C, int64_t ldc, int prec, void* partials,
                              size_t part_cap, float* b32_scratch, int num_sms, cudaStream_t s,
                              int accum = 0);
-// accum != 0: C += op(A) B instead of C = op(A) B.
+// accum > 0: C += op(A) B; accum < 0: C -= op(A) B; 0: C = op(A) B.
 // FP64 GEMM with transposed-B option for the small products of the tail:
 // C = A * op(B), op(B) = B (K x N) or B^T (B is N x K).
 cudaError_t launch_gemm_f64(int transA, int transB, int64_t M, int64_t N, int64_t K,
@@ -173,7 +173,7 @@ cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int 
 // (less works down to one split of each product; too little is an error).
 size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms);
 // adaptive != 0: the second CholeskyQR round runs only when the first
-// Cholesky factor's diagonal spread max|r_ii| / min|r_ii| exceeds 1e4 (the
+// Cholesky factor's diagonal spread max|r_ii| / min|r_ii| exceeds 1e5 (the
 // decision is taken on the device; the second round's kernels return at once
 // otherwise).  R (when requested) is then R1.
 cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, double* R,
@@ -190,10 +190,12 @@ cudaError_t launch_norm2(const void* A, int dtype, int64_t m, int64_t n, int64_t
 cudaError_t launch_colnorm2(int64_t rows, int cols, const double* G, int64_t ldg,
                             double* out, cudaStream_t s);
 // k/E/met from column norms (one thread): out[0] = k, out[1] = met (ints);
-// E written to *E_out (device double).
+// E written to *E_out (device double).  The scan starts from *E_start when
+// given (an indicator carried over from an earlier round), else from *normA2;
+// the tolerance is eps^2 *normA2 either way.
 cudaError_t launch_rank_scan(const double* colnorm2, int cols, const double* normA2,
                              double eps, int b, int precise, int* k_met, double* E_out,
-                             cudaStream_t s);
+                             cudaStream_t s, const double* E_start = nullptr);
 
 // -------------------------------------------------------------- helpers
 cudaError_t launch_copy_cols(int64_t rows, int cols, const double* src, int64_t lds,

@@ -63,11 +63,11 @@ k_colnorm2(int64_t rows, const double* __restrict__ G, int64_t ldg, double* __re
 }
 
 __global__ void k_rank_scan(const double* __restrict__ cn, int cols, const double* __restrict__ normA2,
-                            double eps, int b, int precise, int* __restrict__ k_met,
-                            double* __restrict__ E_out) {
+                            const double* __restrict__ E_start, double eps, int b, int precise,
+                            int* __restrict__ k_met, double* __restrict__ E_out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double E = *normA2;
-    const double acc = eps * eps * E;
+    double E = E_start ? *E_start : *normA2;
+    const double acc = eps * eps * *normA2;
     int k = 0, met = 0;
     for (int t1 = 0; t1 < cols && !met; t1 += b) {
         const int t2 = min(cols, t1 + b);
@@ -130,9 +130,10 @@ cudaError_t launch_colnorm2(int64_t rows, int cols, const double* G, int64_t ldg
 }
 
 cudaError_t launch_rank_scan(const double* colnorm2, int cols, const double* normA2, double eps,
-                             int b, int precise, int* k_met, double* E_out, cudaStream_t s) {
+                             int b, int precise, int* k_met, double* E_out, cudaStream_t s,
+                             const double* E_start) {
     count_launch();
-    k_rank_scan<<<1, 32, 0, s>>>(colnorm2, cols, normA2, eps, b, precise, k_met, E_out);
+    k_rank_scan<<<1, 32, 0, s>>>(colnorm2, cols, normA2, E_start, eps, b, precise, k_met, E_out);
     return cudaGetLastError();
 }
 

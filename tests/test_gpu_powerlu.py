@@ -103,6 +103,47 @@ def test_powerlu_fp_parity(ctx, precise):
     assert rep["passes"] == v + 1
 
 
+@pytest.mark.parametrize("v,precise", [(3, False), (4, True)])
+def test_powerlu_fp_restart_parity(ctx, v, precise):
+    """The restart of the Remark after Alg. adaptivewithoutupdating: l too
+    small for eps, later rounds on the remainder A - A W W^T reach it.  FP64
+    path: the same rank, rounds, pivots and factors as the oracle."""
+    sig = 1.0 / np.arange(1, 601)
+    A = synth.svd_matrix_np(900, 600, sig, seed=31)
+    eps, b, l, rounds = 0.06, 8, 40, 6
+    k, p, q, L, U, E, met = oracle.powerlu_fp(A, eps, b, l, v, seed=5, precise=precise,
+                                              max_rounds=rounds)
+    assert met and k > l
+    gk, gp, gq, gL, gU, gmet, rep = plu.plu_powerlu_fp(ctx, dev(A), eps, b, l, v, seed=5,
+                                                       prec="fp64", precise=precise,
+                                                       max_rounds=rounds)
+    assert (gk, gmet) == (k, met)
+    assert rep["rounds"] >= 2 and rep["passes"] == rep["rounds"] * v + 1
+    check_parity(A, (gp, gq, gL, gU), (p, q, L, U), tol=1e-9)
+    assert oracle.rel_lu_error(A, gp.cpu().numpy(), gq.cpu().numpy(), host(gL), host(gU)) <= eps
+    nA2 = float(np.sum(A * A))
+    assert abs(rep["indicator"] - math.sqrt(max(E, 0) / nA2)) <= 1e-8
+
+
+def test_powerlu_fp_restart_tf32_meets_tolerance(ctx):
+    """The restart in the TF32 mode: same rank as FP64, error within eps and
+    within 1.1x of the FP64 path."""
+    sig = 1.0 / np.arange(1, 1025)
+    A = synth.svd_matrix_np(2048, 1024, sig, seed=32)
+    A32 = A.astype(np.float32)
+    A64h = A32.astype(np.float64)
+    eps, b, l, v, rounds = 0.05, 16, 96, 3, 6
+    res = {}
+    for prec, Ad in (("fp64", dev(A64h)), ("tf32", dev(A32, torch.float32))):
+        gk, gp, gq, gL, gU, gmet, rep = plu.plu_powerlu_fp(ctx, Ad, eps, b, l, v, seed=7,
+                                                           prec=prec, max_rounds=rounds)
+        assert gmet and rep["rounds"] >= 2
+        res[prec] = (gk, oracle.rel_lu_error(A64h, gp.cpu().numpy(), gq.cpu().numpy(),
+                                             host(gL), host(gU)))
+    assert res["tf32"][0] == res["fp64"][0]
+    assert res["tf32"][1] <= eps and res["tf32"][1] <= 1.1 * res["fp64"][1]
+
+
 def test_powerlu_fp_tolerance_not_met(ctx):
     sig = synth.sigma_profile("type1", 300)
     A = synth.svd_matrix_np(400, 300, sig, seed=3)
