@@ -764,6 +764,79 @@ def run_singlepass(args, w):
     return 0
 
 
+def run_randlu(args, w):
+    """The paper's main speed comparison, on this GPU: RandLU (Alg. rlu with
+    Alg. basicpoweriteration, p power iterations, 2p + 2 passes over A)
+    against PowerLU with the same number of passes (v = 2p + 2), same A, same
+    rank and oversampling, same pass precision.  value counts RandLU's pass
+    FLOPs (2 m n l per pass, 2 m n k for the pass that forms B)."""
+    import numpy as np
+    import torch
+    import paper_2002_07138_gb300 as plu
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    Ad = replica_workload(w, rank).build("cuda")
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+    ctx = plu.Context(local, stream.cuda_stream)
+    prec = args.prec
+    piter = args.piter
+    v = 2 * piter + 2
+
+    def timed(fn, steps, warmup):
+        for i in range(warmup):
+            fn(i)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            res = fn(1000 + i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, res
+
+    def rel_error(res, A):
+        p, q, L, U = res[:4]
+        Ap = A.double()[p.long()][:, q.long()]
+        return float(torch.linalg.norm(Ap - L @ U) / torch.linalg.norm(A.double()))
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    dist_barrier(ws)
+    ms, res = timed(lambda s: plu.plu_randlu(ctx, Ad, w.k, w.l, piter, seed=s, prec=prec),
+                    args.steps, args.warmup)
+    dist_barrier(ws)
+    clk = clocks.stop()
+    ms = dist_max(ws, ms)
+    err = rel_error(res, Ad)
+    ms_p, res_p = timed(lambda s: plu.plu_powerlu(ctx, Ad, w.k, w.l, v, seed=s, prec=prec),
+                        args.steps, args.warmup)
+    err_p = rel_error(res_p, Ad)
+    flops = 2.0 * w.m * w.n * (w.l * (v - 1) + w.k)
+    sig = w.sigma_values()
+    opt = float(np.sqrt(np.sum(sig[w.k:] ** 2) / np.sum(sig ** 2)))
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": flops * ws / (ms / 1e3) / 1e12, "unit": "TFLOP/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32"}.get(prec, prec), "data": "synthetic",
+            "config": {"workload": w.name, "algo": "randlu", "m": w.m, "n": w.n, "k": w.k,
+                       "l": w.l, "power_iterations": piter, "passes": v, "sigma": w.sigma,
+                       "pass_precision": prec, "between_passes": "f64",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "rel_error": err, "eckart_young_optimum": opt,
+            "powerlu_same_passes": {"v": v, "ms_per_step": ms_p, "rel_error": err_p},
+            "speedup_powerlu_vs_randlu": ms / ms_p,
+            "gpu_launches": res[4]["launches"], "clocks": clk,
+        }))
+    ctx.close()
+    return 0
+
+
 def synth_colmajor(t):
     import synth
     return synth.colmajor(t)
@@ -779,8 +852,12 @@ def main():
     ap.add_argument("--prec", default="tf32", choices=["fp64", "fp32", "tf32", "bf16", "fp8"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--algo", default="powerlu", choices=["powerlu", "singlepass"],
-                    help="singlepass: Alg. singlepasslu (rank k, one read of A) on the workload")
+    ap.add_argument("--algo", default="powerlu", choices=["powerlu", "singlepass", "randlu"],
+                    help="singlepass: Alg. singlepasslu (rank k, one read of A) on the workload; "
+                         "randlu: RandLU with --piter power iterations against PowerLU with "
+                         "as many passes")
+    ap.add_argument("--piter", type=int, default=1,
+                    help="power iterations of RandLU (--algo randlu): 2 piter + 2 passes")
     args = ap.parse_args()
     if args.workload == "batched_512":
         if args.impl == "reference":
@@ -795,6 +872,8 @@ def main():
         return run_fixed_precision(args, w)
     if args.algo == "singlepass":
         return run_singlepass(args, w)
+    if args.algo == "randlu":
+        return run_randlu(args, w)
     return run_ours(args, w)
 
 

@@ -211,6 +211,20 @@ plu_status plu_singlepass(plu_ctx* ctx, const plu_matrix* A, int k, uint64_t see
                           plu_prec prec, int32_t* p, int32_t* q, double* L, int64_t ldL,
                           double* U, int64_t ldU, plu_report* rep);
 
+/* RandLU with power iteration (Alg. rlu, steps 1-3 replaced by
+ * Alg. basicpoweriteration): the randomized LU the paper compares PowerLU
+ * with.  Omega is n x l (the stream plu_powerlu uses for odd v); Y = A Omega,
+ * then `piter` >= 0 rounds of A^T / A products, each re-orthogonalised by the
+ * permuted L of an LU; the last product's full LU gives P and L_y (first k
+ * columns); B = L_y^+ P A (Eq. pseudoinverse) is formed as
+ * B^T = A^T Q R^{-T} with W = P^T L_y = Q R (CholeskyQR2), and
+ * Q B^T = L' U' gives L = L_y U'^T, U = L'^T.  The call reads A 2 piter + 2
+ * times.  1 <= k <= l < min(m, n), l <= 2048.  Outputs as plu_powerlu:
+ * A[p[i], q[j]] ~= (L U)(i, j). */
+plu_status plu_randlu(plu_ctx* ctx, const plu_matrix* A, int k, int l, int piter,
+                      uint64_t seed, plu_prec prec, int32_t* p, int32_t* q, double* L,
+                      int64_t ldL, double* U, int64_t ldU, plu_report* rep);
+
 /* One problem of a batch (plu_batched).  A is m x n, column-major, device
  * memory, element type `dtype` (plu_dtype).  algo 0: PowerLU (Alg. bpowerlu
  * with Alg. gpowerlu), 1 <= k <= l < min(m, n), v >= 2; algo 1: single pass

@@ -8,7 +8,8 @@ back to another implementation.
 from ._binding import (  # noqa: F401
     lib, LIB_PATH, Context, PLUError, plu_matrix, plu_report, as_plu_matrix, colmajor_empty,
     plu_gaussian, plu_pass, plu_lu_reorth, plu_getrf, plu_qr, plu_norm2, plu_rank,
-    plu_powerlu, plu_powerlu_fp, plu_singlepass, plu_batched, plu_batch_problem, PREC, STATUS,
+    plu_powerlu, plu_powerlu_fp, plu_randlu, plu_singlepass, plu_batched, plu_batch_problem,
+    PREC, STATUS,
     SIGNATURES,
     STREAM_OMEGA_N, STREAM_OMEGA_M, STREAM_OMEGA_SP,
     PLU_FP64, PLU_TF32, PLU_BF16, PLU_FP8_E4M3, PLU_FP32, PLU_F64, PLU_F32,

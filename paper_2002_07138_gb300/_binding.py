@@ -67,6 +67,8 @@ SIGNATURES = {
     "plu_norm2": (c_int, [c_vp, ctypes.POINTER(plu_matrix), ctypes.POINTER(c_dbl)]),
     "plu_powerlu": (c_int, [c_vp, ctypes.POINTER(plu_matrix), c_int, c_int, c_int, c_u64, c_int,
                             c_vp, c_vp, c_vp, c_i64, c_vp, c_i64, ctypes.POINTER(plu_report)]),
+    "plu_randlu": (c_int, [c_vp, ctypes.POINTER(plu_matrix), c_int, c_int, c_int, c_u64, c_int,
+                           c_vp, c_vp, c_vp, c_i64, c_vp, c_i64, ctypes.POINTER(plu_report)]),
     "plu_powerlu_fp": (c_int, [c_vp, ctypes.POINTER(plu_matrix), c_dbl, c_int, c_int, c_int, c_int,
                                c_u64, c_int, ctypes.POINTER(c_int), c_vp, c_vp, c_vp, c_i64, c_vp,
                                c_i64, ctypes.POINTER(plu_report)]),
@@ -251,6 +253,23 @@ def plu_powerlu(ctx, A, k, l, v, seed=0, prec="fp64"):
     Am = as_plu_matrix(A)
     ctx.check(lib().plu_powerlu(ctx.handle, ctypes.byref(Am), k, l, v, seed, PREC[prec], _ptr(p),
                                 _ptr(q), _ptr(L), _ld(L), _ptr(U), _ld(U), ctypes.byref(rep)))
+    return p, q, L, U, rep.as_dict()
+
+
+def plu_randlu(ctx, A, k, l, piter, seed=0, prec="fp64"):
+    """RandLU with `piter` power iterations (2 piter + 2 passes over A).
+    Returns (p, q, L, U, report dict) as plu_powerlu."""
+    torch = _torch()
+    m, n = A.shape
+    p = torch.empty(m, dtype=torch.int32, device=A.device)
+    q = torch.empty(n, dtype=torch.int32, device=A.device)
+    L = colmajor_empty(m, k, device=A.device)
+    U = colmajor_empty(k, n, device=A.device)
+    rep = plu_report()
+    Am = as_plu_matrix(A)
+    ctx.check(lib().plu_randlu(ctx.handle, ctypes.byref(Am), k, l, piter, seed, PREC[prec],
+                               _ptr(p), _ptr(q), _ptr(L), _ld(L), _ptr(U), _ld(U),
+                               ctypes.byref(rep)))
     return p, q, L, U, rep.as_dict()
 
 

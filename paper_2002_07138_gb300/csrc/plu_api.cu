@@ -150,7 +150,7 @@ size_t pass_ws(int64_t M, int64_t N, int64_t K, int prec, int sms) {
 // ws holds ws_cap bytes; a shape that needs more is an error, never an overrun.
 plu_status do_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X, int64_t ldx,
                    int cols, int prec, double* Y, int64_t ldy, char* ws, size_t ws_cap,
-                   const QuantA* q = nullptr, int accum = 0) {
+                   const QuantA* q = nullptr, int accum = 0, const void* xq_pre = nullptr) {
     const int64_t M = trans ? A->n : A->m;
     const int64_t K = trans ? A->m : A->n;
     if ((prec == PLU_BF16 || prec == PLU_FP8_E4M3) && q && cols <= 512) {
@@ -161,7 +161,7 @@ plu_status do_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X, 
     if (is_tc(prec) && A->dtype == PLU_F32 && tc_supported(M, K, cols, A->data, A->ld, trans)) {
         PLU_CUDA(c, launch_tc_pass(trans, A->m, A->n, static_cast<const float*>(A->data), A->ld, X,
                                    ldx, cols, Y, ldy, ws, ws_cap, c->d_status, c->num_sms,
-                                   c->stream, accum));
+                                   c->stream, accum, xq_pre));
         return PLU_OK;
     }
     if (is_tc(prec)) prec = PLU_FP32;
@@ -333,7 +333,8 @@ plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t 
 // Alg. bpowerlu steps 4-8 on Y (m x k, ld m, destroyed) and Vk (n x k, ld n).
 plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const double* Vk,
                     char* ws, const PowerLUPlan& pl, char* step, int32_t* p, int32_t* q,
-                    double* L, int64_t ldL, double* U, int64_t ldU, int32_t* info2dev) {
+                    double* L, int64_t ldL, double* U, int64_t ldU, int32_t* info2dev,
+                    int prec) {
     double* L1 = reinterpret_cast<double*>(ws + pl.L1);
     double* U1T = reinterpret_cast<double*>(ws + pl.U1T);
     double* BT = reinterpret_cast<double*>(ws + pl.BT);
@@ -342,15 +343,28 @@ plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const do
     // [L1, U1, P] = lu(Y)
     PLU_CUDA(c, launch_panel_lu(m, k, Y, m, 1, p, L1, m, 0, U1T, k, 1, info2dev, step, c->d_status,
                                 c->spin_budget, c->num_sms, c->stream));
+    // The two m x k x k products take FP32 FMAs when the passes are not FP64:
+    // Y itself then carries the pass precision's rounding (2^-11 relative for
+    // TF32), far above the ~1e-7 the FP32 products add.  The getrf steps stay
+    // FP64.
+    const bool f32 = prec != PLU_FP64;
     // B^T = Vk U1^T (U1^T lower triangular)
-    PLU_CUDA(c, launch_gemm_f64_tri(0, 3, n, k, k, Vk, n, U1T, k, BT, n, tp, pl.tailpart_bytes,
-                                    c->num_sms, c->stream));
+    if (f32)
+        PLU_CUDA(c, launch_gemm_f32_tri(3, n, k, k, Vk, n, U1T, k, BT, n, tp, pl.tailpart_bytes,
+                                        c->num_sms, c->stream));
+    else
+        PLU_CUDA(c, launch_gemm_f64_tri(0, 3, n, k, k, Vk, n, U1T, k, BT, n, tp,
+                                        pl.tailpart_bytes, c->num_sms, c->stream));
     // [L2, U2, Q] = lu(B^T); U = L2^T written straight into U
     PLU_CUDA(c, launch_panel_lu(n, k, BT, n, 1, q, U, ldU, 1, U2T, k, 1, info2dev + 1, step,
                                 c->d_status, c->spin_budget, c->num_sms, c->stream));
     // L = L1 U2^T (U2^T lower triangular)
-    PLU_CUDA(c, launch_gemm_f64_tri(0, 3, m, k, k, L1, m, U2T, k, L, ldL, tp, pl.tailpart_bytes,
-                                    c->num_sms, c->stream));
+    if (f32)
+        PLU_CUDA(c, launch_gemm_f32_tri(3, m, k, k, L1, m, U2T, k, L, ldL, tp, pl.tailpart_bytes,
+                                        c->num_sms, c->stream));
+    else
+        PLU_CUDA(c, launch_gemm_f64_tri(0, 3, m, k, k, L1, m, U2T, k, L, ldL, tp,
+                                        pl.tailpart_bytes, c->num_sms, c->stream));
     return PLU_OK;
 }
 
@@ -590,7 +604,7 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
     pt.mark();
     ++np;
     int32_t* info = reinterpret_cast<int32_t*>(ws + pl.cn);
-    PLU_TRY(run_tail(c, m, n, k, Z, V, ws, pl, step, p, q, L, ldL, U, ldU, info));
+    PLU_TRY(run_tail(c, m, n, k, Z, V, ws, pl, step, p, q, L, ldL, U, ldU, info, prec));
     if (rep) {
         PLU_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
         int32_t hinfo[2] = {0, 0};
@@ -714,7 +728,7 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
     const int k = kw;
     int32_t* info = reinterpret_cast<int32_t*>(c->d_kmet + 2);
     PLU_TRY(run_tail(c, m, n, k, multi ? Gu : Z, multi ? Wu : V, ws, pl, step, p, q, L, ldL, U,
-                     ldU, info));
+                     ldU, info, prec));
     *k_out = k;
     if (rep) {
         PLU_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
@@ -782,9 +796,10 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
     const size_t dk = size_t(k) * sizeof(double);
     Layout lay;
     const size_t oOm = lay.add(size_t(m) * dk), oH = lay.add(size_t(m) * dk);
-    const size_t oG = lay.add(size_t(n) * dk), oQ = lay.add(size_t(n) * dk);
-    const size_t oW = lay.add(size_t(n) * dk), oL1 = lay.add(size_t(m) * dk);
+    const size_t oG = lay.add(size_t(n) * dk), oW = lay.add(size_t(n) * dk);
+    const size_t oL1 = lay.add(size_t(m) * dk);
     const size_t oR = lay.add(size_t(k) * dk), oRi = lay.add(size_t(k) * dk);
+    const size_t oS = lay.add(size_t(k) * dk);
     const size_t oU1T = lay.add(size_t(k) * dk), oU2T = lay.add(size_t(k) * dk);
     size_t step = 0, t = 0;
     for (int64_t w : {wc, n % wc}) {                // full panels and the last one
@@ -802,15 +817,21 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
     size_t tp = gemm_f64_partials_bytes(n, k, k, c->num_sms);
     t = gemm_f64_partials_bytes(m, k, k, c->num_sms);
     if (t > tp) tp = t;
+    t = gemm_f64_partials_bytes(k, k, k, c->num_sms);
+    if (t > tp) tp = t;
     const size_t oTp = lay.add(tp);
     const size_t oInfo = lay.add(2 * sizeof(int32_t));
+    // Omega in the tensor-core operand form, converted once for all panels
+    const bool hoist = is_tc(prec) && A->dtype == PLU_F32 && k <= 512;
+    const size_t oXq = hoist ? lay.add(tc_operand_bytes(m, k)) : 0;
     PLU_TRY(ensure_ws(c, lay.total + 256));
     char* ws = c->ws;
     double* Om = reinterpret_cast<double*>(ws + oOm);
+    const void* omq = hoist ? static_cast<const void*>(ws + oXq) : nullptr;
     double* H = reinterpret_cast<double*>(ws + oH);
     double* G = reinterpret_cast<double*>(ws + oG);
-    double* Qb = reinterpret_cast<double*>(ws + oQ);
     double* Wb = reinterpret_cast<double*>(ws + oW);
+    double* S = reinterpret_cast<double*>(ws + oS);
     double* L1 = reinterpret_cast<double*>(ws + oL1);
     double* R = reinterpret_cast<double*>(ws + oR);
     double* Rinv = reinterpret_cast<double*>(ws + oRi);
@@ -824,6 +845,8 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
     if (rep) PLU_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
     // Omega (m x k), Alg. singlepasslu step 1
     PLU_CUDA(c, launch_gaussian(m, k, seed, kStreamOmegaSP, Om, m, c->stream));
+    if (hoist)
+        PLU_CUDA(c, launch_tc_operand(m, k, Om, m, ws + oXq, c->num_sms, c->stream));
     // G = A^T Omega and H = A G in one sweep over the columns of A (Sec. 5
     // remark): per column panel, G(panel, :) = A(:, panel)^T Omega, then
     // H += A(:, panel) G(panel, :) while the panel is still in L2
@@ -833,7 +856,7 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
         plu_matrix Ap = *A;
         Ap.n = w;
         Ap.data = static_cast<const char*>(A->data) + size_t(j0) * size_t(A->ld) * size_t(es);
-        PLU_TRY(do_pass(c, &Ap, 1, Om, m, k, prec, G + j0, n, stepp, step));
+        PLU_TRY(do_pass(c, &Ap, 1, Om, m, k, prec, G + j0, n, stepp, step, nullptr, 0, omq));
         PLU_TRY(do_pass(c, &Ap, 0, G + j0, n, k, prec, H, m, stepp, step, nullptr,
                         j0 > 0 ? 1 : 0));
     }
@@ -841,20 +864,33 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
     // [L1, U1, P] = lu(H)
     PLU_CUDA(c, launch_panel_lu(m, k, H, m, 1, p, L1, m, 0, U1T, k, 1, info, stepp, c->d_status,
                                 c->spin_budget, c->num_sms, c->stream));
-    // G^{dagger T} = G (G^T G)^{-1} = Q R^{-T} with G = Q R (CholeskyQR2)
-    PLU_CUDA(c, cudaMemcpyAsync(Qb, G, size_t(n) * dk, cudaMemcpyDeviceToDevice, c->stream));
-    PLU_CUDA(c, launch_cholqr2(n, k, Qb, n, R, k, stepp, step, c->d_status, c->num_sms, c->stream));
+    // G^{dagger T} = G (G^T G)^{-1} = Q1 R^{-T} with one CholeskyQR round,
+    // G = Q1 R and R^T R = G^T G (in place: G becomes Q1)
+    PLU_CUDA(c, launch_cholqr2(n, k, G, n, R, k, stepp, step, c->d_status, c->num_sms, c->stream,
+                               0, 1));
     PLU_CUDA(c, launch_trinv_upper(k, R, Rinv, c->stream));
-    PLU_CUDA(c, launch_gemm_f64(0, 1, n, k, k, Qb, n, Rinv, k, Wb, n, tpp, tp, c->num_sms,
+    // M = G^{dagger T} U1^T = Q1 S with S = R^{-T} U1^T (k x k, lower
+    // triangular); the two m x k x k products take FP32 FMAs when the passes
+    // are not FP64 (G and H carry the pass precision's rounding)
+    PLU_CUDA(c, launch_gemm_f64(1, 0, k, k, k, Rinv, k, U1T, k, S, k, tpp, tp, c->num_sms,
                                 c->stream));
-    // M = G^{dagger T} U1^T, [L2, U2, Q] = lu(M), U = L2^T
-    PLU_CUDA(c, launch_gemm_f64(0, 0, n, k, k, Wb, n, U1T, k, G, n, tpp, tp, c->num_sms,
-                                c->stream));
-    PLU_CUDA(c, launch_panel_lu(n, k, G, n, 1, q, U, ldU, 1, U2T, k, 1, info + 1, stepp,
+    const bool f32 = prec != PLU_FP64;
+    if (f32)
+        PLU_CUDA(c, launch_gemm_f32_tri(3, n, k, k, G, n, S, k, Wb, n, tpp, tp, c->num_sms,
+                                        c->stream));
+    else
+        PLU_CUDA(c, launch_gemm_f64_tri(0, 3, n, k, k, G, n, S, k, Wb, n, tpp, tp, c->num_sms,
+                                        c->stream));
+    // [L2, U2, Q] = lu(M), U = L2^T
+    PLU_CUDA(c, launch_panel_lu(n, k, Wb, n, 1, q, U, ldU, 1, U2T, k, 1, info + 1, stepp,
                                 c->d_status, c->spin_budget, c->num_sms, c->stream));
-    // L = L1 U2^T
-    PLU_CUDA(c, launch_gemm_f64(0, 0, m, k, k, L1, m, U2T, k, L, ldL, tpp, tp, c->num_sms,
-                                c->stream));
+    // L = L1 U2^T (U2^T lower triangular)
+    if (f32)
+        PLU_CUDA(c, launch_gemm_f32_tri(3, m, k, k, L1, m, U2T, k, L, ldL, tpp, tp, c->num_sms,
+                                        c->stream));
+    else
+        PLU_CUDA(c, launch_gemm_f64_tri(0, 3, m, k, k, L1, m, U2T, k, L, ldL, tpp, tp,
+                                        c->num_sms, c->stream));
     if (rep) {
         PLU_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
         int32_t hinfo[2] = {0, 0};
@@ -874,6 +910,139 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
         const double mnd = double(m) * double(n);
         rep->flops_passes = 4.0 * mnd * k;
         rep->bytes_passes = mnd * double(es) + double(m + n) * k * 8.0;
+        rep->launches = int32_t(g_launches - launches0);
+    }
+    return finish(c);
+}
+
+plu_status plu_randlu(plu_ctx* c, const plu_matrix* A, int k, int l, int piter, uint64_t seed,
+                      plu_prec prec, int32_t* p, int32_t* q, double* L, int64_t ldL, double* U,
+                      int64_t ldU, plu_report* rep) {
+    PLU_TRY(bind(c));
+    PLU_TRY(check_matrix(c, A));
+    PLU_TRY(check_prec(c, prec, A));
+    const int64_t m = A->m, n = A->n;
+    const int64_t mn = m < n ? m : n;
+    if (k < 1 || l < k || l >= mn) return fail(c, PLU_EINVAL, "need 1 <= k <= l < min(m, n)");
+    if (piter < 0) return fail(c, PLU_EINVAL, "need piter >= 0");
+    if (l > 2048) return fail(c, PLU_EINVAL, "l > 2048 is not supported");
+    if (!p || !q || !L || !U || ldL < m || ldU < k) return fail(c, PLU_EINVAL, "bad outputs");
+    const int sms = c->num_sms;
+    Layout lay;
+    const size_t oX = lay.add(size_t(n) * l * sizeof(double));
+    const size_t oY = lay.add(size_t(m) * l * sizeof(double));
+    const size_t oL1 = lay.add(size_t(m) * l * sizeof(double));
+    const size_t oUl = lay.add(size_t(l) * l * sizeof(double));
+    const size_t oW = lay.add(size_t(m) * k * sizeof(double));
+    const size_t oR = lay.add(size_t(k) * k * sizeof(double));
+    const size_t oRi = lay.add(size_t(k) * k * sizeof(double));
+    const size_t oT = lay.add(size_t(n) * k * sizeof(double));
+    const size_t oBT = lay.add(size_t(n) * k * sizeof(double));
+    const size_t oU2T = lay.add(size_t(k) * k * sizeof(double));
+    size_t step = pass_ws(m, l, n, prec, sms), t;
+    t = pass_ws(n, l, m, prec, sms);
+    if (t > step) step = t;
+    t = pass_ws(n, k, m, PLU_TF32, sms);
+    if (t > step) step = t;
+    t = pass_ws(n, k, m, prec, sms);
+    if (t > step) step = t;
+    t = panel_scratch_bytes(m > n ? m : n, l);
+    if (t > step) step = t;
+    t = qr_scratch_bytes(m, k, sms);
+    if (t > step) step = t;
+    const size_t oStep = lay.add(step);
+    size_t tp = gemm_f64_partials_bytes(n, k, k, sms);
+    t = gemm_f64_partials_bytes(m, k, k, sms);
+    if (t > tp) tp = t;
+    const size_t oTp = lay.add(tp);
+    const size_t oInfo = lay.add(2 * sizeof(int32_t));
+    const bool quant = prec == PLU_BF16 || prec == PLU_FP8_E4M3;
+    const size_t oQ = quant ? lay.add(tc_quant_bytes(m, n, prec)) : 0;
+    PLU_TRY(ensure_ws(c, lay.total + 256));
+    char* ws = c->ws;
+    double* X = reinterpret_cast<double*>(ws + oX);
+    double* Y = reinterpret_cast<double*>(ws + oY);
+    double* L1 = reinterpret_cast<double*>(ws + oL1);
+    double* Ul = reinterpret_cast<double*>(ws + oUl);
+    double* W = reinterpret_cast<double*>(ws + oW);
+    double* R = reinterpret_cast<double*>(ws + oR);
+    double* Rinv = reinterpret_cast<double*>(ws + oRi);
+    double* T = reinterpret_cast<double*>(ws + oT);
+    double* BT = reinterpret_cast<double*>(ws + oBT);
+    double* U2T = reinterpret_cast<double*>(ws + oU2T);
+    char* stepp = ws + oStep;
+    void* tpp = ws + oTp;
+    int32_t* info = reinterpret_cast<int32_t*>(ws + oInfo);
+    PassTimer pt(c, rep != nullptr);
+    const long long launches0 = g_launches;
+    if (rep) PLU_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+    QuantA qa;
+    if (quant)
+        PLU_CUDA(c, launch_tc_quantize(prec, static_cast<const float*>(A->data), m, n, A->ld,
+                                       ws + oQ, &qa, sms, c->stream));
+    int np = 0;
+    auto pass = [&](int trans, const double* Xin, int64_t ldx, int cols, int pr, double* Yout,
+                    int64_t ldy) -> plu_status {
+        pt.mark();
+        PLU_TRY(do_pass(c, A, trans, Xin, ldx, cols, pr, Yout, ldy, stepp, step,
+                        quant && pr == int(prec) ? &qa : nullptr));
+        pt.mark();
+        ++np;
+        return PLU_OK;
+    };
+    auto reorth = [&](int64_t rows, double* Xr) -> plu_status {
+        PLU_CUDA(c, launch_panel_lu(rows, l, Xr, rows, 0, nullptr, nullptr, 0, 0, nullptr, 0, 0,
+                                    nullptr, stepp, c->d_status, c->spin_budget, sms, c->stream));
+        return PLU_OK;
+    };
+    // Alg. basicpoweriteration: Y = A Omega, then piter rounds of A^T, A
+    PLU_CUDA(c, launch_gaussian(n, l, seed, kStreamOmegaN, X, n, c->stream));
+    PLU_TRY(pass(0, X, n, l, prec, Y, m));
+    if (piter > 0) PLU_TRY(reorth(m, Y));
+    for (int i = 1; i <= piter; ++i) {
+        PLU_TRY(pass(1, Y, m, l, prec, X, n));
+        PLU_TRY(reorth(n, X));
+        PLU_TRY(pass(0, X, n, l, prec, Y, m));
+        if (i < piter) PLU_TRY(reorth(m, Y));
+    }
+    // P Y = L_y U_y (full LU of the m x l product); L_y = its first k columns
+    PLU_CUDA(c, launch_panel_lu(m, l, Y, m, 1, p, L1, m, 0, Ul, l, 1, info, stepp, c->d_status,
+                                c->spin_budget, sms, c->stream));
+    // B^T = (L_y^+ P A)^T = A^T W (W^T W)^{-1} with W = P^T L_y = Q R:
+    // B^T = A^T Q R^{-T}.  The pass reads the FP32 A through TF32 in the
+    // mixed modes (B enters the result to first order).
+    PLU_CUDA(c, launch_scatter_rows(m, k, p, L1, m, W, m, c->stream));
+    PLU_CUDA(c, launch_cholqr2(m, k, W, m, R, k, stepp, step, c->d_status, sms, c->stream));
+    PLU_TRY(pass(1, W, m, k, is_tc(prec) ? int(PLU_TF32) : int(prec), T, n));
+    PLU_CUDA(c, launch_trinv_upper(k, R, Rinv, c->stream));
+    PLU_CUDA(c, launch_gemm_f64(0, 1, n, k, k, T, n, Rinv, k, BT, n, tpp, tp, sms, c->stream));
+    // Q B^T = L' U' (Alg. rlu step 5); U = L'^T written straight into U
+    PLU_CUDA(c, launch_panel_lu(n, k, BT, n, 1, q, U, ldU, 1, U2T, k, 1, info + 1, stepp,
+                                c->d_status, c->spin_budget, sms, c->stream));
+    // L = L_y U'^T (U'^T lower triangular)
+    if (prec != PLU_FP64)
+        PLU_CUDA(c, launch_gemm_f32_tri(3, m, k, k, L1, m, U2T, k, L, ldL, tpp, tp, sms,
+                                        c->stream));
+    else
+        PLU_CUDA(c, launch_gemm_f64_tri(0, 3, m, k, k, L1, m, U2T, k, L, ldL, tpp, tp, sms,
+                                        c->stream));
+    if (rep) {
+        PLU_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+        int32_t hinfo[2] = {0, 0};
+        PLU_CUDA(c, cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, c->stream));
+        PLU_CUDA(c, cudaStreamSynchronize(c->stream));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+        memset(rep, 0, sizeof(*rep));
+        rep->ms_total = ms;
+        rep->ms_passes = pt.pairs_ms();
+        rep->passes = np;
+        rep->rank = k;
+        rep->indicator = -1.0;
+        rep->normA2 = -1.0;
+        rep->info1 = hinfo[0];
+        rep->info2 = hinfo[1];
+        fill_pass_report(rep, A, np - 1, l, k, prec, true);
         rep->launches = int32_t(g_launches - launches0);
     }
     return finish(c);

@@ -294,4 +294,13 @@ cudaError_t launch_gemm_f64_tri(int transA, int tri, int64_t M, int64_t N, int64
                                                               0, skip);
 }
 
+cudaError_t launch_gemm_f32_tri(int tri, int64_t M, int64_t N, int64_t K, const double* A,
+                                int64_t lda, const double* B, int64_t ldb, double* C,
+                                int64_t ldc, void* partials, size_t part_cap, int num_sms,
+                                cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    return run<double, double, float, false, false>(M, N, K, A, lda, B, ldb, C, ldc, partials,
+                                                    part_cap, num_sms, s, tri, 0);
+}
+
 }  // namespace plu

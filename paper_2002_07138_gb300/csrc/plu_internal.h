@@ -126,6 +126,14 @@ cudaError_t launch_gemm_f64_tri(int transA, int tri, int64_t M, int64_t N, int64
                                 double* C, int64_t ldc, void* partials, size_t part_cap,
                                 int num_sms, cudaStream_t s, const int* skip = nullptr);
 
+// As launch_gemm_f64_tri without the A transpose, with FP32 FMAs: A and B are
+// read as FP64 and rounded to FP32, each split sums in FP32 and the splits are
+// added in FP64.  The partial sums take half the bytes of the FP64 version.
+cudaError_t launch_gemm_f32_tri(int tri, int64_t M, int64_t N, int64_t K, const double* A,
+                                int64_t lda, const double* B, int64_t ldb, double* C,
+                                int64_t ldc, void* partials, size_t part_cap, int num_sms,
+                                cudaStream_t s);
+
 // ----------------------------------------------- tensor-core passes (TF32)
 // Y (FP64) = A X (trans 0) or A^T X (trans 1) with FP32 A (m x n, lda) on
 // tcgen05 tensor cores; X is FP64 (K x cols).  tc_supported() tells whether
@@ -134,10 +142,17 @@ cudaError_t launch_gemm_f64_tri(int transA, int tri, int64_t M, int64_t N, int64
 // cols, num_sms) (an error otherwise).
 bool tc_supported(int64_t M, int64_t K, int cols, const void* A, int64_t lda, int trans);
 size_t tc_scratch_bytes(int64_t M, int64_t K, int cols, int num_sms);
+// xq_pre (nullable): X already in operand form (launch_tc_operand with the
+// same K and cols); the pass then reads it instead of converting X.
 cudaError_t launch_tc_pass(int trans, int64_t m, int64_t n, const float* A, int64_t lda,
                            const double* X, int64_t ldx, int cols, double* Y, int64_t ldy,
                            void* scratch, size_t scratch_cap, int* dev_status, int num_sms,
-                           cudaStream_t s, int accum = 0);
+                           cudaStream_t s, int accum = 0, const void* xq_pre = nullptr);
+// The TF32 operand image of X (K x cols, FP64): the tiled, swizzled layout the
+// pass kernel copies one K step at a time.  out holds tc_operand_bytes(K, cols).
+size_t tc_operand_bytes(int64_t K, int cols);
+cudaError_t launch_tc_operand(int64_t K, int cols, const double* X, int64_t ldx, void* out,
+                              int num_sms, cudaStream_t s);
 // Quantized copy of A for the BF16 / FP8-E4M3 passes: column-major, ld a
 // multiple of 16 elements; FP8 carries rank-1 tile scales s_r (per 128 rows)
 // and s_c (per 128 columns) with A(i, j) ~= Aq(i, j) s_r[i/128] s_c[j/128].
@@ -175,10 +190,11 @@ size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms);
 // adaptive != 0: the second CholeskyQR round runs only when the first
 // Cholesky factor's diagonal spread max|r_ii| / min|r_ii| exceeds 1e5 (the
 // decision is taken on the device; the second round's kernels return at once
-// otherwise).  R (when requested) is then R1.
+// otherwise); R cannot be requested then.  rounds = 1 runs one CholeskyQR
+// round (X <- X R1^{-1}, R = R1, with R1^T R1 = X^T X).
 cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, double* R,
                            int64_t ldR, void* scratch, size_t scratch_cap, int* dev_status,
-                           int num_sms, cudaStream_t s, int adaptive = 0);
+                           int num_sms, cudaStream_t s, int adaptive = 0, int rounds = 2);
 
 // Rinv = R^{-1} for an upper triangular n x n R (ld n); Rinv is upper triangular.
 cudaError_t launch_trinv_upper(int n, const double* R, double* Rinv, cudaStream_t s);
@@ -200,6 +216,11 @@ cudaError_t launch_rank_scan(const double* colnorm2, int cols, const double* nor
 // -------------------------------------------------------------- helpers
 cudaError_t launch_copy_cols(int64_t rows, int cols, const double* src, int64_t lds,
                              double* dst, int64_t ldd, cudaStream_t s);
+// W(perm[i], j) = L(i, j) for i < rows, j < cols: the rows of an LU's L (in
+// pivoted order) moved back to the row order of the factored matrix.
+// perm must be a permutation of 0 .. rows-1 (entries outside are skipped).
+cudaError_t launch_scatter_rows(int64_t rows, int cols, const int32_t* perm, const double* L,
+                                int64_t ldl, double* W, int64_t ldw, cudaStream_t s);
 
 // ------------------------------------------------------------- batched
 size_t batch_workspace_bytes(const plu_batch_problem* P, int count);

@@ -100,6 +100,18 @@ __global__ void k_copy_cols(int64_t rows, int cols, const double* __restrict__ s
     }
 }
 
+// CTA row blockIdx.y = column j; x strides over the rows.
+__global__ void k_scatter_rows(int64_t rows, const int32_t* __restrict__ perm,
+                               const double* __restrict__ L, int64_t ldl, double* __restrict__ W,
+                               int64_t ldw) {
+    const int64_t j = blockIdx.y;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < rows;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t r = perm[i];
+        if (r >= 0 && r < rows) W[r + j * ldw] = L[i + j * ldl];
+    }
+}
+
 }  // namespace
 
 size_t norm2_scratch_bytes(int num_sms) { return size_t(num_sms) * 4 * sizeof(double) + 256; }
@@ -145,6 +157,17 @@ cudaError_t launch_copy_cols(int64_t rows, int cols, const double* src, int64_t 
     if (b > 4096) b = 4096;
     count_launch();
     k_copy_cols<<<unsigned(b), 256, 0, s>>>(rows, cols, src, lds, dst, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_rows(int64_t rows, int cols, const int32_t* perm, const double* L,
+                                int64_t ldl, double* W, int64_t ldw, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (cols > 65535) return cudaErrorInvalidValue;
+    int64_t b = (rows + 255) / 256;
+    if (b > 64) b = 64;
+    count_launch();
+    k_scatter_rows<<<dim3(unsigned(b), unsigned(cols)), 256, 0, s>>>(rows, perm, L, ldl, W, ldw);
     return cudaGetLastError();
 }
 

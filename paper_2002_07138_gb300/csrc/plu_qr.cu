@@ -272,9 +272,10 @@ size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms) {
 
 cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, double* R,
                            int64_t ldR, void* scratch, size_t scratch_cap, int* dev_status,
-                           int num_sms, cudaStream_t s, int adaptive) {
+                           int num_sms, cudaStream_t s, int adaptive, int rounds) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     if (adaptive && R) return cudaErrorInvalidValue;     // R would be R1 or R2 R1
+    if (rounds != 1 && rounds != 2) return cudaErrorInvalidValue;
     Workspace ws;
     ws.base = static_cast<char*>(scratch);
     ws.cap = scratch_cap;
@@ -293,7 +294,7 @@ cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, doubl
     if (!W || !Wsave || !Rinv || !R1 || !Rtmp || !part || !ctl || !skip2)
         return cudaErrorInvalidValue;
     cudaError_t e;
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < rounds; ++pass) {
         const int* sk = (pass == 1 && adaptive) ? skip2 : nullptr;
         // W = X^T X, upper triangle only (the Cholesky reads nothing else)
         e = launch_gemm_f64_tri(1, 1, cols, cols, rows, X, ldx, X, ldx, W, cols, part, part_cap,
@@ -352,6 +353,7 @@ cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, doubl
             if (e != cudaSuccess) return e;
         }
     }
+    if (R && rounds == 1) return launch_copy_cols(cols, cols, R1, cols, R, ldR, s);
     if (R) {
         // R = R2 R1 (both upper triangular)
         e = launch_gemm_f64(0, 0, cols, cols, cols, W, cols, R1, cols, Rtmp, cols, part, part_cap,

@@ -529,30 +529,58 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restr
 }
 
 // Y(i, j) = sum over the CTAs whose share touches block i/128 of their partial
-// tile, in CTA order, in FP64.
-__global__ void k_tc_reduce(const float* __restrict__ part, int64_t M, int l, int npad,
-                            int ksteps, int64_t total, int64_t per, int max_segs, int grid,
-                            double* __restrict__ Y, int64_t ldy,
-                            const float* __restrict__ rowblk_scale,
-                            const float* __restrict__ col_scale, int accum) {
-    const int64_t count = M * l;
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < count;
-         e += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t i = e % M, j = e / M;
-        const int64_t blk = i / BM;
-        const int r = int(i % BM);
-        const int64_t first = blk * ksteps, last = min(total, first + ksteps) - 1;
-        int64_t c_lo = first / per, c_hi = last / per;
-        if (c_hi >= grid) c_hi = grid - 1;
-        double acc = 0.0;
-        for (int64_t c = c_lo; c <= c_hi; ++c) {
-            const int64_t cblk0 = (c * per) / ksteps;
-            const int64_t seg = blk - cblk0;
-            acc += double(part[((c * max_segs + seg) * npad + j) * BM + r]);
+// tile, in CTA order, in FP64.  CTA (blk, g): rows blk*128 + threadIdx.x,
+// columns g*RJT .. g*RJT + RJT - 1.  The segment index of CTA c in block blk
+// is blk - floor(c per / ksteps), stepped from one CTA to the next without
+// divisions; the loads of Y (accum) are issued before any store.
+template <int RJT>
+__global__ void __launch_bounds__(BM) k_tc_reduce(const float* __restrict__ part, int64_t M,
+                                                  int l, int npad, int ksteps, int64_t total,
+                                                  int64_t per, int max_segs, int grid,
+                                                  double* __restrict__ Y, int64_t ldy,
+                                                  const float* __restrict__ rowblk_scale,
+                                                  const float* __restrict__ col_scale, int accum) {
+    const int64_t blk = blockIdx.x;
+    const int r = threadIdx.x;
+    const int64_t i = blk * BM + r;
+    if (i >= M) return;
+    const int j0 = blockIdx.y * RJT;
+    const int nj = min(RJT, l - j0);
+    const int64_t first = blk * ksteps, last = min(total, first + ksteps) - 1;
+    const int64_t c_lo = first / per;
+    int64_t c_hi = last / per;
+    if (c_hi >= grid) c_hi = grid - 1;
+    const int64_t pq = per / ksteps, pr = per % ksteps;
+    int64_t cb = (c_lo * per) / ksteps, rem = (c_lo * per) % ksteps;
+    double acc[RJT];
+#pragma unroll
+    for (int q = 0; q < RJT; ++q) acc[q] = 0.0;
+#pragma unroll 4
+    for (int64_t c = c_lo; c <= c_hi; ++c) {
+        const float* src = part + ((c * max_segs + (blk - cb)) * npad + j0) * BM + r;
+#pragma unroll
+        for (int q = 0; q < RJT; ++q)
+            if (q < nj) acc[q] += double(src[int64_t(q) * BM]);
+        cb += pq;
+        rem += pr;
+        if (rem >= ksteps) {
+            rem -= ksteps;
+            ++cb;
         }
-        if (rowblk_scale) acc *= double(rowblk_scale[blk]);
-        if (col_scale) acc *= double(col_scale[j]);
-        Y[i + j * ldy] = accum ? Y[i + j * ldy] + acc : acc;
+    }
+    double yv[RJT];
+#pragma unroll
+    for (int q = 0; q < RJT; ++q)
+        yv[q] = (accum && q < nj) ? Y[i + int64_t(j0 + q) * ldy] : 0.0;
+    const double rs = rowblk_scale ? double(rowblk_scale[blk]) : 1.0;
+#pragma unroll
+    for (int q = 0; q < RJT; ++q) {
+        if (q < nj) {
+            double a = acc[q];
+            if (rowblk_scale) a *= rs;
+            if (col_scale) a *= double(col_scale[j0 + q]);
+            Y[i + int64_t(j0 + q) * ldy] = accum ? yv[q] + a : a;
+        }
     }
 }
 
@@ -570,11 +598,11 @@ __global__ void k_to_operand(int64_t K, int cols, int npad, int ksteps, const do
     constexpr int E = Kind<KIND>::E;
     constexpr int BKE = 128 / E;
     constexpr int T = 16 / E;
-    const int64_t total = int64_t(ksteps) * BKE * npad;
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
-         e += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t k = e % (int64_t(ksteps) * BKE);
-        const int j = int(e / (int64_t(ksteps) * BKE));
+    // CTA row blockIdx.y = operand row j; x strides over the reduction index k
+    const int j = blockIdx.y;
+    const int64_t kall = int64_t(ksteps) * BKE;
+    for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < kall;
+         k += int64_t(gridDim.x) * blockDim.x) {
         const int64_t t = k / BKE;
         const int kk = int(k % BKE);
         unsigned char* dst = out + t * int64_t(npad) * 128 + j * 128 +
@@ -831,7 +859,8 @@ template <int KIND>
 cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t lda,
                          const float* s_r, const float* s_c, const double* X, int64_t ldx,
                          int cols, double* Y, int64_t ldy, void* scratch, size_t scratch_cap,
-                         int* dev_status, int num_sms, cudaStream_t s, int accum) {
+                         int* dev_status, int num_sms, cudaStream_t s, int accum,
+                         const void* xq_pre = nullptr) {
     constexpr int E = Kind<KIND>::E;
     constexpr int BKE = 128 / E;
     const int64_t M = trans ? n : m;
@@ -851,16 +880,18 @@ cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t
     const float* fold = trans ? s_r : s_c;
     const float* rowblk = trans ? s_c : s_r;
     cudaError_t e;
-    {
-        int64_t b = (int64_t(p.ksteps) * BKE * p.npad + 255) / 256;
-        if (b > int64_t(num_sms) * 16) b = int64_t(num_sms) * 16;
+    if (xq_pre && KIND != KIND_TF32) return cudaErrorInvalidValue;
+    if (!xq_pre) {
+        int64_t b = (int64_t(p.ksteps) * BKE + 255) / 256;
+        const int64_t bcap = (int64_t(num_sms) * 16 + p.npad - 1) / p.npad;
+        if (b > bcap) b = bcap;
         if (KIND == KIND_FP8) {
             count_launch();
             k_fp8_colscale<<<cols, 256, 0, s>>>(K, cols, X, ldx, fold, colsc);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         count_launch();
-        k_to_operand<KIND><<<unsigned(b), 256, 0, s>>>(K, cols, p.npad, p.ksteps, X, ldx, fold,
+        k_to_operand<KIND><<<dim3(unsigned(b), unsigned(p.npad)), 256, 0, s>>>(K, cols, p.npad, p.ksteps, X, ldx, fold,
                                                         colsc, xq);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -894,22 +925,32 @@ cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t
                                  int(p.smem));
         if (e != cudaSuccess) return e;
         count_launch();
-        k_tc_pass<false, KIND><<<p.grid, TC_THREADS, p.smem, s>>>(mapA, xq, P);
+        k_tc_pass<false, KIND><<<p.grid, TC_THREADS, p.smem, s>>>(
+            mapA, xq_pre ? static_cast<const unsigned char*>(xq_pre) : xq, P);
     } else {
         e = cudaFuncSetAttribute(k_tc_pass<true, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(p.smem));
         if (e != cudaSuccess) return e;
         count_launch();
-        k_tc_pass<true, KIND><<<p.grid, TC_THREADS_X, p.smem, s>>>(mapA, xq, P);
+        k_tc_pass<true, KIND><<<p.grid, TC_THREADS_X, p.smem, s>>>(
+            mapA, xq_pre ? static_cast<const unsigned char*>(xq_pre) : xq, P);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    int64_t rb = (M * cols + 255) / 256;
-    if (rb > int64_t(num_sms) * 16) rb = int64_t(num_sms) * 16;
+    // eight columns per CTA, or one when that leaves fewer than two CTAs per SM
+    // (few row blocks, each summed over many CTAs' partials)
+    const int64_t nblk = (M + BM - 1) / BM;
+    const bool wide = nblk * ((cols + 7) / 8) >= 2 * int64_t(num_sms);
     count_launch();
-    k_tc_reduce<<<unsigned(rb), 256, 0, s>>>(part, M, cols, p.npad, p.ksteps, p.total, p.per,
-                                              p.max_segs, p.grid, Y, ldy, rowblk,
-                                              KIND == KIND_FP8 ? colsc : nullptr, accum);
+    if (!wide) {
+        k_tc_reduce<1><<<dim3(unsigned(nblk), unsigned(cols)), BM, 0, s>>>(
+            part, M, cols, p.npad, p.ksteps, p.total, p.per, p.max_segs, p.grid, Y, ldy, rowblk,
+            KIND == KIND_FP8 ? colsc : nullptr, accum);
+        return cudaGetLastError();
+    }
+    k_tc_reduce<8><<<dim3(unsigned(nblk), unsigned((cols + 7) / 8)), BM, 0, s>>>(
+        part, M, cols, p.npad, p.ksteps, p.total, p.per, p.max_segs, p.grid, Y, ldy, rowblk,
+        KIND == KIND_FP8 ? colsc : nullptr, accum);
     return cudaGetLastError();
 }
 
@@ -918,9 +959,28 @@ cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t
 cudaError_t launch_tc_pass(int trans, int64_t m, int64_t n, const float* A, int64_t lda,
                            const double* X, int64_t ldx, int cols, double* Y, int64_t ldy,
                            void* scratch, size_t scratch_cap, int* dev_status, int num_sms,
-                           cudaStream_t s, int accum) {
+                           cudaStream_t s, int accum, const void* xq_pre) {
     return tc_pass_kind<KIND_TF32>(trans, m, n, A, lda, nullptr, nullptr, X, ldx, cols, Y, ldy,
-                                   scratch, scratch_cap, dev_status, num_sms, s, accum);
+                                   scratch, scratch_cap, dev_status, num_sms, s, accum, xq_pre);
+}
+
+size_t tc_operand_bytes(int64_t K, int cols) {
+    const TcPlan p = plan_tc(BM, K, cols, 1, false, 4);
+    return size_t(p.ksteps) * p.npad * 128;
+}
+
+cudaError_t launch_tc_operand(int64_t K, int cols, const double* X, int64_t ldx, void* out,
+                              int num_sms, cudaStream_t s) {
+    if (K < 1 || cols < 1 || cols > 512 || !X || !out) return cudaErrorInvalidValue;
+    const TcPlan p = plan_tc(BM, K, cols, num_sms, false, 4);
+    constexpr int BKE = 128 / Kind<KIND_TF32>::E;
+    int64_t b = (int64_t(p.ksteps) * BKE + 255) / 256;
+    const int64_t bcap = (int64_t(num_sms) * 16 + p.npad - 1) / p.npad;
+    if (b > bcap) b = bcap;
+    count_launch();
+    k_to_operand<KIND_TF32><<<dim3(unsigned(b), unsigned(p.npad)), 256, 0, s>>>(
+        K, cols, p.npad, p.ksteps, X, ldx, nullptr, nullptr, static_cast<unsigned char*>(out));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tc_pass_q(int trans, const QuantA& q, const double* X, int64_t ldx, int cols,
