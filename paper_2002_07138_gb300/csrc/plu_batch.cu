@@ -188,13 +188,15 @@ struct BCand {
     int row;
 };
 
+// v = |x|: bit patterns order as integers, NaNs lie above +inf's pattern
 __device__ __forceinline__ bool b_better(const BCand& a, const BCand& b) {
     if (a.row < 0) return false;
     if (b.row < 0) return true;
-    const bool an = a.v != a.v, bn = b.v != b.v;
+    const long long ab = __double_as_longlong(a.v), bb = __double_as_longlong(b.v);
+    const bool an = ab > 0x7FF0000000000000LL, bn = bb > 0x7FF0000000000000LL;
     if (an || bn) return an && bn ? a.pos < b.pos : bn;
-    if (a.v > b.v) return true;
-    if (a.v < b.v) return false;
+    if (ab > bb) return true;
+    if (ab < bb) return false;
     return a.pos < b.pos;
 }
 

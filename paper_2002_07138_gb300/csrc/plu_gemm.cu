@@ -159,13 +159,17 @@ __global__ void k_reduce_splits(int64_t M, int64_t N, int splits, const TC* __re
                                 double* __restrict__ C, int64_t ldc, int accum,
                                 const int* __restrict__ skip) {
     if (skip && *skip) return;
+    // grid rows stride over the columns j, threads over the rows i
     const int64_t total = M * N;
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
-         e += int64_t(gridDim.x) * blockDim.x) {
-        double sum = 0.0;
-        for (int z = 0; z < splits; ++z) sum += double(P[int64_t(z) * total + e]);
-        const int64_t i = e % M, j = e / M;
-        C[i + j * ldc] = accum > 0 ? C[i + j * ldc] + sum : accum < 0 ? C[i + j * ldc] - sum : sum;
+    for (int64_t j = blockIdx.y; j < N; j += gridDim.y) {
+        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < M;
+             i += int64_t(gridDim.x) * blockDim.x) {
+            const int64_t e = i + j * M;
+            double sum = 0.0;
+            for (int z = 0; z < splits; ++z) sum += double(P[int64_t(z) * total + e]);
+            double* c = C + i + j * ldc;
+            *c = accum > 0 ? *c + sum : accum < 0 ? *c - sum : sum;
+        }
     }
 }
 
@@ -221,8 +225,14 @@ cudaError_t run(int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda, const
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     count_launch();
-    k_reduce_splits<TC><<<grid_1d(M * N, num_sms), 256, 0, s>>>(M, N, splits, P, C, ldc, accum,
-                                                                skip);
+    // about 16 CTAs per SM over (row chunks) x (columns)
+    int64_t gx = (M + 255) / 256, gy = N;
+    const int64_t want = int64_t(num_sms) * 16;
+    if (gy > 65535) gy = 65535;
+    if (gx * gy > want) gx = (want + gy - 1) / gy;
+    if (gx < 1) gx = 1;
+    k_reduce_splits<TC><<<dim3(unsigned(gx), unsigned(gy)), 256, 0, s>>>(M, N, splits, P, C, ldc,
+                                                                         accum, skip);
     return cudaGetLastError();
 }
 

@@ -59,15 +59,23 @@ namespace {
 constexpr int NT = 256;
 constexpr int kMaxCols = 2048;
 
+// Candidate values are |x| (sign bit clear), so their IEEE bit patterns order
+// as 64-bit integers and NaNs are exactly the patterns above +inf's: the
+// comparisons run on the integer pipe instead of the narrow FP64 pipe.
+__device__ __forceinline__ bool is_nan_abs(double a) {
+    return __double_as_longlong(a) > 0x7FF0000000000000LL;
+}
+
 __device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
     // true when a should be the pivot rather than b: larger |x| first, then
     // the smaller current position; NaN loses to every number
     if (a.row < 0) return false;
     if (b.row < 0) return true;
-    const bool an = a.v != a.v, bn = b.v != b.v;
+    const long long ab = __double_as_longlong(a.v), bb = __double_as_longlong(b.v);
+    const bool an = ab > 0x7FF0000000000000LL, bn = bb > 0x7FF0000000000000LL;
     if (an || bn) return an && bn ? a.pos < b.pos : bn;
-    if (a.v > b.v) return true;
-    if (a.v < b.v) return false;
+    if (ab > bb) return true;
+    if (ab < bb) return false;
     return a.pos < b.pos;
 }
 
@@ -239,7 +247,7 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
         for (int r = t; r < R; r += NT) {
             if (piv_s[r] >= 0) continue;
             const double a = fabs(P[r]);
-            if (a != a) nan_seen = 1;
+            if (is_nan_abs(a)) nan_seen = 1;
             const Cand c{a, pos_s[r], int(r0 + r)};
             if (better(c, best)) best = c;
         }
@@ -333,7 +341,7 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
                 }
                 if (next) {
                     const double a = fabs(P[(sc + 1) * per + r]);
-                    if (a != a) nan_seen = 1;
+                    if (is_nan_abs(a)) nan_seen = 1;
                     const Cand c{a, pos_s[r], int(r0 + r)};
                     if (better(c, best)) best = c;
                 }
@@ -509,7 +517,7 @@ k_panel_lu_la(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
             for (int r = t; r < R; r += NTP) {
                 if (piv_s[r] >= 0) continue;
                 const double a = fabs(Pc[r]);
-                if (a != a) nan_seen = 1;
+                if (is_nan_abs(a)) nan_seen = 1;
                 const Cand c{a, pos_s[r], int(r0 + r)};
                 if (better(c, best)) best = c;
             }
@@ -604,7 +612,7 @@ k_panel_lu_la(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
                     }
                     if (next) {
                         const double a = fabs(Pc[(sc + 1) * per + r]);
-                        if (a != a) nan_seen = 1;
+                        if (is_nan_abs(a)) nan_seen = 1;
                         const Cand c{a, pos_s[r], int(r0 + r)};
                         if (better(c, best)) best = c;
                     }
@@ -673,10 +681,12 @@ k_panel_lu_la(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
     if (nan_seen) atomicExch(&ps->any_nan, 1);
 }
 
+// After the factorisation: info and the NaN flag; mode 0 writes the unit
+// diagonal and the zeros above it into X (X = P^T L in place); mode 1 writes
+// perm (perm[pos[i]] = i) and the k pivot rows of U (or U^T).
 __global__ void k_panel_finalize(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
                                  int mode, const int* __restrict__ pos,
                                  const int* __restrict__ pivstep, int32_t* __restrict__ perm,
-                                 double* __restrict__ L, int64_t ldL, int l_trans,
                                  double* __restrict__ U, int64_t ldU, int u_trans,
                                  const PanelScratch* __restrict__ ps, int32_t* __restrict__ info,
                                  int* __restrict__ status, const double* __restrict__ Ubuf) {
@@ -702,20 +712,52 @@ __global__ void k_panel_finalize(int64_t rows, int cols, double* __restrict__ X,
         }
         const int64_t pp = pos[i];
         perm[pp] = int32_t(i);
-        for (int c = 0; c < r; ++c) {
-            double v;
-            if (s >= 0 && c == s) v = 1.0;
-            else if (s >= 0 && c > s) v = 0.0;
-            else v = X[i + int64_t(c) * ldx];
-            if (l_trans) L[c + pp * ldL] = v;
-            else L[pp + int64_t(c) * ldL] = v;
-        }
+        // L is written by k_panel_gather_l once perm is complete
         if (s >= 0) {
             for (int c = 0; c < cols; ++c) {
                 const double v = (c < s) ? 0.0
                                          : (Ubuf ? Ubuf[s + int64_t(c) * r] : X[i + int64_t(c) * ldx]);
                 if (u_trans) U[c + int64_t(s) * ldU] = v;
                 else U[s + int64_t(c) * ldU] = v;
+            }
+        }
+    }
+}
+
+// Mode 1, after k_panel_finalize has written perm: L(pp, c) = the factored
+// row perm[pp] of X in column c, with a unit diagonal and zeros above it (or
+// L^T when l_trans).  CTA row blockIdx.y covers columns 8 y .. 8 y + 7; each
+// thread gathers its eight values before it stores any.
+constexpr int GC = 8;
+__global__ void k_panel_gather_l(int64_t rows, int r, const double* __restrict__ X, int64_t ldx,
+                                 const int32_t* __restrict__ perm,
+                                 const int* __restrict__ pivstep, double* __restrict__ L,
+                                 int64_t ldL, int l_trans, const int* __restrict__ status) {
+    if (*reinterpret_cast<const volatile int*>(status) != DEV_OK) return;
+    const int c0 = blockIdx.y * GC;
+    const int nc = min(GC, r - c0);
+    for (int64_t pp = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; pp < rows;
+         pp += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t i = perm[pp];
+        if (i < 0 || int64_t(i) >= rows) continue;        // defensive: never index with junk
+        const int s = pivstep[i];
+        if (s < -1 || s >= r) continue;
+        double v[GC];
+#pragma unroll
+        for (int q = 0; q < GC; ++q) {
+            const int c = c0 + q;
+            v[q] = 0.0;
+            if (q < nc) {
+                if (s >= 0 && c == s) v[q] = 1.0;
+                else if (!(s >= 0 && c > s)) v[q] = X[i + int64_t(c) * ldx];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < GC; ++q) {
+            if (q < nc) {
+                const int c = c0 + q;
+                if (l_trans) L[c + pp * ldL] = v[q];
+                else L[pp + int64_t(c) * ldL] = v[q];
             }
         }
     }
@@ -802,8 +844,20 @@ cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int 
     if (fb > int64_t(num_sms) * 8) fb = int64_t(num_sms) * 8;
     count_launch();
     k_panel_finalize<<<unsigned(fb), 256, 0, s>>>(rows, cols, X, ldx, mode, pos, pivstep, perm,
-                                                  L, ldL, l_trans, U, ldU, u_trans, ps, info,
+                                                  U, ldU, u_trans, ps, info,
                                                   dev_status, (blocked || lookahead) ? Ubuf : nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || mode == 0) return e;
+    const int r = int(rows < int64_t(cols) ? rows : int64_t(cols));
+    const int64_t gy = (r + GC - 1) / GC;
+    int64_t gx = (rows + 255) / 256;
+    const int64_t gcap = (int64_t(num_sms) * 16 + gy - 1) / gy;
+    if (gx > gcap) gx = gcap;
+    if (gy > 65535) return cudaErrorInvalidValue;
+    count_launch();
+    k_panel_gather_l<<<dim3(unsigned(gx), unsigned(gy)), 256, 0, s>>>(rows, r, X, ldx, perm,
+                                                                       pivstep, L, ldL, l_trans,
+                                                                       dev_status);
     return cudaGetLastError();
 }
 

@@ -158,13 +158,14 @@ k_cholesky_coop(int n, double* __restrict__ W, const double* __restrict__ Wsave,
             if (!grid_barrier(&ctl->barrier, ++nbar * nb, status, budget)) return;
             if (ld_volatile_i32(&ctl->broke)) { broke = true; break; }
             // R11 to shared memory, then R12(:, c) = R11^{-T} W12(:, c), one
-            // column per thread of the grid
+            // column per thread, the columns dealt round-robin over the CTAs
+            // (each SM's FP64 pipe takes a share of the solves)
             for (int e = t; e < b * b; e += CBT) {
                 const int a = e % b, c = e / b;
                 D[a][c] = a <= c ? __ldcg(&W[(kb + a) + int64_t(kb + c) * n]) : 0.0;
             }
             __syncthreads();
-            for (int c = kb + b + gtid; c < n; c += gthreads) {
+            for (int c = kb + b + blockIdx.x + nb * t; c < n; c += gthreads) {
                 double x[CB];
 #pragma unroll
                 for (int i = 0; i < CB; ++i) {
@@ -227,13 +228,64 @@ __global__ void k_trinv_upper(int n, const double* __restrict__ R, double* __res
     for (int i = t; i < n; i += blockDim.x) x[i] = (i == j) ? 1.0 : 0.0;
     __syncthreads();
     for (int i = j; i >= 0; --i) {
-        const double xi = x[i] / R[i + int64_t(i) * n];
+        if (t == 0) x[i] = x[i] / R[i + int64_t(i) * n];
         __syncthreads();
-        if (t == 0) x[i] = xi;
+        const double xi = x[i];
         for (int k = t; k < i; k += blockDim.x) x[k] -= xi * R[k + int64_t(i) * n];
         __syncthreads();
     }
     for (int i = t; i < n; i += blockDim.x) Rinv[i + int64_t(j) * n] = x[i];
+}
+
+// As k_trinv_upper, with the columns of R staged in shared memory cw at a
+// time (column c, rows 0..c), so a substitution step reads shared memory
+// only.  Same operations in the same order, so the same result.
+__global__ void k_trinv_upper_staged(int n, const double* __restrict__ R,
+                                     double* __restrict__ Rinv, const int* __restrict__ skip,
+                                     int cw) {
+    if (skip && *skip) return;
+    extern __shared__ double sm[];
+    double* x = sm;                                // n
+    double* Rc = sm + n;                           // cw columns of n
+    const int j = blockIdx.x;
+    const int t = threadIdx.x;
+    for (int i = t; i < n; i += blockDim.x) x[i] = (i == j) ? 1.0 : 0.0;
+    for (int hi = j; hi >= 0; hi -= cw) {
+        const int lo = hi - cw + 1 > 0 ? hi - cw + 1 : 0;
+        __syncthreads();                           // the previous chunk is no longer read
+        for (int c = lo; c <= hi; ++c)
+            for (int k = t; k <= c; k += blockDim.x) Rc[(c - lo) * n + k] = R[k + int64_t(c) * n];
+        __syncthreads();
+        for (int i = hi; i >= lo; --i) {
+            const double* col = Rc + (i - lo) * n;
+            // one thread divides (the FP64 pipe is narrow); the rest read x_i
+            if (t == 0) x[i] = x[i] / col[i];
+            __syncthreads();
+            const double xi = x[i];
+            for (int k = t; k < i; k += blockDim.x) x[k] -= xi * col[k];
+            __syncthreads();
+        }
+    }
+    for (int i = t; i < n; i += blockDim.x) Rinv[i + int64_t(j) * n] = x[i];
+}
+
+// Rinv = R^{-1}: the staged kernel when cw >= 8 columns of R fit in 64 KB.
+cudaError_t trinv_upper(int n, const double* R, double* Rinv, const int* skip, cudaStream_t s) {
+    const int tt = n < 256 ? 128 : 256;
+    const int cw = 8192 / (n > 0 ? n : 1);
+    count_launch();
+    if (cw >= 8) {
+        const int w = cw > 64 ? 64 : cw;
+        const size_t smem = size_t(n) * (w + 1) * sizeof(double);
+        cudaError_t e = cudaFuncSetAttribute(k_trinv_upper_staged,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(smem));
+        if (e != cudaSuccess) return e;
+        k_trinv_upper_staged<<<n, tt, smem, s>>>(n, R, Rinv, skip, w);
+        return cudaGetLastError();
+    }
+    k_trinv_upper<<<n, tt, size_t(n) * sizeof(double), s>>>(n, R, Rinv, skip);
+    return cudaGetLastError();
 }
 
 // skip2 = 1 when the diagonal spread of the first Cholesky factor is at most
@@ -257,10 +309,7 @@ __global__ void k_qr_decide(int n, const double* __restrict__ R, int* __restrict
 
 cudaError_t launch_trinv_upper(int n, const double* R, double* Rinv, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const int tt = n < 256 ? 128 : 256;
-    count_launch();
-    k_trinv_upper<<<n, tt, size_t(n) * sizeof(double), s>>>(n, R, Rinv, nullptr);
-    return cudaGetLastError();
+    return trinv_upper(n, R, Rinv, nullptr, s);
 }
 
 size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms) {
@@ -311,9 +360,10 @@ cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, doubl
         } else {
             e = cudaMemsetAsync(ctl, 0, sizeof(CholCtl), s);
             if (e != cudaSuccess) return e;
-            // about one CTA per 4096 entries of the Gram matrix (the trailing
-            // updates dominate), at least 8, at most one per SM
-            int grid = int(int64_t(cols) * cols / 4096);
+            // about one CTA per 512 entries of the Gram matrix (the trailing
+            // updates and the block-row solves spread over the SMs' FP64
+            // pipes), at least 8, at most one per SM
+            int grid = int(int64_t(cols) * cols / 512);
             if (grid < 8) grid = 8;
             if (grid > num_sms) grid = num_sms;
             // the block rows of R12 (CB x (cols - CB) doubles) in shared memory when they fit
@@ -340,10 +390,7 @@ cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, doubl
             k_qr_decide<<<1, 32, 0, s>>>(cols, W, skip2);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        const int tt = cols < 256 ? 128 : 256;
-        count_launch();
-        k_trinv_upper<<<cols, tt, size_t(cols) * sizeof(double), s>>>(cols, W, Rinv, sk);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = trinv_upper(cols, W, Rinv, sk, s)) != cudaSuccess) return e;
         // X <- X Rinv (the reduction of the partial sums writes X after the product)
         e = launch_gemm_f64_tri(0, 2, rows, cols, cols, X, ldx, Rinv, cols, X, ldx, part,
                                 part_cap, num_sms, s, sk);
