@@ -11,7 +11,9 @@ Readings (the paper is silent on them):
 * pivot of column j: the entry of largest magnitude among the rows not yet
   pivoted, ties going to the row that comes first in the current (swapped)
   row order -- the rule of LAPACK's getf2 behind MATLAB's ``lu``;
-* multipliers are a_ij / u_jj (plain division);
+* multipliers as LAPACK's getf2 / getrf2 form them (the LU behind MATLAB's
+  ``lu``): a_ij times the reciprocal 1 / u_jj when |u_jj| is at least the
+  smallest normal number, else a_ij / u_jj;
 * a column whose candidates are all exactly zero is skipped: no swap, no
   division, its multipliers stay 0, and ``info`` records the first such
   column (1-based), as LAPACK does.
@@ -20,6 +22,8 @@ Pinned by: exact rational elimination on small inputs (Python fractions),
 scipy.linalg.lu (LAPACK getrf) pivots on random panels, and P X = L U.
 """
 import numpy as np
+
+_SMALLEST_NORMAL = np.finfo(np.float64).tiny      # 2^-1022
 
 
 def getrf(X):
@@ -39,7 +43,11 @@ def getrf(X):
             if i != j:
                 A[[j, i], :] = A[[i, j], :]
                 perm[[j, i]] = perm[[i, j]]
-            A[j + 1:, j] = A[j + 1:, j] / A[j, j]
+            piv = A[j, j]
+            if abs(piv) >= _SMALLEST_NORMAL:
+                A[j + 1:, j] = A[j + 1:, j] * (1.0 / piv)
+            else:
+                A[j + 1:, j] = A[j + 1:, j] / piv
         elif info == 0:
             info = j + 1
         if j + 1 < n and j + 1 < m:

@@ -264,10 +264,11 @@ k_b_panel_lu(const LuJob* __restrict__ jobs) {
         __syncthreads();
         const double ujj = urow[j];
         if (ujj != 0.0) {
+            const double rinv = 1.0 / ujj;
             for (int64_t i = t; i < rows; i += LNT) {
                 if (J.pivstep[i] >= 0) continue;
                 double* xi = X + i;
-                const double lij = xi[int64_t(j) * J.ldx] / ujj;
+                const double lij = lu_multiplier(xi[int64_t(j) * J.ldx], ujj, rinv);
                 xi[int64_t(j) * J.ldx] = lij;
                 for (int c = j + 1; c < cols; ++c) {
                     double* p = xi + int64_t(c) * J.ldx;

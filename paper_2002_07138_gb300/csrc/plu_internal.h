@@ -43,6 +43,14 @@ __device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// LU multiplier as LAPACK's getf2 / getrf2 form it (the LU behind MATLAB's
+// lu): x times rinv = 1 / u when |u| is at least the smallest normal number,
+// else x / u.  The comparison runs on the integer pipe.
+__device__ __forceinline__ double lu_multiplier(double x, double u, double rinv) {
+    return (__double_as_longlong(u) & 0x7FFFFFFFFFFFFFFFLL) >= 0x0010000000000000LL ? x * rinv
+                                                                                     : x / u;
+}
+
 __device__ __forceinline__ int ld_volatile_i32(const int* p) {
     return *reinterpret_cast<const volatile int*>(p);
 }

@@ -12,7 +12,8 @@
 //      applies LAPACK's row interchange to the positions of its own rows
 //      (r takes position j, the row at position j takes r's old position),
 //      stages row r's columns j.. in shared memory, and eliminates:
-//      l_ij = x_ij / u_jj, x_ic -= l_ij u_jc for its other active rows, and
+//      l_ij = x_ij (1 / u_jj) (LAPACK's scaling; x_ij / u_jj when u_jj is
+//      subnormal), x_ic -= l_ij u_jc for its other active rows, and
 //      computes its candidate for column j+1 in the same sweep.
 // A column whose candidates are all exactly zero is skipped (no division),
 // as LAPACK does; the first such column is reported in `info`.
@@ -175,13 +176,14 @@ k_panel_lu(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
         }
         __syncthreads();
         const double ujj = urow[j];
+        const double rinv = 1.0 / ujj;
         best = Cand{-1.0, INT_MAX, -1};
         const bool next = j + 1 < steps;
         for (int64_t i = r0 + t; i < r1; i += NT) {
             if (pivstep[i] >= 0) continue;
             double* xi = X + i;
             if (ujj != 0.0) {
-                const double lij = xi[int64_t(j) * ldx] / ujj;
+                const double lij = lu_multiplier(xi[int64_t(j) * ldx], ujj, rinv);
                 xi[int64_t(j) * ldx] = lij;
                 for (int c = j + 1; c < cols; ++c) {
                     double* p = xi + int64_t(c) * ldx;
@@ -329,12 +331,13 @@ k_panel_lu_blocked(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
             // eliminate column sc from the own active rows of the block and,
             // in the same sweep, find the candidate for column sc + 1
             const double ujj = PR[sc * NB + sc];
+            const double rinv = 1.0 / ujj;
             const bool next = sc + 1 < nbk;
             best = Cand{-1.0, INT_MAX, -1};
             for (int r = t; r < R; r += NT) {
                 if (piv_s[r] >= 0) continue;
                 if (ujj != 0.0) {
-                    const double l = P[sc * per + r] / ujj;
+                    const double l = lu_multiplier(P[sc * per + r], ujj, rinv);
                     P[sc * per + r] = l;
                     for (int u = sc + 1; u < nbk; ++u)
                         P[u * per + r] = fma(-l, PR[sc * NB + u], P[u * per + r]);
@@ -472,6 +475,7 @@ k_panel_lu_la(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
     __shared__ int nan_seen;
     __shared__ volatile int panel_ok;
     __shared__ int abort_s;
+    __shared__ double rinv_s;
 
     const int nb = gridDim.x;
     const int t = threadIdx.x;
@@ -584,7 +588,11 @@ k_panel_lu_la(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
                     break;
                 }
                 const double* wsrc = slots + (int64_t(j & 1) * nb + win_slot) * slot_w;
-                if (t < nbk) PR[sc * NB + t] = __ldcg(wsrc + 3 + t);
+                if (t < nbk) {
+                    const double u = __ldcg(wsrc + 3 + t);
+                    PR[sc * NB + t] = u;
+                    if (t == sc) rinv_s = 1.0 / u;   // one FP64 division per step
+                }
                 if (t == 0) prow_id[sc] = pv.row;
                 for (int r = t; r < R; r += NTP) {
                     if (r0 + r == pv.row) {
@@ -605,7 +613,7 @@ k_panel_lu_la(int64_t rows, int cols, double* __restrict__ X, int64_t ldx,
                 for (int r = t; r < R; r += NTP) {
                     if (piv_s[r] >= 0) continue;
                     if (ujj != 0.0) {
-                        const double l = Pc[sc * per + r] / ujj;
+                        const double l = lu_multiplier(Pc[sc * per + r], ujj, rinv_s);
                         Pc[sc * per + r] = l;
                         for (int u = sc + 1; u < nbk; ++u)
                             Pc[u * per + r] = fma(-l, PR[sc * NB + u], Pc[u * per + r]);

@@ -106,6 +106,21 @@ def test_getrf_matches_lapack_pivots():
     assert np.max(np.abs(L)) <= 1.0
 
 
+def test_getrf_multipliers_scale_by_reciprocal_like_lapack():
+    """MATLAB's lu is LAPACK getrf, whose getf2 / getrf2 scale the pivot
+    column by 1 / u_jj (|u_jj| normal): one elimination step matches LAPACK
+    bit for bit, and the plain quotient differs in many entries."""
+    X = np.random.default_rng(21).standard_normal((5000, 1))
+    perm, L, U, _ = getrf(X)
+    _, Ls, _ = scipy.linalg.lu(X)
+    assert np.array_equal(L[:, 0], Ls[:, 0])
+    assert np.sum(X[perm, 0] / X[perm[0], 0] != L[:, 0]) > 100
+    # a subnormal pivot is divided, not inverted (1 / u would overflow)
+    Y = np.array([[4e-320], [2e-320], [1e-320]])
+    perm, L, U, _ = getrf(Y)
+    assert np.array_equal(L[:, 0], Y[perm, 0] / Y[perm[0], 0])
+
+
 def test_permuted_L_rows_align():
     X = np.random.default_rng(12).standard_normal((50, 7))
     Lp = lu_permuted_L(X)
