@@ -146,6 +146,16 @@ plu_status plu_getrf(plu_ctx* ctx, int64_t rows, int cols, double* X, int64_t ld
 plu_status plu_qr(plu_ctx* ctx, int64_t rows, int cols, double* X, int64_t ldx,
                   double* R, int64_t ldR);
 
+/* a5 as the mixed modes run it: one CholeskyQR round, X (rows x cols) <- X
+ * R^{-1} with R^T R = X^T X (Alg. gpowerlu, last step; R, when non-NULL,
+ * receives R, ldR >= cols).  tc != 0: the two FP64 products X^T X and
+ * X R^{-1} run on the BF16 tensor cores as sums of exact products of 7-bit
+ * slices of the operands (FP64-accurate; needs cols <= 511, else
+ * PLU_EUNSUPPORTED); tc = 0: FP64 FMAs.  Orthogonality of one round degrades
+ * with cond(X)^2; plu_qr runs two. */
+plu_status plu_cholqr1(plu_ctx* ctx, int64_t rows, int cols, double* X, int64_t ldx,
+                       double* R, int64_t ldR, int tc);
+
 /* a7. Blocked rank determination (Alg. adaptivewithoutupdating; precise != 0
  * adds the per-column loop of Sec. 6.4): from G = A V (rows x cols) and
  * normA2 = ||A||_F^2 (host value), find the first block of b columns (or

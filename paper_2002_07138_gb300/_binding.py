@@ -62,6 +62,7 @@ SIGNATURES = {
     "plu_lu_reorth": (c_int, [c_vp, c_i64, c_int, c_vp, c_i64]),
     "plu_getrf": (c_int, [c_vp, c_i64, c_int, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_i64, c_vp]),
     "plu_qr": (c_int, [c_vp, c_i64, c_int, c_vp, c_i64, c_vp, c_i64]),
+    "plu_cholqr1": (c_int, [c_vp, c_i64, c_int, c_vp, c_i64, c_vp, c_i64, c_int]),
     "plu_rank": (c_int, [c_vp, c_i64, c_int, c_vp, c_i64, c_dbl, c_dbl, c_int, c_int,
                          ctypes.POINTER(c_int), ctypes.POINTER(c_dbl)]),
     "plu_norm2": (c_int, [c_vp, ctypes.POINTER(plu_matrix), ctypes.POINTER(c_dbl)]),
@@ -223,6 +224,15 @@ def plu_qr(ctx, X, want_r=False):
     ctx.check(lib().plu_qr(ctx.handle, X.shape[0], X.shape[1], _ptr(X), _ld(X), _ptr(R),
                            _ld(R) if R is not None else 0))
     return (X, R) if want_r else X
+
+
+def plu_cholqr1(ctx, X, tc=True):
+    """One CholeskyQR round in place (X <- X R^-1); tc: FP64-accurate products
+    on the BF16 tensor cores.  Returns (X, R)."""
+    R = colmajor_empty(X.shape[1], X.shape[1], device=X.device)
+    ctx.check(lib().plu_cholqr1(ctx.handle, X.shape[0], X.shape[1], _ptr(X), _ld(X), _ptr(R),
+                                _ld(R), int(bool(tc))))
+    return X, R
 
 
 def plu_norm2(ctx, A):

@@ -203,6 +203,11 @@ PowerLUPlan plan_powerlu(int64_t m, int64_t n, int l, int kmax, int prec, int sm
     if (t > step) step = t;
     t = qr_scratch_bytes(n, l, sms);
     if (t > step) step = t;
+    // the mixed modes orthonormalise the kmax leading columns with tensor-core products
+    if (prec != PLU_FP64) {
+        t = qr_scratch_bytes(n, kmax, sms, 1);
+        if (t > step) step = t;
+    }
     p.step = lay.add(step);
     p.step_bytes = step;
     p.L1 = lay.add(size_t(m) * kmax * sizeof(double));
@@ -307,8 +312,12 @@ plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t 
         return PLU_OK;
     };
     auto qr = [&](double* X) -> plu_status {
-        PLU_CUDA(c, launch_cholqr2(n, qr_cols, X, n, nullptr, 0, step, step_cap, c->d_status,
-                                   c->num_sms, c->stream, adaptive_qr));
+        const cudaError_t e = launch_cholqr2(n, qr_cols, X, n, nullptr, 0, step, step_cap,
+                                             c->d_status, c->num_sms, c->stream, adaptive_qr, 2,
+                                             adaptive_qr);
+        if (e != cudaSuccess)
+            return fail(c, PLU_ECUDA, "CholeskyQR (%s): %s", cholqr_failed_step(),
+                        cudaGetErrorString(e));
         return PLU_OK;
     };
     if (v % 2 == 0) {
@@ -528,6 +537,20 @@ plu_status plu_qr(plu_ctx* c, int64_t rows, int cols, double* X, int64_t ldx, do
     PLU_TRY(ensure_ws(c, qw));
     PLU_CUDA(c, launch_cholqr2(rows, cols, X, ldx, R, ldR, c->ws, qw, c->d_status, c->num_sms,
                                c->stream));
+    return finish(c);
+}
+
+plu_status plu_cholqr1(plu_ctx* c, int64_t rows, int cols, double* X, int64_t ldx, double* R,
+                       int64_t ldR, int tc) {
+    PLU_TRY(bind(c));
+    if (cols < 1 || rows < cols || !X || ldx < rows || (R && ldR < cols))
+        return fail(c, PLU_EINVAL, "cholqr1 needs rows >= cols >= 1");
+    if (tc && !oz_supported(rows, cols, c->num_sms))
+        return fail(c, PLU_EUNSUPPORTED, "tensor-core products need cols <= 511 and a shorter X");
+    const size_t qw = qr_scratch_bytes(rows, cols, c->num_sms, tc ? 1 : 0);
+    PLU_TRY(ensure_ws(c, qw));
+    PLU_CUDA(c, launch_cholqr2(rows, cols, X, ldx, R, ldR, c->ws, qw, c->d_status, c->num_sms,
+                               c->stream, 0, 1, tc ? 1 : 0));
     return finish(c);
 }
 

@@ -101,8 +101,8 @@ constexpr int GBM = 64, GBN = 32, GBK = 16, GNT = 256;
 template <typename TC>
 __global__ void __launch_bounds__(GNT)
 k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
-    __shared__ TC As[GBK][GBM + 1];
-    __shared__ TC Bs[GBK][GBN + 1];
+    __shared__ TC As[2][GBK][GBM + 1];
+    __shared__ TC Bs[2][GBK][GBN + 1];
     // job of this tile: last job with tile0 <= blockIdx.x
     int lo = 0, hi = njobs - 1;
     const int64_t tile = blockIdx.x;
@@ -122,10 +122,10 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
     if (skip) kend = 0;
     const float* Af = static_cast<const float*>(J.A);
     const double* Ad = static_cast<const double*>(J.A);
-    TC acc[4][2];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = TC(0);
-    for (int64_t k0 = 0; k0 < kend; k0 += GBK) {
+    // the next K step is loaded into registers while the current one is
+    // multiplied out of shared memory (two buffers, one barrier per step)
+    TC ra[4], rb[2];
+    auto load = [&](int64_t k0) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             int ii, kk;
@@ -137,7 +137,7 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
                 const int64_t off = J.transA ? gk + gi * J.lda : gi + gk * J.lda;
                 v = J.a_f32 ? TC(Af[off]) : TC(Ad[off]);
             }
-            As[kk][ii] = v;
+            ra[r] = v;
         }
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
@@ -147,23 +147,53 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
             const int64_t gj = j0 + jj, gk = k0 + kk;
             TC v = TC(0);
             if (gj < J.N && gk < kend) v = TC(J.transB ? J.B[gj + gk * J.ldb] : J.B[gk + gj * J.ldb]);
-            Bs[kk][jj] = v;
+            rb[r] = v;
         }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int ii, kk;
+            if (J.transA) { kk = t % 16; ii = t / 16 + 16 * r; }
+            else          { ii = t % 64; kk = t / 64 + 4 * r; }
+            As[buf][kk][ii] = ra[r];
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            int jj, kk;
+            if (J.transB) { jj = t % 32; kk = t / 32 + 8 * r; }
+            else          { kk = t % 16; jj = t / 16 + 16 * r; }
+            Bs[buf][kk][jj] = rb[r];
+        }
+    };
+    TC acc[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = TC(0);
+    if (kend > 0) {
+        load(0);
+        store(0);
         __syncthreads();
+        int buf = 0;
+        for (int64_t k0 = 0; k0 < kend; k0 += GBK) {
+            const bool more = k0 + GBK < kend;
+            if (more) load(k0 + GBK);
 #pragma unroll
-        for (int kk = 0; kk < GBK; ++kk) {
-            TC av[4], bv[2];
+            for (int kk = 0; kk < GBK; ++kk) {
+                TC av[4], bv[2];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
-            bv[0] = Bs[kk][tx];
-            bv[1] = Bs[kk][tx + 16];
+                for (int a = 0; a < 4; ++a) av[a] = As[buf][kk][ty + 16 * a];
+                bv[0] = Bs[buf][kk][tx];
+                bv[1] = Bs[buf][kk][tx + 16];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                acc[a][0] = fma(av[a], bv[0], acc[a][0]);
-                acc[a][1] = fma(av[a], bv[1], acc[a][1]);
+                for (int a = 0; a < 4; ++a) {
+                    acc[a][0] = fma(av[a], bv[0], acc[a][0]);
+                    acc[a][1] = fma(av[a], bv[1], acc[a][1]);
+                }
             }
+            if (more) store(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
         }
-        __syncthreads();
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -691,7 +721,7 @@ static void plan_batch(const plu_batch_problem* P, int count, int prec, char* ws
                     gm.push_back(mk_gemm(W[i].V, P[i].n, 0, 0, W[i].T, k, 1, W[i].BT, P[i].n,
                                          int(P[i].n), k, k));
                 }
-            B.gemm(gm, 0);
+            B.gemm(gm, tc32);
         }
         if (anytail || anysp) {
             // [L1, U1, P] = lu(Y)   (Y = A V_k, or H for the single pass; in Z)
@@ -712,7 +742,9 @@ static void plan_batch(const plu_batch_problem* P, int count, int prec, char* ws
                 gm.push_back(mk_gemm(left, P[i].n, 0, 0, W[i].U1T, k, 0, W[i].X2, P[i].n,
                                      int(P[i].n), k, k));
             }
-            B.gemm(gm, 0);
+            // the m x k x k products of the tail take FP32 FMAs with FP32 passes
+            // (the passes' rounding dominates); the LUs stay FP64
+            B.gemm(gm, tc32);
             // [L2, U2, Q] = lu(B^T), U = L2^T
             for (int i = 0; i < count; ++i) {
                 const int kd = ops[i][ph].kind;
@@ -730,7 +762,7 @@ static void plan_batch(const plu_batch_problem* P, int count, int prec, char* ws
                 gm.push_back(mk_gemm(W[i].L1, P[i].m, 0, 0, W[i].U2T, k, 0, P[i].L, P[i].ldL,
                                      int(P[i].m), k, k));
             }
-            B.gemm(gm, 0);
+            B.gemm(gm, tc32);
         }
     }
 }

@@ -174,9 +174,26 @@ struct QuantA {
 size_t tc_quant_bytes(int64_t m, int64_t n, int prec);
 cudaError_t launch_tc_quantize(int prec, const float* A, int64_t m, int64_t n, int64_t lda,
                                void* qbuf, QuantA* out, int num_sms, cudaStream_t s);
+// xq_pre (BF16 only): X already in BF16 operand form, as for launch_tc_pass.
 cudaError_t launch_tc_pass_q(int trans, const QuantA& q, const double* X, int64_t ldx, int cols,
                              double* Y, int64_t ldy, void* scratch, size_t scratch_cap,
-                             int* dev_status, int num_sms, cudaStream_t s, int accum = 0);
+                             int* dev_status, int num_sms, cudaStream_t s, int accum = 0,
+                             const void* xq_pre = nullptr);
+
+// FP64-accurate X^T X and X R^{-1} on the BF16 tensor cores (sums of exact
+// slice products; plu_ozaki.cu).  X is rows x cols (ldx), R^{-1} cols x cols
+// (ld cols); W (cols x cols, ld cols) receives the whole Gram matrix.
+// oz_supported() tells whether the shape keeps every FP32 partial sum exact
+// (cols <= 511 and a bounded stream-K segment); the launchers return an error
+// otherwise.  scratch holds oz_scratch_bytes().
+bool oz_supported(int64_t rows, int cols, int num_sms);
+size_t oz_scratch_bytes(int64_t rows, int cols, int num_sms);
+cudaError_t launch_oz_gram(int64_t rows, int cols, const double* X, int64_t ldx, double* W,
+                           void* scratch, size_t scratch_cap, int* dev_status, int num_sms,
+                           cudaStream_t s);
+cudaError_t launch_oz_xrinv(int64_t rows, int cols, const double* X, int64_t ldx,
+                            const double* Rinv, double* Y, int64_t ldy, void* scratch,
+                            size_t scratch_cap, int* dev_status, int num_sms, cudaStream_t s);
 
 // ------------------------------------------------------- panel LU (a3, a8)
 struct PanelScratch;   // defined in plu_panel.cu
@@ -194,15 +211,22 @@ cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int 
 // --------------------------------------------------------------- QR (a5)
 // scratch holds scratch_cap >= qr_scratch_bytes(rows, cols, num_sms) bytes
 // (less works down to one split of each product; too little is an error).
-size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms);
+size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms, int tc_products = 0);
 // adaptive != 0: the second CholeskyQR round runs only when the first
 // Cholesky factor's diagonal spread max|r_ii| / min|r_ii| exceeds 1e5 (the
 // decision is taken on the device; the second round's kernels return at once
 // otherwise); R cannot be requested then.  rounds = 1 runs one CholeskyQR
-// round (X <- X R1^{-1}, R = R1, with R1^T R1 = X^T X).
+// round (X <- X R1^{-1}, R = R1, with R1^T R1 = X^T X).  tc_products != 0
+// computes the first round's X^T X and X R^{-1} as exact slice products on
+// the BF16 tensor cores (launch_oz_gram / launch_oz_xrinv) when the shape
+// allows it and the scratch holds qr_scratch_bytes(..., 1).
 cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, double* R,
                            int64_t ldR, void* scratch, size_t scratch_cap, int* dev_status,
-                           int num_sms, cudaStream_t s, int adaptive = 0, int rounds = 2);
+                           int num_sms, cudaStream_t s, int adaptive = 0, int rounds = 2,
+                           int tc_products = 0);
+
+// The step of the calling thread's last launch_cholqr2 that returned an error.
+const char* cholqr_failed_step();
 
 // Rinv = R^{-1} for an upper triangular n x n R (ld n); Rinv is upper triangular.
 cudaError_t launch_trinv_upper(int n, const double* R, double* Rinv, cudaStream_t s);

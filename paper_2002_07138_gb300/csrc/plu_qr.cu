@@ -312,16 +312,29 @@ cudaError_t launch_trinv_upper(int n, const double* R, double* Rinv, cudaStream_
     return trinv_upper(n, R, Rinv, nullptr, s);
 }
 
-size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms) {
+size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms, int tc_products) {
     const size_t sq = size_t(cols) * cols * sizeof(double);
-    const size_t p1 = gemm_f64_partials_bytes(cols, cols, rows, num_sms);
+    size_t p = gemm_f64_partials_bytes(cols, cols, rows, num_sms);
     const size_t p2 = gemm_f64_partials_bytes(rows, cols, cols, num_sms);
-    return 5 * sq + (p1 > p2 ? p1 : p2) + 8 * 256;
+    if (p2 > p) p = p2;
+    if (tc_products && oz_supported(rows, cols, num_sms)) {
+        const size_t oz = oz_scratch_bytes(rows, cols, num_sms);
+        if (oz > p) p = oz;
+    }
+    return 5 * sq + p + 8 * 256;
 }
+
+namespace {
+thread_local const char* t_cholqr_step = "";
+}
+
+const char* cholqr_failed_step() { return t_cholqr_step; }
 
 cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, double* R,
                            int64_t ldR, void* scratch, size_t scratch_cap, int* dev_status,
-                           int num_sms, cudaStream_t s, int adaptive, int rounds) {
+                           int num_sms, cudaStream_t s, int adaptive, int rounds,
+                           int tc_products) {
+    t_cholqr_step = "arguments";
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     if (adaptive && R) return cudaErrorInvalidValue;     // R would be R1 or R2 R1
     if (rounds != 1 && rounds != 2) return cudaErrorInvalidValue;
@@ -342,17 +355,29 @@ cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, doubl
     void* part = ws.take(part_cap);
     if (!W || !Wsave || !Rinv || !R1 || !Rtmp || !part || !ctl || !skip2)
         return cudaErrorInvalidValue;
+    // the first round's products as exact slice products on the tensor cores
+    // (a skipped second round cannot run there: its kernels must return on a
+    // device-side flag, which the FP64 kernels do)
+    const bool oz = tc_products && oz_supported(rows, cols, num_sms) &&
+                    part_cap >= oz_scratch_bytes(rows, cols, num_sms);
     cudaError_t e;
     for (int pass = 0; pass < rounds; ++pass) {
         const int* sk = (pass == 1 && adaptive) ? skip2 : nullptr;
-        // W = X^T X, upper triangle only (the Cholesky reads nothing else)
-        e = launch_gemm_f64_tri(1, 1, cols, cols, rows, X, ldx, X, ldx, W, cols, part, part_cap,
-                                num_sms, s, sk);
+        const bool tc = oz && pass == 0;
+        // W = X^T X, upper triangle only (the Cholesky reads nothing else;
+        // the tensor-core form writes both triangles)
+        t_cholqr_step = tc ? "Gram (tensor cores)" : "Gram";
+        if (tc)
+            e = launch_oz_gram(rows, cols, X, ldx, W, part, part_cap, dev_status, num_sms, s);
+        else
+            e = launch_gemm_f64_tri(1, 1, cols, cols, rows, X, ldx, X, ldx, W, cols, part,
+                                    part_cap, num_sms, s, sk);
         if (e != cudaSuccess) return e;
         if (pass == 0) {
             e = cudaMemcpyAsync(Wsave, W, sq, cudaMemcpyDeviceToDevice, s);
             if (e != cudaSuccess) return e;
         }
+        t_cholqr_step = "Cholesky";
         if (cols <= 128) {
             count_launch();
             k_cholesky<<<1, CT, 0, s>>>(cols, W, Wsave, rows, pass == 0 ? 1 : 0, dev_status, sk);
@@ -390,10 +415,17 @@ cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, doubl
             k_qr_decide<<<1, 32, 0, s>>>(cols, W, skip2);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
+        t_cholqr_step = "triangular inverse";
         if ((e = trinv_upper(cols, W, Rinv, sk, s)) != cudaSuccess) return e;
-        // X <- X Rinv (the reduction of the partial sums writes X after the product)
-        e = launch_gemm_f64_tri(0, 2, rows, cols, cols, X, ldx, Rinv, cols, X, ldx, part,
-                                part_cap, num_sms, s, sk);
+        t_cholqr_step = tc ? "X R^-1 (tensor cores)" : "X R^-1";
+        // X <- X Rinv (the reduction of the partial sums writes X after the
+        // product; the tensor-core form reads X's slices, made first)
+        if (tc)
+            e = launch_oz_xrinv(rows, cols, X, ldx, Rinv, X, ldx, part, part_cap, dev_status,
+                                num_sms, s);
+        else
+            e = launch_gemm_f64_tri(0, 2, rows, cols, cols, X, ldx, Rinv, cols, X, ldx, part,
+                                    part_cap, num_sms, s, sk);
         if (e != cudaSuccess) return e;
         if (pass == 0) {
             e = cudaMemcpyAsync(R1, W, sq, cudaMemcpyDeviceToDevice, s);

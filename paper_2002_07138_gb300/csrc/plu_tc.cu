@@ -880,7 +880,7 @@ cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t
     const float* fold = trans ? s_r : s_c;
     const float* rowblk = trans ? s_c : s_r;
     cudaError_t e;
-    if (xq_pre && KIND != KIND_TF32) return cudaErrorInvalidValue;
+    if (xq_pre && KIND == KIND_FP8) return cudaErrorInvalidValue;   // FP8 folds scales into X
     if (!xq_pre) {
         int64_t b = (int64_t(p.ksteps) * BKE + 255) / 256;
         const int64_t bcap = (int64_t(num_sms) * 16 + p.npad - 1) / p.npad;
@@ -985,11 +985,13 @@ cudaError_t launch_tc_operand(int64_t K, int cols, const double* X, int64_t ldx,
 
 cudaError_t launch_tc_pass_q(int trans, const QuantA& q, const double* X, int64_t ldx, int cols,
                              double* Y, int64_t ldy, void* scratch, size_t scratch_cap,
-                             int* dev_status, int num_sms, cudaStream_t s, int accum) {
+                             int* dev_status, int num_sms, cudaStream_t s, int accum,
+                             const void* xq_pre) {
     if (q.prec == PLU_BF16)
         return tc_pass_kind<KIND_BF16>(trans, q.m, q.n, q.data, q.ld, nullptr, nullptr, X, ldx,
                                        cols, Y, ldy, scratch, scratch_cap, dev_status, num_sms, s,
-                                       accum);
+                                       accum, xq_pre);
+    if (xq_pre) return cudaErrorInvalidValue;
     return tc_pass_kind<KIND_FP8>(trans, q.m, q.n, q.data, q.ld, q.s_r, q.s_c, X, ldx, cols, Y,
                                   ldy, scratch, scratch_cap, dev_status, num_sms, s, accum);
 }

@@ -351,3 +351,51 @@ def test_pass_fp8_matches_fp8_operands(ctx, m, n, cols, trans):
     assert rel(got, ref) < 2e-5
     exact = A32.astype(np.float64) @ X if trans == 0 else A32.astype(np.float64).T @ X
     assert rel(got, exact) < 0.1
+
+
+def _cholqr1(ctx, X, tc):
+    Xd = plu.colmajor_empty(X.shape[0], X.shape[1])
+    Xd.copy_(torch.from_numpy(np.ascontiguousarray(X)))
+    Q, R = plu.plu_cholqr1(ctx, Xd, tc=tc)
+    return Q.cpu().numpy(), R.cpu().numpy()
+
+
+@pytest.mark.parametrize("rows,cols", [(4096, 200), (3000, 256), (1000, 37)])
+def test_cholqr1_tensor_core_products_match_fp64(ctx, rows, cols):
+    """One CholeskyQR round with X^T X and X R^-1 as exact slice products on
+    the BF16 tensor cores: the same R and Q as the FP64 round to ~1e-14
+    (well-conditioned X), and R^T R = X^T X to FP64 accuracy."""
+    X = np.random.default_rng(rows + cols).standard_normal((rows, cols))
+    Qt, Rt = _cholqr1(ctx, X, True)
+    Qf, Rf = _cholqr1(ctx, X, False)
+    assert np.linalg.norm(Rt - Rf) <= 1e-13 * np.linalg.norm(Rf)
+    assert np.linalg.norm(Qt - Qf) <= 1e-13 * np.linalg.norm(Qf)
+    G = X.T @ X
+    assert np.linalg.norm(np.triu(Rt).T @ np.triu(Rt) - G) <= 1e-14 * np.linalg.norm(G)
+
+
+def test_cholqr1_tensor_core_products_row_and_column_scales(ctx):
+    """Rows spanning 2^-8 .. 2^8 and columns 10^-1 .. 10^1: per-row slices of
+    X and per-column slices of R^-1 keep every row of Q = X R^-1 as accurate,
+    relative to that row, as the FP64 round (Q R reproduces X row by row), and
+    the Gram matrix to FP64 accuracy."""
+    rng = np.random.default_rng(7)
+    rows, cols = 5000, 120
+    X = rng.standard_normal((rows, cols))
+    X *= np.exp2(rng.integers(-8, 9, size=rows))[:, None]
+    X *= 10.0 ** rng.uniform(-1, 1, size=cols)[None, :]
+    Qt, Rt = _cholqr1(ctx, X, True)
+    Qf, Rf = _cholqr1(ctx, X, False)
+    Rt = np.triu(Rt)
+    G = X.T @ X
+    assert np.linalg.norm(Rt.T @ Rt - G) <= 1e-13 * np.linalg.norm(G)
+    resid_t = np.linalg.norm(Qt @ Rt - X, axis=1) / np.linalg.norm(X, axis=1)
+    resid_f = np.linalg.norm(Qf @ np.triu(Rf) - X, axis=1) / np.linalg.norm(X, axis=1)
+    assert resid_t.max() <= 10 * resid_f.max() + 1e-13
+
+
+def test_cholqr1_tensor_core_rejects_wide_x(ctx):
+    X = plu.colmajor_empty(2000, 600)
+    X.normal_()
+    with pytest.raises(plu.PLUError):
+        plu.plu_cholqr1(ctx, X, tc=True)
