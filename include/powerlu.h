@@ -150,7 +150,7 @@ plu_status plu_qr(plu_ctx* ctx, int64_t rows, int cols, double* X, int64_t ldx,
  * R^{-1} with R^T R = X^T X (Alg. gpowerlu, last step; R, when non-NULL,
  * receives R, ldR >= cols).  tc != 0: the two FP64 products X^T X and
  * X R^{-1} run on the BF16 tensor cores as sums of exact products of 7-bit
- * slices of the operands (FP64-accurate; needs cols <= 511, else
+ * slices of the operands (FP64-accurate; needs cols <= 512, else
  * PLU_EUNSUPPORTED); tc = 0: FP64 FMAs.  Orthogonality of one round degrades
  * with cond(X)^2; plu_qr runs two. */
 plu_status plu_cholqr1(plu_ctx* ctx, int64_t rows, int cols, double* X, int64_t ldx,

@@ -203,9 +203,12 @@ PowerLUPlan plan_powerlu(int64_t m, int64_t n, int l, int kmax, int prec, int sm
     if (t > step) step = t;
     t = qr_scratch_bytes(n, l, sms);
     if (t > step) step = t;
-    // the mixed modes orthonormalise the kmax leading columns with tensor-core products
+    // the mixed modes orthonormalise with tensor-core products (the kmax
+    // leading columns at fixed rank, all l columns at fixed precision)
     if (prec != PLU_FP64) {
         t = qr_scratch_bytes(n, kmax, sms, 1);
+        if (t > step) step = t;
+        t = qr_scratch_bytes(n, l, sms, 1);
         if (t > step) step = t;
     }
     p.step = lay.add(step);
@@ -292,7 +295,7 @@ plu_status remainder_correct(plu_ctx* c, const plu_matrix* A, const Remainder& r
 plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t seed, int prec,
                         double* V, double* Z, char* step, size_t step_cap, PassTimer& pt,
                         int* passes, const QuantA* q, int qr_cols, int adaptive_qr,
-                        const Remainder& rem = Remainder(), int round = 0) {
+                        int tc_qr, const Remainder& rem = Remainder(), int round = 0) {
     const int64_t m = A->m, n = A->n;
     const int p = (v - 1) / 2;
     const uint32_t shift = kStreamRestartStride * uint32_t(round);
@@ -314,7 +317,7 @@ plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t 
     auto qr = [&](double* X) -> plu_status {
         const cudaError_t e = launch_cholqr2(n, qr_cols, X, n, nullptr, 0, step, step_cap,
                                              c->d_status, c->num_sms, c->stream, adaptive_qr, 2,
-                                             adaptive_qr);
+                                             tc_qr);
         if (e != cudaSuccess)
             return fail(c, PLU_ECUDA, "CholeskyQR (%s): %s", cholqr_failed_step(),
                         cudaGetErrorString(e));
@@ -546,7 +549,7 @@ plu_status plu_cholqr1(plu_ctx* c, int64_t rows, int cols, double* X, int64_t ld
     if (cols < 1 || rows < cols || !X || ldx < rows || (R && ldR < cols))
         return fail(c, PLU_EINVAL, "cholqr1 needs rows >= cols >= 1");
     if (tc && !oz_supported(rows, cols, c->num_sms))
-        return fail(c, PLU_EUNSUPPORTED, "tensor-core products need cols <= 511 and a shorter X");
+        return fail(c, PLU_EUNSUPPORTED, "tensor-core products need cols <= 512 and a shorter X");
     const size_t qw = qr_scratch_bytes(rows, cols, c->num_sms, tc ? 1 : 0);
     PLU_TRY(ensure_ws(c, qw));
     PLU_CUDA(c, launch_cholqr2(rows, cols, X, ldx, R, ldR, c->ws, qw, c->d_status, c->num_sms,
@@ -618,7 +621,8 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
     // mixed modes: one CholeskyQR round when it is orthogonal enough (see
     // launch_cholqr2); the FP64 path keeps both rounds
     PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pl.step_bytes, pt, &np,
-                         quant ? &qa : nullptr, k, prec != PLU_FP64 ? 1 : 0));
+                         quant ? &qa : nullptr, k, prec != PLU_FP64 ? 1 : 0,
+                         prec != PLU_FP64 ? 1 : 0));
     // Y = A V(:, 1:k) (Alg. bpowerlu step 3), the v-th pass; in the mixed
     // modes it reads the FP32 A through TF32 (it enters the result to first order)
     pt.mark();
@@ -715,7 +719,7 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
         }
         int npr = 0;
         PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pl.step_bytes, pt, &npr,
-                             quant ? &qa : nullptr, l, 0, rem, r));
+                             quant ? &qa : nullptr, l, 0, prec != PLU_FP64 ? 1 : 0, rem, r));
         np += npr;
         // G = A V (step 3), the v-th pass.  Its column norms decide the rank:
         // E = ||A||_F^2 - sum ||G(:, j)||^2 must resolve eps^2 ||A||_F^2, which
@@ -834,7 +838,7 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
     }
     t = panel_scratch_bytes(m > n ? m : n, k);
     if (t > step) step = t;
-    t = qr_scratch_bytes(n, k, c->num_sms);
+    t = qr_scratch_bytes(n, k, c->num_sms, prec != PLU_FP64 ? 1 : 0);
     if (t > step) step = t;
     const size_t oStep = lay.add(step);
     size_t tp = gemm_f64_partials_bytes(n, k, k, c->num_sms);
@@ -890,7 +894,7 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
     // G^{dagger T} = G (G^T G)^{-1} = Q1 R^{-T} with one CholeskyQR round,
     // G = Q1 R and R^T R = G^T G (in place: G becomes Q1)
     PLU_CUDA(c, launch_cholqr2(n, k, G, n, R, k, stepp, step, c->d_status, c->num_sms, c->stream,
-                               0, 1));
+                               0, 1, prec != PLU_FP64 ? 1 : 0));
     PLU_CUDA(c, launch_trinv_upper(k, R, Rinv, c->stream));
     // M = G^{dagger T} U1^T = Q1 S with S = R^{-T} U1^T (k x k, lower
     // triangular); the two m x k x k products take FP32 FMAs when the passes
@@ -971,7 +975,7 @@ plu_status plu_randlu(plu_ctx* c, const plu_matrix* A, int k, int l, int piter, 
     if (t > step) step = t;
     t = panel_scratch_bytes(m > n ? m : n, l);
     if (t > step) step = t;
-    t = qr_scratch_bytes(m, k, sms);
+    t = qr_scratch_bytes(m, k, sms, prec != PLU_FP64 ? 1 : 0);
     if (t > step) step = t;
     const size_t oStep = lay.add(step);
     size_t tp = gemm_f64_partials_bytes(n, k, k, sms);
@@ -1035,7 +1039,8 @@ plu_status plu_randlu(plu_ctx* c, const plu_matrix* A, int k, int l, int piter, 
     // B^T = A^T Q R^{-T}.  The pass reads the FP32 A through TF32 in the
     // mixed modes (B enters the result to first order).
     PLU_CUDA(c, launch_scatter_rows(m, k, p, L1, m, W, m, c->stream));
-    PLU_CUDA(c, launch_cholqr2(m, k, W, m, R, k, stepp, step, c->d_status, sms, c->stream));
+    PLU_CUDA(c, launch_cholqr2(m, k, W, m, R, k, stepp, step, c->d_status, sms, c->stream, 0, 2,
+                               prec != PLU_FP64 ? 1 : 0));
     PLU_TRY(pass(1, W, m, k, is_tc(prec) ? int(PLU_TF32) : int(prec), T, n));
     PLU_CUDA(c, launch_trinv_upper(k, R, Rinv, c->stream));
     PLU_CUDA(c, launch_gemm_f64(0, 1, n, k, k, T, n, Rinv, k, BT, n, tpp, tp, sms, c->stream));

@@ -184,7 +184,7 @@ cudaError_t launch_tc_pass_q(int trans, const QuantA& q, const double* X, int64_
 // slice products; plu_ozaki.cu).  X is rows x cols (ldx), R^{-1} cols x cols
 // (ld cols); W (cols x cols, ld cols) receives the whole Gram matrix.
 // oz_supported() tells whether the shape keeps every FP32 partial sum exact
-// (cols <= 511 and a bounded stream-K segment); the launchers return an error
+// (cols <= 512 and a bounded stream-K segment); the launchers return an error
 // otherwise.  scratch holds oz_scratch_bytes().
 bool oz_supported(int64_t rows, int cols, int num_sms);
 size_t oz_scratch_bytes(int64_t rows, int cols, int num_sms);
@@ -217,9 +217,10 @@ size_t qr_scratch_bytes(int64_t rows, int cols, int num_sms, int tc_products = 0
 // decision is taken on the device; the second round's kernels return at once
 // otherwise); R cannot be requested then.  rounds = 1 runs one CholeskyQR
 // round (X <- X R1^{-1}, R = R1, with R1^T R1 = X^T X).  tc_products != 0
-// computes the first round's X^T X and X R^{-1} as exact slice products on
-// the BF16 tensor cores (launch_oz_gram / launch_oz_xrinv) when the shape
-// allows it and the scratch holds qr_scratch_bytes(..., 1).
+// computes X^T X and X R^{-1} as exact slice products on the BF16 tensor
+// cores (launch_oz_gram / launch_oz_xrinv; in every round, except the
+// device-skippable second round of the adaptive form) when the shape allows
+// it and the scratch holds qr_scratch_bytes(..., 1).
 cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, double* R,
                            int64_t ldR, void* scratch, size_t scratch_cap, int* dev_status,
                            int num_sms, cudaStream_t s, int adaptive = 0, int rounds = 2,

@@ -11,8 +11,8 @@
 // FP32 accumulation: every term is a multiple of the same power of two (the
 // row and column exponents and 7 (i + j) fix it), each term is at most
 // 64 * 64 = 2^12 of those units, and every FP32 partial sum the tensor-core
-// pass forms covers fewer than 4096 terms (asserted on the host), so it stays
-// below 2^24 units.  The pass sums its partial tiles in FP64, which is also
+// pass forms covers at most 4096 terms (asserted on the host), so it stays
+// within 2^24 units.  The pass sums its partial tiles in FP64, which is also
 // exact here.  Pairs with the same i + j = t share their units, so they are
 // stacked along the reduction index and computed by one pass per t; the
 // passes for t = 2 .. OZ_S + 1 are added in FP64.  The pairs dropped (i + j >
@@ -257,11 +257,14 @@ int grid_rows(int64_t rows, int cols, int num_sms) {
 }  // namespace
 
 bool oz_supported(int64_t rows, int cols, int num_sms) {
-    if (cols < 1 || cols > 511 || rows < cols) return false;
-    // every FP32 partial sum below 4096 terms (each term <= 2^12 units)
-    if (int64_t(OZ_S) * cols >= 4096) return false;
+    if (cols < 1 || cols > 512 || rows < cols) return false;
+    // every FP32 partial sum covers at most 4096 terms of at most 2^12 units,
+    // so every partial sum is an integer number of units below 2^24 + 1
+    if (int64_t(OZ_S) * cols > 4096) return false;
     const OzLayout L = oz_layout(rows, cols, num_sms);
-    return oz_seg_terms(cols, int64_t(OZ_S) * L.nr, num_sms) < 4096;
+    for (int t = 2; t <= OZ_S + 1; ++t)
+        if (oz_seg_terms(cols, int64_t(t - 1) * L.nr, num_sms) > 4096) return false;
+    return true;
 }
 
 size_t oz_scratch_bytes(int64_t rows, int cols, int num_sms) {

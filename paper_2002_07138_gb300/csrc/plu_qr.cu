@@ -355,15 +355,15 @@ cudaError_t launch_cholqr2(int64_t rows, int cols, double* X, int64_t ldx, doubl
     void* part = ws.take(part_cap);
     if (!W || !Wsave || !Rinv || !R1 || !Rtmp || !part || !ctl || !skip2)
         return cudaErrorInvalidValue;
-    // the first round's products as exact slice products on the tensor cores
-    // (a skipped second round cannot run there: its kernels must return on a
+    // the products as exact slice products on the tensor cores, except in
+    // the second round of the adaptive form (its kernels must return on a
     // device-side flag, which the FP64 kernels do)
     const bool oz = tc_products && oz_supported(rows, cols, num_sms) &&
                     part_cap >= oz_scratch_bytes(rows, cols, num_sms);
     cudaError_t e;
     for (int pass = 0; pass < rounds; ++pass) {
         const int* sk = (pass == 1 && adaptive) ? skip2 : nullptr;
-        const bool tc = oz && pass == 0;
+        const bool tc = oz && (pass == 0 || !adaptive);
         // W = X^T X, upper triangle only (the Cholesky reads nothing else;
         // the tensor-core form writes both triangles)
         t_cholqr_step = tc ? "Gram (tensor cores)" : "Gram";

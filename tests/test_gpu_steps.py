@@ -360,7 +360,7 @@ def _cholqr1(ctx, X, tc):
     return Q.cpu().numpy(), R.cpu().numpy()
 
 
-@pytest.mark.parametrize("rows,cols", [(4096, 200), (3000, 256), (1000, 37)])
+@pytest.mark.parametrize("rows,cols", [(4096, 200), (3000, 256), (1000, 37), (6000, 512)])
 def test_cholqr1_tensor_core_products_match_fp64(ctx, rows, cols):
     """One CholeskyQR round with X^T X and X R^-1 as exact slice products on
     the BF16 tensor cores: the same R and Q as the FP64 round to ~1e-14
