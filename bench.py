@@ -418,16 +418,25 @@ def kernel_rooflines(torch, plu, ctx, Ad, w, prec, stream, peaks):
     ms = max(ms - ms_copy, 1e-6)
     out["panel_lu"] = (ms, max(v - 2, 0) + 2, dict(fp64, achieved=lu_flops(m, l) / ms / 1e9),
                        panel_kernel_name(m, l, torch.cuda.get_device_properties(0).multi_processor_count))
-    # CholeskyQR2 of the n x k leading basis columns (all the fixed-rank call needs)
+    # the orthonormalisation of the n x k leading basis columns as the call runs
+    # it: FP64 CholeskyQR2 in the FP64 path; in the mixed modes one round whose
+    # X^T X and X R^-1 are exact slice products on the BF16 tensor cores (the
+    # second round is skipped on the device for this spectrum)
     Xk = X[:, :k].clone()
     Xc = Xk.clone()
-    ms = time_calls(torch, lambda: (Xc.copy_(Xk), plu.plu_qr(ctx, Xc)), 3, stream)
+    if prec == "fp64":
+        qr_call, rounds = (lambda: plu.plu_qr(ctx, Xc)), 2
+        qname = "cholqr2 (k_gemm_simt FP64 + Cholesky)"
+    else:
+        qr_call, rounds = (lambda: plu.plu_cholqr1(ctx, Xc, tc=True)), 1
+        qname = "cholqr1 (BF16 tensor-core slice products + FP64 Cholesky)"
+    ms = time_calls(torch, lambda: (Xc.copy_(Xk), qr_call()), 3, stream)
     ms_copy = time_calls(torch, lambda: Xc.copy_(Xk), 3, stream)
     ms = max(ms - ms_copy, 1e-6)
     # per round: the symmetric Gram n k^2, the triangular product X R^-1 n k^2,
-    # the Cholesky k^3/3 and the triangular inverse k^3/3
-    fl = 2 * (2.0 * n * k * k + 2.0 * k ** 3 / 3.0)
-    out["qr"] = (ms, 1, dict(fp64, achieved=fl / ms / 1e9), "cholqr2 (k_gemm_simt FP64 + Cholesky)")
+    # the Cholesky k^3/3 and the triangular inverse k^3/3 (FP64-equivalent flops)
+    fl = rounds * (2.0 * n * k * k + 2.0 * k ** 3 / 3.0)
+    out["qr"] = (ms, 1, dict(fp64, achieved=fl / ms / 1e9), qname)
     return out
 
 
