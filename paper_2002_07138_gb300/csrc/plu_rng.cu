@@ -6,16 +6,16 @@
 // multiplications by 0xD2511F53 / 0xCD9E8D57 with a Weyl key schedule
 // 0x9E3779B9 / 0xBB67AE85) and the Box-Muller transform.  Entry t = i + j*rows
 // is output t mod 2 of pair t/2, counter (t/2 lo, t/2 hi, stream_id, 0),
-// key (seed lo, seed hi):
-//   u = ((w0 >> 5) 2^26 + (w1 >> 6) + 1) 2^-53 in (0, 1]
-//   r = sqrt(-2 ln u), theta = 2 pi w2 / 2^32, entry = r cos / r sin.
+// key (seed lo, seed hi), in IEEE single precision:
+//   u = ((w0 >> 8) + 1) 2^-24 in (0, 1]
+//   r = sqrt(-2 ln u), theta = 2 pi (w2 >> 8) / 2^24, entry = r cos / r sin.
 // ln and sin/cos are evaluated from their series (atanh form of ln on
 // [sqrt(1/2), sqrt(2)); Taylor sin/cos on |phi| <= pi/4 after taking the
-// quarter turn from the top bits of w2; the series terms multiply by the
-// correctly rounded reciprocals of their denominators) with explicitly
-// rounded IEEE operations (no contraction into FMA), so every value is a
-// fixed sequence of correctly rounded +, -, *, /, sqrt and is reproducible
-// bit for bit.
+// quarter turn from the top bits of the angle; the series terms multiply by
+// the float32 reciprocals of their denominators) with explicitly rounded
+// IEEE float32 operations (no contraction into FMA), so every value is a
+// fixed sequence of correctly rounded +, -, *, /, sqrt, reproducible bit for
+// bit, and exact in the FP64 output.
 #include "plu_internal.h"
 
 #include "plu_rng.cuh"
@@ -23,20 +23,18 @@
 namespace plu {
 namespace {
 
-__global__ void k_gaussian(int64_t rows, int64_t total, uint64_t npairs, uint32_t k0,
-                           uint32_t k1, uint32_t stream_id, double* __restrict__ out,
-                           int64_t ld) {
-    for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < npairs;
-         q += uint64_t(gridDim.x) * blockDim.x) {
-        double ze, zo;
-        rng::gaussian_pair(q, k0, k1, stream_id, ze, zo);
-        const int64_t t0 = int64_t(2 * q);
-        const int64_t i0 = t0 % rows, j0 = t0 / rows;
-        out[i0 + j0 * ld] = ze;
-        const int64_t t1 = t0 + 1;
-        if (t1 < total) {
-            const int64_t i1 = t1 % rows, j1 = t1 / rows;
-            out[i1 + j1 * ld] = zo;
+// One thread per entry (CTA row blockIdx.y strides over the columns): the
+// entry's pair is generated and the entry's half kept, so no thread divides
+// by the column length.
+__global__ void k_gaussian(int64_t rows, int64_t cols, uint32_t k0, uint32_t k1,
+                           uint32_t stream_id, double* __restrict__ out, int64_t ld) {
+    for (int64_t j = blockIdx.y; j < cols; j += gridDim.y) {
+        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < rows;
+             i += int64_t(gridDim.x) * blockDim.x) {
+            const uint64_t t = uint64_t(j) * uint64_t(rows) + uint64_t(i);
+            double ze, zo;
+            rng::gaussian_pair(t >> 1, k0, k1, stream_id, ze, zo);
+            out[i + j * ld] = (t & 1) ? zo : ze;
         }
     }
 }
@@ -45,15 +43,16 @@ __global__ void k_gaussian(int64_t rows, int64_t total, uint64_t npairs, uint32_
 
 cudaError_t launch_gaussian(int64_t rows, int64_t cols, uint64_t seed, uint32_t stream_id,
                             double* out, int64_t ld, cudaStream_t s) {
-    const int64_t total = rows * cols;
-    if (total <= 0) return cudaSuccess;
-    const uint64_t npairs = uint64_t(total + 1) / 2;
-    const int threads = 256;
-    uint64_t blocks = (npairs + threads - 1) / threads;
-    if (blocks > 152ull * 32) blocks = 152ull * 32;
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    // about 32 CTAs of 256 threads per SM over (row chunks) x (columns)
+    int64_t gy = cols < 65535 ? cols : 65535;
+    int64_t gx = (rows + 255) / 256;
+    const int64_t want = int64_t(152) * 32;
+    if (gx * gy > want) gx = (want + gy - 1) / gy;
+    if (gx < 1) gx = 1;
     count_launch();
-    k_gaussian<<<unsigned(blocks), threads, 0, s>>>(rows, total, npairs, uint32_t(seed),
-                                                   uint32_t(seed >> 32), stream_id, out, ld);
+    k_gaussian<<<dim3(unsigned(gx), unsigned(gy)), 256, 0, s>>>(
+        rows, cols, uint32_t(seed), uint32_t(seed >> 32), stream_id, out, ld);
     return cudaGetLastError();
 }
 

@@ -27,57 +27,56 @@ __device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32
     }
 }
 
-// ln(u) for u in (0, 1]: u = f 2^e, f in [sqrt(1/2), sqrt(2)),
-// ln u = e ln2 + 2 s sum_{k=0}^{12} s^{2k}/(2k+1), s = (f-1)/(f+1).
-__device__ __forceinline__ double ln_unit(double u) {
-    const long long bits = __double_as_longlong(u);
-    int e = int((bits >> 52) & 0x7FF) - 1022;                   // u normal here
-    double f = __longlong_as_double((bits & 0x800FFFFFFFFFFFFFLL) | (1022LL << 52));
-    const double sqrt_half = 0.70710678118654752440;            // nearest double
-    if (f < sqrt_half) {
-        f = __dmul_rn(f, 2.0);
+// ln(u) for float32 u in (0, 1]: u = f 2^e, f in [sqrt(1/2), sqrt(2)),
+// ln u = e ln2 + 2 s sum_{k=0}^{6} s^{2k}/(2k+1), s = (f-1)/(f+1); every step
+// a correctly rounded float32 operation.
+__device__ __forceinline__ float ln_unit(float u) {
+    const int bits = __float_as_int(u);
+    int e = ((bits >> 23) & 0xFF) - 126;                         // u normal here
+    float f = __int_as_float((bits & 0x807FFFFF) | (126 << 23));  // f in [0.5, 1)
+    if (f < __int_as_float(0x3F3504F3)) {                         // float32 sqrt(1/2)
+        f = __fmul_rn(f, 2.0f);
         e -= 1;
     }
-    const double s = __ddiv_rn(__dsub_rn(f, 1.0), __dadd_rn(f, 1.0));
-    const double w = __dmul_rn(s, s);
-    // 1/(2k+1), k = 0..12, as correctly rounded constants (the same values the
-    // division would give)
-    constexpr double inv_odd[13] = {1.0 / 1.0,  1.0 / 3.0,  1.0 / 5.0,  1.0 / 7.0,  1.0 / 9.0,
-                                    1.0 / 11.0, 1.0 / 13.0, 1.0 / 15.0, 1.0 / 17.0, 1.0 / 19.0,
-                                    1.0 / 21.0, 1.0 / 23.0, 1.0 / 25.0};
-    double t = inv_odd[12];
+    const float s = __fdiv_rn(__fsub_rn(f, 1.0f), __fadd_rn(f, 1.0f));
+    const float w = __fmul_rn(s, s);
+    // 1/(2k+1), k = 0..6, as float32 divisions
+    constexpr float inv_odd[7] = {1.0f / 1.0f, 1.0f / 3.0f,  1.0f / 5.0f, 1.0f / 7.0f,
+                                  1.0f / 9.0f, 1.0f / 11.0f, 1.0f / 13.0f};
+    float t = inv_odd[6];
 #pragma unroll
-    for (int k = 11; k >= 0; --k) t = __dadd_rn(__dmul_rn(t, w), inv_odd[k]);
-    const double ln2 = 0.69314718055994530942;
-    return __dadd_rn(__dmul_rn(double(e), ln2), __dmul_rn(__dmul_rn(2.0, s), t));
+    for (int k = 5; k >= 0; --k) t = __fadd_rn(__fmul_rn(t, w), inv_odd[k]);
+    const float ln2 = __int_as_float(0x3F317218);                 // float32 ln 2
+    return __fadd_rn(__fmul_rn(__int2float_rn(e), ln2), __fmul_rn(__fmul_rn(2.0f, s), t));
 }
 
-// (sin, cos) of 2 pi x / 2^32.
-__device__ __forceinline__ void sincos_turn(uint32_t x, double& so, double& co) {
-    int quad = int(x >> 30);
-    const int rem = int(x & 0x3FFFFFFFu);
+// (sin, cos) of 2 pi (x >> 8) / 2^24 in float32.
+__device__ __forceinline__ void sincos_turn(uint32_t x, float& so, float& co) {
+    const int a = int(x >> 8);
+    int quad = a >> 22;
+    const int rem = a & 0x3FFFFF;
     int d = rem;
-    if (rem >= (1 << 29)) {
-        d = rem - (1 << 30);
+    if (rem >= (1 << 21)) {
+        d = rem - (1 << 22);
         quad = (quad + 1) & 3;
     }
-    const double pi_over_2_31 = 3.141592653589793116 * (1.0 / 2147483648.0);
-    const double phi = __dmul_rn(double(d), pi_over_2_31);
-    const double x2 = __dmul_rn(phi, phi);
+    // |d| <= 2^21 converts exactly; float32 pi times 2^-23
+    const float phi = __fmul_rn(__int2float_rn(d), __int_as_float(0x34C90FDB));
+    const float x2 = __fmul_rn(phi, phi);
     // nested Taylor series; 1/d of the denominators d = (2i)(2i+1), (2i-1)(2i)
-    // as correctly rounded constants (compile-time IEEE divisions)
-    constexpr double sinv[9] = {1.0 / 342.0, 1.0 / 272.0, 1.0 / 210.0, 1.0 / 156.0, 1.0 / 110.0,
-                                1.0 / 72.0,  1.0 / 42.0,  1.0 / 20.0,  1.0 / 6.0};
-    constexpr double cinv[10] = {1.0 / 380.0, 1.0 / 306.0, 1.0 / 240.0, 1.0 / 182.0, 1.0 / 132.0,
-                                 1.0 / 90.0,  1.0 / 56.0,  1.0 / 30.0,  1.0 / 12.0,  1.0 / 2.0};
-    double ts = 1.0;
+    // as float32 divisions
+    constexpr float sinv[5] = {1.0f / 110.0f, 1.0f / 72.0f, 1.0f / 42.0f, 1.0f / 20.0f,
+                               1.0f / 6.0f};
+    constexpr float cinv[6] = {1.0f / 132.0f, 1.0f / 90.0f, 1.0f / 56.0f, 1.0f / 30.0f,
+                               1.0f / 12.0f,  1.0f / 2.0f};
+    float ts = 1.0f;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) ts = __dsub_rn(1.0, __dmul_rn(__dmul_rn(x2, sinv[i]), ts));
-    const double s = __dmul_rn(phi, ts);
-    double tc = 1.0;
+    for (int i = 0; i < 5; ++i) ts = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(x2, sinv[i]), ts));
+    const float s = __fmul_rn(phi, ts);
+    float tc = 1.0f;
 #pragma unroll
-    for (int i = 0; i < 10; ++i) tc = __dsub_rn(1.0, __dmul_rn(__dmul_rn(x2, cinv[i]), tc));
-    const double c = tc;
+    for (int i = 0; i < 6; ++i) tc = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(x2, cinv[i]), tc));
+    const float c = tc;
     switch (quad) {
         case 0: so = s; co = c; break;
         case 1: so = c; co = -s; break;
@@ -86,18 +85,19 @@ __device__ __forceinline__ void sincos_turn(uint32_t x, double& so, double& co) 
     }
 }
 
-// Both Box-Muller outputs of pair q of stream (seed, stream_id).
+// Both Box-Muller outputs of pair q of stream (seed, stream_id), in float32,
+// returned exactly as doubles.
 __device__ __forceinline__ void gaussian_pair(uint64_t q, uint32_t k0, uint32_t k1,
                                               uint32_t stream_id, double& z_even, double& z_odd) {
     uint32_t c0 = uint32_t(q), c1 = uint32_t(q >> 32), c2 = stream_id, c3 = 0;
     philox4x32_10(c0, c1, c2, c3, k0, k1);
-    const uint64_t kint = (uint64_t(c0 >> 5) << 26) + uint64_t(c1 >> 6) + 1ull;
-    const double u = __dmul_rn(double(kint), 1.0 / 9007199254740992.0);   // 2^-53
-    const double r = __dsqrt_rn(__dmul_rn(-2.0, ln_unit(u)));
-    double sn, cs;
+    // u = ((w0 >> 8) + 1) 2^-24 in (0, 1], exact
+    const float u = __fmul_rn(__uint2float_rn((c0 >> 8) + 1u), __int_as_float(0x33800000));
+    const float r = __fsqrt_rn(__fmul_rn(-2.0f, ln_unit(u)));
+    float sn, cs;
     sincos_turn(c2, sn, cs);
-    z_even = __dmul_rn(r, cs);
-    z_odd = __dmul_rn(r, sn);
+    z_even = double(__fmul_rn(r, cs));
+    z_odd = double(__fmul_rn(r, sn));
 }
 
 }  // namespace rng
