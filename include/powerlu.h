@@ -112,8 +112,10 @@ plu_status plu_set_wait_budget(plu_ctx* ctx, int64_t spins);
 /* a1. Gaussian test matrix Omega (Alg. bpowerlu step 1; Alg. gpowerlu):
  * out (rows x cols, ld) receives i.i.d. N(0,1) values, entry (i, j) being the
  * Box-Muller output number t = i + j*rows of the Philox4x32-10 stream
- * (key = seed, counter = (t/2, stream_id)).  The same (seed, stream_id,
- * rows, cols) gives bit-identical values on every call. */
+ * (key = seed, counter = (t/2, stream_id)), computed in correctly rounded
+ * float32 steps (the values are float32 numbers, exact in the FP64 output).
+ * The same (seed, stream_id, rows, cols) gives bit-identical values on every
+ * call. */
 plu_status plu_gaussian(plu_ctx* ctx, int64_t rows, int64_t cols, uint64_t seed,
                         uint32_t stream_id, double* out, int64_t ld);
 
