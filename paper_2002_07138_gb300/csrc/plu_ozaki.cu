@@ -34,8 +34,10 @@ constexpr int OZ_S = 8;          // slices per operand
 constexpr int OZ_BITS = 7;       // bits per slice (|n_i| <= 64)
 
 // E with max|x| < 2^(E-1), so the first slice's integer is at most 64; INT_MIN
-// for an all-zero line.
+// for an all-zero line, INT_MAX for a line holding an inf or a NaN (its slices
+// are NaN, so the products report it).
 __device__ __forceinline__ int oz_exponent(double maxabs) {
+    if (!(maxabs <= 1.7976931348623157e308)) return INT_MAX;
     if (!(maxabs > 0.0)) return INT_MIN;
     int e;
     frexp(maxabs, &e);               // maxabs < 2^e
@@ -74,9 +76,10 @@ __device__ __forceinline__ void oz_digits(double x, int E, int dig[OZ_S]) {
 
 // The slices of x with exponent E: out[i] = n_i 2^(E - 7 (i + 1)).
 __device__ __forceinline__ void oz_split(double x, int E, double out[OZ_S]) {
-    if (E == INT_MIN) {
+    if (E == INT_MIN || E == INT_MAX) {
+        const double v = E == INT_MAX ? __longlong_as_double(0x7FF8000000000000LL) : 0.0;
 #pragma unroll
-        for (int i = 0; i < OZ_S; ++i) out[i] = 0.0;
+        for (int i = 0; i < OZ_S; ++i) out[i] = v;
         return;
     }
     double y = ldexp(x, OZ_BITS - E);                 // |y| < 64, exact scaling
@@ -88,20 +91,26 @@ __device__ __forceinline__ void oz_split(double x, int E, double out[OZ_S]) {
     }
 }
 
+// |x| as the 64-bit pattern of its absolute value: for finite values these
+// order like the values, so maxima run on the integer pipe.
+__device__ __forceinline__ long long abs_bits(double x) {
+    return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL;
+}
+
 // Per-column exponents of X (rows x cols): one CTA per column.
 __global__ void k_oz_colexp(int64_t rows, const double* __restrict__ X, int64_t ldx,
                             int* __restrict__ Ecol) {
-    __shared__ double red[256];
+    __shared__ long long red[256];
     const int a = blockIdx.x;
-    double mx = 0.0;
-    for (int64_t r = threadIdx.x; r < rows; r += 256) mx = fmax(mx, fabs(X[r + a * ldx]));
+    long long mx = 0;
+    for (int64_t r = threadIdx.x; r < rows; r += 256) mx = max(mx, abs_bits(X[r + a * ldx]));
     red[threadIdx.x] = mx;
     __syncthreads();
     for (int s2 = 128; s2 > 0; s2 >>= 1) {
-        if (threadIdx.x < s2) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s2]);
+        if (threadIdx.x < s2) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + s2]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) Ecol[a] = oz_exponent(red[0]);
+    if (threadIdx.x == 0) Ecol[a] = oz_exponent(__longlong_as_double(red[0]));
 }
 
 // Per-row exponents of X (rows x cols): one thread per row.
@@ -109,9 +118,9 @@ __global__ void k_oz_rowexp(int64_t rows, int cols, const double* __restrict__ X
                             int* __restrict__ Erow) {
     for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < rows;
          r += int64_t(gridDim.x) * blockDim.x) {
-        double mx = 0.0;
-        for (int a = 0; a < cols; ++a) mx = fmax(mx, fabs(X[r + a * ldx]));
-        Erow[r] = oz_exponent(mx);
+        long long mx = 0;
+        for (int a = 0; a < cols; ++a) mx = max(mx, abs_bits(X[r + a * ldx]));
+        Erow[r] = oz_exponent(__longlong_as_double(mx));
     }
 }
 
@@ -132,15 +141,17 @@ __global__ void k_oz_slice_gram(int64_t rows, int64_t nr, const double* __restri
     for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < nr;
          r += int64_t(gridDim.x) * blockDim.x) {
         int dig[OZ_S];
-        oz_digits(r < rows ? X[r + a * ldx] : 0.0, r < rows ? E : INT_MIN, dig);
-        const int Es = E == INT_MIN ? 0 : E;      // all digits are 0 then
+        oz_digits(r < rows ? X[r + a * ldx] : 0.0, (r < rows && E != INT_MAX) ? E : INT_MIN,
+                  dig);
+        const int Es = (E == INT_MIN || E == INT_MAX) ? 0 : E;   // digits 0 then
+        const bool bad = E == INT_MAX && r < rows;                // inf / NaN column
         const int64_t s = r / 64;
         const int kk = int(r % 64);
         const int64_t in_step = int64_t(a) * 128 + (((kk / 8) ^ (a & 7)) << 4) + (kk % 8) * 2;
 #pragma unroll
         for (int i = 0; i < OZ_S; ++i) {
-            const __nv_bfloat16 v =
-                __float2bfloat16_rn(ldexpf(float(dig[i]), Es - OZ_BITS * (i + 1)));
+            const __nv_bfloat16 v = __float2bfloat16_rn(
+                bad ? __int_as_float(0x7FC00000) : ldexpf(float(dig[i]), Es - OZ_BITS * (i + 1)));
             Sv[int64_t(i) * nr + r + a * ldv] = v;
             const int64_t step = int64_t(OZ_S - 1 - i) * steps + s;
             *reinterpret_cast<__nv_bfloat16*>(img + step * int64_t(npad) * 128 + in_step) = v;
@@ -158,12 +169,13 @@ __global__ void k_oz_slice_rows(int64_t rows, int cols, const double* __restrict
          r += int64_t(gridDim.x) * blockDim.x) {
         int dig[OZ_S];
         const int E = Erow[r];
-        oz_digits(X[r + a * ldx], E, dig);
-        const int Es = E == INT_MIN ? 0 : E;      // all digits are 0 then
+        oz_digits(X[r + a * ldx], E == INT_MAX ? INT_MIN : E, dig);
+        const int Es = (E == INT_MIN || E == INT_MAX) ? 0 : E;   // digits 0 then
 #pragma unroll
         for (int i = 0; i < OZ_S; ++i)
-            Sh[r + (int64_t(i) * cols + a) * lds] =
-                __float2bfloat16_rn(ldexpf(float(dig[i]), Es - OZ_BITS * (i + 1)));
+            Sh[r + (int64_t(i) * cols + a) * lds] = __float2bfloat16_rn(
+                E == INT_MAX ? __int_as_float(0x7FC00000)
+                             : ldexpf(float(dig[i]), Es - OZ_BITS * (i + 1)));
     }
 }
 
@@ -173,18 +185,18 @@ __global__ void k_oz_slice_rows(int64_t rows, int cols, const double* __restrict
 // One CTA per column.
 __global__ void k_oz_slice_rinv(int n, const double* __restrict__ Rinv,
                                 double* __restrict__ Trev) {
-    __shared__ double red[256];
+    __shared__ long long red[256];
     __shared__ int Es;
     const int c = blockIdx.x;
-    double mx = 0.0;
-    for (int r = threadIdx.x; r < n; r += 256) mx = fmax(mx, fabs(Rinv[r + int64_t(c) * n]));
+    long long mx = 0;
+    for (int r = threadIdx.x; r < n; r += 256) mx = max(mx, abs_bits(Rinv[r + int64_t(c) * n]));
     red[threadIdx.x] = mx;
     __syncthreads();
     for (int s2 = 128; s2 > 0; s2 >>= 1) {
-        if (threadIdx.x < s2) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s2]);
+        if (threadIdx.x < s2) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + s2]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) Es = oz_exponent(red[0]);
+    if (threadIdx.x == 0) Es = oz_exponent(__longlong_as_double(red[0]));
     __syncthreads();
     const int64_t ldt = int64_t(OZ_S) * n;
     for (int r = threadIdx.x; r < n; r += 256) {

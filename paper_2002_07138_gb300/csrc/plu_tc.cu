@@ -543,15 +543,27 @@ __global__ void __launch_bounds__(BM) k_tc_reduce(const float* __restrict__ part
     const int64_t blk = blockIdx.x;
     const int r = threadIdx.x;
     const int64_t i = blk * BM + r;
+    // the contributing CTAs of this row block, found once per CTA (64-bit
+    // divisions are long instruction sequences)
+    __shared__ int64_t sh[6];
+    if (r == 0) {
+        const int64_t first = blk * ksteps, last = min(total, first + ksteps) - 1;
+        const int64_t lo = first / per;
+        int64_t hi = last / per;
+        if (hi >= grid) hi = grid - 1;
+        sh[0] = lo;
+        sh[1] = hi;
+        sh[2] = per / ksteps;
+        sh[3] = per % ksteps;
+        sh[4] = (lo * per) / ksteps;
+        sh[5] = (lo * per) % ksteps;
+    }
+    __syncthreads();
     if (i >= M) return;
     const int j0 = blockIdx.y * RJT;
     const int nj = min(RJT, l - j0);
-    const int64_t first = blk * ksteps, last = min(total, first + ksteps) - 1;
-    const int64_t c_lo = first / per;
-    int64_t c_hi = last / per;
-    if (c_hi >= grid) c_hi = grid - 1;
-    const int64_t pq = per / ksteps, pr = per % ksteps;
-    int64_t cb = (c_lo * per) / ksteps, rem = (c_lo * per) % ksteps;
+    const int64_t c_lo = sh[0], c_hi = sh[1], pq = sh[2], pr = sh[3];
+    int64_t cb = sh[4], rem = sh[5];
     double acc[RJT];
 #pragma unroll
     for (int q = 0; q < RJT; ++q) acc[q] = 0.0;

@@ -399,3 +399,13 @@ def test_cholqr1_tensor_core_rejects_wide_x(ctx):
     X.normal_()
     with pytest.raises(plu.PLUError):
         plu.plu_cholqr1(ctx, X, tc=True)
+
+
+@pytest.mark.parametrize("tc", [True, False])
+def test_cholqr1_reports_non_finite_input(ctx, tc):
+    """A NaN in X reaches the Cholesky through either form of the products
+    (the tensor-core slices of a non-finite line are NaN) and is reported."""
+    X = np.random.default_rng(9).standard_normal((2000, 64))
+    X[123, 7] = np.nan
+    with pytest.raises(plu.PLUError):
+        _cholqr1(ctx, X, tc)
