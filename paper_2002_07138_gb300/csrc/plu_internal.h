@@ -174,11 +174,25 @@ struct QuantA {
 size_t tc_quant_bytes(int64_t m, int64_t n, int prec);
 cudaError_t launch_tc_quantize(int prec, const float* A, int64_t m, int64_t n, int64_t lda,
                                void* qbuf, QuantA* out, int num_sms, cudaStream_t s);
+// The stream-K partial tiles of one pass, left in its scratch for a later
+// reduction: CTA c's segment for row block b at part + ((c max_segs + b -
+// c per / ksteps) npad) 128.
+constexpr int kMaxBands = 16;
+struct TcPartials {
+    const float* part = nullptr;
+    int npad = 0, ksteps = 0, max_segs = 0, grid = 0;
+    int64_t total = 0, per = 0;
+};
 // xq_pre (BF16 only): X already in BF16 operand form, as for launch_tc_pass.
+// keep (BF16 only, non-null): the pass leaves its partial tiles in scratch,
+// described by *keep, and does not write Y.
 cudaError_t launch_tc_pass_q(int trans, const QuantA& q, const double* X, int64_t ldx, int cols,
                              double* Y, int64_t ldy, void* scratch, size_t scratch_cap,
                              int* dev_status, int num_sms, cudaStream_t s, int accum = 0,
-                             const void* xq_pre = nullptr);
+                             const void* xq_pre = nullptr, TcPartials* keep = nullptr);
+// Y (M x cols, ldy) = the bands' FP64 reductions added in order (one write).
+cudaError_t launch_tc_reduce_bands(const TcPartials* bands, int nbands, int64_t M, int cols,
+                                   double* Y, int64_t ldy, cudaStream_t s);
 
 // FP64-accurate X^T X and X R^{-1} on the BF16 tensor cores (sums of exact
 // slice products; plu_ozaki.cu).  X is rows x cols (ldx), R^{-1} cols x cols

@@ -119,6 +119,7 @@ __global__ void k_oz_rowexp(int64_t rows, int cols, const double* __restrict__ X
     for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < rows;
          r += int64_t(gridDim.x) * blockDim.x) {
         long long mx = 0;
+#pragma unroll 16
         for (int a = 0; a < cols; ++a) mx = max(mx, abs_bits(X[r + a * ldx]));
         Erow[r] = oz_exponent(__longlong_as_double(mx));
     }
@@ -211,6 +212,7 @@ struct OzLayout {
     int64_t nr, ldv, lds;
     int npad;
     size_t e_off, a_off, b_off, pass_off, total;
+    size_t xr_band;            // X R^{-1}: one pass scratch per band (kept partials)
 };
 
 // Both phases share one region: the Gram's Sv + img, then (after the
@@ -236,14 +238,16 @@ OzLayout oz_layout(int64_t rows, int cols, int num_sms) {
     L.pass_off = off;
     // the pass scratch of every band t (it is not monotone in the reduction
     // length: the stream-K grid changes with it)
-    size_t pmax = 0;
+    size_t pg = 0, px = 0;
     for (int t = 2; t <= OZ_S + 1; ++t) {
         const size_t p1 = tc_scratch_bytes(cols, int64_t(t - 1) * L.nr, cols, num_sms);
         const size_t p2 = tc_scratch_bytes(rows, int64_t(t - 1) * cols, cols, num_sms);
-        if (p1 > pmax) pmax = p1;
-        if (p2 > pmax) pmax = p2;
+        if (p1 > pg) pg = p1;
+        if (p2 > px) px = p2;
     }
-    off = up(off + pmax);
+    L.xr_band = up(px);
+    const size_t xr_all = L.xr_band * OZ_S;
+    off = up(off + (pg > xr_all ? pg : xr_all));
     L.total = off;
     return L;
 }
@@ -343,6 +347,9 @@ cudaError_t launch_oz_xrinv(int64_t rows, int cols, const double* X, int64_t ldx
     count_launch();
     k_oz_slice_rinv<<<cols, 256, 0, s>>>(cols, Rinv, Trev);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // every band's partial tiles stay in their own scratch; one reduction then
+    // adds the bands (in order) and writes Y once
+    TcPartials bands[OZ_S];
     for (int t = 2; t <= OZ_S + 1; ++t) {
         // sum over i + j = t: [S_1 .. S_{t-1}] [T_{t-1}; ..; T_1]
         QuantA q;
@@ -352,11 +359,12 @@ cudaError_t launch_oz_xrinv(int64_t rows, int cols, const double* X, int64_t ldx
         q.n = int64_t(t - 1) * cols;
         q.prec = PLU_BF16;
         const double* Tt = Trev + size_t(OZ_S + 1 - t) * cols;
-        e = launch_tc_pass_q(0, q, Tt, int64_t(OZ_S) * cols, cols, Y, ldy, base + L.pass_off,
-                             scratch_cap - L.pass_off, dev_status, num_sms, s, t > 2 ? 1 : 0);
+        e = launch_tc_pass_q(0, q, Tt, int64_t(OZ_S) * cols, cols, Y, ldy,
+                             base + L.pass_off + size_t(t - 2) * L.xr_band, L.xr_band, dev_status,
+                             num_sms, s, 0, nullptr, &bands[t - 2]);
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return launch_tc_reduce_bands(bands, OZ_S, rows, cols, Y, ldy, s);
 }
 
 }  // namespace plu

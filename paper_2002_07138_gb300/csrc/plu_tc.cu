@@ -596,6 +596,68 @@ __global__ void __launch_bounds__(BM) k_tc_reduce(const float* __restrict__ part
     }
 }
 
+// Y(i, j) = sum over bands b of (sum over the CTAs whose share touches block
+// i/128 of band b's partial tile, in CTA order), the bands added in order, in
+// FP64: the reduction of several passes into one Y with one write.  CTA
+// (blk, g): rows blk*128 + threadIdx.x, columns 8 g .. 8 g + 7.
+struct TcBands {
+    TcPartials b[kMaxBands];
+    int n;
+};
+
+__global__ void __launch_bounds__(BM) k_tc_reduce_bands(TcBands bands, int64_t M, int l,
+                                                        double* __restrict__ Y, int64_t ldy) {
+    constexpr int RJT = 8;
+    const int64_t blk = blockIdx.x;
+    const int r = threadIdx.x;
+    const int64_t i = blk * BM + r;
+    __shared__ int64_t sh[kMaxBands][4];
+    if (r < bands.n) {
+        const TcPartials& B = bands.b[r];
+        const int64_t first = blk * B.ksteps, last = min(B.total, first + B.ksteps) - 1;
+        const int64_t lo = first / B.per;
+        int64_t hi = last / B.per;
+        if (hi >= B.grid) hi = B.grid - 1;
+        sh[r][0] = lo;
+        sh[r][1] = hi;
+        sh[r][2] = (lo * B.per) / B.ksteps;
+        sh[r][3] = (lo * B.per) % B.ksteps;
+    }
+    __syncthreads();
+    if (i >= M) return;
+    const int j0 = blockIdx.y * RJT;
+    const int nj = min(RJT, l - j0);
+    double tot[RJT];
+#pragma unroll
+    for (int q = 0; q < RJT; ++q) tot[q] = 0.0;
+    for (int bi = 0; bi < bands.n; ++bi) {
+        const TcPartials& B = bands.b[bi];
+        const int64_t pq = B.per / B.ksteps, pr = B.per % B.ksteps;
+        int64_t cb = sh[bi][2], rem = sh[bi][3];
+        double acc[RJT];
+#pragma unroll
+        for (int q = 0; q < RJT; ++q) acc[q] = 0.0;
+#pragma unroll 4
+        for (int64_t c = sh[bi][0]; c <= sh[bi][1]; ++c) {
+            const float* src = B.part + ((c * B.max_segs + (blk - cb)) * B.npad + j0) * BM + r;
+#pragma unroll
+            for (int q = 0; q < RJT; ++q)
+                if (q < nj) acc[q] += double(src[int64_t(q) * BM]);
+            cb += pq;
+            rem += pr;
+            if (rem >= B.ksteps) {
+                rem -= B.ksteps;
+                ++cb;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RJT; ++q) tot[q] = bi == 0 ? acc[q] : tot[q] + acc[q];
+    }
+#pragma unroll
+    for (int q = 0; q < RJT; ++q)
+        if (q < nj) Y[i + int64_t(j0 + q) * ldy] = tot[q];
+}
+
 // Small operand X (FP64, K x cols, ldx) -> operand type, written as the
 // shared-memory image of each K step: step t holds rows j < npad of 128 bytes
 // (K = t BKE .. t BKE + BKE - 1), 16-byte chunk c of row j stored at chunk
@@ -872,7 +934,7 @@ cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t
                          const float* s_r, const float* s_c, const double* X, int64_t ldx,
                          int cols, double* Y, int64_t ldy, void* scratch, size_t scratch_cap,
                          int* dev_status, int num_sms, cudaStream_t s, int accum,
-                         const void* xq_pre = nullptr) {
+                         const void* xq_pre = nullptr, TcPartials* keep = nullptr) {
     constexpr int E = Kind<KIND>::E;
     constexpr int BKE = 128 / E;
     const int64_t M = trans ? n : m;
@@ -952,6 +1014,16 @@ cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t
     // eight columns per CTA, or one when that leaves fewer than two CTAs per SM
     // (few row blocks, each summed over many CTAs' partials)
     const int64_t nblk = (M + BM - 1) / BM;
+    if (keep) {              // the caller reduces later (launch_tc_reduce_bands)
+        keep->part = part;
+        keep->npad = p.npad;
+        keep->ksteps = p.ksteps;
+        keep->max_segs = p.max_segs;
+        keep->grid = p.grid;
+        keep->total = p.total;
+        keep->per = p.per;
+        return cudaSuccess;
+    }
     const bool wide = nblk * ((cols + 7) / 8) >= 2 * int64_t(num_sms);
     count_launch();
     if (!wide) {
@@ -976,6 +1048,18 @@ cudaError_t launch_tc_pass(int trans, int64_t m, int64_t n, const float* A, int6
                                    scratch, scratch_cap, dev_status, num_sms, s, accum, xq_pre);
 }
 
+cudaError_t launch_tc_reduce_bands(const TcPartials* bands, int nbands, int64_t M, int cols,
+                                  double* Y, int64_t ldy, cudaStream_t s) {
+    if (nbands < 1 || nbands > kMaxBands || M < 1 || cols < 1) return cudaErrorInvalidValue;
+    TcBands tb;
+    tb.n = nbands;
+    for (int b = 0; b < nbands; ++b) tb.b[b] = bands[b];
+    count_launch();
+    k_tc_reduce_bands<<<dim3(unsigned((M + BM - 1) / BM), unsigned((cols + 7) / 8)), BM, 0, s>>>(
+        tb, M, cols, Y, ldy);
+    return cudaGetLastError();
+}
+
 size_t tc_operand_bytes(int64_t K, int cols) {
     const TcPlan p = plan_tc(BM, K, cols, 1, false, 4);
     return size_t(p.ksteps) * p.npad * 128;
@@ -998,12 +1082,12 @@ cudaError_t launch_tc_operand(int64_t K, int cols, const double* X, int64_t ldx,
 cudaError_t launch_tc_pass_q(int trans, const QuantA& q, const double* X, int64_t ldx, int cols,
                              double* Y, int64_t ldy, void* scratch, size_t scratch_cap,
                              int* dev_status, int num_sms, cudaStream_t s, int accum,
-                             const void* xq_pre) {
+                             const void* xq_pre, TcPartials* keep) {
     if (q.prec == PLU_BF16)
         return tc_pass_kind<KIND_BF16>(trans, q.m, q.n, q.data, q.ld, nullptr, nullptr, X, ldx,
                                        cols, Y, ldy, scratch, scratch_cap, dev_status, num_sms, s,
-                                       accum, xq_pre);
-    if (xq_pre) return cudaErrorInvalidValue;
+                                       accum, xq_pre, keep);
+    if (xq_pre || keep) return cudaErrorInvalidValue;
     return tc_pass_kind<KIND_FP8>(trans, q.m, q.n, q.data, q.ld, q.s_r, q.s_c, X, ldx, cols, Y,
                                   ldy, scratch, scratch_cap, dev_status, num_sms, s, accum);
 }
