@@ -25,6 +25,7 @@ Multi-GPU (torchrun): replicas only -- every rank factors its own matrix,
 no data-path collective; value sums the ranks' work over the slowest rank.
 """
 import argparse
+import collections
 import json
 import math
 import os
@@ -164,6 +165,8 @@ def run_batched(args):
                        "parallelism": "replicas" if ws > 1 else "single"},
             "wall_ms_per_step": wall_ms,
             "rel_error_sample_max": max(errs), "rel_error_sample_median": statistics.median(errs),
+            "gemm_tiles_autotuned": dict(collections.Counter(
+                "%dx%d" % t for t in plu.plu_batched_tiles(ctx))),
             "gpu_launches": launches,
             "clocks": clk,
             "cpu_baseline": cpu,

@@ -268,6 +268,19 @@ typedef struct {
 plu_status plu_batched(plu_ctx* ctx, const plu_batch_problem* problems, int count, plu_prec prec,
                        plu_report* rep);
 
+/* The tile shapes (rows bm[i] x columns bn[i] per CTA) of the grouped GEMM
+ * launches of the last plu_batched call on ctx, in launch order.  The first
+ * call for a batch signature (the problems' m, n, k, l, v, algo, dtype, ld and
+ * the precision) times every launch in each shape the library has and keeps
+ * the fastest; later calls with the same signature reuse that choice.  *count
+ * receives the number of launches; at most cap entries are written. */
+plu_status plu_batched_tiles(plu_ctx* ctx, int* bm, int* bn, int cap, int* count);
+
+/* Every grouped GEMM of later plu_batched calls on ctx takes the tile shape
+ * bm x bn (64 x 32, 64 x 64 or 128 x 32; PLU_EINVAL otherwise) instead of the
+ * autotuner's choice; bm = bn = 0 restores the autotuner. */
+plu_status plu_set_batched_tile(plu_ctx* ctx, int bm, int bn);
+
 /* ---------------------------------------------------------------------
  * Allocation-free variant (the paper has no counterpart: this is a service
  * for callers that cannot allocate device memory, such as code running

@@ -8,7 +8,9 @@ back to another implementation.
 from ._binding import (  # noqa: F401
     lib, LIB_PATH, Context, PLUError, plu_matrix, plu_report, as_plu_matrix, colmajor_empty,
     plu_gaussian, plu_pass, plu_lu_reorth, plu_getrf, plu_qr, plu_cholqr1, plu_norm2, plu_rank,
-    plu_powerlu, plu_powerlu_fp, plu_randlu, plu_singlepass, plu_batched, plu_batch_problem,
+    plu_powerlu, plu_powerlu_fp, plu_randlu, plu_singlepass, plu_batched, plu_batched_tiles,
+    plu_set_batched_tile,
+    plu_batch_problem,
     PREC, STATUS,
     SIGNATURES,
     STREAM_OMEGA_N, STREAM_OMEGA_M, STREAM_OMEGA_SP,

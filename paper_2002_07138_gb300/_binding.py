@@ -81,6 +81,9 @@ SIGNATURES = {
                                c_vp, c_i64, c_vp, c_i64, ctypes.POINTER(plu_report)]),
     "plu_lu_reorth_static": (c_int, [c_vp, c_i64, c_int, c_vp, c_i64, ctypes.c_char_p,
                                      ctypes.c_size_t]),
+    "plu_set_batched_tile": (c_int, [c_vp, c_int, c_int]),
+    "plu_batched_tiles": (c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_int,
+                                  ctypes.POINTER(c_int)]),
     "plu_batched": (c_int, [c_vp, ctypes.POINTER(plu_batch_problem), c_int, c_int,
                             ctypes.POINTER(plu_report)]),
 }
@@ -224,6 +227,22 @@ def plu_qr(ctx, X, want_r=False):
     ctx.check(lib().plu_qr(ctx.handle, X.shape[0], X.shape[1], _ptr(X), _ld(X), _ptr(R),
                            _ld(R) if R is not None else 0))
     return (X, R) if want_r else X
+
+
+def plu_set_batched_tile(ctx, bm=0, bn=0):
+    """Fix the batched GEMM tile shape (bm x bn); (0, 0) restores the autotuner."""
+    ctx.check(lib().plu_set_batched_tile(ctx.handle, bm, bn))
+
+
+def plu_batched_tiles(ctx):
+    """Tile shapes (rows, columns) the autotuner chose for the grouped GEMM
+    launches of the last plu_batched call, in launch order."""
+    n = c_int()
+    ctx.check(lib().plu_batched_tiles(ctx.handle, None, None, 0, ctypes.byref(n)))
+    bm = (c_int * max(n.value, 1))()
+    bn = (c_int * max(n.value, 1))()
+    ctx.check(lib().plu_batched_tiles(ctx.handle, bm, bn, n.value, ctypes.byref(n)))
+    return [(bm[i], bn[i]) for i in range(n.value)]
 
 
 def plu_cholqr1(ctx, X, tc=True):

@@ -7,7 +7,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
+#include <vector>
 
 using namespace plu;
 
@@ -30,6 +32,11 @@ struct plu_ctx {
     char err[512] = {0};
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaStream_t capture = nullptr;   // private stream for graph capture (batched)
+    // batched: the autotuner's tile shapes per batch signature, and those of
+    // the last call
+    std::map<uint64_t, std::vector<int>> batch_tiles;
+    std::vector<int> last_tiles;
+    int forced_tile = -1;             // a fixed tile shape instead of the autotuner
     static constexpr int64_t kDefaultSpin = 16LL << 20;
 };
 
@@ -1076,6 +1083,33 @@ plu_status plu_randlu(plu_ctx* c, const plu_matrix* A, int k, int l, int piter, 
     return finish(c);
 }
 
+plu_status plu_set_batched_tile(plu_ctx* c, int bm, int bn) {
+    if (!c) return PLU_EINVAL;
+    if (bm == 0 && bn == 0) {
+        c->forced_tile = -1;
+        return PLU_OK;
+    }
+    for (int v = 0;; ++v) {
+        int tm = 0, tn = 0;
+        if (!batch_gemm_tile(v, &tm, &tn)) break;
+        if (tm == bm && tn == bn) {
+            c->forced_tile = v;
+            return PLU_OK;
+        }
+    }
+    return fail(c, PLU_EINVAL, "no grouped-GEMM tile shape %d x %d", bm, bn);
+}
+
+plu_status plu_batched_tiles(plu_ctx* c, int* bm, int* bn, int cap, int* count) {
+    if (!c || !count || cap < 0 || (cap > 0 && (!bm || !bn))) return fail(c, PLU_EINVAL, "bad arguments");
+    const int n = int(c->last_tiles.size());
+    *count = n;
+    for (int i = 0; i < n && i < cap; ++i)
+        if (!batch_gemm_tile(c->last_tiles[i], bm + i, bn + i))
+            return fail(c, PLU_EINVAL, "bad tile index");
+    return PLU_OK;
+}
+
 plu_status plu_batched(plu_ctx* c, const plu_batch_problem* P, int count, plu_prec prec,
                        plu_report* rep) {
     PLU_TRY(bind(c));
@@ -1114,10 +1148,27 @@ plu_status plu_batched(plu_ctx* c, const plu_batch_problem* P, int count, plu_pr
     PLU_TRY(ensure_ws(c, wsb + tb));
     // the capture stream must see the work already queued on the context stream
     PLU_CUDA(c, cudaStreamSynchronize(c->stream));
+    // the batch's signature (FNV-1a over the shapes that decide the plan)
+    uint64_t sig = 1469598103934665603ULL;
+    auto mix = [&](int64_t x) {
+        for (int b = 0; b < 8; ++b) {
+            sig ^= uint64_t(x >> (8 * b)) & 0xFF;
+            sig *= 1099511628211ULL;
+        }
+    };
+    mix(count);
+    mix(prec);
+    for (int i = 0; i < count; ++i) {
+        mix(P[i].m); mix(P[i].n); mix(P[i].k); mix(P[i].l); mix(P[i].v); mix(P[i].algo);
+        mix(P[i].dtype); mix(P[i].ld);
+    }
+    std::vector<int> forced;
+    std::vector<int>& tiles = c->forced_tile >= 0 ? forced : c->batch_tiles[sig];
     int nl = 0;
     float ms = 0.f;
     PLU_CUDA(c, run_batch(P, count, prec, c->ws, c->ws + wsb, tb, c->d_status, c->num_sms, c->stream,
-                          c->capture, &nl, &ms));
+                          c->capture, &nl, &ms, &tiles, c->forced_tile));
+    c->last_tiles = tiles;
     if (rep) {
         memset(rep, 0, sizeof(*rep));
         rep->ms_total = ms;

@@ -95,14 +95,21 @@ __global__ void k_b_gaussian(const GaussJob* __restrict__ jobs) {
 }
 
 // ------------------------------------------------------ grouped GEMM
-// C = op(A) op(B) (+ C), op(A) M x K, op(B) K x N; one 64 x 32 tile per CTA.
-constexpr int GBM = 64, GBN = 32, GBK = 16, GNT = 256;
+// C = op(A) op(B) (+ C), op(A) M x K, op(B) K x N; one BMV x BNV tile per CTA
+// of 256 threads, each thread (BMV/16) x (BNV/16) outputs.  The tile shape of
+// every grouped launch is picked by timing (run_batch's autotuner) among
+// kGemmVariants shapes.
+constexpr int GBK = 16, GNT = 256;
+constexpr int kGemmVariants = 3;
+constexpr int kVarBM[kGemmVariants] = {64, 64, 128};
+constexpr int kVarBN[kGemmVariants] = {32, 64, 32};
 
-template <typename TC>
+template <typename TC, int BMV, int BNV>
 __global__ void __launch_bounds__(GNT)
 k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
-    __shared__ TC As[2][GBK][GBM + 1];
-    __shared__ TC Bs[2][GBK][GBN + 1];
+    constexpr int TM = BMV / 16, TN = BNV / 16;
+    __shared__ TC As[2][GBK][BMV + 1];
+    __shared__ TC Bs[2][GBK][BNV + 1];
     // job of this tile: last job with tile0 <= blockIdx.x
     int lo = 0, hi = njobs - 1;
     const int64_t tile = blockIdx.x;
@@ -113,24 +120,24 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
     }
     const GemmJob J = jobs[lo];
     const int64_t local = tile - J.tile0;
-    const int64_t i0 = (local % J.tiles_m) * GBM;
-    const int64_t j0 = (local / J.tiles_m) * GBN;
+    const int64_t i0 = (local % J.tiles_m) * BMV;
+    const int64_t j0 = (local / J.tiles_m) * BNV;
     const int t = threadIdx.x, tx = t % 16, ty = t / 16;
     int64_t kend = J.K;
-    if (J.tri == 2 && kend > j0 + GBN) kend = j0 + GBN;
-    const bool skip = (J.tri == 1 && i0 >= j0 + GBN);
+    if (J.tri == 2 && kend > j0 + BNV) kend = j0 + BNV;
+    const bool skip = (J.tri == 1 && i0 >= j0 + BNV);
     if (skip) kend = 0;
     const float* Af = static_cast<const float*>(J.A);
     const double* Ad = static_cast<const double*>(J.A);
     // the next K step is loaded into registers while the current one is
     // multiplied out of shared memory (two buffers, one barrier per step)
-    TC ra[4], rb[2];
+    TC ra[TM], rb[TN];
     auto load = [&](int64_t k0) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < TM; ++r) {
             int ii, kk;
             if (J.transA) { kk = t % 16; ii = t / 16 + 16 * r; }
-            else          { ii = t % 64; kk = t / 64 + 4 * r; }
+            else          { ii = t % BMV; kk = t / BMV + (GNT / BMV) * r; }
             const int64_t gi = i0 + ii, gk = k0 + kk;
             TC v = TC(0);
             if (gi < J.M && gk < kend) {
@@ -140,9 +147,9 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
             ra[r] = v;
         }
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < TN; ++r) {
             int jj, kk;
-            if (J.transB) { jj = t % 32; kk = t / 32 + 8 * r; }
+            if (J.transB) { jj = t % BNV; kk = t / BNV + (GNT / BNV) * r; }
             else          { kk = t % 16; jj = t / 16 + 16 * r; }
             const int64_t gj = j0 + jj, gk = k0 + kk;
             TC v = TC(0);
@@ -152,23 +159,25 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
     };
     auto store = [&](int buf) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < TM; ++r) {
             int ii, kk;
             if (J.transA) { kk = t % 16; ii = t / 16 + 16 * r; }
-            else          { ii = t % 64; kk = t / 64 + 4 * r; }
+            else          { ii = t % BMV; kk = t / BMV + (GNT / BMV) * r; }
             As[buf][kk][ii] = ra[r];
         }
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < TN; ++r) {
             int jj, kk;
-            if (J.transB) { jj = t % 32; kk = t / 32 + 8 * r; }
+            if (J.transB) { jj = t % BNV; kk = t / BNV + (GNT / BNV) * r; }
             else          { kk = t % 16; jj = t / 16 + 16 * r; }
             Bs[buf][kk][jj] = rb[r];
         }
     };
-    TC acc[4][2];
+    TC acc[TM][TN];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = TC(0);
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[a][c] = TC(0);
     if (kend > 0) {
         load(0);
         store(0);
@@ -179,16 +188,15 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
             if (more) load(k0 + GBK);
 #pragma unroll
             for (int kk = 0; kk < GBK; ++kk) {
-                TC av[4], bv[2];
+                TC av[TM], bv[TN];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) av[a] = As[buf][kk][ty + 16 * a];
-                bv[0] = Bs[buf][kk][tx];
-                bv[1] = Bs[buf][kk][tx + 16];
+                for (int a = 0; a < TM; ++a) av[a] = As[buf][kk][ty + 16 * a];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    acc[a][0] = fma(av[a], bv[0], acc[a][0]);
-                    acc[a][1] = fma(av[a], bv[1], acc[a][1]);
-                }
+                for (int c = 0; c < TN; ++c) bv[c] = Bs[buf][kk][tx + 16 * c];
+#pragma unroll
+                for (int a = 0; a < TM; ++a)
+#pragma unroll
+                    for (int c = 0; c < TN; ++c) acc[a][c] = fma(av[a], bv[c], acc[a][c]);
             }
             if (more) store(buf ^ 1);
             __syncthreads();
@@ -196,17 +204,34 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
         }
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < TM; ++a) {
         const int64_t gi = i0 + ty + 16 * a;
         if (gi >= J.M) continue;
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int64_t gj = j0 + tx + 16 * b;
+        for (int c = 0; c < TN; ++c) {
+            const int64_t gj = j0 + tx + 16 * c;
             if (gj >= J.N) continue;
-            double* c = J.C + gi + gj * J.ldc;
-            *c = J.accum ? *c + double(acc[a][b]) : double(acc[a][b]);
+            double* cp = J.C + gi + gj * J.ldc;
+            *cp = J.accum ? *cp + double(acc[a][c]) : double(acc[a][c]);
         }
     }
+}
+
+// One grouped GEMM launch in tile shape `variant` over a job table whose tile
+// fields were laid out for that shape.
+cudaError_t launch_b_gemm(int variant, int tc32, const GemmJob* tab, int njobs, int64_t tiles,
+                          cudaStream_t s) {
+    if (tiles < 1) return cudaSuccess;
+    switch (variant * 2 + (tc32 ? 1 : 0)) {
+        case 0: k_b_gemm<double, 64, 32><<<unsigned(tiles), GNT, 0, s>>>(tab, njobs); break;
+        case 1: k_b_gemm<float, 64, 32><<<unsigned(tiles), GNT, 0, s>>>(tab, njobs); break;
+        case 2: k_b_gemm<double, 64, 64><<<unsigned(tiles), GNT, 0, s>>>(tab, njobs); break;
+        case 3: k_b_gemm<float, 64, 64><<<unsigned(tiles), GNT, 0, s>>>(tab, njobs); break;
+        case 4: k_b_gemm<double, 128, 32><<<unsigned(tiles), GNT, 0, s>>>(tab, njobs); break;
+        case 5: k_b_gemm<float, 128, 32><<<unsigned(tiles), GNT, 0, s>>>(tab, njobs); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // ------------------------------------------- one-CTA partial-pivoting LU
@@ -444,7 +469,23 @@ struct LaunchRec {
     int64_t tiles;     // gemm: total tiles
     int maxn;          // trinv / lu smem
     int tc32;          // gemm arithmetic FP32
+    int gidx = -1;     // gemm: index of its job list in Builder::gjobs
+    int variant = 0;   // gemm: tile shape (kVarBM / kVarBN)
 };
+
+// The tile fields of a grouped GEMM's jobs for tile shape `variant`; returns
+// the total number of tiles.
+int64_t lay_tiles(std::vector<GemmJob>& jobs, int variant) {
+    const int bm = kVarBM[variant], bn = kVarBN[variant];
+    int64_t tiles = 0;
+    for (auto& j : jobs) {
+        j.tiles_m = (j.M + bm - 1) / bm;
+        j.tiles_n = (j.N + bn - 1) / bn;
+        j.tile0 = tiles;
+        tiles += int64_t(j.tiles_m) * j.tiles_n;
+    }
+    return tiles;
+}
 
 struct Builder {
     std::vector<unsigned char> blob;
@@ -456,18 +497,25 @@ struct Builder {
         memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
         return off;
     }
+    // grouped GEMMs: the job lists are kept aside until their tile shapes are
+    // chosen (place_gemms)
+    std::vector<std::vector<GemmJob>> gjobs;
     void gemm(std::vector<GemmJob>& jobs, int tc32) {
         if (jobs.empty()) return;
-        int64_t tiles = 0;
-        for (auto& j : jobs) {
-            j.tiles_m = (j.M + GBM - 1) / GBM;
-            j.tiles_n = (j.N + GBN - 1) / GBN;
-            j.tile0 = tiles;
-            tiles += int64_t(j.tiles_m) * j.tiles_n;
-        }
-        LaunchRec r{1, put(jobs), int(jobs.size()), tiles, 0, tc32};
+        LaunchRec r{1, 0, int(jobs.size()), 0, 0, tc32};
+        r.gidx = int(gjobs.size());
+        gjobs.push_back(jobs);
         recs.push_back(r);
         jobs.clear();
+    }
+    // every grouped GEMM's table, laid out for its chosen shape, into the blob
+    void place_gemms(const std::vector<int>& variant) {
+        for (auto& r : recs) {
+            if (r.kind != 1) continue;
+            r.variant = variant[r.gidx];
+            r.tiles = lay_tiles(gjobs[r.gidx], r.variant);
+            r.off = put(gjobs[r.gidx]);
+        }
     }
     void lu(std::vector<LuJob>& jobs) {
         if (jobs.empty()) return;
@@ -780,12 +828,9 @@ cudaError_t launch_batch_plan(const Builder& B, const char* dtab, int* dev_statu
                     reinterpret_cast<const GaussJob*>(tab));
                 break;
             case 1:
-                if (r.tc32)
-                    k_b_gemm<float><<<unsigned(r.tiles), GNT, 0, s>>>(
-                        reinterpret_cast<const GemmJob*>(tab), r.njobs);
-                else
-                    k_b_gemm<double><<<unsigned(r.tiles), GNT, 0, s>>>(
-                        reinterpret_cast<const GemmJob*>(tab), r.njobs);
+                e = launch_b_gemm(r.variant, r.tc32, reinterpret_cast<const GemmJob*>(tab),
+                                  r.njobs, r.tiles, s);
+                if (e != cudaSuccess) return e;
                 break;
             case 2:
                 k_b_panel_lu<<<unsigned(r.njobs), LNT, size_t(r.maxn) * sizeof(double), s>>>(
@@ -809,11 +854,72 @@ cudaError_t launch_batch_plan(const Builder& B, const char* dtab, int* dev_statu
 
 // Plan, upload the job tables, capture the grouped launches in a CUDA graph
 // and launch it.  `tables` must hold batch_tables_bytes() bytes.
+// The autotuner: every grouped GEMM of the plan is timed alone in each tile
+// shape on its real job list (CUDA events, the better of two runs after one
+// warm-up; the operands may hold anything then, as the graph recomputes every
+// phase in order afterwards), and the fastest shape is kept.
+cudaError_t tune_gemms(Builder& B, char* tables, size_t tables_cap, cudaStream_t s,
+                       std::vector<int>* tuned) {
+    const size_t base = (B.blob.size() + 255) & ~size_t(255);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cudaErrorUnknown;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cudaErrorUnknown;
+    }
+    tuned->assign(B.gjobs.size(), 0);
+    cudaError_t e = cudaSuccess;
+    for (const LaunchRec& r : B.recs) {
+        if (r.kind != 1) continue;
+        std::vector<GemmJob> jobs = B.gjobs[r.gidx];
+        float best = 0.f;
+        for (int v = 0; v < kGemmVariants && e == cudaSuccess; ++v) {
+            const int64_t tiles = lay_tiles(jobs, v);
+            const size_t bytes = jobs.size() * sizeof(GemmJob);
+            if (base + bytes > tables_cap) {
+                e = cudaErrorInvalidValue;
+                break;
+            }
+            GemmJob* tab = reinterpret_cast<GemmJob*>(tables + base);
+            if ((e = cudaMemcpyAsync(tab, jobs.data(), bytes, cudaMemcpyHostToDevice, s)) !=
+                cudaSuccess)
+                break;
+            float t_v = 0.f;
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                cudaEventRecord(e0, s);
+                e = launch_b_gemm(v, r.tc32, tab, int(jobs.size()), tiles, s);
+                cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep == 1 || (rep == 2 && ms < t_v)) t_v = ms;
+            }
+            if (v == 0 || t_v < best) {
+                best = t_v;
+                (*tuned)[r.gidx] = v;
+            }
+        }
+        if (e != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return e;
+}
+
 cudaError_t run_batch(const plu_batch_problem* P, int count, int prec, char* ws, char* tables,
                       size_t tables_cap, int* dev_status, int num_sms, cudaStream_t s,
-                      cudaStream_t cs, int* nlaunch, float* ms_graph) {
+                      cudaStream_t cs, int* nlaunch, float* ms_graph, std::vector<int>* tuned,
+                      int forced) {
     Builder B;
     plan_batch(P, count, prec, ws, B);
+    if (forced >= 0) {
+        if (forced >= kGemmVariants) return cudaErrorInvalidValue;
+        tuned->assign(B.gjobs.size(), forced);
+    } else if (tuned->size() != B.gjobs.size()) {
+        const cudaError_t te = tune_gemms(B, tables, tables_cap, s, tuned);
+        if (te != cudaSuccess) return te;
+    }
+    B.place_gemms(*tuned);
     if (B.blob.size() > tables_cap) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemcpyAsync(tables, B.blob.data(), B.blob.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
@@ -855,8 +961,16 @@ cudaError_t run_batch(const plu_batch_problem* P, int count, int prec, char* ws,
 }
 
 size_t batch_tables_bytes(int count) {
-    // generous: every phase's tables for all problems
-    return size_t(count) * 64 * sizeof(GemmJob) + (1 << 20);
+    // generous: every phase's tables for all problems, and room for the
+    // autotuner's trial table
+    return size_t(count) * 72 * sizeof(GemmJob) + (1 << 20);
+}
+
+int batch_gemm_tile(int variant, int* bm, int* bn) {
+    if (variant < 0 || variant >= kGemmVariants) return 0;
+    *bm = kVarBM[variant];
+    *bn = kVarBN[variant];
+    return 1;
 }
 
 }  // namespace plu

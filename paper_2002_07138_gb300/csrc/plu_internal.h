@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
+#include <vector>
 
 #include "../../include/powerlu.h"
 
@@ -272,8 +273,14 @@ cudaError_t launch_scatter_rows(int64_t rows, int cols, const int32_t* perm, con
 // ------------------------------------------------------------- batched
 size_t batch_workspace_bytes(const plu_batch_problem* P, int count);
 size_t batch_tables_bytes(int count);
+// tuned: the tile shape of every grouped GEMM of the plan; when it does not
+// match the plan's GEMM count the autotuner times the shapes and fills it.
+// forced >= 0 takes that shape for every grouped GEMM instead.
 cudaError_t run_batch(const plu_batch_problem* P, int count, int prec, char* ws, char* tables,
                       size_t tables_cap, int* dev_status, int num_sms, cudaStream_t s,
-                      cudaStream_t capture_stream, int* nlaunch, float* ms_graph);
+                      cudaStream_t capture_stream, int* nlaunch, float* ms_graph,
+                      std::vector<int>* tuned, int forced);
+// Tile shape (rows, columns) of grouped-GEMM variant v; 0 for a bad index.
+int batch_gemm_tile(int variant, int* bm, int* bn);
 
 }  // namespace plu

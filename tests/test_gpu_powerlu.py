@@ -281,6 +281,51 @@ def test_batched_fp64_matches_oracle_per_problem(ctx):
         check_parity(A, (gp, gq, gL, gU), ref, tol=1e-9)
 
 
+@pytest.mark.parametrize("bm,bn", [(64, 32), (64, 64), (128, 32)])
+def test_batched_each_gemm_tile_shape_matches_oracle(ctx, bm, bn):
+    """Every grouped-GEMM tile shape the autotuner can pick, forced for the
+    whole batch: identical pivots and factors to 1e-9 against the oracle."""
+    cases = _batch_cases()[:7]
+    mats, probs = [], []
+    for c in cases:
+        sig = synth.sigma_profile("expk", min(c["m"], c["n"]), k=c["k"])
+        A = synth.svd_matrix_np(c["m"], c["n"], sig, seed=c["seed"])
+        mats.append(A)
+        probs.append(dict(A=dev(A), k=c["k"], l=c["l"], v=c["v"], algo=c["algo"], seed=c["seed"]))
+    plu.plu_set_batched_tile(ctx, bm, bn)
+    try:
+        outs, _ = plu.plu_batched(ctx, probs, prec="fp64")
+        assert set(plu.plu_batched_tiles(ctx)) == {(bm, bn)}
+    finally:
+        plu.plu_set_batched_tile(ctx, 0, 0)
+    for c, A, (gp, gq, gL, gU) in zip(cases, mats, outs):
+        if c["algo"] == 1:
+            ref = oracle.singlepass(A, c["k"], seed=c["seed"])
+        else:
+            ref = oracle.powerlu(A, c["k"], c["l"], c["v"], seed=c["seed"])
+        check_parity(A, (gp, gq, gL, gU), ref, tol=1e-9)
+
+
+def test_batched_autotuner_choice_is_cached_and_valid(ctx):
+    """The first call of a batch signature times the tile shapes; a second
+    call reuses the same choice; every chosen shape is one the library has;
+    a shape it does not have is refused."""
+    cases = _batch_cases()[7:]
+    probs = []
+    for c in cases:
+        A = synth.svd_matrix_np(c["m"], c["n"], synth.sigma_profile("type2", min(c["m"], c["n"])),
+                                seed=c["seed"])
+        probs.append(dict(A=dev(A.astype(np.float32), torch.float32), k=c["k"], l=c["l"], v=c["v"],
+                          algo=c["algo"], seed=c["seed"]))
+    plu.plu_batched(ctx, probs, prec="fp32")
+    first = plu.plu_batched_tiles(ctx)
+    plu.plu_batched(ctx, probs, prec="fp32")
+    assert plu.plu_batched_tiles(ctx) == first
+    assert len(first) > 0 and set(first) <= {(64, 32), (64, 64), (128, 32)}
+    with pytest.raises(plu.PLUError):
+        plu.plu_set_batched_tile(ctx, 48, 48)
+
+
 def test_batched_fp32_error_close_to_fp64(ctx):
     cases = _batch_cases()[:8]
     probs32, probs64, mats = [], [], []
