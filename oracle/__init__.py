@@ -19,6 +19,8 @@ numpy primitives (matmul, argmax, norms) as steps and no blocking or fusion:
 * ``powerlu``   -- Algorithms gpowerlu, bpowerlu, adaptivewithoutupdating
                    (+ the precise-rank variant of Sec. 6.4), powerlufp,
                    rlu + basicpoweriteration and singlepasslu.
+* ``sparse``    -- products with a sparse A in CSR (the sprand experiment
+                   of Sec. 6), as passes the algorithms above accept.
 * ``metrics``   -- relative Frobenius error (Eq. error), Eckart-Young optimum
                    (Eq. ey) and principal angles.
 
@@ -32,6 +34,7 @@ from .qr import qr_economy
 from .powerlu import (gpowerlu, powerlu, adaptive_rank, adaptive_rank_restart, Remainder,
                       RESTART_STREAM_STRIDE, rank_scan, powerlu_fp, randlu,
                       basic_power_iteration_lu, singlepass, PassCounter)
+from .sparse import csr_mul, csr_tmul, SparsePassCounter
 from .metrics import (rel_lu_error, eckart_young_error, eckart_young_rank,
                       max_principal_sine)
 
@@ -42,5 +45,6 @@ __all__ = [
     "gpowerlu", "powerlu", "adaptive_rank", "adaptive_rank_restart", "Remainder",
     "RESTART_STREAM_STRIDE", "rank_scan", "powerlu_fp", "randlu",
     "basic_power_iteration_lu", "singlepass", "PassCounter",
+    "csr_mul", "csr_tmul", "SparsePassCounter",
     "rel_lu_error", "eckart_young_error", "eckart_young_rank", "max_principal_sine",
 ]

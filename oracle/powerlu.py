@@ -40,6 +40,7 @@ from .gaussian import gaussian_matrix
 from .philox import STREAM_OMEGA_N, STREAM_OMEGA_M, STREAM_OMEGA_SP
 from .lu import getrf, lu_permuted_L
 from .qr import qr_economy
+from .sparse import SparsePassCounter
 
 
 class PassCounter:
@@ -53,6 +54,9 @@ class PassCounter:
     def shape(self):
         return self.A.shape
 
+    def frob2(self):            # ||A||_F^2
+        return float(np.sum(self.A * self.A))
+
     def mul(self, X):           # A X
         self.passes += 1
         return self.A @ X
@@ -63,7 +67,7 @@ class PassCounter:
 
 
 def _wrap(A):
-    return A if isinstance(A, (PassCounter, Remainder)) else PassCounter(A)
+    return A if isinstance(A, (PassCounter, Remainder, SparsePassCounter)) else PassCounter(A)
 
 
 class Remainder:
@@ -82,6 +86,9 @@ class Remainder:
     @property
     def shape(self):
         return self.base.shape
+
+    def frob2(self):            # ||A||_F^2 of the original A
+        return self.base.frob2()
 
     @property
     def passes(self):
@@ -185,7 +192,7 @@ def adaptive_rank(A, eps, b, l, v, seed, precise=False):
     residual indicator after k columns (Thm. errorerror), met whether
     E <= eps^2 ||A||_F^2 was reached."""
     Ac = _wrap(A)
-    E0 = float(np.sum(Ac.A * Ac.A))
+    E0 = Ac.frob2()
     V = gpowerlu(Ac, l, v, seed)
     G = Ac.mul(V)
     k, E, met = rank_scan(G, E0, eps, b, precise)
@@ -198,7 +205,7 @@ def adaptive_rank_restart(A, eps, b, l, v, seed, precise=False, max_rounds=1):
     Returns (k, W, G, E, met, rounds): W n x k, G = A W m x k."""
     Ac = _wrap(A)
     m, n = Ac.shape
-    nA2 = float(np.sum(Ac.A * Ac.A))
+    nA2 = Ac.frob2()
     W = np.zeros((n, 0))
     G = np.zeros((m, 0))
     E = nA2

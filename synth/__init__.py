@@ -209,3 +209,64 @@ def batched_problems(count=512, seed=0):
         v = 2 if i % 2 == 0 else 3
         probs.append(dict(m=m, n=n, k=k, l=l, v=v, seed=int(seed * 100003 + i)))
     return probs
+
+
+# --------------------------------------------------------------------------
+# sparse matrices (the sparse runtime experiment of Sec. 6: MATLAB sprand)
+# --------------------------------------------------------------------------
+def sprand_csr(m, n, density, seed):
+    """A seeded stand-in for MATLAB's sprand(m, n, density): about
+    density * m * n nonzeros at uniformly random positions, values uniform on
+    [0, 1).  Positions are drawn with replacement and repeats dropped, so
+    each (i, j) appears once and nnz is slightly below round(density m n).
+    Returns the CSR of A: (row_ptr int64 (m + 1), col_idx int32, val float64),
+    columns sorted within each row."""
+    rng = np.random.default_rng(seed)
+    want = int(round(density * m * n))
+    lin = np.unique(rng.integers(0, m * n, size=want, dtype=np.int64))
+    rows = lin // n
+    cols = (lin - rows * n).astype(np.int32)
+    val = rng.random(lin.size)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=m), out=row_ptr[1:])
+    return row_ptr, cols, val
+
+
+def csr_transpose(m, n, row_ptr, col_idx, val):
+    """The CSR of A^T (n x m) from the CSR of A (m x n): a stable reordering
+    of the same entries by column.  Returns (t_row_ptr, t_col_idx, t_val)."""
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(row_ptr))
+    order = np.argsort(col_idx, kind="stable")
+    t_row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(col_idx, minlength=n), out=t_row_ptr[1:])
+    return t_row_ptr, rows[order].astype(np.int32), val[order]
+
+
+def csr_to_dense(m, n, row_ptr, col_idx, val):
+    """The dense m x n A (Fortran order) of a CSR whose positions are unique."""
+    A = np.zeros((m, n), order="F")
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(row_ptr))
+    A[rows, col_idx] = val
+    return A
+
+
+def dense_to_csr(A):
+    """CSR of the nonzeros of a dense array, row by row (format conversion)."""
+    m, n = A.shape
+    rows, cols = np.nonzero(A)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=m), out=row_ptr[1:])
+    return row_ptr, cols.astype(np.int32), np.asarray(A)[rows, cols].astype(np.float64)
+
+
+def sparse_rank_r(m, n, r, seed, frac=0.15):
+    """A dense array holding a sparse matrix of exact rank r: the sum of r
+    outer products of Gaussian vectors whose entries are kept with
+    probability frac."""
+    rng = np.random.default_rng(seed)
+    A = np.zeros((m, n), order="F")
+    for _ in range(r):
+        u = rng.standard_normal(m) * (rng.random(m) < frac)
+        v = rng.standard_normal(n) * (rng.random(n) < frac)
+        A += np.outer(u, v)
+    return A
