@@ -9,7 +9,8 @@ already resident in HBM.  Default workload: the mixed-precision one, m = n =
 between steps), sigma_i = i^-1.5, k = 256, l = 276, v = 3, passes on TF32
 tensor cores; the BF16 and FP8-E4M3 passes are reported beside it.
 --workload fixed_rank_8192 runs the 8192^2 FP32 workload, batched_512 the
-batch of 512 problems.
+batch of 512 problems, sparse_32000 PowerLU on a 32000^2 sprand-like matrix
+at 0.3% density (FP64 sparse passes; Sec. 6, l = 200).
 
 value = algorithmic pass flops (2 m n l per power pass + 2 m n k for the
 last pass) over the whole call time, in TFLOP/s, summed over ranks.
@@ -59,7 +60,8 @@ def workloads():
     return {"fixed_rank_8192": synth.FIXED_RANK_8192, "mixed_32768": synth.MIXED_32768,
             "mixed_16384": synth.MIXED_16384,
             "fixed_prec_20000x10000": synth.FIXED_PREC_20000x10000,
-            "plain_2000x1500": synth.PLAIN_2000x1500, "batched_512": None}
+            "plain_2000x1500": synth.PLAIN_2000x1500, "batched_512": None,
+            "sparse_32000": None}
 
 
 def batch_specs(count=512, seed=0):
@@ -849,6 +851,232 @@ def run_randlu(args, w):
     return 0
 
 
+# ---------------------------------------------------------------- sparse
+SPARSE = {"name": "sparse_32000_d0.003_k200_l200_v4", "n": 32000, "density": 0.003,
+          "k": 200, "l": 200, "v": 4, "seed": 0}
+
+
+def sparse_host(seed):
+    import synth
+    sp = SPARSE
+    rp, ci, val = synth.sprand_csr(sp["n"], sp["n"], sp["density"], seed)
+    return rp, ci, val
+
+
+def sparse_pass_bytes(n, nnz, cols):
+    """Algorithmic bytes of one sparse pass: the CSR arrays (8 B value +
+    4 B index per nonzero, the row pointers), X read once and Y written once."""
+    return nnz * 12.0 + (n + 1) * 8.0 + 2.0 * n * cols * 8.0
+
+
+def run_sparse(args):
+    """PowerLU (Alg. bpowerlu + Alg. gpowerlu) on the sparse workload, every
+    pass an FP64 sparse product.  value = the passes' algorithmic flops
+    (2 nnz per column) over the call time."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2002_07138_gb300 as plu
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    peaks = {"hbm_gbs": 6791.0, "bf16_tflops": 1934.6, "sm_max_mhz": 2070.0}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks.update(json.load(f))
+    except OSError:
+        peaks["source"] = "fallback"
+    sp = SPARSE
+    n, k, l, v = sp["n"], sp["k"], sp["l"], sp["v"]
+    rp, ci, val = sparse_host(sp["seed"] + rank)
+    nnz = int(rp[-1])
+    host_arrays = (rp, ci, val) + tuple(synth.csr_transpose(n, n, rp, ci, val))
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in host_arrays]
+    dev_arrays = [t.cuda() for t in pinned]
+    S = plu.CsrMatrix(n, n, *dev_arrays)
+    stream = torch.cuda.current_stream()
+    ctx = plu.Context(local, stream.cuda_stream)
+    flops = 2.0 * nnz * (l * (v - 1) + k)
+
+    def call(seed, A=S, vv=v):
+        return plu.plu_powerlu_csr(ctx, A, k, l, vv, seed=seed)
+
+    # the CSR arrays of A and A^T (about 74 MB) fit L2: a 256 MB write flushes
+    # it before every timed call, outside the call's events
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    for i in range(args.warmup):
+        call(i)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    dist_barrier(ws)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    reps = []
+    for i, (e0, e1) in enumerate(evs):
+        flush.zero_()
+        e0.record(stream)
+        reps.append(call(1000 + i)[4])
+        e1.record(stream)
+    torch.cuda.synchronize()
+    dist_barrier(ws)
+    clk = clocks.stop()
+    ms_total = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    ms_max = dist_max(ws, ms_total)
+    ms_step = ms_max / args.steps
+    value = flops * args.steps * ws / (ms_max / 1e3) / 1e12
+    launches = int(sum(r["launches"] for r in reps))
+    ms_pass = statistics.mean(r["ms_passes"] / r["passes"] for r in reps)
+
+    # v = 2 (no power iteration, the paper's left panel), one timed call
+    call(0, vv=2)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    call(5, vv=2)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms_v2 = t0.elapsed_time(t1)
+
+    # end to end: the CSR arrays host -> device, the call, the factors back
+    dev_e = [torch.empty_like(t) for t in dev_arrays]
+    Se = plu.CsrMatrix(n, n, *dev_e)
+    ph = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    qh = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    Lh = torch.empty(k, n, dtype=torch.float64, pin_memory=True).t()
+    Uh = torch.empty(n, k, dtype=torch.float64, pin_memory=True).t()
+
+    def e2e_step(seed):
+        for d, h in zip(dev_e, pinned):
+            d.copy_(h, non_blocking=True)
+        p, q, L, U, _ = call(seed, Se)
+        ph.copy_(p, non_blocking=True)
+        qh.copy_(q, non_blocking=True)
+        Lh.copy_(L, non_blocking=True)
+        Uh.copy_(U, non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_step(0)
+    ne = max(2, min(args.steps, 5))
+    t0h = time.perf_counter()
+    for i in range(ne):
+        e2e_step(3000 + i)
+    e2e_ms = dist_max(ws, 1e3 * (time.perf_counter() - t0h) / ne)
+    h2d = sum(t.numel() * t.element_size() for t in pinned)
+    d2h = 8 * n + 16 * n * k
+
+    # the steps timed alone (asynchronous context: no host sync per call)
+    plu.lib().plu_set_async(ctx.handle, 1)
+    X = plu.colmajor_empty(n, l)
+    X.normal_()
+    Z = plu.colmajor_empty(n, l)
+    ms0 = time_calls(torch, lambda: plu.plu_spmm(ctx, S, 0, X, out=Z), 5, stream)
+    ms1 = time_calls(torch, lambda: plu.plu_spmm(ctx, S, 1, Z, out=X), 5, stream)
+    ms_sp = 0.5 * (ms0 + ms1)
+    Zc = Z.clone()
+    ms_lu = time_calls(torch, lambda: (Zc.copy_(Z), plu.plu_lu_reorth(ctx, Zc)), 3, stream)
+    ms_cp = time_calls(torch, lambda: Zc.copy_(Z), 3, stream)
+    ms_lu = max(ms_lu - ms_cp, 1e-6)
+    plu.lib().plu_set_async(ctx.handle, 0)
+    ctx.check(plu.lib().plu_check(ctx.handle))
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    # launches per call: v passes; v - 2 re-orthogonalising LUs (v > 2) and
+    # the tail's two LUs of n x k panels
+    share = {"spmm": ms_sp * v, "panel_lu": ms_lu * (max(v - 2, 0) + 2)}
+    pbytes = sparse_pass_bytes(n, nnz, l)
+    rf_sp = {"bound": "hbm", "achieved": pbytes / ms_sp / 1e6, "peak": peaks["hbm_gbs"],
+             "unit": "GB/s", "peak_source": "measured copy bandwidth",
+             "kernel": "k_spmm_csr + k_to_rowmajor", "ms_per_launch": ms_sp,
+             "traffic": None, "share_of_step": share["spmm"] / ms_step,
+             "l2_gather_gbs": nnz * l * 8.0 / ms_sp / 1e6,
+             "note": "the rows of X a pass gathers (nnz x l x 8 B) come from L2"}
+    rf_sp["frac"] = rf_sp["achieved"] / rf_sp["peak"]
+    rf_lu = {"bound": "alu", "achieved": lu_flops(n, l) / ms_lu / 1e9, "peak": 1.25,
+             "unit": "TFLOP/s", "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)",
+             "kernel": panel_kernel_name(n, l, sms), "ms_per_launch": ms_lu, "traffic": None,
+             "share_of_step": share["panel_lu"] / ms_step}
+    rf_lu["frac"] = rf_lu["achieved"] / rf_lu["peak"]
+    rf = rf_sp if share["spmm"] >= share["panel_lu"] else rf_lu
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        dt, sfl, desc = sparse_oracle_sample(n, rp, ci, val, seed=0)
+        cpu = {"value": sfl / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
+               "kind": "oracle", "sample": "%s on the same matrix, %.1f s" % (desc, dt)}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": sp["name"], "m": n, "n": n, "nnz": nnz,
+                       "density": sp["density"], "values": "uniform [0, 1)", "k": k, "l": l,
+                       "v": v, "pass_precision": "fp64 (sparse)", "between_passes": "f64",
+                       "l2_flush": "256 MB write before every timed call, outside its "
+                                   "events (the CSR arrays of A and A^T are %.0f MB)" % (h2d / 1e6),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "ms_per_pass": ms_pass, "ms_per_step_v2": ms_v2,
+            "tflops_per_pass": 2.0 * nnz * l / (ms_pass / 1e3) / 1e12,
+            "e2e": {"value": flops * ws / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                    "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clk, "roofline": rf, "roofline_spmm": rf_sp,
+            "roofline_panel_lu": rf_lu,
+            "kernel_ms": {"spmm": {"ms_per_launch": ms_sp, "launches_per_step": v},
+                          "panel_lu": {"ms_per_launch": ms_lu,
+                                       "launches_per_step": max(v - 2, 0) + 2}},
+            "cpu_baseline": cpu,
+        }))
+    ctx.close()
+    return 0
+
+
+def sparse_oracle_sample(n, rp, ci, val, seed):
+    """The oracle's first pass of Alg. gpowerlu on the sparse A (v even:
+    A^T Omega) and its LU re-orthogonalisation.  Returns (seconds, flops,
+    description)."""
+    import oracle
+    l = SPARSE["l"]
+    t0 = time.perf_counter()
+    Om = oracle.gaussian_matrix(n, l, seed, oracle.STREAM_OMEGA_M)
+    Y = oracle.csr_tmul(n, rp, ci, val, Om)
+    oracle.lu_permuted_L(Y)
+    dt = time.perf_counter() - t0
+    return dt, 2.0 * int(rp[-1]) * l, ("the oracle's first pass of Alg. gpowerlu (A^T Omega "
+                                       "from the CSR, FP64) and its LU re-orthogonalisation")
+
+
+def run_reference_sparse(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    sp = SPARSE
+    rp, ci, val = sparse_host(sp["seed"])
+    for i in range(args.warmup):
+        sparse_oracle_sample(sp["n"], rp, ci, val, seed=i)
+    times = []
+    for i in range(args.steps):
+        dt, flops, desc = sparse_oracle_sample(sp["n"], rp, ci, val, seed=i)
+        times.append(dt)
+    total = sum(times)
+    value = flops * args.steps / total / 1e12
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": sp["name"], "m": sp["n"], "n": sp["n"], "nnz": int(rp[-1]),
+                   "density": sp["density"], "k": sp["k"], "l": sp["l"], "v": sp["v"]},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": desc + " per step"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
 def synth_colmajor(t):
     import synth
     return synth.colmajor(t)
@@ -877,6 +1105,8 @@ def main():
                               "reference arm; use the default workload"}))
             return 0
         return run_batched(args)
+    if args.workload == "sparse_32000":
+        return run_reference_sparse(args) if args.impl == "reference" else run_sparse(args)
     w = workloads()[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)

@@ -62,7 +62,8 @@ typedef enum {
     PLU_ENUMERIC = 4,      /* non-finite value or zero pivot in a final LU       */
     PLU_ETIMEOUT = 5,      /* a device-side wait ran out of its iteration budget */
     PLU_TOL_NOT_MET = 6,   /* fixed precision: l columns did not reach eps       */
-    PLU_EUNSUPPORTED = 7   /* combination not built (e.g. precision for dtype)   */
+    PLU_EUNSUPPORTED = 7,  /* combination not built (e.g. precision for dtype)   */
+    PLU_EINDEX = 8         /* a sparse index or row pointer out of range (device) */
 } plu_status;
 
 /* Dense input matrix A (m x n), column-major, device memory, not owned. */
@@ -71,6 +72,27 @@ typedef struct {
     int32_t dtype;          /* plu_dtype */
     const void* data;
 } plu_matrix;
+
+/* Sparse input matrix A (m x n) in compressed sparse rows, device memory,
+ * not owned (the sparse experiment of Sec. 6 uses MATLAB sprand matrices).
+ * Row i holds the nonzeros row_ptr[i] .. row_ptr[i+1]-1: column col_idx[t]
+ * (0-based) and value val[t].  row_ptr has m + 1 entries, row_ptr[0] = 0,
+ * row_ptr[m] = nnz, non-decreasing; column indices need not be sorted, and
+ * each position (i, j) is stored at most once (plu_powerlu_fp_csr takes
+ * ||A||_F^2 as the sum of val^2).  The passes read A^T through its own CSR (t_*: the
+ * CSR of the n x m matrix A^T, i.e. the compressed columns of A), which must
+ * hold the same entries.  A row pointer outside [0, nnz] or a column index
+ * outside its range is detected on the device: the entry is skipped and the
+ * call returns PLU_EINDEX. */
+typedef struct {
+    int64_t m, n, nnz;
+    const int64_t* row_ptr;     /* m + 1 */
+    const int32_t* col_idx;     /* nnz, in [0, n) */
+    const double* val;          /* nnz */
+    const int64_t* t_row_ptr;   /* n + 1 */
+    const int32_t* t_col_idx;   /* nnz, in [0, m) */
+    const double* t_val;        /* nnz */
+} plu_csr;
 
 /* Per-call report (host struct, filled when a non-NULL pointer is given). */
 typedef struct {
@@ -125,6 +147,14 @@ plu_status plu_gaussian(plu_ctx* ctx, int64_t rows, int64_t cols, uint64_t seed,
  * X and Y are FP64 and must not overlap. */
 plu_status plu_pass(plu_ctx* ctx, const plu_matrix* A, int trans, const double* X,
                     int64_t ldx, int cols, plu_prec prec, double* Y, int64_t ldy);
+
+/* a2/a4/a6 on a sparse A: Y = A X (trans = 0; X n x cols, Y m x cols) or
+ * Y = A^T X (trans = 1, through the CSR of A^T; X m x cols, Y n x cols),
+ * FP64.  Each entry of Y is the sum over the nonzeros of its row of S (A or
+ * A^T) in CSR order, so the result does not depend on the launch.  X and Y
+ * must not overlap.  PLU_EINDEX: see plu_csr. */
+plu_status plu_spmm(plu_ctx* ctx, const plu_csr* A, int trans, const double* X, int64_t ldx,
+                    int cols, double* Y, int64_t ldy);
 
 /* a3. [X, ~] = lu(X) in place (Alg. gpowerlu, the LU re-orthogonalisation):
  * X (rows x cols, rows >= cols) is overwritten by the permuted unit lower
@@ -236,6 +266,22 @@ plu_status plu_singlepass(plu_ctx* ctx, const plu_matrix* A, int k, uint64_t see
 plu_status plu_randlu(plu_ctx* ctx, const plu_matrix* A, int k, int l, int piter,
                       uint64_t seed, plu_prec prec, int32_t* p, int32_t* q, double* L,
                       int64_t ldL, double* U, int64_t ldU, plu_report* rep);
+
+/* plu_powerlu on a sparse A: every pass over A (v of them) is an FP64 sparse
+ * product (plu_spmm), everything else as plu_powerlu in PLU_FP64, so the
+ * result is that of plu_powerlu on the dense A up to the rounding order of
+ * the products.  rep->flops_passes counts 2 nnz flops per column of a pass
+ * and rep->bytes_passes the CSR arrays plus the operands. */
+plu_status plu_powerlu_csr(plu_ctx* ctx, const plu_csr* A, int k, int l, int v, uint64_t seed,
+                           int32_t* p, int32_t* q, double* L, int64_t ldL, double* U,
+                           int64_t ldU, plu_report* rep);
+
+/* plu_powerlu_fp_restart on a sparse A, with FP64 sparse passes
+ * (max_rounds = 1 is plu_powerlu_fp); ||A||_F^2 is the sum of val^2. */
+plu_status plu_powerlu_fp_csr(plu_ctx* ctx, const plu_csr* A, double eps, int b, int l, int v,
+                              int precise, int max_rounds, uint64_t seed, int* k_out,
+                              int32_t* p, int32_t* q, double* L, int64_t ldL, double* U,
+                              int64_t ldU, plu_report* rep);
 
 /* One problem of a batch (plu_batched).  A is m x n, column-major, device
  * memory, element type `dtype` (plu_dtype).  algo 0: PowerLU (Alg. bpowerlu

@@ -11,6 +11,7 @@ from ._binding import (  # noqa: F401
     plu_powerlu, plu_powerlu_fp, plu_randlu, plu_singlepass, plu_batched, plu_batched_tiles,
     plu_set_batched_tile,
     plu_batch_problem,
+    plu_csr, CsrMatrix, plu_spmm, plu_powerlu_csr, plu_powerlu_fp_csr,
     PREC, STATUS,
     SIGNATURES,
     STREAM_OMEGA_N, STREAM_OMEGA_M, STREAM_OMEGA_SP,

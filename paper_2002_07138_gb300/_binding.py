@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libpowerlu.so")
 PLU_FP64, PLU_TF32, PLU_BF16, PLU_FP8_E4M3, PLU_FP32 = 0, 1, 2, 3, 4
 PLU_F64, PLU_F32 = 0, 1
 STATUS = {0: "PLU_OK", 1: "PLU_EINVAL", 2: "PLU_ENOMEM", 3: "PLU_ECUDA", 4: "PLU_ENUMERIC",
-          5: "PLU_ETIMEOUT", 6: "PLU_TOL_NOT_MET", 7: "PLU_EUNSUPPORTED"}
+          5: "PLU_ETIMEOUT", 6: "PLU_TOL_NOT_MET", 7: "PLU_EUNSUPPORTED", 8: "PLU_EINDEX"}
 PREC = {"fp64": PLU_FP64, "tf32": PLU_TF32, "bf16": PLU_BF16, "fp8": PLU_FP8_E4M3,
         "fp32": PLU_FP32}
 
@@ -29,6 +29,11 @@ c_i64, c_i32, c_u64, c_u32, c_int, c_dbl, c_vp = (ctypes.c_int64, ctypes.c_int32
 
 class plu_matrix(ctypes.Structure):
     _fields_ = [("m", c_i64), ("n", c_i64), ("ld", c_i64), ("dtype", c_i32), ("data", c_vp)]
+
+
+class plu_csr(ctypes.Structure):
+    _fields_ = [("m", c_i64), ("n", c_i64), ("nnz", c_i64), ("row_ptr", c_vp), ("col_idx", c_vp),
+                ("val", c_vp), ("t_row_ptr", c_vp), ("t_col_idx", c_vp), ("t_val", c_vp)]
 
 
 class plu_report(ctypes.Structure):
@@ -79,6 +84,12 @@ SIGNATURES = {
                                        ctypes.POINTER(plu_report)]),
     "plu_singlepass": (c_int, [c_vp, ctypes.POINTER(plu_matrix), c_int, c_u64, c_int, c_vp, c_vp,
                                c_vp, c_i64, c_vp, c_i64, ctypes.POINTER(plu_report)]),
+    "plu_spmm": (c_int, [c_vp, ctypes.POINTER(plu_csr), c_int, c_vp, c_i64, c_int, c_vp, c_i64]),
+    "plu_powerlu_csr": (c_int, [c_vp, ctypes.POINTER(plu_csr), c_int, c_int, c_int, c_u64, c_vp,
+                                c_vp, c_vp, c_i64, c_vp, c_i64, ctypes.POINTER(plu_report)]),
+    "plu_powerlu_fp_csr": (c_int, [c_vp, ctypes.POINTER(plu_csr), c_dbl, c_int, c_int, c_int,
+                                   c_int, c_int, c_u64, ctypes.POINTER(c_int), c_vp, c_vp, c_vp,
+                                   c_i64, c_vp, c_i64, ctypes.POINTER(plu_report)]),
     "plu_lu_reorth_static": (c_int, [c_vp, c_i64, c_int, c_vp, c_i64, ctypes.c_char_p,
                                      ctypes.c_size_t]),
     "plu_set_batched_tile": (c_int, [c_vp, c_int, c_int]),
@@ -368,3 +379,75 @@ def plu_batched(ctx, problems, prec="fp32"):
     rep = plu_report()
     ctx.check(lib().plu_batched(ctx.handle, arr, len(problems), PREC[prec], ctypes.byref(rep)))
     return outs, rep.as_dict()
+
+
+# ------------------------------------------------------------- sparse A
+class CsrMatrix:
+    """A sparse m x n A on the device as plu_csr wants it: the CSR of A and
+    the CSR of A^T (int64 row pointers, int32 column indices, float64
+    values, all CUDA tensors).  Holds the tensors so they outlive the calls."""
+
+    def __init__(self, m, n, row_ptr, col_idx, val, t_row_ptr, t_col_idx, t_val):
+        torch = _torch()
+        want = ((row_ptr, torch.int64, m + 1), (col_idx, torch.int32, None),
+                (val, torch.float64, None), (t_row_ptr, torch.int64, n + 1),
+                (t_col_idx, torch.int32, None), (t_val, torch.float64, None))
+        for t, dt, size in want:
+            if t.dtype != dt or not t.is_cuda or not t.is_contiguous() or t.dim() != 1:
+                raise ValueError("CSR arrays must be contiguous 1-D CUDA tensors "
+                                 "(int64 row pointers, int32 indices, float64 values)")
+            if size is not None and t.numel() != size:
+                raise ValueError("row pointer arrays need m + 1 and n + 1 entries")
+        nnz = val.numel()
+        if col_idx.numel() != nnz or t_col_idx.numel() != nnz or t_val.numel() != nnz:
+            raise ValueError("A and A^T must have the same number of nonzeros")
+        self.m, self.n, self.nnz = int(m), int(n), int(nnz)
+        self.shape = (self.m, self.n)
+        self.device = val.device
+        self.tensors = (row_ptr, col_idx, val, t_row_ptr, t_col_idx, t_val)
+        self.struct = plu_csr(self.m, self.n, self.nnz, *(t.data_ptr() for t in self.tensors))
+
+
+def plu_spmm(ctx, A, trans, X, out=None):
+    """Y = A X (trans 0) or A^T X (trans 1) for a CsrMatrix A, FP64."""
+    M = A.n if trans else A.m
+    cols = X.shape[1]
+    out = out if out is not None else colmajor_empty(M, cols, device=X.device)
+    ctx.check(lib().plu_spmm(ctx.handle, ctypes.byref(A.struct), int(trans), _ptr(X), _ld(X), cols,
+                             _ptr(out), _ld(out)))
+    return out
+
+
+def plu_powerlu_csr(ctx, A, k, l, v, seed=0):
+    """Fixed rank on a CsrMatrix A (FP64 sparse passes).  Returns
+    (p, q, L, U, report dict) as plu_powerlu."""
+    torch = _torch()
+    m, n = A.shape
+    p = torch.empty(m, dtype=torch.int32, device=A.device)
+    q = torch.empty(n, dtype=torch.int32, device=A.device)
+    L = colmajor_empty(m, k, device=A.device)
+    U = colmajor_empty(k, n, device=A.device)
+    rep = plu_report()
+    ctx.check(lib().plu_powerlu_csr(ctx.handle, ctypes.byref(A.struct), k, l, v, seed, _ptr(p),
+                                    _ptr(q), _ptr(L), _ld(L), _ptr(U), _ld(U), ctypes.byref(rep)))
+    return p, q, L, U, rep.as_dict()
+
+
+def plu_powerlu_fp_csr(ctx, A, eps, b, l, v, seed=0, precise=False, max_rounds=1):
+    """Fixed precision on a CsrMatrix A.  Returns
+    (k, p, q, L[:, :k], U[:k], met, report dict) as plu_powerlu_fp."""
+    torch = _torch()
+    m, n = A.shape
+    K = l * max_rounds
+    p = torch.empty(m, dtype=torch.int32, device=A.device)
+    q = torch.empty(n, dtype=torch.int32, device=A.device)
+    L = colmajor_empty(m, K, device=A.device)
+    U = colmajor_empty(K, n, device=A.device)
+    rep = plu_report()
+    k = c_int()
+    st = ctx.check(lib().plu_powerlu_fp_csr(
+        ctx.handle, ctypes.byref(A.struct), float(eps), b, l, v, int(bool(precise)), max_rounds,
+        seed, ctypes.byref(k), _ptr(p), _ptr(q), _ptr(L), _ld(L), _ptr(U), _ld(U),
+        ctypes.byref(rep)), allow=(6,))
+    kk = k.value
+    return kk, p, q, L[:, :kk], U[:kk, :], st == 0, rep.as_dict()

@@ -37,6 +37,8 @@ struct plu_ctx {
     std::map<uint64_t, std::vector<int>> batch_tiles;
     std::vector<int> last_tiles;
     int forced_tile = -1;             // a fixed tile shape instead of the autotuner
+    // set while a sparse driver runs: every pass over A is then a sparse product
+    const plu_csr* csr = nullptr;
     static constexpr int64_t kDefaultSpin = 16LL << 20;
 };
 
@@ -134,6 +136,8 @@ plu_status finish(plu_ctx* c) {
 plu_status dev_status_to_plu(plu_ctx* c, int st) {
     if (st == DEV_OK) return PLU_OK;
     if (st == DEV_TIMEOUT) return fail(c, PLU_ETIMEOUT, "a device-side wait ran out of its budget");
+    if (st == DEV_BADINDEX)
+        return fail(c, PLU_EINDEX, "a sparse row pointer or column index is out of range");
     return fail(c, PLU_ENUMERIC, "non-finite value or breakdown in an FP64 factorisation");
 }
 
@@ -160,6 +164,14 @@ plu_status do_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X, 
                    const QuantA* q = nullptr, int accum = 0, const void* xq_pre = nullptr) {
     const int64_t M = trans ? A->n : A->m;
     const int64_t K = trans ? A->m : A->n;
+    if (c->csr) {
+        const plu_csr* S = c->csr;
+        PLU_CUDA(c, launch_spmm_csr(M, K, S->nnz, trans ? S->t_row_ptr : S->row_ptr,
+                                    trans ? S->t_col_idx : S->col_idx, trans ? S->t_val : S->val,
+                                    X, ldx, cols, Y, ldy, ws, ws_cap, c->d_status, c->num_sms,
+                                    c->stream));
+        return PLU_OK;
+    }
     if ((prec == PLU_BF16 || prec == PLU_FP8_E4M3) && q && cols <= 512) {
         PLU_CUDA(c, launch_tc_pass_q(trans, *q, X, ldx, cols, Y, ldy, ws, ws_cap, c->d_status,
                                      c->num_sms, c->stream, accum));
@@ -198,7 +210,8 @@ struct PowerLUPlan {
 // Shared by the fixed-rank and fixed-precision drivers: workspace for
 // Alg. gpowerlu (basis V n x l, products Z m x l, step scratch) and the tail
 // (Alg. bpowerlu steps 4-8) at rank kmax.
-PowerLUPlan plan_powerlu(int64_t m, int64_t n, int l, int kmax, int prec, int sms) {
+PowerLUPlan plan_powerlu(int64_t m, int64_t n, int l, int kmax, int prec, int sms,
+                         bool sparse = false) {
     Layout lay;
     PowerLUPlan p{};
     p.V = lay.add(size_t(n) * l * sizeof(double));
@@ -210,6 +223,10 @@ PowerLUPlan plan_powerlu(int64_t m, int64_t n, int l, int kmax, int prec, int sm
     if (t > step) step = t;
     t = qr_scratch_bytes(n, l, sms);
     if (t > step) step = t;
+    if (sparse) {
+        t = spmm_scratch_bytes(m > n ? m : n, l);
+        if (t > step) step = t;
+    }
     // the mixed modes orthonormalise with tensor-core products (the kmax
     // leading columns at fixed rank, all l columns at fixed precision)
     if (prec != PLU_FP64) {
@@ -388,9 +405,13 @@ plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const do
 }
 
 void fill_pass_report(plu_report* rep, const plu_matrix* A, int passes_l, int l, int k_last,
-                      int prec, bool final_pass) {
-    const double mn = double(A->m) * double(A->n);
-    const double abytes = mn * (A->dtype == PLU_F32 ? 4.0 : 8.0);
+                      int prec, bool final_pass, const plu_csr* sp = nullptr) {
+    // a sparse pass does 2 flops per nonzero and column and reads the CSR
+    // arrays of A or A^T (the larger row-pointer array counted)
+    const double mn = sp ? double(sp->nnz) : double(A->m) * double(A->n);
+    const double abytes =
+        sp ? double(sp->nnz) * 12.0 + double((A->m > A->n ? A->m : A->n) + 1) * 8.0
+           : mn * (A->dtype == PLU_F32 ? 4.0 : 8.0);
     double fl = 2.0 * mn * l * passes_l;
     double by = (abytes + double(A->m + A->n) * l * 8.0) * passes_l;
     if (final_pass) {
@@ -401,6 +422,39 @@ void fill_pass_report(plu_report* rep, const plu_matrix* A, int passes_l, int l,
     rep->flops_passes = fl;
     rep->bytes_passes = by;
 }
+
+}  // namespace
+
+// ---- sparse A
+namespace {
+
+plu_status check_csr(plu_ctx* c, const plu_csr* A) {
+    if (!A) return fail(c, PLU_EINVAL, "A is NULL");
+    if (A->m < 1 || A->n < 1) return fail(c, PLU_EINVAL, "A must be at least 1 x 1");
+    if (A->m > (int64_t(1) << 31) - 1 || A->n > (int64_t(1) << 31) - 1)
+        return fail(c, PLU_EINVAL, "dimensions must fit int32");
+    if (A->nnz < 0) return fail(c, PLU_EINVAL, "nnz < 0");
+    if (!A->row_ptr || !A->t_row_ptr) return fail(c, PLU_EINVAL, "row pointers are NULL");
+    if (A->nnz > 0 && (!A->col_idx || !A->val || !A->t_col_idx || !A->t_val))
+        return fail(c, PLU_EINVAL, "index or value arrays are NULL");
+    return PLU_OK;
+}
+
+// The dense drivers run on A's shape with every pass routed to the sparse
+// product while the guard lives.
+struct CsrScope {
+    plu_ctx* c;
+    plu_matrix shape;
+    CsrScope(plu_ctx* ctx, const plu_csr* A) : c(ctx) {
+        c->csr = A;
+        shape.m = A->m;
+        shape.n = A->n;
+        shape.ld = A->m;
+        shape.dtype = PLU_F64;
+        shape.data = A->row_ptr;
+    }
+    ~CsrScope() { c->csr = nullptr; }
+};
 
 }  // namespace
 
@@ -610,7 +664,7 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
     if (v < 2) return fail(c, PLU_EINVAL, "need v >= 2 passes");
     if (l > 2048) return fail(c, PLU_EINVAL, "l > 2048 is not supported");
     if (!p || !q || !L || !U || ldL < m || ldU < k) return fail(c, PLU_EINVAL, "bad outputs");
-    const PowerLUPlan pl = plan_powerlu(m, n, l, k, prec, c->num_sms);
+    const PowerLUPlan pl = plan_powerlu(m, n, l, k, prec, c->num_sms, c->csr != nullptr);
     PLU_TRY(ensure_ws(c, pl.total));
     char* ws = c->ws;
     double* V = reinterpret_cast<double*>(ws + pl.V);
@@ -655,7 +709,7 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
         rep->normA2 = -1.0;
         rep->info1 = hinfo[0];
         rep->info2 = hinfo[1];
-        fill_pass_report(rep, A, np - 1, l, k, prec, true);
+        fill_pass_report(rep, A, np - 1, l, k, prec, true, c->csr);
         rep->launches = int32_t(g_launches - launches0);
     }
     return finish(c);
@@ -683,7 +737,7 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
     const int K = l * max_rounds;                       // largest possible rank
     if (!k_out || !p || !q || !L || !U || ldL < m || ldU < K)
         return fail(c, PLU_EINVAL, "bad outputs (L needs m x %d, U %d x n)", K, K);
-    const PowerLUPlan pl = plan_powerlu(m, n, l, K, prec, c->num_sms);
+    const PowerLUPlan pl = plan_powerlu(m, n, l, K, prec, c->num_sms, c->csr != nullptr);
     // restart rounds: the union of the bases W (n x K), G = A W (m x K), and
     // the corrections' scratch T (K x l)
     Layout lay;
@@ -707,7 +761,12 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
     if (rep) PLU_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
     // E = ||A||_F^2 (Alg. adaptivewithoutupdating step 1)
     pt.mark();
-    PLU_CUDA(c, launch_norm2(A->data, A->dtype, m, n, A->ld, c->d_scal, nscr, c->num_sms, c->stream));
+    if (c->csr)       // the squares of the nonzeros
+        PLU_CUDA(c, launch_sumsq(c->csr->val, c->csr->nnz, c->d_scal, nscr, c->num_sms,
+                                 c->stream));
+    else
+        PLU_CUDA(c, launch_norm2(A->data, A->dtype, m, n, A->ld, c->d_scal, nscr, c->num_sms,
+                                 c->stream));
     pt.mark();
     int np = 0;
     QuantA qa;
@@ -782,7 +841,7 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
         rep->info1 = hinfo[0];
         rep->info2 = hinfo[1];
         rep->rounds = rounds;
-        fill_pass_report(rep, A, np, l, 0, prec, false);
+        fill_pass_report(rep, A, np, l, 0, prec, false, c->csr);
         rep->launches = int32_t(g_launches - launches0);
     }
     plu_status st = finish(c);
@@ -1077,7 +1136,7 @@ plu_status plu_randlu(plu_ctx* c, const plu_matrix* A, int k, int l, int piter, 
         rep->normA2 = -1.0;
         rep->info1 = hinfo[0];
         rep->info2 = hinfo[1];
-        fill_pass_report(rep, A, np - 1, l, k, prec, true);
+        fill_pass_report(rep, A, np - 1, l, k, prec, true, c->csr);
         rep->launches = int32_t(g_launches - launches0);
     }
     return finish(c);
@@ -1182,6 +1241,40 @@ plu_status plu_batched(plu_ctx* c, const plu_batch_problem* P, int count, plu_pr
         rep->launches = nl;
     }
     return finish(c);
+}
+
+plu_status plu_spmm(plu_ctx* c, const plu_csr* A, int trans, const double* X, int64_t ldx,
+                    int cols, double* Y, int64_t ldy) {
+    PLU_TRY(bind(c));
+    PLU_TRY(check_csr(c, A));
+    const int64_t M = trans ? A->n : A->m;
+    const int64_t K = trans ? A->m : A->n;
+    if (cols < 1 || !X || !Y || ldx < K || ldy < M) return fail(c, PLU_EINVAL, "bad spmm operands");
+    const size_t sw = spmm_scratch_bytes(K, cols);
+    PLU_TRY(ensure_ws(c, sw));
+    CsrScope scope(c, A);
+    PLU_TRY(do_pass(c, &scope.shape, trans, X, ldx, cols, PLU_FP64, Y, ldy, c->ws, sw));
+    return finish(c);
+}
+
+plu_status plu_powerlu_csr(plu_ctx* c, const plu_csr* A, int k, int l, int v, uint64_t seed,
+                           int32_t* p, int32_t* q, double* L, int64_t ldL, double* U,
+                           int64_t ldU, plu_report* rep) {
+    PLU_TRY(bind(c));
+    PLU_TRY(check_csr(c, A));
+    CsrScope scope(c, A);
+    return plu_powerlu(c, &scope.shape, k, l, v, seed, PLU_FP64, p, q, L, ldL, U, ldU, rep);
+}
+
+plu_status plu_powerlu_fp_csr(plu_ctx* c, const plu_csr* A, double eps, int b, int l, int v,
+                              int precise, int max_rounds, uint64_t seed, int* k_out,
+                              int32_t* p, int32_t* q, double* L, int64_t ldL, double* U,
+                              int64_t ldU, plu_report* rep) {
+    PLU_TRY(bind(c));
+    PLU_TRY(check_csr(c, A));
+    CsrScope scope(c, A);
+    return powerlu_fp_rounds(c, &scope.shape, eps, b, l, v, precise, max_rounds, seed, PLU_FP64,
+                             k_out, p, q, L, ldL, U, ldU, rep);
 }
 
 }  // extern "C"

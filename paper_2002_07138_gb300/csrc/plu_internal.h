@@ -16,6 +16,7 @@ enum DevStatus : int {
     DEV_OK = 0,
     DEV_TIMEOUT = 1,     // a grid barrier ran out of its spin budget
     DEV_NUMERIC = 2,     // Cholesky breakdown / non-finite value
+    DEV_BADINDEX = 3,    // a sparse index or row pointer out of range
 };
 
 // Kernels launched by this host thread (the per-call report counts them).
@@ -247,10 +248,25 @@ const char* cholqr_failed_step();
 // Rinv = R^{-1} for an upper triangular n x n R (ld n); Rinv is upper triangular.
 cudaError_t launch_trinv_upper(int n, const double* R, double* Rinv, cudaStream_t s);
 
+// -------------------------------------------------------- sparse passes
+// Y (rows x cols, ld ldy) = S X for S rows x K in CSR (row_ptr rows + 1,
+// col_idx / val nnz entries) and X K x cols (ld ldx), FP64.  The scratch
+// holds the row-major copy of X.  A column index outside [0, K) or a row
+// pointer outside [0, nnz] sets DEV_BADINDEX and the entry is skipped.
+int spmm_row_stride(int cols);
+size_t spmm_scratch_bytes(int64_t K, int cols);
+cudaError_t launch_spmm_csr(int64_t rows, int64_t K, int64_t nnz, const int64_t* row_ptr,
+                            const int32_t* col_idx, const double* val, const double* X,
+                            int64_t ldx, int cols, double* Y, int64_t ldy, void* scratch,
+                            size_t scratch_cap, int* dev_status, int num_sms, cudaStream_t s);
+
 // -------------------------------------------------------- rank and norms
 size_t norm2_scratch_bytes(int num_sms);
 cudaError_t launch_norm2(const void* A, int dtype, int64_t m, int64_t n, int64_t lda,
                          double* out, void* scratch, int num_sms, cudaStream_t s);
+// *out = sum of x[i]^2 over count entries (scratch: norm2_scratch_bytes).
+cudaError_t launch_sumsq(const double* x, int64_t count, double* out, void* scratch,
+                         int num_sms, cudaStream_t s);
 cudaError_t launch_colnorm2(int64_t rows, int cols, const double* G, int64_t ldg,
                             double* out, cudaStream_t s);
 // k/E/met from column norms (one thread): out[0] = k, out[1] = met (ints);

@@ -44,6 +44,19 @@ k_norm2_partial(const T* __restrict__ A, int64_t m, int64_t n, int64_t lda,
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// Sum of squares of a flat array (the nonzeros of a sparse A): CTA b sums
+// the entries b*RT + t + i*gridDim.x*RT in a fixed order.
+__global__ void __launch_bounds__(RT)
+k_sumsq_partial(const double* __restrict__ x, int64_t count, double* __restrict__ part) {
+    __shared__ double sh[RT];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(RT) + threadIdx.x; i < count;
+         i += int64_t(gridDim.x) * RT)
+        acc = fma(x[i], x[i], acc);
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
 __global__ void k_sum_partials(const double* __restrict__ part, int count, double* __restrict__ out) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         double s = 0.0;
@@ -115,6 +128,22 @@ __global__ void k_scatter_rows(int64_t rows, const int32_t* __restrict__ perm,
 }  // namespace
 
 size_t norm2_scratch_bytes(int num_sms) { return size_t(num_sms) * 4 * sizeof(double) + 256; }
+
+cudaError_t launch_sumsq(const double* x, int64_t count, double* out, void* scratch,
+                         int num_sms, cudaStream_t s) {
+    if (count < 0 || (count > 0 && !x)) return cudaErrorInvalidValue;
+    int64_t blocks = (count + RT - 1) / RT;
+    if (blocks > int64_t(num_sms) * 4) blocks = int64_t(num_sms) * 4;
+    if (blocks < 1) blocks = 1;
+    double* part = static_cast<double*>(scratch);
+    count_launch();
+    k_sumsq_partial<<<unsigned(blocks), RT, 0, s>>>(x, count, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_sum_partials<<<1, 32, 0, s>>>(part, int(blocks), out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_norm2(const void* A, int dtype, int64_t m, int64_t n, int64_t lda,
                          double* out, void* scratch, int num_sms, cudaStream_t s) {
