@@ -986,11 +986,15 @@ def run_sparse(args):
     # launches per call: v passes; v - 2 re-orthogonalising LUs (v > 2) and
     # the tail's two LUs of n x k panels
     share = {"spmm": ms_sp * v, "panel_lu": ms_lu * (max(v - 2, 0) + 2)}
+    # the sparse pass issues one FP64 FMA per nonzero and column: at GB300's
+    # FP64 rate that, not HBM (the CSR arrays and two n x l operands) or the
+    # L2 gathers of X's rows, is its bound
     pbytes = sparse_pass_bytes(n, nnz, l)
-    rf_sp = {"bound": "hbm", "achieved": pbytes / ms_sp / 1e6, "peak": peaks["hbm_gbs"],
-             "unit": "GB/s", "peak_source": "measured copy bandwidth",
+    rf_sp = {"bound": "alu", "achieved": 2.0 * nnz * l / ms_sp / 1e9, "peak": 1.25,
+             "unit": "TFLOP/s", "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)",
              "kernel": "k_spmm_csr + k_to_rowmajor", "ms_per_launch": ms_sp,
              "traffic": None, "share_of_step": share["spmm"] / ms_step,
+             "hbm_gbs": pbytes / ms_sp / 1e6, "hbm_frac": pbytes / ms_sp / 1e6 / peaks["hbm_gbs"],
              "l2_gather_gbs": nnz * l * 8.0 / ms_sp / 1e6,
              "note": "the rows of X a pass gathers (nnz x l x 8 B) come from L2"}
     rf_sp["frac"] = rf_sp["achieved"] / rf_sp["peak"]

@@ -268,16 +268,21 @@ plu_status plu_randlu(plu_ctx* ctx, const plu_matrix* A, int k, int l, int piter
                       int64_t ldL, double* U, int64_t ldU, plu_report* rep);
 
 /* plu_powerlu on a sparse A: every pass over A (v of them) is an FP64 sparse
- * product (plu_spmm), everything else as plu_powerlu in PLU_FP64, so the
- * result is that of plu_powerlu on the dense A up to the rounding order of
- * the products.  rep->flops_passes counts 2 nnz flops per column of a pass
- * and rep->bytes_passes the CSR arrays plus the operands. */
+ * product (plu_spmm), everything else as plu_powerlu in PLU_FP64, except
+ * that the dense products between the passes (CholeskyQR's X^T X and
+ * X R^{-1}, the tail's B^T = V_k U_1^T and L = L_1 U_2^T) run as
+ * FP64-accurate sums of exact BF16 slice products on the tensor cores (as
+ * plu_cholqr1 with tc) when k, l <= 512.  The result is that of plu_powerlu
+ * on the dense A in FP64 up to rounding.  rep->flops_passes counts 2 nnz
+ * flops per column of a pass and rep->bytes_passes the CSR arrays plus the
+ * operands. */
 plu_status plu_powerlu_csr(plu_ctx* ctx, const plu_csr* A, int k, int l, int v, uint64_t seed,
                            int32_t* p, int32_t* q, double* L, int64_t ldL, double* U,
                            int64_t ldU, plu_report* rep);
 
-/* plu_powerlu_fp_restart on a sparse A, with FP64 sparse passes
- * (max_rounds = 1 is plu_powerlu_fp); ||A||_F^2 is the sum of val^2. */
+/* plu_powerlu_fp_restart on a sparse A, with FP64 sparse passes and the
+ * products between them as in plu_powerlu_csr (max_rounds = 1 is
+ * plu_powerlu_fp); ||A||_F^2 is the sum of val^2. */
 plu_status plu_powerlu_fp_csr(plu_ctx* ctx, const plu_csr* A, double eps, int b, int l, int v,
                               int precise, int max_rounds, uint64_t seed, int* k_out,
                               int32_t* p, int32_t* q, double* L, int64_t ldL, double* U,

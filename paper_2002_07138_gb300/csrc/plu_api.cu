@@ -226,10 +226,18 @@ PowerLUPlan plan_powerlu(int64_t m, int64_t n, int l, int kmax, int prec, int sm
     if (sparse) {
         t = spmm_scratch_bytes(m > n ? m : n, l);
         if (t > step) step = t;
+        // the tail's slice products at any rank up to kmax
+        for (int kk = 1; kk <= kmax; ++kk)
+            for (const int64_t rows : {m, n})
+                if (oz_supported(rows, kk, sms)) {
+                    t = oz_scratch_bytes(rows, kk, sms);
+                    if (t > step) step = t;
+                }
     }
-    // the mixed modes orthonormalise with tensor-core products (the kmax
-    // leading columns at fixed rank, all l columns at fixed precision)
-    if (prec != PLU_FP64) {
+    // the mixed modes and the sparse path orthonormalise with tensor-core
+    // products (the kmax leading columns at fixed rank, all l columns at
+    // fixed precision)
+    if (prec != PLU_FP64 || sparse) {
         t = qr_scratch_bytes(n, kmax, sms, 1);
         if (t > step) step = t;
         t = qr_scratch_bytes(n, l, sms, 1);
@@ -370,7 +378,7 @@ plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t 
 plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const double* Vk,
                     char* ws, const PowerLUPlan& pl, char* step, int32_t* p, int32_t* q,
                     double* L, int64_t ldL, double* U, int64_t ldU, int32_t* info2dev,
-                    int prec) {
+                    int prec, bool oz = false) {
     double* L1 = reinterpret_cast<double*>(ws + pl.L1);
     double* U1T = reinterpret_cast<double*>(ws + pl.U1T);
     double* BT = reinterpret_cast<double*>(ws + pl.BT);
@@ -384,8 +392,18 @@ plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const do
     // TF32), far above the ~1e-7 the FP32 products add.  The getrf steps stay
     // FP64.
     const bool f32 = prec != PLU_FP64;
+    // oz: the FP64 products as FP64-accurate sums of exact BF16 slice
+    // products on the tensor cores (U1^T and U2^T are stored whole, zeros
+    // above the diagonal, so the dense slice product applies)
+    const bool oz_bt = oz && !f32 && oz_supported(n, k, c->num_sms) &&
+                       oz_scratch_bytes(n, k, c->num_sms) <= pl.step_bytes;
+    const bool oz_l = oz && !f32 && oz_supported(m, k, c->num_sms) &&
+                      oz_scratch_bytes(m, k, c->num_sms) <= pl.step_bytes;
     // B^T = Vk U1^T (U1^T lower triangular)
-    if (f32)
+    if (oz_bt)
+        PLU_CUDA(c, launch_oz_xrinv(n, k, Vk, n, U1T, BT, n, step, pl.step_bytes, c->d_status,
+                                    c->num_sms, c->stream));
+    else if (f32)
         PLU_CUDA(c, launch_gemm_f32_tri(3, n, k, k, Vk, n, U1T, k, BT, n, tp, pl.tailpart_bytes,
                                         c->num_sms, c->stream));
     else
@@ -395,7 +413,10 @@ plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const do
     PLU_CUDA(c, launch_panel_lu(n, k, BT, n, 1, q, U, ldU, 1, U2T, k, 1, info2dev + 1, step,
                                 c->d_status, c->spin_budget, c->num_sms, c->stream));
     // L = L1 U2^T (U2^T lower triangular)
-    if (f32)
+    if (oz_l)
+        PLU_CUDA(c, launch_oz_xrinv(m, k, L1, m, U2T, L, ldL, step, pl.step_bytes, c->d_status,
+                                    c->num_sms, c->stream));
+    else if (f32)
         PLU_CUDA(c, launch_gemm_f32_tri(3, m, k, k, L1, m, U2T, k, L, ldL, tp, pl.tailpart_bytes,
                                         c->num_sms, c->stream));
     else
@@ -680,10 +701,13 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
         PLU_CUDA(c, launch_tc_quantize(prec, static_cast<const float*>(A->data), m, n, A->ld,
                                        ws + pl.quant, &qa, c->num_sms, c->stream));
     // mixed modes: one CholeskyQR round when it is orthogonal enough (see
-    // launch_cholqr2); the FP64 path keeps both rounds
+    // launch_cholqr2); the FP64 path keeps both rounds.  The sparse path (FP64
+    // passes) takes CholeskyQR's products, and the tail's, as FP64-accurate
+    // slice products on the tensor cores: at GB300's FP64 FMA rate they would
+    // outlast the sparse passes.
     PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pl.step_bytes, pt, &np,
                          quant ? &qa : nullptr, k, prec != PLU_FP64 ? 1 : 0,
-                         prec != PLU_FP64 ? 1 : 0));
+                         prec != PLU_FP64 || c->csr ? 1 : 0));
     // Y = A V(:, 1:k) (Alg. bpowerlu step 3), the v-th pass; in the mixed
     // modes it reads the FP32 A through TF32 (it enters the result to first order)
     pt.mark();
@@ -692,7 +716,8 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
     pt.mark();
     ++np;
     int32_t* info = reinterpret_cast<int32_t*>(ws + pl.cn);
-    PLU_TRY(run_tail(c, m, n, k, Z, V, ws, pl, step, p, q, L, ldL, U, ldU, info, prec));
+    PLU_TRY(run_tail(c, m, n, k, Z, V, ws, pl, step, p, q, L, ldL, U, ldU, info, prec,
+                     c->csr != nullptr));
     if (rep) {
         PLU_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
         int32_t hinfo[2] = {0, 0};
@@ -785,7 +810,8 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
         }
         int npr = 0;
         PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pl.step_bytes, pt, &npr,
-                             quant ? &qa : nullptr, l, 0, prec != PLU_FP64 ? 1 : 0, rem, r));
+                             quant ? &qa : nullptr, l, 0, prec != PLU_FP64 || c->csr ? 1 : 0,
+                             rem, r));
         np += npr;
         // G = A V (step 3), the v-th pass.  Its column norms decide the rank:
         // E = ||A||_F^2 - sum ||G(:, j)||^2 must resolve eps^2 ||A||_F^2, which
@@ -821,7 +847,7 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
     const int k = kw;
     int32_t* info = reinterpret_cast<int32_t*>(c->d_kmet + 2);
     PLU_TRY(run_tail(c, m, n, k, multi ? Gu : Z, multi ? Wu : V, ws, pl, step, p, q, L, ldL, U,
-                     ldU, info, prec));
+                     ldU, info, prec, c->csr != nullptr));
     *k_out = k;
     if (rep) {
         PLU_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
