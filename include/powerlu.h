@@ -150,8 +150,9 @@ plu_status plu_pass(plu_ctx* ctx, const plu_matrix* A, int trans, const double* 
 
 /* a2/a4/a6 on a sparse A: Y = A X (trans = 0; X n x cols, Y m x cols) or
  * Y = A^T X (trans = 1, through the CSR of A^T; X m x cols, Y n x cols),
- * FP64.  Each entry of Y is the sum over the nonzeros of its row of S (A or
- * A^T) in CSR order, so the result does not depend on the launch.  X and Y
+ * FP64.  Each entry of Y sums the nonzeros of its row of S (A or A^T) in a
+ * fixed order (alternate nonzeros, in CSR order, into two partial sums that
+ * are then added), so the result does not depend on the launch.  X and Y
  * must not overlap.  PLU_EINDEX: see plu_csr. */
 plu_status plu_spmm(plu_ctx* ctx, const plu_csr* A, int trans, const double* X, int64_t ldx,
                     int cols, double* Y, int64_t ldy);

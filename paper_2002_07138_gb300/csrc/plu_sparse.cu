@@ -3,14 +3,18 @@
 // A^T X), X and Y dense column-major, FP64.
 //
 // X is first copied to row-major (row stride xs = cols rounded up to even,
-// the pad column zero), so that a warp reads one contiguous row of X per
-// nonzero with 16-byte loads.  A CTA owns 32 rows of Y; each warp sums its
-// rows' nonzeros in CSR order (so the result does not depend on the launch),
-// the lanes of a warp splitting the columns, with the nonzeros' indices and
-// values loaded 32 at a time and broadcast by shuffles.  The 32 rows are
-// staged in shared memory and written to the column-major Y in 256-byte
-// column segments.  A column index outside [0, K) or a row pointer outside
-// [0, nnz] sets DEV_BADINDEX in the status word and the entry is skipped.
+// the pad column zero), so that a half-warp reads one contiguous stretch of
+// a row of X per nonzero.  A CTA owns 32 rows of Y and a warp one row at a
+// time: its nonzeros' indices and values are loaded 32 at a time and
+// broadcast by shuffles, the two half-warps take alternate nonzeros (each
+// lane owning every 16th column), and the halves' sums are added at the end
+// -- a fixed order, so the result does not depend on the launch.  The pass
+// issues one FP64 FMA per nonzero and column, and GB300's FP64 pipe is its
+// bound: the 16-column granularity keeps the issued FMAs within 16 columns
+// of the useful ones (l = 200: 208 of 200).  The 32 rows are staged in
+// shared memory and written to the column-major Y in 256-byte column
+// segments.  A column index outside [0, K) or a row pointer outside [0, nnz]
+// sets DEV_BADINDEX in the status word and the entry is skipped.
 #include "plu_internal.h"
 
 namespace plu {
@@ -18,9 +22,9 @@ namespace {
 
 constexpr int SP_ROWS = 32;       // rows of Y per CTA
 constexpr int SP_WARPS = 8;
-constexpr int SP_CHUNK = 256;     // columns of Y per sweep of a row (4 double2 per lane)
+constexpr int SP_CHUNK = 208;     // columns of Y per sweep of a row (13 per lane)
 constexpr int SP_SMEM = SP_ROWS * (SP_CHUNK + 1) * int(sizeof(double));
-constexpr int SP_CTAS_PER_SM = 2;   // 120 registers x 256 threads: two CTAs an SM
+constexpr int SP_CTAS_PER_SM = 2;   // 124 registers x 256 threads: two CTAs an SM
 
 // Xr (K x xs, row-major) = X (K x cols, column-major, ld); Xr[r * xs + cols]
 // is zeroed when xs > cols.
@@ -53,24 +57,30 @@ k_spmm_csr(int64_t rows, int64_t K, int64_t nnz, int cols, int xs,
            double* __restrict__ Y, int64_t ldy, int* status) {
     extern __shared__ double ys[];            // SP_ROWS x (SP_CHUNK + 1)
     constexpr int YS = SP_CHUNK + 1;
+    constexpr int NCM = SP_CHUNK / 16;        // column slots of a lane
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the two half-warps take alternate nonzeros; lane `sub` of a half owns
+    // the columns sub, sub + 16, ... of the chunk
+    const int grp = lane >> 4, sub = lane & 15;
     const unsigned full = 0xffffffffu;
     for (int64_t R0 = int64_t(blockIdx.x) * SP_ROWS; R0 < rows;
          R0 += int64_t(gridDim.x) * SP_ROWS) {
         for (int c0 = 0; c0 < cols; c0 += SP_CHUNK) {
             const int ch = cols - c0 < SP_CHUNK ? cols - c0 : SP_CHUNK;
+            const int nc = (ch + 15) >> 4;    // slots in use: a warp-uniform bound,
+                                              // so unused slots issue no FMA
             for (int rr = warp; rr < SP_ROWS; rr += SP_WARPS) {
                 const int64_t r = R0 + rr;
-                double2 acc[4];
+                double acc[NCM];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
+                for (int i = 0; i < NCM; ++i) acc[i] = 0.0;
                 if (r < rows) {
                     int64_t b = row_ptr[r], e = row_ptr[r + 1];
                     if (b < 0 || e > nnz || b > e) {
                         if (lane == 0) flag_bad_index(status);
                         b = e = 0;
                     }
-                    const double* xbase = Xr + c0 + 2 * lane;
+                    const double* xbase = Xr + c0 + sub;
                     for (int64_t t0 = b; t0 < e; t0 += 32) {
                         const int64_t t = t0 + lane;
                         int col = 0;
@@ -85,39 +95,34 @@ k_spmm_csr(int64_t rows, int64_t K, int64_t nnz, int cols, int xs,
                             }
                         }
                         const int cnt = e - t0 < 32 ? int(e - t0) : 32;
-                        // 4 nonzeros per step: their 16 row loads are issued together
-                        for (int j0 = 0; j0 < cnt; j0 += 4) {
-                            double2 x[4][4];
-                            double aj[4];
+                        // 2 nonzeros per step, one per half-warp
+                        for (int j0 = 0; j0 < cnt; j0 += 2) {
+                            const int j = j0 + grp;
+                            const int cj = __shfl_sync(full, col, j & 31);
+                            const double av = __shfl_sync(full, a, j & 31);
+                            const double aj = j < cnt ? av : 0.0;
+                            const double* xr = xbase + int64_t(j < cnt ? cj : 0) * xs;
+                            double x[NCM];
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const int j = j0 + u;     // lanes j >= cnt hold col 0, a 0
-                                const int cj = __shfl_sync(full, col, j & 31);
-                                aj[u] = __shfl_sync(full, a, j & 31);
-                                if (j >= cnt) aj[u] = 0.0;
-                                const double* xr = xbase + int64_t(j < cnt ? cj : 0) * xs;
+                            for (int i = 0; i < NCM; ++i)
+                                if (i < nc) x[i] = (sub + 16 * i < ch) ? xr[16 * i] : 0.0;
 #pragma unroll
-                                for (int q = 0; q < 4; ++q)
-                                    x[u][q] = (2 * lane + 64 * q < ch)
-                                                  ? *reinterpret_cast<const double2*>(xr + 64 * q)
-                                                  : make_double2(0.0, 0.0);
-                            }
-#pragma unroll
-                            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                                for (int q = 0; q < 4; ++q) {
-                                    acc[q].x = fma(aj[u], x[u][q].x, acc[q].x);
-                                    acc[q].y = fma(aj[u], x[u][q].y, acc[q].y);
-                                }
+                            for (int i = 0; i < NCM; ++i)
+                                if (i < nc) acc[i] = fma(aj, x[i], acc[i]);
                         }
                     }
                 }
-                double* yrow = ys + rr * YS;
+                // the second half-warp's sums join the first's
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int c = 2 * lane + 64 * q;
-                    if (c < ch) yrow[c] = acc[q].x;
-                    if (c + 1 < ch) yrow[c + 1] = acc[q].y;
+                for (int i = 0; i < NCM; ++i)
+                    if (i < nc) acc[i] += __shfl_down_sync(full, acc[i], 16);
+                if (grp == 0) {
+                    double* yrow = ys + rr * YS;
+#pragma unroll
+                    for (int i = 0; i < NCM; ++i) {
+                        const int c = sub + 16 * i;
+                        if (i < nc && c < ch) yrow[c] = acc[i];
+                    }
                 }
             }
             __syncthreads();
