@@ -1049,7 +1049,8 @@ def sparse_oracle_sample(n, rp, ci, val, seed):
     oracle.lu_permuted_L(Y)
     dt = time.perf_counter() - t0
     return dt, 2.0 * int(rp[-1]) * l, ("the oracle's first pass of Alg. gpowerlu (A^T Omega "
-                                       "from the CSR, FP64) and its LU re-orthogonalisation")
+                                       "from the CSR, FP64, on one core) and its LU "
+                                       "re-orthogonalisation (numpy BLAS threads)")
 
 
 def run_reference_sparse(args):
