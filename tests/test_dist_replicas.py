@@ -76,3 +76,15 @@ def test_reference_arm_prints_on_rank_0_only():
     rec = json.loads(lines0[0])
     assert rec["impl"] == "reference" and rec["value"] > 0
     assert rec["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_sparse_replicas_draw_different_matrices():
+    """The sparse workload's rank r factors the sprand draw of seed 0 + r."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    a = bench.sparse_host(bench.SPARSE["seed"])
+    b = bench.sparse_host(bench.SPARSE["seed"] + 1)
+    n = bench.SPARSE["n"]
+    assert a[0].size == n + 1 and b[0].size == n + 1
+    assert not (a[0].size == b[0].size and np.array_equal(a[1], b[1]))

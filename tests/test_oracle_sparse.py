@@ -162,3 +162,21 @@ def test_powerlu_fp_sparse_finds_rank():
     k, p, q, L, U, E, met = powerlu_fp(S, 1e-6, 1, 20, 3, seed=4)
     assert met and k == r
     assert rel_lu_error(A, p, q, L, U) < 1e-10
+
+
+def test_powerlu_fp_restart_sparse_equals_dense():
+    """The restart on the remainder (two rounds) gives the same rank, pivots
+    and factors on the sparse passes as on the dense A."""
+    m, n = 300, 220
+    rp, ci, val = synth.sprand_csr(m, n, 0.03, seed=21)
+    A = synth.csr_to_dense(m, n, rp, ci, val)
+    S = SparsePassCounter(m, n, rp, ci, val)
+    ks, ps, qs, Ls, Us, Es, mets = powerlu_fp(S, 0.05, 4, 12, 3, seed=8, max_rounds=2)
+    kd, pd, qd, Ld, Ud, Ed, metd = powerlu_fp(PassCounter(A), 0.05, 4, 12, 3, seed=8,
+                                                max_rounds=2)
+    assert ks == kd == 24 and not mets and not metd
+    np.testing.assert_array_equal(ps, pd)
+    np.testing.assert_array_equal(qs, qd)
+    assert np.linalg.norm(Ls - Ld) <= 1e-12 * np.linalg.norm(Ld)
+    assert np.linalg.norm(Us - Ud) <= 1e-12 * np.linalg.norm(Ud)
+    assert abs(Es - Ed) <= 1e-10 * S.frob2()
