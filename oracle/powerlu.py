@@ -255,7 +255,11 @@ def basic_power_iteration_lu(A, l, p, seed):
 
 def randlu(A, k, l, p, seed):
     """Alg. rlu with steps 1-3 replaced by Alg. basicpoweriteration.
-    Returns (P, Q, L, U) as index vectors: A[P][:, Q] ~= L U."""
+    Returns (P, Q, L, U) as index vectors: A[P][:, Q] ~= L U.
+    Pinned by: the pass count 2p + 2; Thm. acc:t (same range as PowerLU);
+    the tail identity L U = (Pi P A) Q^T with Pi the orthogonal projector
+    onto range(L_y(:, 1:k)) (Eq. pseudoinverse); exact reconstruction of a
+    rank-k A; U unit upper with |u_ij| <= 1 and L lower trapezoidal."""
     Ac = _wrap(A)
     perm, Ly, Uy = basic_power_iteration_lu(Ac, l, p, seed)
     Ly = Ly[:, :k]
@@ -272,8 +276,10 @@ def randlu(A, k, l, p, seed):
 
 def singlepass(A, k, seed):
     """Alg. singlepasslu.  Returns (p, q, L, U): A[p][:, q] ~= L U.
-    Parity unpinned beyond H = A A^T Omega, the column-streaming form of
-    Sec. 5 (Eqs. gi, hi) and the structural invariants."""
+    Pinned by: H = A A^T Omega and the column-streaming form of Sec. 5
+    (Eqs. gi, hi); the identity L U = P (A P_G) Q^T with P_G the orthogonal
+    projector onto range(A^T Omega), which holds in exact arithmetic; the
+    structural invariants and the Eckart-Young lower bound."""
     Ac = _wrap(A)
     m, n = Ac.shape
     Omega = gaussian_matrix(m, k, seed, STREAM_OMEGA_SP)
