@@ -347,8 +347,10 @@ plu_status plu_set_batched_tile(plu_ctx* ctx, int bm, int bn);
  * rejected with PLU_EINVAL and a message.  The work is enqueued on
  * `cuda_stream` (a cudaStream_t, NULL = legacy default stream) of the current
  * device; the call then synchronises that stream and returns the device
- * status (PLU_ETIMEOUT, PLU_ENUMERIC).  The first call on a device looks up
- * the array's device address: make it before any stream capture.  All calls
+ * status (PLU_ETIMEOUT, PLU_ENUMERIC).  The first call in each CUDA context
+ * of a device (so the first call on the device, and the first one after a
+ * device reset) looks up the array's device address: make that call before
+ * any stream capture begins.  All calls
  * share the array, so calls whose GPU work overlaps race; each call clears
  * what must start at zero.  err (host buffer of err_len bytes, nullable)
  * receives a message on failure.

@@ -13,14 +13,20 @@
 // (2 MiB), which every GPU that loads the library holds until the process
 // exits.  Hence the size limits: rows <= 65536 and cols <= 256.
 //
-// Set-up: the first call on a device, with that device current, looks up the
-// device address of the array (cudaGetSymbolAddress) and the SM count; make
-// that first call before any stream capture.  Every call shares the array and
+// Set-up: the first call in each CUDA context of a device (the device
+// current) looks up the device address of the array (cudaGetSymbolAddress)
+// and the SM count; make that first call before any stream capture.  The
+// cached address is tied to the context's unique id, so after a device reset
+// (a new primary context, in which the module and its array may sit
+// elsewhere) the next call repeats the set-up.  Every call shares the array and
 // finds the previous call's contents there; the call clears what must start
 // at zero (the status word and the barrier header).  Calls whose work overlaps
 // on the GPU (on different streams, or from several host threads without
 // ordering) race on the array and must not be issued.
 #include "plu_internal.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include <cstdarg>
 #include <cstdio>
@@ -38,11 +44,37 @@ static __device__ __align__(256) unsigned char g_plu_static_scratch[kStaticBytes
 
 struct DeviceSlot {
     bool ready = false;
-    char* base = nullptr;      // device address of g_plu_static_scratch on that device
+    unsigned long long ctx_id = 0;   // unique id of the context the address belongs to
+    char* base = nullptr;            // device address of g_plu_static_scratch on that device
     int num_sms = 0;
 };
 DeviceSlot g_slots[kMaxDevices];
 std::mutex g_mutex;
+
+// Unique id of the calling thread's current context (0 when the driver does
+// not report one: the set-up then runs on every call).
+unsigned long long current_ctx_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+        looked = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_cur || !get_id || get_cur(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 plu_status say(char* err, size_t err_len, plu_status st, const char* fmt, ...) {
     if (err && err_len > 0) {
@@ -78,7 +110,9 @@ extern "C" plu_status plu_lu_reorth_static(void* cuda_stream, int64_t rows, int 
     DeviceSlot slot;
     {
         std::lock_guard<std::mutex> lock(g_mutex);
-        if (!g_slots[dev].ready) {
+        // 0 before the runtime has made the device's primary context current
+        const unsigned long long id = current_ctx_id();
+        if (!g_slots[dev].ready || id == 0 || g_slots[dev].ctx_id != id) {
             void* ptr = nullptr;
             e = cudaGetSymbolAddress(&ptr, g_plu_static_scratch);
             if (e != cudaSuccess)
@@ -89,6 +123,7 @@ extern "C" plu_status plu_lu_reorth_static(void* cuda_stream, int64_t rows, int 
                 return say(err, err_len, PLU_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
             g_slots[dev].base = static_cast<char*>(ptr);
             g_slots[dev].num_sms = sms;
+            g_slots[dev].ctx_id = current_ctx_id();   // the lookup made the context current
             g_slots[dev].ready = true;
         }
         slot = g_slots[dev];
