@@ -126,6 +126,18 @@ plu_status plu_check(plu_ctx* ctx);
  * the default (about a second).  A tiny budget makes the waits give up and
  * the call return PLU_ETIMEOUT, with the context still usable. */
 plu_status plu_set_wait_budget(plu_ctx* ctx, int64_t spins);
+/* How every panel LU of the context (the re-orthogonalising lu of
+ * Alg. gpowerlu, the getrf steps of Alg. bpowerlu / powerlufp / rlu /
+ * singlepasslu, plu_lu_reorth, plu_getrf) forms its trailing updates between
+ * 32-column blocks: mode 0 with FP64 FMAs; mode 1 on the tensor cores, as
+ * sums of exact FP16 digit products rounded once to FP64 (FP64-accurate: the
+ * error stays below an FP64 dot product's rounding bound); mode -1 (the
+ * default) mode 1 for the mixed-precision modes and the sparse path, mode 0
+ * for the FP64 path.  The pivot rule (largest |x|, ties to the first row in
+ * the current order) and the outputs are the same in both modes; shapes the
+ * tensor-core kernels do not take (more than 2048 columns, or too many rows
+ * per SM for shared memory) use mode 0.  PLU_EINVAL for another mode. */
+plu_status plu_set_lu_updates(plu_ctx* ctx, int mode);
 
 /* ---------------------------------------------------------------------
  * Steps of the hot path, one entry point each (Sec. 3, Alg. gpowerlu).

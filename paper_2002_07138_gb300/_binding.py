@@ -61,6 +61,7 @@ SIGNATURES = {
     "plu_set_async": (c_int, [c_vp, c_int]),
     "plu_check": (c_int, [c_vp]),
     "plu_set_wait_budget": (c_int, [c_vp, c_i64]),
+    "plu_set_lu_updates": (c_int, [c_vp, c_int]),
     "plu_gaussian": (c_int, [c_vp, c_i64, c_i64, c_u64, c_u32, c_vp, c_i64]),
     "plu_pass": (c_int, [c_vp, ctypes.POINTER(plu_matrix), c_int, c_vp, c_i64, c_int, c_int,
                          c_vp, c_i64]),
@@ -196,6 +197,10 @@ class Context:
 
     def set_wait_budget(self, spins):
         return self.check(lib().plu_set_wait_budget(self._h, int(spins)))
+
+    def set_lu_updates(self, mode):
+        """-1: default, 0: FP64 FMAs, 1: tensor-core digit products."""
+        return self.check(lib().plu_set_lu_updates(self._h, int(mode)))
 
 
 # ------------------------------------------------------------ entry points

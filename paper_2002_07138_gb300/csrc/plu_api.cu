@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -37,6 +38,9 @@ struct plu_ctx {
     std::map<uint64_t, std::vector<int>> batch_tiles;
     std::vector<int> last_tiles;
     int forced_tile = -1;             // a fixed tile shape instead of the autotuner
+    // panel LU trailing updates: -1 default (tensor cores in the mixed modes and
+    // on the sparse path, FP64 FMAs in the FP64 path), 0 FP64 FMAs, 1 tensor cores
+    int lu_tc = -1;
     // set while a sparse driver runs: every pass over A is then a sparse product
     const plu_csr* csr = nullptr;
     static constexpr int64_t kDefaultSpin = 16LL << 20;
@@ -144,6 +148,29 @@ plu_status dev_status_to_plu(plu_ctx* c, int st) {
 // ---- workspace needs of the steps
 bool is_tc(int prec) { return prec == PLU_TF32 || prec == PLU_BF16 || prec == PLU_FP8_E4M3; }
 
+// Scratch of a panel LU of either kind (FP64 FMA updates or tensor-core updates).
+size_t lu_scratch_bytes(int64_t rows, int cols) {
+    const size_t a = panel_scratch_bytes(rows, cols), b = tclu_scratch_bytes(rows, cols);
+    return a > b ? a : b;
+}
+
+// The panel LU of a step: trailing updates on the tensor cores (FP64-accurate
+// exact digit products, plu_tclu.cu) when the context asks for them, and by
+// default in the mixed-precision modes and on the sparse path (which already
+// takes its other FP64 products that way); FP64 FMAs otherwise.  Both give
+// the same pivot rule and outputs.
+cudaError_t launch_lu(const plu_ctx* c, int prec, int64_t rows, int cols, double* X, int64_t ldx,
+                      int mode, int32_t* perm, double* L, int64_t ldL, int l_trans, double* U,
+                      int64_t ldU, int u_trans, int32_t* info, void* scratch, int* dev_status,
+                      int64_t spin_budget, int num_sms, cudaStream_t s) {
+    const bool want = c->lu_tc == 1 || (c->lu_tc < 0 && (prec != PLU_FP64 || c->csr != nullptr));
+    if (want && tclu_supported(rows, cols, num_sms))
+        return launch_panel_lu_tc(rows, cols, X, ldx, mode, perm, L, ldL, l_trans, U, ldU, u_trans,
+                                  info, scratch, dev_status, spin_budget, num_sms, s);
+    return launch_panel_lu(rows, cols, X, ldx, mode, perm, L, ldL, l_trans, U, ldU, u_trans, info,
+                           scratch, dev_status, spin_budget, num_sms, s);
+}
+
 size_t pass_ws(int64_t M, int64_t N, int64_t K, int prec, int sms) {
     const int sprec = is_tc(prec) ? PLU_FP32 : prec;
     size_t b = gemm_partials_bytes(M, N, K, sprec, sms) + 256;
@@ -201,6 +228,46 @@ plu_status do_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X, 
     return PLU_OK;
 }
 
+// Largest scratch over every rank 1..kmax the tail (and, on the sparse path,
+// its slice products) may run at.  Neither size is monotone in the rank (the
+// split count of a product changes with its shape), so every rank is
+// evaluated; the result is kept per shape, so a driver pays the scan once.
+struct TailScratchKey {
+    int64_t m, n;
+    int kmax, sms;
+    bool oz;
+    bool operator<(const TailScratchKey& o) const {
+        if (m != o.m) return m < o.m;
+        if (n != o.n) return n < o.n;
+        if (kmax != o.kmax) return kmax < o.kmax;
+        if (sms != o.sms) return sms < o.sms;
+        return oz < o.oz;
+    }
+};
+
+size_t tail_scratch_max(int64_t m, int64_t n, int kmax, int sms, bool oz) {
+    static std::mutex mu;
+    static std::map<TailScratchKey, size_t> memo;
+    const TailScratchKey key{m, n, kmax, sms, oz};
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = memo.find(key);
+        if (it != memo.end()) return it->second;
+    }
+    size_t best = 0;
+    for (int kk = 1; kk <= kmax; ++kk)
+        for (const int64_t rows : {m, n}) {
+            size_t t;
+            if (oz) t = oz_supported(rows, kk, sms) ? oz_scratch_bytes(rows, kk, sms) : 0;
+            else t = gemm_f64_partials_bytes(rows, kk, kk, sms);
+            if (t > best) best = t;
+        }
+    std::lock_guard<std::mutex> lock(mu);
+    if (memo.size() > 256) memo.clear();
+    memo[key] = best;
+    return best;
+}
+
 struct PowerLUPlan {
     // offsets into the workspace
     size_t V, Z, step, L1, U1T, BT, U2T, tailpart, cn, quant, total;
@@ -219,7 +286,7 @@ PowerLUPlan plan_powerlu(int64_t m, int64_t n, int l, int kmax, int prec, int sm
     size_t step = pass_ws(m, l, n, prec, sms);
     size_t t = pass_ws(n, l, m, prec, sms);
     if (t > step) step = t;
-    t = panel_scratch_bytes(m > n ? m : n, l);
+    t = lu_scratch_bytes(m > n ? m : n, l);
     if (t > step) step = t;
     t = qr_scratch_bytes(n, l, sms);
     if (t > step) step = t;
@@ -227,12 +294,8 @@ PowerLUPlan plan_powerlu(int64_t m, int64_t n, int l, int kmax, int prec, int sm
         t = spmm_scratch_bytes(m > n ? m : n, l);
         if (t > step) step = t;
         // the tail's slice products at any rank up to kmax
-        for (int kk = 1; kk <= kmax; ++kk)
-            for (const int64_t rows : {m, n})
-                if (oz_supported(rows, kk, sms)) {
-                    t = oz_scratch_bytes(rows, kk, sms);
-                    if (t > step) step = t;
-                }
+        t = tail_scratch_max(m, n, kmax, sms, true);
+        if (t > step) step = t;
     }
     // the mixed modes and the sparse path orthonormalise with tensor-core
     // products (the kmax leading columns at fixed rank, all l columns at
@@ -251,13 +314,7 @@ PowerLUPlan plan_powerlu(int64_t m, int64_t n, int l, int kmax, int prec, int sm
     p.U2T = lay.add(size_t(kmax) * kmax * sizeof(double));
     // the tail runs at any rank k <= kmax (fixed precision): the largest
     // preferred partial-sum size over those ranks
-    size_t tp = 0;
-    for (int kk = 1; kk <= kmax; ++kk) {
-        t = gemm_f64_partials_bytes(n, kk, kk, sms);
-        if (t > tp) tp = t;
-        t = gemm_f64_partials_bytes(m, kk, kk, sms);
-        if (t > tp) tp = t;
-    }
+    const size_t tp = tail_scratch_max(m, n, kmax, sms, false);
     p.tailpart = lay.add(tp);
     p.tailpart_bytes = tp;
     p.cn = lay.add(size_t(l) * sizeof(double) + norm2_scratch_bytes(sms));
@@ -341,7 +398,7 @@ plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t 
         return PLU_OK;
     };
     auto reorth = [&](int64_t rows, double* X) -> plu_status {
-        PLU_CUDA(c, launch_panel_lu(rows, l, X, rows, 0, nullptr, nullptr, 0, 0, nullptr, 0, 0,
+        PLU_CUDA(c, launch_lu(c, prec, rows, l, X, rows, 0, nullptr, nullptr, 0, 0, nullptr, 0, 0,
                                     nullptr, step, c->d_status, c->spin_budget, c->num_sms,
                                     c->stream));
         return PLU_OK;
@@ -385,7 +442,7 @@ plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const do
     double* U2T = reinterpret_cast<double*>(ws + pl.U2T);
     void* tp = ws + pl.tailpart;
     // [L1, U1, P] = lu(Y)
-    PLU_CUDA(c, launch_panel_lu(m, k, Y, m, 1, p, L1, m, 0, U1T, k, 1, info2dev, step, c->d_status,
+    PLU_CUDA(c, launch_lu(c, prec, m, k, Y, m, 1, p, L1, m, 0, U1T, k, 1, info2dev, step, c->d_status,
                                 c->spin_budget, c->num_sms, c->stream));
     // The two m x k x k products take FP32 FMAs when the passes are not FP64:
     // Y itself then carries the pass precision's rounding (2^-11 relative for
@@ -410,7 +467,7 @@ plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const do
         PLU_CUDA(c, launch_gemm_f64_tri(0, 3, n, k, k, Vk, n, U1T, k, BT, n, tp,
                                         pl.tailpart_bytes, c->num_sms, c->stream));
     // [L2, U2, Q] = lu(B^T); U = L2^T written straight into U
-    PLU_CUDA(c, launch_panel_lu(n, k, BT, n, 1, q, U, ldU, 1, U2T, k, 1, info2dev + 1, step,
+    PLU_CUDA(c, launch_lu(c, prec, n, k, BT, n, 1, q, U, ldU, 1, U2T, k, 1, info2dev + 1, step,
                                 c->d_status, c->spin_budget, c->num_sms, c->stream));
     // L = L1 U2^T (U2^T lower triangular)
     if (oz_l)
@@ -551,6 +608,13 @@ plu_status plu_set_wait_budget(plu_ctx* c, int64_t spins) {
     return PLU_OK;
 }
 
+plu_status plu_set_lu_updates(plu_ctx* c, int mode) {
+    if (!c) return PLU_EINVAL;
+    if (mode < -1 || mode > 1) return fail(c, PLU_EINVAL, "lu update mode must be -1, 0 or 1");
+    c->lu_tc = mode;
+    return PLU_OK;
+}
+
 plu_status plu_check(plu_ctx* c) {
     PLU_TRY(bind(c));
     PLU_CUDA(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -596,8 +660,8 @@ plu_status plu_lu_reorth(plu_ctx* c, int64_t rows, int cols, double* X, int64_t 
     PLU_TRY(bind(c));
     if (cols < 1 || rows < cols || !X || ldx < rows || cols > 2048)
         return fail(c, PLU_EINVAL, "lu_reorth needs rows >= cols >= 1, cols <= 2048, ldx >= rows");
-    PLU_TRY(ensure_ws(c, panel_scratch_bytes(rows, cols)));
-    PLU_CUDA(c, launch_panel_lu(rows, cols, X, ldx, 0, nullptr, nullptr, 0, 0, nullptr, 0, 0, nullptr,
+    PLU_TRY(ensure_ws(c, lu_scratch_bytes(rows, cols)));
+    PLU_CUDA(c, launch_lu(c, PLU_FP64, rows, cols, X, ldx, 0, nullptr, nullptr, 0, 0, nullptr, 0, 0, nullptr,
                                 c->ws, c->d_status, c->spin_budget, c->num_sms, c->stream));
     return finish(c);
 }
@@ -608,8 +672,8 @@ plu_status plu_getrf(plu_ctx* c, int64_t rows, int cols, double* X, int64_t ldx,
     if (cols < 1 || rows < cols || !X || ldx < rows || cols > 2048 || !perm || !L || !U ||
         ldL < rows || ldU < cols)
         return fail(c, PLU_EINVAL, "getrf needs rows >= cols >= 1, cols <= 2048 and valid outputs");
-    PLU_TRY(ensure_ws(c, panel_scratch_bytes(rows, cols)));
-    PLU_CUDA(c, launch_panel_lu(rows, cols, X, ldx, 1, perm, L, ldL, 0, U, ldU, 0, info, c->ws,
+    PLU_TRY(ensure_ws(c, lu_scratch_bytes(rows, cols)));
+    PLU_CUDA(c, launch_lu(c, PLU_FP64, rows, cols, X, ldx, 1, perm, L, ldL, 0, U, ldU, 0, info, c->ws,
                                 c->d_status, c->spin_budget, c->num_sms, c->stream));
     return finish(c);
 }
@@ -928,7 +992,7 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
         t = pass_ws(m, k, w, prec, c->num_sms);
         if (t > step) step = t;
     }
-    t = panel_scratch_bytes(m > n ? m : n, k);
+    t = lu_scratch_bytes(m > n ? m : n, k);
     if (t > step) step = t;
     t = qr_scratch_bytes(n, k, c->num_sms, prec != PLU_FP64 ? 1 : 0);
     if (t > step) step = t;
@@ -981,7 +1045,7 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
     }
     pt.mark();
     // [L1, U1, P] = lu(H)
-    PLU_CUDA(c, launch_panel_lu(m, k, H, m, 1, p, L1, m, 0, U1T, k, 1, info, stepp, c->d_status,
+    PLU_CUDA(c, launch_lu(c, prec, m, k, H, m, 1, p, L1, m, 0, U1T, k, 1, info, stepp, c->d_status,
                                 c->spin_budget, c->num_sms, c->stream));
     // G^{dagger T} = G (G^T G)^{-1} = Q1 R^{-T} with one CholeskyQR round,
     // G = Q1 R and R^T R = G^T G (in place: G becomes Q1)
@@ -1001,7 +1065,7 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
         PLU_CUDA(c, launch_gemm_f64_tri(0, 3, n, k, k, G, n, S, k, Wb, n, tpp, tp, c->num_sms,
                                         c->stream));
     // [L2, U2, Q] = lu(M), U = L2^T
-    PLU_CUDA(c, launch_panel_lu(n, k, Wb, n, 1, q, U, ldU, 1, U2T, k, 1, info + 1, stepp,
+    PLU_CUDA(c, launch_lu(c, prec, n, k, Wb, n, 1, q, U, ldU, 1, U2T, k, 1, info + 1, stepp,
                                 c->d_status, c->spin_budget, c->num_sms, c->stream));
     // L = L1 U2^T (U2^T lower triangular)
     if (f32)
@@ -1065,7 +1129,7 @@ plu_status plu_randlu(plu_ctx* c, const plu_matrix* A, int k, int l, int piter, 
     if (t > step) step = t;
     t = pass_ws(n, k, m, prec, sms);
     if (t > step) step = t;
-    t = panel_scratch_bytes(m > n ? m : n, l);
+    t = lu_scratch_bytes(m > n ? m : n, l);
     if (t > step) step = t;
     t = qr_scratch_bytes(m, k, sms, prec != PLU_FP64 ? 1 : 0);
     if (t > step) step = t;
@@ -1110,7 +1174,7 @@ plu_status plu_randlu(plu_ctx* c, const plu_matrix* A, int k, int l, int piter, 
         return PLU_OK;
     };
     auto reorth = [&](int64_t rows, double* Xr) -> plu_status {
-        PLU_CUDA(c, launch_panel_lu(rows, l, Xr, rows, 0, nullptr, nullptr, 0, 0, nullptr, 0, 0,
+        PLU_CUDA(c, launch_lu(c, prec, rows, l, Xr, rows, 0, nullptr, nullptr, 0, 0, nullptr, 0, 0,
                                     nullptr, stepp, c->d_status, c->spin_budget, sms, c->stream));
         return PLU_OK;
     };
@@ -1125,7 +1189,7 @@ plu_status plu_randlu(plu_ctx* c, const plu_matrix* A, int k, int l, int piter, 
         if (i < piter) PLU_TRY(reorth(m, Y));
     }
     // P Y = L_y U_y (full LU of the m x l product); L_y = its first k columns
-    PLU_CUDA(c, launch_panel_lu(m, l, Y, m, 1, p, L1, m, 0, Ul, l, 1, info, stepp, c->d_status,
+    PLU_CUDA(c, launch_lu(c, prec, m, l, Y, m, 1, p, L1, m, 0, Ul, l, 1, info, stepp, c->d_status,
                                 c->spin_budget, sms, c->stream));
     // B^T = (L_y^+ P A)^T = A^T W (W^T W)^{-1} with W = P^T L_y = Q R:
     // B^T = A^T Q R^{-T}.  The pass reads the FP32 A through TF32 in the
@@ -1137,7 +1201,7 @@ plu_status plu_randlu(plu_ctx* c, const plu_matrix* A, int k, int l, int piter, 
     PLU_CUDA(c, launch_trinv_upper(k, R, Rinv, c->stream));
     PLU_CUDA(c, launch_gemm_f64(0, 1, n, k, k, T, n, Rinv, k, BT, n, tpp, tp, sms, c->stream));
     // Q B^T = L' U' (Alg. rlu step 5); U = L'^T written straight into U
-    PLU_CUDA(c, launch_panel_lu(n, k, BT, n, 1, q, U, ldU, 1, U2T, k, 1, info + 1, stepp,
+    PLU_CUDA(c, launch_lu(c, prec, n, k, BT, n, 1, q, U, ldU, 1, U2T, k, 1, info + 1, stepp,
                                 c->d_status, c->spin_budget, sms, c->stream));
     // L = L_y U'^T (U'^T lower triangular)
     if (prec != PLU_FP64)

@@ -212,7 +212,16 @@ cudaError_t launch_oz_xrinv(int64_t rows, int cols, const double* X, int64_t ldx
                             size_t scratch_cap, int* dev_status, int num_sms, cudaStream_t s);
 
 // ------------------------------------------------------- panel LU (a3, a8)
-struct PanelScratch;   // defined in plu_panel.cu
+struct PanelScratch;   // defined in plu_panel.cu; starts with a PanelHead
+// Head of a panel LU's scratch: the grid-barrier counter, the first exactly
+// zero pivot column (1-based, as LAPACK's info) and the non-finite flag.
+struct PanelHead {
+    unsigned int barrier;
+    int info;
+    int any_nan;
+    int pad;
+};
+size_t panel_head_bytes();
 size_t panel_scratch_bytes(int64_t rows, int cols);
 // Factor X (rows x cols) in place with partial pivoting (virtual row order).
 // mode 0: leave X = P^T L (reorthogonalisation).
@@ -223,6 +232,26 @@ cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int 
                             double* U, int64_t ldU, int u_trans, int32_t* info,
                             void* scratch, int* dev_status, int64_t spin_budget,
                             int num_sms, cudaStream_t s);
+
+// After a factorisation with rows in place: info and the non-finite flag;
+// mode 0 writes P^T L into X, mode 1 writes perm, L (or L^T) and U (or U^T)
+// from the U rows in Ubuf (steps x cols, ld steps; nullptr: from X).
+cudaError_t launch_panel_finish(int64_t rows, int cols, double* X, int64_t ldx, int mode,
+                                int32_t* perm, double* L, int64_t ldL, int l_trans, double* U,
+                                int64_t ldU, int u_trans, int32_t* info, const void* head,
+                                const int* pos, const int* pivstep, const double* Ubuf,
+                                int* dev_status, int num_sms, cudaStream_t s);
+
+// The same factorisation as launch_panel_lu (same pivots, rows in place),
+// with the trailing updates between 32-column leaves computed on the tensor
+// cores as FP64-accurate sums of exact FP16 digit products (plu_tclu.cu).
+// tclu_supported() tells whether the shape fits its kernels.
+bool tclu_supported(int64_t rows, int cols, int num_sms);
+size_t tclu_scratch_bytes(int64_t rows, int cols);
+cudaError_t launch_panel_lu_tc(int64_t rows, int cols, double* X, int64_t ldx, int mode,
+                               int32_t* perm, double* L, int64_t ldL, int l_trans, double* U,
+                               int64_t ldU, int u_trans, int32_t* info, void* scratch,
+                               int* dev_status, int64_t spin_budget, int num_sms, cudaStream_t s);
 
 // --------------------------------------------------------------- QR (a5)
 // scratch holds scratch_cap >= qr_scratch_bytes(rows, cols, num_sms) bytes

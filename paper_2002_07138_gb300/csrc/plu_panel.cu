@@ -38,6 +38,7 @@
 #include "plu_internal.h"
 
 #include <climits>
+#include <cstddef>
 
 namespace plu {
 
@@ -54,6 +55,9 @@ struct PanelScratch {
     int pad;
     Cand cand[2][kMaxGrid];
 };
+static_assert(offsetof(PanelScratch, info) == offsetof(PanelHead, info) &&
+                  offsetof(PanelScratch, any_nan) == offsetof(PanelHead, any_nan),
+              "PanelScratch starts with a PanelHead");
 
 namespace {
 
@@ -696,7 +700,7 @@ __global__ void k_panel_finalize(int64_t rows, int cols, double* __restrict__ X,
                                  int mode, const int* __restrict__ pos,
                                  const int* __restrict__ pivstep, int32_t* __restrict__ perm,
                                  double* __restrict__ U, int64_t ldU, int u_trans,
-                                 const PanelScratch* __restrict__ ps, int32_t* __restrict__ info,
+                                 const PanelHead* __restrict__ ps, int32_t* __restrict__ info,
                                  int* __restrict__ status, const double* __restrict__ Ubuf) {
     const int r = int(rows < int64_t(cols) ? rows : int64_t(cols));
     // after a failed factorisation (barrier timeout, NaN panel) the row state
@@ -848,13 +852,26 @@ cudaError_t launch_panel_lu(int64_t rows, int cols, double* X, int64_t ldx, int 
                                         args, smem, s);
     }
     if (e != cudaSuccess) return e;
+    return launch_panel_finish(rows, cols, X, ldx, mode, perm, L, ldL, l_trans, U, ldU, u_trans,
+                               info, ps, pos, pivstep, (blocked || lookahead) ? Ubuf : nullptr,
+                               dev_status, num_sms, s);
+}
+
+size_t panel_head_bytes() { return sizeof(PanelScratch); }
+
+cudaError_t launch_panel_finish(int64_t rows, int cols, double* X, int64_t ldx, int mode,
+                                int32_t* perm, double* L, int64_t ldL, int l_trans, double* U,
+                                int64_t ldU, int u_trans, int32_t* info, const void* head,
+                                const int* pos, const int* pivstep, const double* Ubuf,
+                                int* dev_status, int num_sms, cudaStream_t s) {
     int64_t fb = (rows + 255) / 256;
     if (fb > int64_t(num_sms) * 8) fb = int64_t(num_sms) * 8;
     count_launch();
     k_panel_finalize<<<unsigned(fb), 256, 0, s>>>(rows, cols, X, ldx, mode, pos, pivstep, perm,
-                                                  U, ldU, u_trans, ps, info,
-                                                  dev_status, (blocked || lookahead) ? Ubuf : nullptr);
-    e = cudaGetLastError();
+                                                  U, ldU, u_trans,
+                                                  static_cast<const PanelHead*>(head), info,
+                                                  dev_status, Ubuf);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || mode == 0) return e;
     const int r = int(rows < int64_t(cols) ? rows : int64_t(cols));
     const int64_t gy = (r + GC - 1) / GC;
