@@ -381,6 +381,79 @@ def time_calls(torch, fn, reps, stream):
     return s.elapsed_time(e) / reps
 
 
+def measure_peaks(torch, plu, ctx, stream, device):
+    """The compute ceilings the rooflines divide by, measured here outside the
+    timed region (best of several runs, CUDA events), with the SM clock
+    sampled meanwhile: FP64 (torch.matmul 4096^3 and the library's own FP64
+    GEMM, one 16384^2 x 256 pass), TF32 (torch.matmul 8192^3 with TF32
+    allowed) and FP8-E4M3 (torch._scaled_mm 8192^3, when torch has it)."""
+    out = {}
+    clocks = ClockSampler(device)
+    clocks.start()
+    time.sleep(0.2)
+
+    def best(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            fn()
+            s1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(s0.elapsed_time(s1))
+        return min(ts)
+
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    out["fp64_torch_tflops"] = 2.0 * n ** 3 / best(lambda: a @ b, 5) / 1e9
+    del a, b
+    m2, c2 = 16384, 256
+    A64 = plu.colmajor_empty(m2, m2, dtype=torch.float64)
+    A64.normal_()
+    X64 = plu.colmajor_empty(m2, c2, dtype=torch.float64)
+    X64.normal_()
+    Y64 = plu.colmajor_empty(m2, c2, dtype=torch.float64)
+    out["fp64_own_gemm_tflops"] = 2.0 * m2 * m2 * c2 / best(
+        lambda: plu.plu_pass(ctx, A64, 1, X64, "fp64", out=Y64), 3) / 1e9
+    del A64, X64, Y64
+    n = 8192
+    old_tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    a = torch.randn(n, n, dtype=torch.float32, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float32, device="cuda")
+    out["tf32_tflops"] = 2.0 * n ** 3 / best(lambda: a @ b, 10) / 1e9
+    torch.backends.cuda.matmul.allow_tf32 = old_tf32
+    del a, b
+    try:
+        a8 = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b8 = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device="cuda")
+        out["fp8_tflops"] = 2.0 * n ** 3 / best(
+            lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one, out_dtype=torch.bfloat16),
+            10) / 1e9
+        del a8, b8
+    except Exception as exc:                                   # torch without FP8 GEMM
+        out["fp8_tflops"] = None
+        out["fp8_note"] = "torch._scaled_mm unavailable: %s" % type(exc).__name__
+    torch.cuda.empty_cache()
+    out["clocks"] = clocks.stop()
+    out["how"] = ("best of 3-10 runs with CUDA events; FP64: torch.matmul 4096^3 and the "
+                  "library's FP64 pass (16384^2 x 256); TF32: torch.matmul 8192^3; "
+                  "FP8-E4M3: torch._scaled_mm 8192^3")
+    out["fp64_tflops"] = max(out["fp64_torch_tflops"], out["fp64_own_gemm_tflops"])
+    return out
+
+
+def leaf_flops(rows, w):
+    """FP64 flops of one 32-column leaf of the tensor-core panel LU: the
+    elimination inside the leaf, sum_j 2 (rows - j - 1)(w - j - 1)."""
+    return sum(2.0 * (rows - j - 1) * (w - j - 1) for j in range(w))
+
+
 def kernel_rooflines(torch, plu, ctx, Ad, w, prec, stream, peaks):
     """Time each step's kernels alone, at the sizes one call uses, with CUDA
     events on the library's stream.  Returns {name: (ms per launch, launches
@@ -393,9 +466,12 @@ def kernel_rooflines(torch, plu, ctx, Ad, w, prec, stream, peaks):
     out = {}
     sm_clock_ghz = peaks["sm_max_mhz"] / 1e3
     fp32_alu = 152 * 128 * 2 * sm_clock_ghz * 1e9 / 1e12          # TFLOP/s
-    fp64_peak = 1.25                                             # nominal, TFLOP/s
-    fp64 = {"bound": "alu", "peak": fp64_peak, "unit": "TFLOP/s",
-            "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)"}
+    if peaks.get("fp64_tflops"):
+        fp64 = {"bound": "alu", "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                "peak_source": "measured FP64 GEMM (of measured, peaks_measured)"}
+    else:
+        fp64 = {"bound": "alu", "peak": 1.25, "unit": "TFLOP/s",
+                "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)"}
 
     # the passes: A X (trans 0) and A^T X (trans 1) over the l-wide basis
     abytes = m * n * Ad.element_size()
@@ -415,14 +491,35 @@ def kernel_rooflines(torch, plu, ctx, Ad, w, prec, stream, peaks):
     rf["ms_trans1"] = ms1
     kname = "k_tc_pass" if prec in ("tf32", "bf16", "fp8") else "k_gemm_simt"
     out["pass"] = (ms, v, rf, kname)
-    # re-orthogonalising LU of the m x l panel (the tail's two getrf of m x k
-    # and n x k panels run the same kernel)
+    # re-orthogonalising LU of the m x l panel, as the call runs it (the tail's
+    # two getrf of m x k and n x k panels run the same kernels).  In the mixed
+    # modes the trailing updates run on the tensor cores and the 32-column
+    # leaves (k_lu_leaf) carry the FP64 work and the column-step exchanges:
+    # their roofline is the FP64 pipe, timed on an m x 32 panel (one leaf).
+    tc_lu = prec != "fp64"
+    ctx.set_lu_updates(1 if tc_lu else 0)
     Zc = Z.clone()
     ms = time_calls(torch, lambda: (Zc.copy_(Z), plu.plu_lu_reorth(ctx, Zc)), 3, stream)
     ms_copy = time_calls(torch, lambda: Zc.copy_(Z), 3, stream)
     ms = max(ms - ms_copy, 1e-6)
-    out["panel_lu"] = (ms, max(v - 2, 0) + 2, dict(fp64, achieved=lu_flops(m, l) / ms / 1e9),
-                       panel_kernel_name(m, l, torch.cuda.get_device_properties(0).multi_processor_count))
+    if tc_lu:
+        Z32 = Z[:, :32].clone()
+        Zc32 = Z32.clone()
+        ms_leaf = time_calls(torch, lambda: (Zc32.copy_(Z32), plu.plu_lu_reorth(ctx, Zc32)), 5,
+                             stream)
+        ms_leaf = max(ms_leaf - time_calls(torch, lambda: Zc32.copy_(Z32), 5, stream), 1e-6)
+        nleaf = -(-l // 32)
+        rf_lu = dict(fp64, achieved=leaf_flops(m, 32) / ms_leaf / 1e9)
+        rf_lu["ms_whole_lu"] = ms
+        rf_lu["fp64_equivalent_tflops_whole_lu"] = lu_flops(m, l) / ms / 1e9
+        rf_lu["leaves_per_lu"] = nleaf
+        rf_lu["us_per_column_step"] = 1e3 * ms_leaf / 32
+        out["panel_lu"] = (ms_leaf, nleaf * (max(v - 2, 0) + 2), rf_lu, "k_lu_leaf")
+        out["panel_lu_whole"] = (ms, max(v - 2, 0) + 2, dict(rf_lu), "k_lu_leaf + k_lu_update")
+    else:
+        out["panel_lu"] = (ms, max(v - 2, 0) + 2, dict(fp64, achieved=lu_flops(m, l) / ms / 1e9),
+                           panel_kernel_name(m, l, torch.cuda.get_device_properties(0).multi_processor_count))
+    ctx.set_lu_updates(-1)
     # the orthonormalisation of the n x k leading basis columns as the call runs
     # it: FP64 CholeskyQR2 in the FP64 path; in the mixed modes one round whose
     # X^T X and X R^-1 are exact slice products on the BF16 tensor cores (the
@@ -554,10 +651,13 @@ def run_ours(args, w):
     h2d = w.m * w.n * Ad.element_size()
     d2h = 4 * (w.m + w.n) + 8 * (w.m * w.k + w.k * w.n)
 
-    # roofline of the dominant step (timed alone, live), and of the pass
+    # measured compute ceilings, then the roofline of the dominant kernel
+    # (timed alone, live) and of the pass
+    pm = measure_peaks(torch, plu, ctx, stream, device)
+    peaks["fp64_tflops"] = pm["fp64_tflops"]
     kr = kernel_rooflines(torch, plu, ctx, Ad, w, prec, stream, peaks)
     share = {name: ms * cnt for name, (ms, cnt, _, _) in kr.items()}
-    dom = max(share, key=share.get)
+    dom = max((nm for nm in share if nm != "panel_lu_whole"), key=share.get)
 
     def roofline_of(name):
         ms_k, cnt_k, rf_k, kname = kr[name]
@@ -581,6 +681,15 @@ def run_ours(args, w):
         cpu = {"value": sfl / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
                "kind": "oracle", "sample": "%s (FP64, numpy BLAS) on the same %dx%d matrix, "
                "%.1f s" % (desc, w.m, w.n, dt)}
+        # beside the sample: one whole oracle call on the 8192^2 fixed-rank
+        # workload (k = 100, l = 110, v = 3), which fits in seconds
+        w8 = workloads()["fixed_rank_8192"]
+        A8 = build_host_matrix(w8)
+        dt8, _ = oracle_call(A8, w8, seed=0)
+        del A8
+        cpu["whole_call_8192"] = {"ms_per_call": 1e3 * dt8, "unit": "ms",
+                                  "tflops": pass_flops(w8.m, w8.n, w8.k, w8.l, w8.v) / dt8 / 1e12,
+                                  "workload": w8.name}
 
     # the other mixed precisions on the same matrix (one call each)
     by_prec = {}
@@ -626,6 +735,9 @@ def run_ours(args, w):
             "roofline_pass": rf_pass,
             "kernel_ms": {name: {"ms_per_launch": ms, "launches_per_step": cnt}
                           for name, (ms, cnt, _, _) in kr.items()},
+            "ms_phase": {nm: statistics.mean(r["ms_phase"][nm] for r in reps)
+                         for nm in reps[0]["ms_phase"]},
+            "peaks_measured": pm,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

@@ -94,6 +94,24 @@ typedef struct {
     const double* t_val;        /* nnz */
 } plu_csr;
 
+/* Phases of a call, for plu_report.ms_phase: the Gaussian sketch (and the
+ * quantised copy of A in the BF16 / FP8 modes); the passes of the power
+ * iteration (Alg. gpowerlu); the re-orthogonalising LUs between them; the
+ * final QR; the last pass (Y = A V_k or G = A V); the rank determination
+ * (||A||_F^2, column norms, rank scan, restart copies); the two getrf of the
+ * tail; the tail's two m x k x k products. */
+enum {
+    PLU_PHASE_SKETCH = 0,
+    PLU_PHASE_POWER_PASSES = 1,
+    PLU_PHASE_REORTH = 2,
+    PLU_PHASE_QR = 3,
+    PLU_PHASE_LAST_PASS = 4,
+    PLU_PHASE_RANK = 5,
+    PLU_PHASE_TAIL_LU = 6,
+    PLU_PHASE_TAIL_PRODUCTS = 7,
+    PLU_NPHASES = 8
+};
+
 /* Per-call report (host struct, filled when a non-NULL pointer is given). */
 typedef struct {
     double ms_total;        /* device time of the call (CUDA events)             */
@@ -107,6 +125,9 @@ typedef struct {
     double bytes_passes;    /* algorithmic bytes of the passes (A + operands)    */
     int32_t launches;       /* library kernels launched by the call              */
     int32_t rounds;         /* fixed precision: rounds of the rank determination */
+    double ms_phase[PLU_NPHASES];  /* device time per phase (CUDA events between the
+                                      phase boundaries; plu_powerlu, plu_powerlu_fp
+                                      and their sparse forms; 0 elsewhere)        */
 } plu_report;
 
 typedef struct plu_ctx plu_ctx;

@@ -40,10 +40,15 @@ class plu_report(ctypes.Structure):
     _fields_ = [("ms_total", c_dbl), ("ms_passes", c_dbl), ("passes", c_i32), ("rank", c_i32),
                 ("indicator", c_dbl), ("normA2", c_dbl), ("info1", c_i32), ("info2", c_i32),
                 ("flops_passes", c_dbl), ("bytes_passes", c_dbl), ("launches", c_i32),
-                ("rounds", c_i32)]
+                ("rounds", c_i32), ("ms_phase", c_dbl * 8)]
+
+    PHASES = ("sketch", "power_passes", "reorth", "qr", "last_pass", "rank", "tail_lu",
+              "tail_products")
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "ms_phase"}
+        d["ms_phase"] = {nm: float(self.ms_phase[i]) for i, nm in enumerate(self.PHASES)}
+        return d
 
 
 class plu_batch_problem(ctypes.Structure):

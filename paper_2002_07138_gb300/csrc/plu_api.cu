@@ -323,14 +323,36 @@ PowerLUPlan plan_powerlu(int64_t m, int64_t n, int l, int kmax, int prec, int sm
     return p;
 }
 
+// CUDA events of a call (only when a report is requested): pairs around the
+// passes, and phase boundaries (each phase lasts until the next boundary).
 struct PassTimer {
     plu_ctx* c;
     bool on;
     cudaEvent_t ev[64];
     int n = 0;
+    static constexpr int kMaxPhaseMarks = 128;
+    cudaEvent_t pev[kMaxPhaseMarks];
+    int pid[kMaxPhaseMarks];
+    int np = 0;
     explicit PassTimer(plu_ctx* ctx, bool enable) : c(ctx), on(enable) {}
     ~PassTimer() {
         for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
+        for (int i = 0; i < np; ++i) cudaEventDestroy(pev[i]);
+    }
+    // start of phase id (PLU_PHASE_*; -1 ends the last one)
+    void phase(int id) {
+        if (!on || np >= kMaxPhaseMarks) return;
+        cudaEventCreate(&pev[np]);
+        cudaEventRecord(pev[np], c->stream);
+        pid[np++] = id;
+    }
+    void phases_ms(double* out) {
+        for (int i = 0; i < PLU_NPHASES; ++i) out[i] = 0.0;
+        for (int i = 0; i + 1 < np; ++i) {
+            if (pid[i] < 0 || pid[i] >= PLU_NPHASES) continue;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, pev[i], pev[i + 1]) == cudaSuccess) out[pid[i]] += ms;
+        }
     }
     void mark() {
         if (!on || n >= 64) return;
@@ -390,6 +412,7 @@ plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t 
     const uint32_t shift = kStreamRestartStride * uint32_t(round);
     int np = 0;
     auto pass = [&](int trans, const double* X, int64_t ldx, double* Y, int64_t ldy) -> plu_status {
+        pt.phase(PLU_PHASE_POWER_PASSES);
         pt.mark();
         PLU_TRY(do_pass(c, A, trans, X, ldx, l, prec, Y, ldy, step, step_cap, q));
         pt.mark();
@@ -398,12 +421,14 @@ plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t 
         return PLU_OK;
     };
     auto reorth = [&](int64_t rows, double* X) -> plu_status {
+        pt.phase(PLU_PHASE_REORTH);
         PLU_CUDA(c, launch_lu(c, prec, rows, l, X, rows, 0, nullptr, nullptr, 0, 0, nullptr, 0, 0,
                                     nullptr, step, c->d_status, c->spin_budget, c->num_sms,
                                     c->stream));
         return PLU_OK;
     };
     auto qr = [&](double* X) -> plu_status {
+        pt.phase(PLU_PHASE_QR);
         const cudaError_t e = launch_cholqr2(n, qr_cols, X, n, nullptr, 0, step, step_cap,
                                              c->d_status, c->num_sms, c->stream, adaptive_qr, 2,
                                              tc_qr);
@@ -412,6 +437,7 @@ plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t 
                         cudaGetErrorString(e));
         return PLU_OK;
     };
+    pt.phase(PLU_PHASE_SKETCH);
     if (v % 2 == 0) {
         PLU_CUDA(c, launch_gaussian(m, l, seed, kStreamOmegaM + shift, Z, m, c->stream));
         PLU_TRY(pass(1, Z, m, V, n));                 // A^T Omega
@@ -435,13 +461,14 @@ plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t 
 plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const double* Vk,
                     char* ws, const PowerLUPlan& pl, char* step, int32_t* p, int32_t* q,
                     double* L, int64_t ldL, double* U, int64_t ldU, int32_t* info2dev,
-                    int prec, bool oz = false) {
+                    int prec, bool oz, PassTimer& pt) {
     double* L1 = reinterpret_cast<double*>(ws + pl.L1);
     double* U1T = reinterpret_cast<double*>(ws + pl.U1T);
     double* BT = reinterpret_cast<double*>(ws + pl.BT);
     double* U2T = reinterpret_cast<double*>(ws + pl.U2T);
     void* tp = ws + pl.tailpart;
     // [L1, U1, P] = lu(Y)
+    pt.phase(PLU_PHASE_TAIL_LU);
     PLU_CUDA(c, launch_lu(c, prec, m, k, Y, m, 1, p, L1, m, 0, U1T, k, 1, info2dev, step, c->d_status,
                                 c->spin_budget, c->num_sms, c->stream));
     // The two m x k x k products take FP32 FMAs when the passes are not FP64:
@@ -457,6 +484,7 @@ plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const do
     const bool oz_l = oz && !f32 && oz_supported(m, k, c->num_sms) &&
                       oz_scratch_bytes(m, k, c->num_sms) <= pl.step_bytes;
     // B^T = Vk U1^T (U1^T lower triangular)
+    pt.phase(PLU_PHASE_TAIL_PRODUCTS);
     if (oz_bt)
         PLU_CUDA(c, launch_oz_xrinv(n, k, Vk, n, U1T, BT, n, step, pl.step_bytes, c->d_status,
                                     c->num_sms, c->stream));
@@ -467,9 +495,11 @@ plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const do
         PLU_CUDA(c, launch_gemm_f64_tri(0, 3, n, k, k, Vk, n, U1T, k, BT, n, tp,
                                         pl.tailpart_bytes, c->num_sms, c->stream));
     // [L2, U2, Q] = lu(B^T); U = L2^T written straight into U
+    pt.phase(PLU_PHASE_TAIL_LU);
     PLU_CUDA(c, launch_lu(c, prec, n, k, BT, n, 1, q, U, ldU, 1, U2T, k, 1, info2dev + 1, step,
                                 c->d_status, c->spin_budget, c->num_sms, c->stream));
     // L = L1 U2^T (U2^T lower triangular)
+    pt.phase(PLU_PHASE_TAIL_PRODUCTS);
     if (oz_l)
         PLU_CUDA(c, launch_oz_xrinv(m, k, L1, m, U2T, L, ldL, step, pl.step_bytes, c->d_status,
                                     c->num_sms, c->stream));
@@ -761,6 +791,7 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
     int np = 0;
     QuantA qa;
     const bool quant = prec == PLU_BF16 || prec == PLU_FP8_E4M3;
+    pt.phase(PLU_PHASE_SKETCH);
     if (quant)
         PLU_CUDA(c, launch_tc_quantize(prec, static_cast<const float*>(A->data), m, n, A->ld,
                                        ws + pl.quant, &qa, c->num_sms, c->stream));
@@ -774,6 +805,7 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
                          prec != PLU_FP64 || c->csr ? 1 : 0));
     // Y = A V(:, 1:k) (Alg. bpowerlu step 3), the v-th pass; in the mixed
     // modes it reads the FP32 A through TF32 (it enters the result to first order)
+    pt.phase(PLU_PHASE_LAST_PASS);
     pt.mark();
     PLU_TRY(do_pass(c, A, 0, V, n, k, is_tc(prec) ? int(PLU_TF32) : int(prec), Z, m, step,
                     pl.step_bytes));
@@ -781,7 +813,8 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
     ++np;
     int32_t* info = reinterpret_cast<int32_t*>(ws + pl.cn);
     PLU_TRY(run_tail(c, m, n, k, Z, V, ws, pl, step, p, q, L, ldL, U, ldU, info, prec,
-                     c->csr != nullptr));
+                     c->csr != nullptr, pt));
+    pt.phase(-1);
     if (rep) {
         PLU_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
         int32_t hinfo[2] = {0, 0};
@@ -800,6 +833,7 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
         rep->info2 = hinfo[1];
         fill_pass_report(rep, A, np - 1, l, k, prec, true, c->csr);
         rep->launches = int32_t(g_launches - launches0);
+        pt.phases_ms(rep->ms_phase);
     }
     return finish(c);
 }
@@ -849,6 +883,7 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
     const long long launches0 = g_launches;
     if (rep) PLU_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
     // E = ||A||_F^2 (Alg. adaptivewithoutupdating step 1)
+    pt.phase(PLU_PHASE_RANK);
     pt.mark();
     if (c->csr)       // the squares of the nonzeros
         PLU_CUDA(c, launch_sumsq(c->csr->val, c->csr->nnz, c->d_scal, nscr, c->num_sms,
@@ -860,6 +895,7 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
     int np = 0;
     QuantA qa;
     const bool quant = prec == PLU_BF16 || prec == PLU_FP8_E4M3;
+    pt.phase(PLU_PHASE_SKETCH);
     if (quant)
         PLU_CUDA(c, launch_tc_quantize(prec, static_cast<const float*>(A->data), m, n, A->ld,
                                        ws + pl.quant, &qa, c->num_sms, c->stream));
@@ -881,12 +917,14 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
         // E = ||A||_F^2 - sum ||G(:, j)||^2 must resolve eps^2 ||A||_F^2, which
         // TF32 rounding (relative bias ~1e-3) cannot, so the mixed modes take
         // this pass in FP32 arithmetic on the FP32 A.
+        pt.phase(PLU_PHASE_LAST_PASS);
         pt.mark();
         PLU_TRY(do_pass(c, A, 0, V, n, l, is_tc(prec) ? int(PLU_FP32) : int(prec), Z, m, step,
                         pl.step_bytes));
         pt.mark();
         PLU_TRY(remainder_correct(c, A, rem, 0, V, n, l, Z, m, step, pl.step_bytes));
         ++np;
+        pt.phase(PLU_PHASE_RANK);
         PLU_CUDA(c, launch_colnorm2(m, l, Z, m, cn, c->stream));
         PLU_CUDA(c, launch_rank_scan(cn, l, c->d_scal, eps, b, precise, c->d_kmet, c->d_scal + 1,
                                      c->stream, r > 0 ? c->d_scal + 1 : nullptr));
@@ -911,7 +949,8 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
     const int k = kw;
     int32_t* info = reinterpret_cast<int32_t*>(c->d_kmet + 2);
     PLU_TRY(run_tail(c, m, n, k, multi ? Gu : Z, multi ? Wu : V, ws, pl, step, p, q, L, ldL, U,
-                     ldU, info, prec, c->csr != nullptr));
+                     ldU, info, prec, c->csr != nullptr, pt));
+    pt.phase(-1);
     *k_out = k;
     if (rep) {
         PLU_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
@@ -933,6 +972,7 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
         rep->rounds = rounds;
         fill_pass_report(rep, A, np, l, 0, prec, false, c->csr);
         rep->launches = int32_t(g_launches - launches0);
+        pt.phases_ms(rep->ms_phase);
     }
     plu_status st = finish(c);
     if (st != PLU_OK) return st;
