@@ -981,6 +981,29 @@ def sparse_pass_bytes(n, nnz, cols):
     return nnz * 12.0 + (n + 1) * 8.0 + 2.0 * n * cols * 8.0
 
 
+def sparse_rel_error(torch, m, rp, ci, val, p, q, L, U):
+    """||A - P^T L U Q||_F / ||A||_F for a sparse A (CUDA CSR tensors rp, ci,
+    val) without forming L U: ||A||^2 = sum val^2, <A, P^T L U Q> one k-length
+    dot product per nonzero, ||L U||^2 = trace((L^T L)(U U^T)).  Measurement
+    only (torch), outside the timed region."""
+    dev = L.device
+    pinv = torch.empty_like(p.long())
+    pinv[p.long()] = torch.arange(m, device=dev)
+    qinv = torch.empty_like(q.long())
+    qinv[q.long()] = torch.arange(q.numel(), device=dev)
+    rows = torch.repeat_interleave(torch.arange(m, device=dev), rp[1:] - rp[:-1])
+    cil = ci.long()
+    normA2 = float((val * val).sum())
+    inner = 0.0
+    step = 1 << 19
+    for s0 in range(0, val.numel(), step):
+        r = pinv[rows[s0:s0 + step]]
+        c = qinv[cil[s0:s0 + step]]
+        inner += float((val[s0:s0 + step] * (L[r] * U[:, c].t()).sum(1)).sum())
+    normLU2 = float(((L.t() @ L) * (U @ U.t())).sum())
+    return max(normA2 - 2.0 * inner + normLU2, 0.0) ** 0.5 / normA2 ** 0.5
+
+
 def run_sparse(args):
     """PowerLU (Alg. bpowerlu + Alg. gpowerlu) on the sparse workload, every
     pass an FP64 sparse product.  value = the passes' algorithmic flops
@@ -1089,9 +1112,11 @@ def run_sparse(args):
     ms1 = time_calls(torch, lambda: plu.plu_spmm(ctx, S, 1, Z, out=X), 5, stream)
     ms_sp = 0.5 * (ms0 + ms1)
     Zc = Z.clone()
+    ctx.set_lu_updates(1)              # as the sparse call runs its LUs
     ms_lu = time_calls(torch, lambda: (Zc.copy_(Z), plu.plu_lu_reorth(ctx, Zc)), 3, stream)
     ms_cp = time_calls(torch, lambda: Zc.copy_(Z), 3, stream)
     ms_lu = max(ms_lu - ms_cp, 1e-6)
+    ctx.set_lu_updates(-1)
     plu.lib().plu_set_async(ctx.handle, 0)
     ctx.check(plu.lib().plu_check(ctx.handle))
     sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -1102,20 +1127,35 @@ def run_sparse(args):
     # FP64 rate that, not HBM (the CSR arrays and two n x l operands) or the
     # L2 gathers of X's rows, is its bound
     pbytes = sparse_pass_bytes(n, nnz, l)
-    rf_sp = {"bound": "alu", "achieved": 2.0 * nnz * l / ms_sp / 1e9, "peak": 1.25,
-             "unit": "TFLOP/s", "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)",
+    pm = measure_peaks(torch, plu, ctx, stream, local)
+    fp64pk = pm["fp64_tflops"]
+    rf_sp = {"bound": "alu", "achieved": 2.0 * nnz * l / ms_sp / 1e9, "peak": fp64pk,
+             "unit": "TFLOP/s", "peak_source": "measured FP64 GEMM (of measured, peaks_measured)",
              "kernel": "k_spmm_csr + k_to_rowmajor", "ms_per_launch": ms_sp,
              "traffic": None, "share_of_step": share["spmm"] / ms_step,
              "hbm_gbs": pbytes / ms_sp / 1e6, "hbm_frac": pbytes / ms_sp / 1e6 / peaks["hbm_gbs"],
              "l2_gather_gbs": nnz * l * 8.0 / ms_sp / 1e6,
              "note": "the rows of X a pass gathers (nnz x l x 8 B) come from L2"}
     rf_sp["frac"] = rf_sp["achieved"] / rf_sp["peak"]
-    rf_lu = {"bound": "alu", "achieved": lu_flops(n, l) / ms_lu / 1e9, "peak": 1.25,
-             "unit": "TFLOP/s", "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)",
-             "kernel": panel_kernel_name(n, l, sms), "ms_per_launch": ms_lu, "traffic": None,
-             "share_of_step": share["panel_lu"] / ms_step}
+    # the leaf kernel of the tensor-core LU (one 32-column leaf, timed alone)
+    # against the FP64 pipe; the whole LU's FP64-equivalent rate beside it
+    Z32 = Z[:, :32].clone()
+    Zc32 = Z32.clone()
+    ctx.set_lu_updates(1)
+    ms_leaf = time_calls(torch, lambda: (Zc32.copy_(Z32), plu.plu_lu_reorth(ctx, Zc32)), 5, stream)
+    ms_leaf = max(ms_leaf - time_calls(torch, lambda: Zc32.copy_(Z32), 5, stream), 1e-6)
+    ctx.set_lu_updates(-1)
+    rf_lu = {"bound": "alu", "achieved": leaf_flops(n, 32) / ms_leaf / 1e9, "peak": fp64pk,
+             "unit": "TFLOP/s", "peak_source": "measured FP64 GEMM (of measured, peaks_measured)",
+             "kernel": "k_lu_leaf", "ms_per_launch": ms_leaf, "traffic": None,
+             "share_of_step": share["panel_lu"] / ms_step, "ms_whole_lu": ms_lu,
+             "fp64_equivalent_tflops_whole_lu": lu_flops(n, l) / ms_lu / 1e9}
     rf_lu["frac"] = rf_lu["achieved"] / rf_lu["peak"]
     rf = rf_sp if share["spmm"] >= share["panel_lu"] else rf_lu
+
+    # accuracy of one call, formed from the nonzeros (outside the timed region)
+    res = call(7)
+    rel_err = sparse_rel_error(torch, n, dev_arrays[0], dev_arrays[1], dev_arrays[2], *res[:4])
 
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
@@ -1134,7 +1174,7 @@ def run_sparse(args):
                        "l2_flush": "256 MB write before every timed call, outside its "
                                    "events (the CSR arrays of A and A^T are %.0f MB)" % (h2d / 1e6),
                        "parallelism": "replicas" if ws > 1 else "single"},
-            "ms_per_pass": ms_pass, "ms_per_step_v2": ms_v2,
+            "ms_per_pass": ms_pass, "ms_per_step_v2": ms_v2, "rel_error": rel_err,
             "tflops_per_pass": 2.0 * nnz * l / (ms_pass / 1e3) / 1e12,
             "e2e": {"value": flops * ws / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s",
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -1143,6 +1183,9 @@ def run_sparse(args):
             "kernel_ms": {"spmm": {"ms_per_launch": ms_sp, "launches_per_step": v},
                           "panel_lu": {"ms_per_launch": ms_lu,
                                        "launches_per_step": max(v - 2, 0) + 2}},
+            "ms_phase": {nm: statistics.mean(r["ms_phase"][nm] for r in reps)
+                         for nm in reps[0]["ms_phase"]},
+            "peaks_measured": pm,
             "cpu_baseline": cpu,
         }))
     ctx.close()

@@ -186,9 +186,12 @@ size_t pass_ws(int64_t M, int64_t N, int64_t K, int prec, int sms) {
 // per call); TF32 reads the FP32 A directly; shapes the tensor-core kernel
 // does not take (more than 512 columns, unaligned A) use the FP32 SIMT kernel.
 // ws holds ws_cap bytes; a shape that needs more is an error, never an overrun.
+// norm (nullable): ||A||_F^2 summed by the pass kernel from the entries it
+// reads (not for the passes over a quantised copy: its quantisation does it).
 plu_status do_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X, int64_t ldx,
                    int cols, int prec, double* Y, int64_t ldy, char* ws, size_t ws_cap,
-                   const QuantA* q = nullptr, int accum = 0, const void* xq_pre = nullptr) {
+                   const QuantA* q = nullptr, int accum = 0, const void* xq_pre = nullptr,
+                   const NormOut* norm = nullptr) {
     const int64_t M = trans ? A->n : A->m;
     const int64_t K = trans ? A->m : A->n;
     if (c->csr) {
@@ -196,10 +199,11 @@ plu_status do_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X, 
         PLU_CUDA(c, launch_spmm_csr(M, K, S->nnz, trans ? S->t_row_ptr : S->row_ptr,
                                     trans ? S->t_col_idx : S->col_idx, trans ? S->t_val : S->val,
                                     X, ldx, cols, Y, ldy, ws, ws_cap, c->d_status, c->num_sms,
-                                    c->stream));
+                                    c->stream, norm));
         return PLU_OK;
     }
     if ((prec == PLU_BF16 || prec == PLU_FP8_E4M3) && q && cols <= 512) {
+        if (norm) return fail(c, PLU_EINVAL, "a pass over a quantised copy cannot sum ||A||^2");
         PLU_CUDA(c, launch_tc_pass_q(trans, *q, X, ldx, cols, Y, ldy, ws, ws_cap, c->d_status,
                                      c->num_sms, c->stream, accum));
         return PLU_OK;
@@ -207,7 +211,7 @@ plu_status do_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X, 
     if (is_tc(prec) && A->dtype == PLU_F32 && tc_supported(M, K, cols, A->data, A->ld, trans)) {
         PLU_CUDA(c, launch_tc_pass(trans, A->m, A->n, static_cast<const float*>(A->data), A->ld, X,
                                    ldx, cols, Y, ldy, ws, ws_cap, c->d_status, c->num_sms,
-                                   c->stream, accum, xq_pre));
+                                   c->stream, accum, xq_pre, norm));
         return PLU_OK;
     }
     if (is_tc(prec)) prec = PLU_FP32;
@@ -224,8 +228,22 @@ plu_status do_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X, 
     const size_t part_cap = ws_cap > off ? ws_cap - off : 0;
     void* part = w.take(part_cap);
     PLU_CUDA(c, launch_gemm_simt(trans, M, cols, K, A->data, A->dtype, A->ld, X, ldx, Y, ldy, prec,
-                                 part, part_cap, b32, c->num_sms, c->stream, accum));
+                                 part, part_cap, b32, c->num_sms, c->stream, accum, norm));
     return PLU_OK;
+}
+
+// Room for the per-CTA partials of ||A||_F^2 in whichever kernel runs the
+// first pass (tensor-core pass, quantisation, SIMT GEMM or sparse pass).
+int norm_parts_needed(int64_t m, int64_t n, int l, int sms) {
+    int p = quant_norm_parts(sms);
+    for (const int64_t M : {m, n}) {
+        const int64_t K = M == m ? n : m;
+        const int g = gemm_norm_parts(M, l, K, sms);
+        if (g > p) p = g;
+        const int sp = spmm_norm_parts(M, sms);
+        if (sp > p) p = sp;
+    }
+    return p;
 }
 
 // Largest scratch over every rank 1..kmax the tail (and, on the sparse path,
@@ -270,7 +288,8 @@ size_t tail_scratch_max(int64_t m, int64_t n, int kmax, int sms, bool oz) {
 
 struct PowerLUPlan {
     // offsets into the workspace
-    size_t V, Z, step, L1, U1T, BT, U2T, tailpart, cn, quant, total;
+    size_t V, Z, step, L1, U1T, BT, U2T, tailpart, cn, normparts, quant, total;
+    int normparts_cap;
     size_t step_bytes, tailpart_bytes;
 };
 
@@ -318,6 +337,8 @@ PowerLUPlan plan_powerlu(int64_t m, int64_t n, int l, int kmax, int prec, int sm
     p.tailpart = lay.add(tp);
     p.tailpart_bytes = tp;
     p.cn = lay.add(size_t(l) * sizeof(double) + norm2_scratch_bytes(sms));
+    p.normparts_cap = norm_parts_needed(m, n, l, sms);
+    p.normparts = lay.add(size_t(p.normparts_cap) * sizeof(double));
     p.quant = (prec == PLU_BF16 || prec == PLU_FP8_E4M3) ? lay.add(tc_quant_bytes(m, n, prec)) : 0;
     p.total = lay.total + 256;
     return p;
@@ -403,10 +424,12 @@ plu_status remainder_correct(plu_ctx* c, const plu_matrix* A, const Remainder& r
 // path reads only V(:, 1:k) (Alg. bpowerlu step 3 and the tail).  With a
 // remainder (restart round r), every pass is over A_r and Omega comes from
 // the streams shifted by 16 r.
+// first_norm (nullable): the first pass also sums ||A||_F^2 into it.
 plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t seed, int prec,
                         double* V, double* Z, char* step, size_t step_cap, PassTimer& pt,
                         int* passes, const QuantA* q, int qr_cols, int adaptive_qr,
-                        int tc_qr, const Remainder& rem = Remainder(), int round = 0) {
+                        int tc_qr, const Remainder& rem = Remainder(), int round = 0,
+                        const NormOut* first_norm = nullptr) {
     const int64_t m = A->m, n = A->n;
     const int p = (v - 1) / 2;
     const uint32_t shift = kStreamRestartStride * uint32_t(round);
@@ -414,7 +437,8 @@ plu_status run_gpowerlu(plu_ctx* c, const plu_matrix* A, int l, int v, uint64_t 
     auto pass = [&](int trans, const double* X, int64_t ldx, double* Y, int64_t ldy) -> plu_status {
         pt.phase(PLU_PHASE_POWER_PASSES);
         pt.mark();
-        PLU_TRY(do_pass(c, A, trans, X, ldx, l, prec, Y, ldy, step, step_cap, q));
+        PLU_TRY(do_pass(c, A, trans, X, ldx, l, prec, Y, ldy, step, step_cap, q, 0, nullptr,
+                        np == 0 ? first_norm : nullptr));
         pt.mark();
         PLU_TRY(remainder_correct(c, A, rem, trans, X, ldx, l, Y, ldy, step, step_cap));
         ++np;
@@ -878,27 +902,24 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
     double* T = multi ? reinterpret_cast<double*>(ws + oT) : nullptr;
     char* step = ws + pl.step;
     double* cn = reinterpret_cast<double*>(ws + pl.cn);
-    void* nscr = ws + pl.cn + ((size_t(l) * sizeof(double) + 255) & ~size_t(255));
     PassTimer pt(c, rep != nullptr);
     const long long launches0 = g_launches;
     if (rep) PLU_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
-    // E = ||A||_F^2 (Alg. adaptivewithoutupdating step 1)
-    pt.phase(PLU_PHASE_RANK);
-    pt.mark();
-    if (c->csr)       // the squares of the nonzeros
-        PLU_CUDA(c, launch_sumsq(c->csr->val, c->csr->nnz, c->d_scal, nscr, c->num_sms,
-                                 c->stream));
-    else
-        PLU_CUDA(c, launch_norm2(A->data, A->dtype, m, n, A->ld, c->d_scal, nscr, c->num_sms,
-                                 c->stream));
-    pt.mark();
+    // E = ||A||_F^2 (Alg. adaptivewithoutupdating step 1) is summed from the
+    // entries of A that the first read of A stages: the first pass of
+    // Alg. gpowerlu, or the quantisation in the BF16 / FP8 modes (itself a
+    // read of A).  So A is read v times, as the algorithm counts passes.
+    NormOut norm;
+    norm.parts = reinterpret_cast<double*>(ws + pl.normparts);
+    norm.cap = pl.normparts_cap;
+    norm.out = c->d_scal;
     int np = 0;
     QuantA qa;
     const bool quant = prec == PLU_BF16 || prec == PLU_FP8_E4M3;
     pt.phase(PLU_PHASE_SKETCH);
     if (quant)
         PLU_CUDA(c, launch_tc_quantize(prec, static_cast<const float*>(A->data), m, n, A->ld,
-                                       ws + pl.quant, &qa, c->num_sms, c->stream));
+                                       ws + pl.quant, &qa, c->num_sms, c->stream, &norm));
     int kw = 0, met = 0, rounds = 0;
     for (int r = 0; r < max_rounds; ++r) {
         Remainder rem;
@@ -911,7 +932,7 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
         int npr = 0;
         PLU_TRY(run_gpowerlu(c, A, l, v, seed, prec, V, Z, step, pl.step_bytes, pt, &npr,
                              quant ? &qa : nullptr, l, 0, prec != PLU_FP64 || c->csr ? 1 : 0,
-                             rem, r));
+                             rem, r, (r == 0 && !quant) ? &norm : nullptr));
         np += npr;
         // G = A V (step 3), the v-th pass.  Its column norms decide the rank:
         // E = ||A||_F^2 - sum ||G(:, j)||^2 must resolve eps^2 ||A||_F^2, which
@@ -962,7 +983,7 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
         memset(rep, 0, sizeof(*rep));
         rep->ms_total = ms;
         rep->ms_passes = pt.pairs_ms();
-        rep->passes = np + 1;
+        rep->passes = np;
         rep->rank = k;
         const double nA2 = c->h_scal[0], E = c->h_scal[1];
         rep->normA2 = nA2;

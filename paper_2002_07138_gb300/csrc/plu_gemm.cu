@@ -30,8 +30,13 @@ template <typename TA, typename TB, typename TC, bool TRANSA, bool TRANSB>
 __global__ void __launch_bounds__(NT)
 k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t lda,
             const TB* __restrict__ B, int64_t ldb, TC* __restrict__ P, int64_t kchunk, int tri,
-            const int* __restrict__ skip) {
+            const int* __restrict__ skip, double* __restrict__ norm_parts) {
     if (skip && *skip) return;                      // work cancelled on the device
+    // ||A||_F^2 from the entries this CTA loads (the CTAs of the first column
+    // tile cover every entry of A once)
+    const bool want_norm = norm_parts != nullptr && blockIdx.y == 0;
+    SqSum32 nsq;
+    double nsq64 = 0.0;
     __shared__ TC As[2][BK][BM + 1];
     __shared__ TC Bs[2][BK][BN + 1];
     const int t = threadIdx.x;
@@ -63,7 +68,14 @@ k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t l
             else        { ii = t % 64; kk = t / 64 + 4 * r; }
             const int64_t gi = i0 + ii, gk = k0 + kk;
             TC v = TC(0);
-            if (gi < M && gk < kend) v = TC(TRANSA ? A[gk + gi * lda] : A[gi + gk * lda]);
+            if (gi < M && gk < kend) {
+                const TA a = TRANSA ? A[gk + gi * lda] : A[gi + gk * lda];
+                if (want_norm) {
+                    if constexpr (sizeof(TA) == 4) nsq.add(float(a));
+                    else nsq64 = fma(double(a), double(a), nsq64);
+                }
+                v = TC(a);
+            }
             ra[r] = v;
         }
     };
@@ -139,6 +151,11 @@ k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t l
         __syncthreads();
         buf ^= 1;
     }
+    if (norm_parts) {                                  // uniform over the CTA
+        const double tot = cta_sum(want_norm ? nsq.value() + nsq64 : 0.0);
+        if (want_norm && threadIdx.x == 0)
+            norm_parts[blockIdx.x + int64_t(gridDim.x) * blockIdx.z] = tot;
+    }
     TC* Pz = P + int64_t(blockIdx.z) * M * N;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -210,7 +227,7 @@ template <typename TA, typename TB, typename TC, bool TA_T, bool TB_T>
 cudaError_t run(int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda, const TB* B,
                 int64_t ldb, double* C, int64_t ldc, void* partials, size_t part_cap,
                 int num_sms, cudaStream_t s, int tri = 0, int accum = 0,
-                const int* skip = nullptr) {
+                const int* skip = nullptr, const NormOut* norm = nullptr) {
     int splits = choose_splits(M, N, K, num_sms);
     const size_t one = size_t(M) * size_t(N) * sizeof(TC);
     if (!partials || part_cap < one) return cudaErrorInvalidValue;
@@ -219,11 +236,16 @@ cudaError_t run(int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda, const
     kchunk = (kchunk + BK - 1) / BK * BK;
     dim3 grid(unsigned((M + BM - 1) / BM), unsigned((N + BN - 1) / BN), unsigned(splits));
     TC* P = static_cast<TC*>(partials);
+    const int64_t nparts = int64_t(grid.x) * grid.z;
+    if (norm && (!norm->parts || !norm->out || nparts > norm->cap)) return cudaErrorInvalidValue;
     count_launch();
     k_gemm_simt<TA, TB, TC, TA_T, TB_T><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, P, kchunk,
-                                                           tri, skip);
+                                                           tri, skip,
+                                                           norm ? norm->parts : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (norm && (e = launch_sum_partials(norm->parts, int(nparts), norm->out, s)) != cudaSuccess)
+        return e;
     count_launch();
     // about 16 CTAs per SM over (row chunks) x (columns)
     int64_t gx = (M + 255) / 256, gy = N;
@@ -252,7 +274,7 @@ cudaError_t launch_gemm_simt(int trans, int64_t M, int64_t N, int64_t K, const v
                              int dtype, int64_t lda, const double* B, int64_t ldb,
                              double* C, int64_t ldc, int prec, void* partials,
                              size_t part_cap, float* b32_scratch, int num_sms, cudaStream_t s,
-                             int accum) {
+                             int accum, const NormOut* norm) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (prec == PLU_FP32) {
         count_launch();
@@ -261,21 +283,25 @@ cudaError_t launch_gemm_simt(int trans, int64_t M, int64_t N, int64_t K, const v
         if (e != cudaSuccess) return e;
         if (dtype == PLU_F32) {
             const float* Af = static_cast<const float*>(A);
-            return trans ? run<float, float, float, true, false>(M, N, K, Af, lda, b32_scratch, K, C, ldc, partials, part_cap, num_sms, s, 0, accum)
-                         : run<float, float, float, false, false>(M, N, K, Af, lda, b32_scratch, K, C, ldc, partials, part_cap, num_sms, s, 0, accum);
+            return trans ? run<float, float, float, true, false>(M, N, K, Af, lda, b32_scratch, K, C, ldc, partials, part_cap, num_sms, s, 0, accum, nullptr, norm)
+                         : run<float, float, float, false, false>(M, N, K, Af, lda, b32_scratch, K, C, ldc, partials, part_cap, num_sms, s, 0, accum, nullptr, norm);
         }
         const double* Ad = static_cast<const double*>(A);
-        return trans ? run<double, float, float, true, false>(M, N, K, Ad, lda, b32_scratch, K, C, ldc, partials, part_cap, num_sms, s, 0, accum)
-                     : run<double, float, float, false, false>(M, N, K, Ad, lda, b32_scratch, K, C, ldc, partials, part_cap, num_sms, s, 0, accum);
+        return trans ? run<double, float, float, true, false>(M, N, K, Ad, lda, b32_scratch, K, C, ldc, partials, part_cap, num_sms, s, 0, accum, nullptr, norm)
+                     : run<double, float, float, false, false>(M, N, K, Ad, lda, b32_scratch, K, C, ldc, partials, part_cap, num_sms, s, 0, accum, nullptr, norm);
     }
     if (dtype == PLU_F32) {
         const float* Af = static_cast<const float*>(A);
-        return trans ? run<float, double, double, true, false>(M, N, K, Af, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s, 0, accum)
-                     : run<float, double, double, false, false>(M, N, K, Af, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s, 0, accum);
+        return trans ? run<float, double, double, true, false>(M, N, K, Af, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s, 0, accum, nullptr, norm)
+                     : run<float, double, double, false, false>(M, N, K, Af, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s, 0, accum, nullptr, norm);
     }
     const double* Ad = static_cast<const double*>(A);
-    return trans ? run<double, double, double, true, false>(M, N, K, Ad, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s, 0, accum)
-                 : run<double, double, double, false, false>(M, N, K, Ad, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s, 0, accum);
+    return trans ? run<double, double, double, true, false>(M, N, K, Ad, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s, 0, accum, nullptr, norm)
+                 : run<double, double, double, false, false>(M, N, K, Ad, lda, B, ldb, C, ldc, partials, part_cap, num_sms, s, 0, accum, nullptr, norm);
+}
+
+int gemm_norm_parts(int64_t M, int64_t N, int64_t K, int num_sms) {
+    return int(((M + BM - 1) / BM) * choose_splits(M, N, K, num_sms));
 }
 
 cudaError_t launch_gemm_f64(int transA, int transB, int64_t M, int64_t N, int64_t K,

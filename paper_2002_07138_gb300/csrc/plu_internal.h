@@ -53,6 +53,43 @@ __device__ __forceinline__ double lu_multiplier(double x, double u, double rinv)
                                                                                      : x / u;
 }
 
+// Sum of squares of FP32 values without the FP64 pipe: each square is split
+// exactly into its FP32 product and the product's FMA residual, and the
+// products are added with a compensated (error-free) FP32 sum whose errors,
+// and the residuals, go to a second word.  value() is accurate to a few units
+// of 2^-44 relative for up to ~2^20 terms.  The explicit _rn intrinsics keep
+// the compiler from contracting the steps into other FMAs.  Squares above
+// ~1.8e38 overflow to inf.
+struct SqSum32 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float a) {
+        const float p = __fmul_rn(a, a);
+        const float e = __fmaf_rn(a, a, -p);          // a * a = p + e exactly
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        s = t;                                          // s + p = t + err exactly
+        c = __fadd_rn(c, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
+// Sum over the CTA of one double per thread (blockDim.x a multiple of 32, at
+// most 1024), in a fixed order; the result in thread 0.
+__device__ __forceinline__ double cta_sum(double v) {
+    __shared__ double wsum[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) wsum[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) s += wsum[w];
+    return s;
+}
+
 __device__ __forceinline__ int ld_volatile_i32(const int* p) {
     return *reinterpret_cast<const volatile int*>(p);
 }
@@ -101,6 +138,19 @@ struct Workspace {
     }
 };
 
+// ||A||_F^2 of the matrix a pass reads, accumulated by the pass kernel from
+// the entries it stages (every entry once, Alg. adaptivewithoutupdating step
+// 1 fused into the first pass): the kernel writes one FP64 partial per CTA to
+// parts (room for cap), the launcher then sums them in a fixed order into
+// *out (a device double).
+struct NormOut {
+    double* parts = nullptr;
+    int cap = 0;
+    double* out = nullptr;
+};
+// *out = the sum of part[0 .. count-1] in a fixed order (one CTA).
+cudaError_t launch_sum_partials(const double* part, int count, double* out, cudaStream_t s);
+
 // ---------------------------------------------------------------- RNG (a1)
 cudaError_t launch_gaussian(int64_t rows, int64_t cols, uint64_t seed, uint32_t stream_id,
                             double* out, int64_t ld, cudaStream_t s);
@@ -117,7 +167,9 @@ cudaError_t launch_gemm_simt(int trans, int64_t M, int64_t N, int64_t K, const v
                              int dtype, int64_t lda, const double* B, int64_t ldb,
                              double* C, int64_t ldc, int prec, void* partials,
                              size_t part_cap, float* b32_scratch, int num_sms, cudaStream_t s,
-                             int accum = 0);
+                             int accum = 0, const NormOut* norm = nullptr);
+// Partials a pass with the NormOut needs (one per CTA of the first column tile).
+int gemm_norm_parts(int64_t M, int64_t N, int64_t K, int num_sms);
 // accum > 0: C += op(A) B; accum < 0: C -= op(A) B; 0: C = op(A) B.
 // FP64 GEMM with transposed-B option for the small products of the tail:
 // C = A * op(B), op(B) = B (K x N) or B^T (B is N x K).
@@ -157,7 +209,8 @@ size_t tc_scratch_bytes(int64_t M, int64_t K, int cols, int num_sms);
 cudaError_t launch_tc_pass(int trans, int64_t m, int64_t n, const float* A, int64_t lda,
                            const double* X, int64_t ldx, int cols, double* Y, int64_t ldy,
                            void* scratch, size_t scratch_cap, int* dev_status, int num_sms,
-                           cudaStream_t s, int accum = 0, const void* xq_pre = nullptr);
+                           cudaStream_t s, int accum = 0, const void* xq_pre = nullptr,
+                           const NormOut* norm = nullptr);
 // The TF32 operand image of X (K x cols, FP64): the tiled, swizzled layout the
 // pass kernel copies one K step at a time.  out holds tc_operand_bytes(K, cols).
 size_t tc_operand_bytes(int64_t K, int cols);
@@ -175,7 +228,10 @@ struct QuantA {
 };
 size_t tc_quant_bytes(int64_t m, int64_t n, int prec);
 cudaError_t launch_tc_quantize(int prec, const float* A, int64_t m, int64_t n, int64_t lda,
-                               void* qbuf, QuantA* out, int num_sms, cudaStream_t s);
+                               void* qbuf, QuantA* out, int num_sms, cudaStream_t s,
+                               const NormOut* norm = nullptr);
+// Partials the quantisation (or a tensor-core pass) needs for the NormOut.
+int quant_norm_parts(int num_sms);
 // The stream-K partial tiles of one pass, left in its scratch for a later
 // reduction: CTA c's segment for row block b at part + ((c max_segs + b -
 // c per / ksteps) npad) 128.
@@ -287,7 +343,11 @@ size_t spmm_scratch_bytes(int64_t K, int cols);
 cudaError_t launch_spmm_csr(int64_t rows, int64_t K, int64_t nnz, const int64_t* row_ptr,
                             const int32_t* col_idx, const double* val, const double* X,
                             int64_t ldx, int cols, double* Y, int64_t ldy, void* scratch,
-                            size_t scratch_cap, int* dev_status, int num_sms, cudaStream_t s);
+                            size_t scratch_cap, int* dev_status, int num_sms, cudaStream_t s,
+                            const NormOut* norm = nullptr);
+// Partials the sparse pass needs for the NormOut (the sum of the squared
+// values of the CSR it reads).
+int spmm_norm_parts(int64_t rows, int num_sms);
 
 // -------------------------------------------------------- rank and norms
 size_t norm2_scratch_bytes(int num_sms);

@@ -65,6 +65,16 @@ __global__ void k_sum_partials(const double* __restrict__ part, int count, doubl
     }
 }
 
+// *out = sum of part[0 .. count): thread t adds part[t], part[t + 1024], ...,
+// then a fixed tree over the threads (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024)
+k_sum_partials_wide(const double* __restrict__ part, int count, double* __restrict__ out) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < count; i += 1024) s += part[i];
+    s = cta_sum(s);
+    if (threadIdx.x == 0) *out = s;
+}
+
 __global__ void __launch_bounds__(RT)
 k_colnorm2(int64_t rows, const double* __restrict__ G, int64_t ldg, double* __restrict__ out) {
     __shared__ double sh[RT];
@@ -128,6 +138,13 @@ __global__ void k_scatter_rows(int64_t rows, const int32_t* __restrict__ perm,
 }  // namespace
 
 size_t norm2_scratch_bytes(int num_sms) { return size_t(num_sms) * 4 * sizeof(double) + 256; }
+
+cudaError_t launch_sum_partials(const double* part, int count, double* out, cudaStream_t s) {
+    if (count < 0 || !out || (count > 0 && !part)) return cudaErrorInvalidValue;
+    count_launch();
+    k_sum_partials_wide<<<1, 1024, 0, s>>>(part, count, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sumsq(const double* x, int64_t count, double* out, void* scratch,
                          int num_sms, cudaStream_t s) {

@@ -54,7 +54,10 @@ __global__ void __launch_bounds__(SP_WARPS * 32, SP_CTAS_PER_SM)
 k_spmm_csr(int64_t rows, int64_t K, int64_t nnz, int cols, int xs,
            const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
            const double* __restrict__ val, const double* __restrict__ Xr,
-           double* __restrict__ Y, int64_t ldy, int* status) {
+           double* __restrict__ Y, int64_t ldy, int* status, double* __restrict__ norm_parts) {
+    // norm_parts (nullable): the CTA's sum of the squared values it reads
+    // (in the first column chunk, where every nonzero is read once)
+    double nsq = 0.0;
     extern __shared__ double ys[];            // SP_ROWS x (SP_CHUNK + 1)
     constexpr int YS = SP_CHUNK + 1;
     constexpr int NCM = SP_CHUNK / 16;        // column slots of a lane
@@ -93,6 +96,7 @@ k_spmm_csr(int64_t rows, int64_t K, int64_t nnz, int cols, int xs,
                                 col = 0;
                                 a = 0.0;
                             }
+                            if (norm_parts && c0 == 0) nsq = fma(a, a, nsq);
                         }
                         const int cnt = e - t0 < 32 ? int(e - t0) : 32;
                         // 2 nonzeros per step, one per half-warp
@@ -135,6 +139,10 @@ k_spmm_csr(int64_t rows, int64_t K, int64_t nnz, int cols, int xs,
             __syncthreads();
         }
     }
+    if (norm_parts) {
+        const double tot = cta_sum(nsq);
+        if (threadIdx.x == 0) norm_parts[blockIdx.x] = tot;
+    }
 }
 
 }  // namespace
@@ -148,7 +156,8 @@ size_t spmm_scratch_bytes(int64_t K, int cols) {
 cudaError_t launch_spmm_csr(int64_t rows, int64_t K, int64_t nnz, const int64_t* row_ptr,
                             const int32_t* col_idx, const double* val, const double* X,
                             int64_t ldx, int cols, double* Y, int64_t ldy, void* scratch,
-                            size_t scratch_cap, int* dev_status, int num_sms, cudaStream_t s) {
+                            size_t scratch_cap, int* dev_status, int num_sms, cudaStream_t s,
+                            const NormOut* norm) {
     if (rows < 1 || K < 1 || cols < 1 || nnz < 0 || !row_ptr || !X || !Y || !dev_status)
         return cudaErrorInvalidValue;
     if (nnz > 0 && (!col_idx || !val)) return cudaErrorInvalidValue;
@@ -168,10 +177,20 @@ cudaError_t launch_spmm_csr(int64_t rows, int64_t K, int64_t nnz, const int64_t*
     int64_t blocks = (rows + SP_ROWS - 1) / SP_ROWS;
     const int64_t cap = int64_t(num_sms) * SP_CTAS_PER_SM;
     if (blocks > cap) blocks = cap;
+    if (norm && (!norm->parts || !norm->out || blocks > norm->cap)) return cudaErrorInvalidValue;
     count_launch();
     k_spmm_csr<<<unsigned(blocks), SP_WARPS * 32, SP_SMEM, s>>>(
-        rows, K, nnz, cols, xs, row_ptr, col_idx, val, Xr, Y, ldy, dev_status);
-    return cudaGetLastError();
+        rows, K, nnz, cols, xs, row_ptr, col_idx, val, Xr, Y, ldy, dev_status,
+        norm ? norm->parts : nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (norm) return launch_sum_partials(norm->parts, int(blocks), norm->out, s);
+    return cudaSuccess;
+}
+
+int spmm_norm_parts(int64_t rows, int num_sms) {
+    const int64_t blocks = (rows + SP_ROWS - 1) / SP_ROWS;
+    const int64_t cap = int64_t(num_sms) * SP_CTAS_PER_SM;
+    return int(blocks < cap ? blocks : cap);
 }
 
 }  // namespace plu

@@ -97,6 +97,7 @@ struct TcParams {
     int b_bytes;        // npad * 128
     uint32_t tmem_cols;
     float* part;        // [grid][max_segs][npad][128]
+    double* norm_parts; // per-CTA sums of squares of the A tiles (NORM kernels)
     int* status;
 };
 
@@ -122,8 +123,15 @@ constexpr int MAX_SA = 16, MAX_SK = 4;
 // g - sb after having checked that of stage g - npa - sb, so it never lags by
 // a full ring: that needs npa <= sa for A^T X (a_empty, depth sa) and
 // npa <= sb = sk for A X (k_empty, depth sk).
-template <bool XPOSE, int KIND>
-__global__ void __launch_bounds__(XPOSE ? TC_THREADS_X : TC_THREADS, 1)
+//
+// NORM (TF32 only): the kernel also sums the squares of every entry of A it
+// stages (each entry once over the grid: the stream-K shares partition the
+// iteration space), for ||A||_F^2 of Alg. adaptivewithoutupdating step 1
+// fused into the first pass.  For Y = A X the transposer threads add the
+// entries they move; for Y = A^T X four more warps (10-13) read each A stage
+// and release it together with the MMA commit.
+template <bool XPOSE, int KIND, bool NORM = false>
+__global__ void __launch_bounds__((XPOSE || NORM) ? TC_THREADS_X : TC_THREADS, 1)
 k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restrict__ Bt,
           const TcParams P) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -145,6 +153,7 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restr
     constexpr int EPI_WARP = 4, MMA_WARP = 8, XP_WARP = 10;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    SqSum32 nsq;                                  // NORM: this thread's share of ||A||^2
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     // [A ring: sa x 16 KB][K-major ring: sk x 16 KB][B ring: sb x b_bytes]
@@ -159,7 +168,8 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restr
         abort_flag = 0;
         for (int i = 0; i < P.sa; ++i) {
             mbar_init(&a_full[i], 1);
-            mbar_init(&a_empty[i], XPOSE ? 4 : 1);      // transposer warps, or the MMA commit
+            // transposer warps, or the MMA commit (plus the norm warps)
+            mbar_init(&a_empty[i], XPOSE ? 4 : (NORM ? 5 : 1));
         }
         for (int i = 0; i < P.sk; ++i) {
             mbar_init(&k_full[i], 4);                   // one arrival per transposer warp
@@ -320,6 +330,7 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restr
                         if constexpr (E == 4) v = *reinterpret_cast<const uint32_t*>(src);
                         else if constexpr (E == 2) v = *reinterpret_cast<const uint16_t*>(src);
                         else v = *src;
+                        if constexpr (NORM && E == 4) nsq.add(__uint_as_float(v));
                         w[(e * E) >> 2] |= v << (((e * E) & 3) * 8);
                     }
                     *reinterpret_cast<uint4*>(kt + m * 128 + ((c ^ (m & 7)) << 4)) =
@@ -333,6 +344,30 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restr
                 }
                 if (++sa_ == P.sa) { sa_ = 0; ph_a ^= 1u; }
                 if (++sk_ == P.sk) { sk_ = 0; ++kround; }
+            }
+        } else if (NORM && !XPOSE && warp >= XP_WARP && warp < XP_WARP + 4) {
+            // ----------------------------------------- norm readers (A^T X)
+            // thread tn reads 16-byte words tn, tn + 128, ... of each A stage
+            const int tn = threadIdx.x - 32 * XP_WARP;
+            int sa_ = 0;
+            uint32_t ph_a = 0;
+            for (int64_t it = 0; it < s1 - s0; ++it) {
+                if (!mbar_wait(&a_full[sa_], ph_a, &abort_flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                const uint4* tile = reinterpret_cast<const uint4*>(a_ring + sa_ * A_TILE);
+#pragma unroll
+                for (int q = 0; q < A_TILE / 16 / 128; ++q) {
+                    const uint4 v = tile[tn + 128 * q];
+                    nsq.add(__uint_as_float(v.x));
+                    nsq.add(__uint_as_float(v.y));
+                    nsq.add(__uint_as_float(v.z));
+                    nsq.add(__uint_as_float(v.w));
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&a_empty[sa_]);   // with the MMA commit
+                if (++sa_ == P.sa) { sa_ = 0; ph_a ^= 1u; }
             }
         } else if (warp >= EPI_WARP && warp < EPI_WARP + 4) {
             // -------------------------------------------------- epilogue
@@ -363,6 +398,10 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restr
                 s = next;
             }
         }
+    }
+    if constexpr (NORM) {
+        const double tot = cta_sum(nsq.value());     // threads without entries add 0
+        if (threadIdx.x == 0) P.norm_parts[blockIdx.x] = tot;
     }
     __syncthreads();
     if (abort_flag) {
@@ -579,12 +618,23 @@ __global__ void k_fp8_colscale(int64_t K, int cols, const double* __restrict__ X
 }
 
 // FP32 A -> BF16 copy (column-major, ld ldq), round to nearest even.
+// norm_parts (nullable): the CTA's sum of squares of the entries it reads
+// (the quantisation reads every entry once: ||A||_F^2 comes with it).
 __global__ void k_quant_bf16(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda,
-                             __nv_bfloat16* __restrict__ Aq, int64_t ldq) {
+                             __nv_bfloat16* __restrict__ Aq, int64_t ldq,
+                             double* __restrict__ norm_parts) {
+    SqSum32 nsq;
     for (int64_t j = blockIdx.y; j < n; j += gridDim.y)
         for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m;
-             i += int64_t(gridDim.x) * blockDim.x)
-            Aq[i + j * ldq] = __float2bfloat16_rn(A[i + j * lda]);
+             i += int64_t(gridDim.x) * blockDim.x) {
+            const float a = A[i + j * lda];
+            if (norm_parts) nsq.add(a);
+            Aq[i + j * ldq] = __float2bfloat16_rn(a);
+        }
+    if (norm_parts) {
+        const double tot = cta_sum(nsq.value());
+        if (threadIdx.x == 0) norm_parts[blockIdx.x + int64_t(gridDim.x) * blockIdx.y] = tot;
+    }
 }
 
 // amax of every 128 x 128 tile of A (tile (rb, cb) at amax[rb + cb * RB]).
@@ -624,15 +674,25 @@ __global__ void k_tile_scales(const float* __restrict__ amax, int RB, int CB,
 }
 
 // FP32 A -> FP8-E4M3 copy A(i, j) / (s_r[i/128] s_c[j/128]), saturated.
+// norm_parts (nullable): as in k_quant_bf16.
 __global__ void k_quant_fp8(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda,
                             const float* __restrict__ s_r, const float* __restrict__ s_c,
-                            __nv_fp8_storage_t* __restrict__ Aq, int64_t ldq) {
+                            __nv_fp8_storage_t* __restrict__ Aq, int64_t ldq,
+                            double* __restrict__ norm_parts) {
+    SqSum32 nsq;
     for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
         const float cs = s_c[j / 128];
         for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m;
-             i += int64_t(gridDim.x) * blockDim.x)
-            Aq[i + j * ldq] = __nv_cvt_float_to_fp8(A[i + j * lda] / (s_r[i / 128] * cs),
-                                                    __NV_SATFINITE, __NV_E4M3);
+             i += int64_t(gridDim.x) * blockDim.x) {
+            const float a = A[i + j * lda];
+            if (norm_parts) nsq.add(a);
+            Aq[i + j * ldq] = __nv_cvt_float_to_fp8(a / (s_r[i / 128] * cs), __NV_SATFINITE,
+                                                    __NV_E4M3);
+        }
+    }
+    if (norm_parts) {
+        const double tot = cta_sum(nsq.value());
+        if (threadIdx.x == 0) norm_parts[blockIdx.x + int64_t(gridDim.x) * blockIdx.y] = tot;
     }
 }
 
@@ -746,7 +806,8 @@ size_t tc_quant_bytes(int64_t m, int64_t n, int prec) {
 }
 
 cudaError_t launch_tc_quantize(int prec, const float* A, int64_t m, int64_t n, int64_t lda,
-                               void* qbuf, QuantA* out, int num_sms, cudaStream_t s) {
+                               void* qbuf, QuantA* out, int num_sms, cudaStream_t s,
+                               const NormOut* norm) {
     const int E = prec == PLU_BF16 ? 2 : 1;
     const int64_t ldq = (m + 15) / 16 * 16;
     const int64_t RB = (m + 127) / 128, CB = (n + 127) / 128;
@@ -758,12 +819,21 @@ cudaError_t launch_tc_quantize(int prec, const float* A, int64_t m, int64_t n, i
     float* s_r = static_cast<float*>(w.take(size_t(RB) * sizeof(float)));
     float* s_c = static_cast<float*>(w.take(size_t(CB) * sizeof(float)));
     if (!Aq || !amax || !s_r || !s_c) return cudaErrorInvalidValue;
-    const unsigned gy = unsigned(n < 65535 ? n : 65535);
-    const unsigned gx = unsigned((m + 255) / 256 < 64 ? (m + 255) / 256 : 64);
+    unsigned gy = unsigned(n < 65535 ? n : 65535);
+    unsigned gx = unsigned((m + 255) / 256 < 64 ? (m + 255) / 256 : 64);
+    double* nparts = nullptr;
+    if (norm) {
+        // one partial per CTA: at most 8 x 152-ish CTAs
+        if (gx > 8) gx = 8;
+        if (gy > unsigned(num_sms)) gy = unsigned(num_sms);
+        if (!norm->parts || !norm->out || int64_t(gx) * gy > norm->cap) return cudaErrorInvalidValue;
+        nparts = norm->parts;
+    }
     cudaError_t e;
     if (prec == PLU_BF16) {
         count_launch();
-        k_quant_bf16<<<dim3(gx, gy), 256, 0, s>>>(A, m, n, lda, static_cast<__nv_bfloat16*>(Aq), ldq);
+        k_quant_bf16<<<dim3(gx, gy), 256, 0, s>>>(A, m, n, lda, static_cast<__nv_bfloat16*>(Aq), ldq,
+                                                  nparts);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         out->s_r = nullptr;
@@ -777,11 +847,13 @@ cudaError_t launch_tc_quantize(int prec, const float* A, int64_t m, int64_t n, i
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         count_launch();
         k_quant_fp8<<<dim3(gx, gy), 256, 0, s>>>(A, m, n, lda, s_r, s_c,
-                                                 static_cast<__nv_fp8_storage_t*>(Aq), ldq);
+                                                 static_cast<__nv_fp8_storage_t*>(Aq), ldq, nparts);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         out->s_r = s_r;
         out->s_c = s_c;
     }
+    if (norm && (e = launch_sum_partials(nparts, int(gx * gy), norm->out, s)) != cudaSuccess)
+        return e;
     out->data = Aq;
     out->ld = ldq;
     out->prec = prec;
@@ -797,7 +869,8 @@ cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t
                          const float* s_r, const float* s_c, const double* X, int64_t ldx,
                          int cols, double* Y, int64_t ldy, void* scratch, size_t scratch_cap,
                          int* dev_status, int num_sms, cudaStream_t s, int accum,
-                         const void* xq_pre = nullptr, TcPartials* keep = nullptr) {
+                         const void* xq_pre = nullptr, TcPartials* keep = nullptr,
+                         const NormOut* norm = nullptr) {
     constexpr int E = Kind<KIND>::E;
     constexpr int BKE = 128 / E;
     const int64_t M = trans ? n : m;
@@ -857,7 +930,28 @@ cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t
     P.tmem_cols = p.tmem_cols;
     P.part = part;
     P.status = dev_status;
-    if (trans) {
+    P.norm_parts = nullptr;
+    if (norm) {
+        if (KIND != KIND_TF32 || !norm->parts || !norm->out || p.grid > norm->cap)
+            return cudaErrorInvalidValue;
+        P.norm_parts = norm->parts;
+        const unsigned char* op = xq_pre ? static_cast<const unsigned char*>(xq_pre) : xq;
+        if (trans) {
+            e = cudaFuncSetAttribute(k_tc_pass<false, KIND, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(p.smem));
+            if (e != cudaSuccess) return e;
+            count_launch();
+            k_tc_pass<false, KIND, true><<<p.grid, TC_THREADS_X, p.smem, s>>>(mapA, op, P);
+        } else {
+            e = cudaFuncSetAttribute(k_tc_pass<true, KIND, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(p.smem));
+            if (e != cudaSuccess) return e;
+            count_launch();
+            k_tc_pass<true, KIND, true><<<p.grid, TC_THREADS_X, p.smem, s>>>(mapA, op, P);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_sum_partials(norm->parts, p.grid, norm->out, s)) != cudaSuccess) return e;
+    } else if (trans) {
         e = cudaFuncSetAttribute(k_tc_pass<false, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(p.smem));
         if (e != cudaSuccess) return e;
@@ -906,10 +1000,13 @@ cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t
 cudaError_t launch_tc_pass(int trans, int64_t m, int64_t n, const float* A, int64_t lda,
                            const double* X, int64_t ldx, int cols, double* Y, int64_t ldy,
                            void* scratch, size_t scratch_cap, int* dev_status, int num_sms,
-                           cudaStream_t s, int accum, const void* xq_pre) {
+                           cudaStream_t s, int accum, const void* xq_pre, const NormOut* norm) {
     return tc_pass_kind<KIND_TF32>(trans, m, n, A, lda, nullptr, nullptr, X, ldx, cols, Y, ldy,
-                                   scratch, scratch_cap, dev_status, num_sms, s, accum, xq_pre);
+                                   scratch, scratch_cap, dev_status, num_sms, s, accum, xq_pre,
+                                   nullptr, norm);
 }
+
+int quant_norm_parts(int num_sms) { return num_sms * 8; }
 
 cudaError_t launch_tc_reduce_bands(const TcPartials* bands, int nbands, int64_t M, int cols,
                                   double* Y, int64_t ldy, cudaStream_t s) {

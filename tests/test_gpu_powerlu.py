@@ -100,7 +100,8 @@ def test_powerlu_fp_parity(ctx, precise):
     nA2 = float(np.sum(A * A))
     assert abs(rep["normA2"] - nA2) <= 1e-12 * nA2
     assert abs(rep["indicator"] - math.sqrt(max(E, 0) / nA2)) <= 1e-8
-    assert rep["passes"] == v + 1
+    # ||A||_F^2 comes from the first pass: A is read exactly v times
+    assert rep["passes"] == v
 
 
 @pytest.mark.parametrize("v,precise", [(3, False), (4, True)])
@@ -118,7 +119,7 @@ def test_powerlu_fp_restart_parity(ctx, v, precise):
                                                        prec="fp64", precise=precise,
                                                        max_rounds=rounds)
     assert (gk, gmet) == (k, met)
-    assert rep["rounds"] >= 2 and rep["passes"] == rep["rounds"] * v + 1
+    assert rep["rounds"] >= 2 and rep["passes"] == rep["rounds"] * v
     check_parity(A, (gp, gq, gL, gU), (p, q, L, U), tol=1e-9)
     assert oracle.rel_lu_error(A, gp.cpu().numpy(), gq.cpu().numpy(), host(gL), host(gU)) <= eps
     nA2 = float(np.sum(A * A))
@@ -366,3 +367,21 @@ def test_fixed_precision_20000x10000_full_size(ctx):
     assert tmet and tk == k
     e32 = oracle.rel_lu_error(Ah, tp.cpu().numpy(), tq.cpu().numpy(), host(tL), host(tU))
     assert e64 <= w.eps and e32 <= 1.1 * e64, (e32, e64)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16", "fp8"])
+@pytest.mark.parametrize("v", [3, 4])
+def test_powerlu_fp_norm_from_first_read(ctx, prec, v):
+    """Alg. adaptivewithoutupdating step 1 fused into the first read of A:
+    ||A||_F^2 summed by the first pass (A Omega for odd v, A^T Omega for even
+    v: both tensor-core orientations, the SIMT passes) or by the quantisation
+    (BF16, FP8) equals the sum of the squares of the stored entries, and A is
+    read exactly v times."""
+    m, n = 3001, 2003                      # ragged tiles in both orientations
+    A32 = synth.svd_matrix_np(m, n, synth.sigma_profile("type2", n), seed=4).astype(np.float32)
+    A32[7, 5] = 3.0e3                      # a large entry among small ones
+    gk, gp, gq, gL, gU, gmet, rep = plu.plu_powerlu_fp(ctx, dev(A32, torch.float32), 1e-3, 8, 48,
+                                                       v, seed=1, prec=prec)
+    nA2 = float(np.sum(A32.astype(np.float64) ** 2))
+    assert abs(rep["normA2"] - nA2) <= 1e-12 * nA2
+    assert rep["passes"] == v

@@ -195,9 +195,36 @@ def test_spmm_full_size_sampled(ctx, full_sprand):
         assert np.all(np.abs(Y - ref) <= 2.3e-16 * 200 * bound)
 
 
+def sparse_rel_error(m, rp, ci, val, p, q, L, U):
+    """||A - P^T L U Q||_F / ||A||_F for a sparse A without forming L U:
+    ||A||^2 is the sum of the squared values, <A, P^T L U Q> a k-length dot
+    product per nonzero (row pinv[i] of L, column qinv[j] of U), and
+    ||L U||^2 = trace((L^T L)(U U^T)).  CUDA tensors; rp, ci, val the CSR."""
+    dev = L.device
+    rpt = torch.as_tensor(rp, device=dev)
+    cit = torch.as_tensor(ci, device=dev).long()
+    vt = torch.as_tensor(val, device=dev)
+    pinv = torch.empty_like(p.long())
+    pinv[p.long()] = torch.arange(m, device=dev)
+    qinv = torch.empty_like(q.long())
+    qinv[q.long()] = torch.arange(q.numel(), device=dev)
+    rows = torch.repeat_interleave(torch.arange(m, device=dev), rpt[1:] - rpt[:-1])
+    normA2 = float((vt * vt).sum())
+    inner = 0.0
+    step = 1 << 19
+    for s0 in range(0, vt.numel(), step):
+        r = pinv[rows[s0:s0 + step]]
+        c = qinv[cit[s0:s0 + step]]
+        inner += float((vt[s0:s0 + step] * (L[r] * U[:, c].t()).sum(1)).sum())
+    normLU2 = float(((L.t() @ L) * (U @ U.t())).sum())
+    return max(normA2 - 2.0 * inner + normLU2, 0.0) ** 0.5 / normA2 ** 0.5
+
+
 def test_powerlu_csr_full_size(ctx, full_sprand):
     """PowerLU on the full-size sprand A (k = l = 200, v = 4): valid
-    permutations, unit lower L in pivoted order, finite factors, 4 passes."""
+    permutations, finite factors, 4 passes, and the relative error (formed
+    from the nonzeros) equal to that of the dense FP64 path on the same
+    matrix, whose pivots it shares."""
     n, rp, ci, val = full_sprand
     S = to_device(n, n, rp, ci, val)
     k = l = 200
@@ -206,3 +233,16 @@ def test_powerlu_csr_full_size(ctx, full_sprand):
     assert np.array_equal(np.sort(p), np.arange(n)) and np.array_equal(np.sort(q), np.arange(n))
     assert torch.isfinite(gL).all() and torch.isfinite(gU).all()
     assert rep["passes"] == 4
+    err = sparse_rel_error(n, rp, ci, val, gp, gq, gL, gU)
+    # the same algorithm with dense FP64 passes over the densified A
+    Ad = plu.colmajor_empty(n, n)
+    Ad.zero_()
+    rows = torch.repeat_interleave(torch.arange(n), torch.from_numpy(np.diff(rp)))
+    Ad.index_put_((rows.cuda(), torch.from_numpy(ci).long().cuda()), torch.from_numpy(val).cuda())
+    dp, dq, dL, dU, _ = plu.plu_powerlu(ctx, Ad, k, l, 4, seed=0, prec="fp64")
+    del Ad
+    torch.cuda.empty_cache()
+    assert np.array_equal(dp.cpu().numpy(), p) and np.array_equal(dq.cpu().numpy(), q)
+    err_dense = sparse_rel_error(n, rp, ci, val, dp, dq, dL, dU)
+    assert 0.0 < err < 1.0
+    assert abs(err - err_dense) <= 1e-9 * err_dense
