@@ -38,17 +38,26 @@ extern "C" {
  * PLU_FP64: FP64 FMA.  PLU_FP32: FP32 FMA, FP32 accumulation.
  * PLU_TF32, PLU_BF16, PLU_FP8_E4M3: tensor-core products with FP32
  * accumulation.  TF32 reads the FP32 A directly; BF16 and FP8 read a
- * quantised copy made once per call (FP8 with per-tile scales).  In these
- * modes the last pass Y = A V_k reads the FP32 A through TF32, and the
- * fixed-precision pass G = A V (whose column norms decide the rank) runs in
- * FP32 arithmetic.  Everything between the passes (LU, QR, rank, tail) is
- * FP64 in every mode. */
+ * quantised copy made once per call (FP8 with per-tile scales).
+ * PLU_TF32X3: split-precision tensor-core products, FP32-accurate: A and the
+ * small operand are each split into a TF32 head and a TF32 remainder and
+ * three TF32 products (head x head, remainder x head, head x remainder) are
+ * summed in FP32 (about 3x the tensor work of PLU_TF32, same HBM traffic).
+ * In the TF32, BF16 and FP8 modes the products that enter the result to first
+ * order run as PLU_TF32X3 on the FP32 A: the last pass Y = A V_k of PowerLU
+ * and RandLU's pass B^T = A^T W.  The fixed-precision pass G = A V, whose
+ * column norms decide the rank, runs with FP32 FMAs in every mode but FP64
+ * (the tensor cores' accumulation shrinks sums by ~1e-6 relative even when
+ * split, which would bias the rank indicator).  Everything between the passes
+ * (LU, QR, rank, tail) is FP64 in every mode.  The tensor-core modes need A
+ * stored in FP32. */
 typedef enum {
     PLU_FP64 = 0,
     PLU_TF32 = 1,
     PLU_BF16 = 2,
     PLU_FP8_E4M3 = 3,
-    PLU_FP32 = 4
+    PLU_FP32 = 4,
+    PLU_TF32X3 = 5
 } plu_prec;
 
 /* Element type of A. */

@@ -15,5 +15,5 @@ from ._binding import (  # noqa: F401
     PREC, STATUS,
     SIGNATURES,
     STREAM_OMEGA_N, STREAM_OMEGA_M, STREAM_OMEGA_SP,
-    PLU_FP64, PLU_TF32, PLU_BF16, PLU_FP8_E4M3, PLU_FP32, PLU_F64, PLU_F32,
+    PLU_FP64, PLU_TF32, PLU_BF16, PLU_FP8_E4M3, PLU_FP32, PLU_TF32X3, PLU_F64, PLU_F32,
 )

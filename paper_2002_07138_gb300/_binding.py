@@ -13,12 +13,12 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpowerlu.so")
 
-PLU_FP64, PLU_TF32, PLU_BF16, PLU_FP8_E4M3, PLU_FP32 = 0, 1, 2, 3, 4
+PLU_FP64, PLU_TF32, PLU_BF16, PLU_FP8_E4M3, PLU_FP32, PLU_TF32X3 = 0, 1, 2, 3, 4, 5
 PLU_F64, PLU_F32 = 0, 1
 STATUS = {0: "PLU_OK", 1: "PLU_EINVAL", 2: "PLU_ENOMEM", 3: "PLU_ECUDA", 4: "PLU_ENUMERIC",
           5: "PLU_ETIMEOUT", 6: "PLU_TOL_NOT_MET", 7: "PLU_EUNSUPPORTED", 8: "PLU_EINDEX"}
 PREC = {"fp64": PLU_FP64, "tf32": PLU_TF32, "bf16": PLU_BF16, "fp8": PLU_FP8_E4M3,
-        "fp32": PLU_FP32}
+        "fp32": PLU_FP32, "tf32x3": PLU_TF32X3}
 
 STREAM_OMEGA_N, STREAM_OMEGA_M, STREAM_OMEGA_SP = 1, 2, 3
 

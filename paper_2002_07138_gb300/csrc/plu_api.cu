@@ -123,7 +123,7 @@ plu_status check_matrix(plu_ctx* c, const plu_matrix* A) {
 
 plu_status check_prec(plu_ctx* c, int prec, const plu_matrix* A) {
     if (prec == PLU_FP64 || prec == PLU_FP32) return PLU_OK;
-    if (prec == PLU_TF32 || prec == PLU_BF16 || prec == PLU_FP8_E4M3) {
+    if (prec == PLU_TF32 || prec == PLU_BF16 || prec == PLU_FP8_E4M3 || prec == PLU_TF32X3) {
         if (A && A->dtype != PLU_F32)
             return fail(c, PLU_EUNSUPPORTED, "tensor-core passes need A stored in FP32");
         return PLU_OK;
@@ -147,6 +147,12 @@ plu_status dev_status_to_plu(plu_ctx* c, int st) {
 
 // ---- workspace needs of the steps
 bool is_tc(int prec) { return prec == PLU_TF32 || prec == PLU_BF16 || prec == PLU_FP8_E4M3; }
+
+// FP32-accurate split products on the tensor cores (3xTF32, plu_tcsplit.cu)
+// over an FP32 A, FP32 SIMT FMAs where the split kernel does not take the
+// shape.  The mixed modes take it for the products that enter the result to
+// first order: PowerLU's last pass and RandLU's B pass.
+constexpr int kPrecSplit = PLU_TF32X3;
 
 // Scratch of a panel LU of either kind (FP64 FMA updates or tensor-core updates).
 size_t lu_scratch_bytes(int64_t rows, int cols) {
@@ -172,11 +178,15 @@ cudaError_t launch_lu(const plu_ctx* c, int prec, int64_t rows, int cols, double
 }
 
 size_t pass_ws(int64_t M, int64_t N, int64_t K, int prec, int sms) {
-    const int sprec = is_tc(prec) ? PLU_FP32 : prec;
+    const int sprec = (is_tc(prec) || prec == kPrecSplit) ? PLU_FP32 : prec;
     size_t b = gemm_partials_bytes(M, N, K, sprec, sms) + 256;
     if (sprec == PLU_FP32) b += size_t(K) * N * sizeof(float) + 256;
     if (is_tc(prec)) {
         const size_t t = tc_scratch_bytes(M, K, int(N), sms);
+        if (t > b) b = t;
+    }
+    if (is_tc(prec) || prec == kPrecSplit) {
+        const size_t t = tcs_scratch_bytes(M, K, int(N), sms);
         if (t > b) b = t;
     }
     return b;
@@ -214,7 +224,15 @@ plu_status do_pass(plu_ctx* c, const plu_matrix* A, int trans, const double* X, 
                                    c->stream, accum, xq_pre, norm));
         return PLU_OK;
     }
-    if (is_tc(prec)) prec = PLU_FP32;
+    if (prec == kPrecSplit && A->dtype == PLU_F32 &&
+        tcs_supported(M, K, cols, A->data, A->ld, trans)) {
+        // xq_pre: X already in the split operand form (launch_tcs_operand)
+        PLU_CUDA(c, launch_tc_split_pass(trans, A->m, A->n, static_cast<const float*>(A->data),
+                                         A->ld, X, ldx, cols, Y, ldy, ws, ws_cap, c->d_status,
+                                         c->num_sms, c->stream, accum, xq_pre, norm));
+        return PLU_OK;
+    }
+    if (is_tc(prec) || prec == kPrecSplit) prec = PLU_FP32;
     Workspace w;
     w.base = ws;
     w.cap = ws_cap;
@@ -828,10 +846,11 @@ plu_status plu_powerlu(plu_ctx* c, const plu_matrix* A, int k, int l, int v, uin
                          quant ? &qa : nullptr, k, prec != PLU_FP64 ? 1 : 0,
                          prec != PLU_FP64 || c->csr ? 1 : 0));
     // Y = A V(:, 1:k) (Alg. bpowerlu step 3), the v-th pass; in the mixed
-    // modes it reads the FP32 A through TF32 (it enters the result to first order)
+    // modes it reads the FP32 A with FP32-accurate split products (3xTF32):
+    // it enters the result to first order
     pt.phase(PLU_PHASE_LAST_PASS);
     pt.mark();
-    PLU_TRY(do_pass(c, A, 0, V, n, k, is_tc(prec) ? int(PLU_TF32) : int(prec), Z, m, step,
+    PLU_TRY(do_pass(c, A, 0, V, n, k, is_tc(prec) ? kPrecSplit : int(prec), Z, m, step,
                     pl.step_bytes));
     pt.mark();
     ++np;
@@ -935,13 +954,16 @@ plu_status powerlu_fp_rounds(plu_ctx* c, const plu_matrix* A, double eps, int b,
                              rem, r, (r == 0 && !quant) ? &norm : nullptr));
         np += npr;
         // G = A V (step 3), the v-th pass.  Its column norms decide the rank:
-        // E = ||A||_F^2 - sum ||G(:, j)||^2 must resolve eps^2 ||A||_F^2, which
-        // TF32 rounding (relative bias ~1e-3) cannot, so the mixed modes take
-        // this pass in FP32 arithmetic on the FP32 A.
+        // E = ||A||_F^2 - sum ||G(:, j)||^2 must resolve eps^2 ||A||_F^2 without
+        // bias.  The tensor cores' accumulator adds shrink every sum toward
+        // zero (measured at 32768^2: -4e-4 relative for TF32 and -2e-6 for the
+        // split products even with FP64 sums of 1024-long segments), which
+        // biases sum ||G(:, j)||^2 by more than eps^2 = 1e-6; so every mode but
+        // FP64 takes this pass with FP32 FMAs and FP64 partial sums (unbiased).
         pt.phase(PLU_PHASE_LAST_PASS);
         pt.mark();
-        PLU_TRY(do_pass(c, A, 0, V, n, l, is_tc(prec) ? int(PLU_FP32) : int(prec), Z, m, step,
-                        pl.step_bytes));
+        PLU_TRY(do_pass(c, A, 0, V, n, l, prec == PLU_FP64 ? int(prec) : int(PLU_FP32), Z, m,
+                        step, pl.step_bytes));
         pt.mark();
         PLU_TRY(remainder_correct(c, A, rem, 0, V, n, l, Z, m, step, pl.step_bytes));
         ++np;
@@ -1066,8 +1088,9 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
     const size_t oTp = lay.add(tp);
     const size_t oInfo = lay.add(2 * sizeof(int32_t));
     // Omega in the tensor-core operand form, converted once for all panels
-    const bool hoist = is_tc(prec) && A->dtype == PLU_F32 && k <= 512;
-    const size_t oXq = hoist ? lay.add(tc_operand_bytes(m, k)) : 0;
+    const bool hoist = (is_tc(prec) || prec == kPrecSplit) && A->dtype == PLU_F32 && k <= 512;
+    const size_t oXq =
+        hoist ? lay.add(prec == kPrecSplit ? tcs_operand_bytes(m, k) : tc_operand_bytes(m, k)) : 0;
     PLU_TRY(ensure_ws(c, lay.total + 256));
     char* ws = c->ws;
     double* Om = reinterpret_cast<double*>(ws + oOm);
@@ -1089,7 +1112,9 @@ plu_status plu_singlepass(plu_ctx* c, const plu_matrix* A, int k, uint64_t seed,
     if (rep) PLU_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
     // Omega (m x k), Alg. singlepasslu step 1
     PLU_CUDA(c, launch_gaussian(m, k, seed, kStreamOmegaSP, Om, m, c->stream));
-    if (hoist)
+    if (hoist && prec == kPrecSplit)
+        PLU_CUDA(c, launch_tcs_operand(m, k, Om, m, ws + oXq, c->num_sms, c->stream));
+    else if (hoist)
         PLU_CUDA(c, launch_tc_operand(m, k, Om, m, ws + oXq, c->num_sms, c->stream));
     // G = A^T Omega and H = A G in one sweep over the columns of A (Sec. 5
     // remark): per column panel, G(panel, :) = A(:, panel)^T Omega, then
@@ -1186,7 +1211,7 @@ plu_status plu_randlu(plu_ctx* c, const plu_matrix* A, int k, int l, int piter, 
     size_t step = pass_ws(m, l, n, prec, sms), t;
     t = pass_ws(n, l, m, prec, sms);
     if (t > step) step = t;
-    t = pass_ws(n, k, m, PLU_TF32, sms);
+    t = pass_ws(n, k, m, is_tc(prec) ? kPrecSplit : int(prec), sms);
     if (t > step) step = t;
     t = pass_ws(n, k, m, prec, sms);
     if (t > step) step = t;
@@ -1253,12 +1278,12 @@ plu_status plu_randlu(plu_ctx* c, const plu_matrix* A, int k, int l, int piter, 
     PLU_CUDA(c, launch_lu(c, prec, m, l, Y, m, 1, p, L1, m, 0, Ul, l, 1, info, stepp, c->d_status,
                                 c->spin_budget, sms, c->stream));
     // B^T = (L_y^+ P A)^T = A^T W (W^T W)^{-1} with W = P^T L_y = Q R:
-    // B^T = A^T Q R^{-T}.  The pass reads the FP32 A through TF32 in the
-    // mixed modes (B enters the result to first order).
+    // B^T = A^T Q R^{-T}.  The pass reads the FP32 A with FP32-accurate
+    // split products in the mixed modes (B enters the result to first order).
     PLU_CUDA(c, launch_scatter_rows(m, k, p, L1, m, W, m, c->stream));
     PLU_CUDA(c, launch_cholqr2(m, k, W, m, R, k, stepp, step, c->d_status, sms, c->stream, 0, 2,
                                prec != PLU_FP64 ? 1 : 0));
-    PLU_TRY(pass(1, W, m, k, is_tc(prec) ? int(PLU_TF32) : int(prec), T, n));
+    PLU_TRY(pass(1, W, m, k, is_tc(prec) ? kPrecSplit : int(prec), T, n));
     PLU_CUDA(c, launch_trinv_upper(k, R, Rinv, c->stream));
     PLU_CUDA(c, launch_gemm_f64(0, 1, n, k, k, T, n, Rinv, k, BT, n, tpp, tp, sms, c->stream));
     // Q B^T = L' U' (Alg. rlu step 5); U = L'^T written straight into U

@@ -2,6 +2,7 @@
 // library (not part of the C ABI; see include/powerlu.h for that).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
@@ -248,6 +249,33 @@ cudaError_t launch_tc_pass_q(int trans, const QuantA& q, const double* X, int64_
                              double* Y, int64_t ldy, void* scratch, size_t scratch_cap,
                              int* dev_status, int num_sms, cudaStream_t s, int accum = 0,
                              const void* xq_pre = nullptr, TcPartials* keep = nullptr);
+// Y (M x cols, ldy) = (accum != 0: Y +, else) the FP64 sum of
+// the stream-K partial tiles P in CTA order.
+cudaError_t launch_tc_reduce(const TcPartials& P, int64_t M, int cols, double* Y, int64_t ldy,
+                             int accum, int num_sms, cudaStream_t s);
+// A 2-D tensor map (128-byte swizzle) over a column-major matrix: element
+// size dtype_code (4 FP32, 2 BF16, 1 one-byte), dim0 contiguous.
+bool tc_make_map_2d(CUtensorMap* map, int dtype_code, const void* base, uint64_t dim0,
+                    uint64_t dim1, uint64_t stride1_bytes, uint32_t box0, uint32_t box1);
+
+// Split-precision passes (3xTF32, plu_tcsplit.cu): Y = op(A) X with FP32 A
+// = A_hi + A_lo and X = X_hi + X_lo (hi the TF32 rounding, lo the TF32
+// rounding of the remainder), Y = A_hi X_hi + A_lo X_hi + A_hi X_lo on the
+// tensor cores with FP32 accumulation: FP32-accurate products.
+bool tcs_supported(int64_t M, int64_t K, int cols, const void* A, int64_t lda, int trans);
+size_t tcs_scratch_bytes(int64_t M, int64_t K, int cols, int num_sms);
+// The small operand X (K x cols) in the split pass's hi/lo operand form, made
+// once for several passes that share it (ximg_pre).
+size_t tcs_operand_bytes(int64_t K, int cols);
+cudaError_t launch_tcs_operand(int64_t K, int cols, const double* X, int64_t ldx, void* out,
+                               int num_sms, cudaStream_t s);
+// norm (nullable): ||A||_F^2 of the entries the pass reads, summed into *norm->out.
+cudaError_t launch_tc_split_pass(int trans, int64_t m, int64_t n, const float* A, int64_t lda,
+                                 const double* X, int64_t ldx, int cols, double* Y, int64_t ldy,
+                                 void* scratch, size_t scratch_cap, int* dev_status, int num_sms,
+                                 cudaStream_t s, int accum = 0, const void* ximg_pre = nullptr,
+                                 const NormOut* norm = nullptr);
+
 // Y (M x cols, ldy) = the bands' FP64 reductions added in order (one write).
 cudaError_t launch_tc_reduce_bands(const TcPartials* bands, int nbands, int64_t M, int cols,
                                    double* Y, int64_t ldy, cudaStream_t s);

@@ -773,6 +773,31 @@ TcPlan plan_tc(int64_t M, int64_t K, int cols, int num_sms, bool xpose, int E = 
 
 }  // namespace
 
+bool tc_make_map_2d(CUtensorMap* map, int dtype_code, const void* base, uint64_t dim0,
+                    uint64_t dim1, uint64_t stride1_bytes, uint32_t box0, uint32_t box1) {
+    const CUtensorMapDataType dt = dtype_code == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : dtype_code == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    return make_map_2d(map, dt, base, dim0, dim1, stride1_bytes, box0, box1);
+}
+
+cudaError_t launch_tc_reduce(const TcPartials& P, int64_t M, int cols, double* Y, int64_t ldy,
+                             int accum, int num_sms, cudaStream_t s) {
+    const int64_t nblk = (M + BM - 1) / BM;
+    const bool wide = nblk * ((cols + 7) / 8) >= 2 * int64_t(num_sms);
+    count_launch();
+    if (!wide) {
+        k_tc_reduce<1><<<dim3(unsigned(nblk), unsigned(cols)), BM, 0, s>>>(
+            P.part, M, cols, P.npad, P.ksteps, P.total, P.per, P.max_segs, P.grid, Y, ldy,
+            nullptr, nullptr, accum);
+        return cudaGetLastError();
+    }
+    k_tc_reduce<8><<<dim3(unsigned(nblk), unsigned((cols + 7) / 8)), BM, 0, s>>>(
+        P.part, M, cols, P.npad, P.ksteps, P.total, P.per, P.max_segs, P.grid, Y, ldy, nullptr,
+        nullptr, accum);
+    return cudaGetLastError();
+}
+
 bool tc_supported(int64_t M, int64_t K, int cols, const void* A, int64_t lda, int trans) {
     if (cols < 1 || cols > 512 || M < 1 || K < 1) return false;
     if ((reinterpret_cast<uintptr_t>(A) & 15) != 0 || (lda % 4) != 0) return false;

@@ -369,12 +369,13 @@ def test_fixed_precision_20000x10000_full_size(ctx):
     assert e64 <= w.eps and e32 <= 1.1 * e64, (e32, e64)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16", "fp8"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16", "fp8", "tf32x3"])
 @pytest.mark.parametrize("v", [3, 4])
 def test_powerlu_fp_norm_from_first_read(ctx, prec, v):
     """Alg. adaptivewithoutupdating step 1 fused into the first read of A:
     ||A||_F^2 summed by the first pass (A Omega for odd v, A^T Omega for even
-    v: both tensor-core orientations, the SIMT passes) or by the quantisation
+    v: both tensor-core orientations, the split passes' splitter and
+    transposer warps, the SIMT passes) or by the quantisation
     (BF16, FP8) equals the sum of the squares of the stored entries, and A is
     read exactly v times."""
     m, n = 3001, 2003                      # ragged tiles in both orientations
