@@ -80,12 +80,25 @@ k_cholesky(int n, double* __restrict__ W, const double* __restrict__ Wsave, int6
 
 // Blocked upper Cholesky W = R^T R over a cooperative grid (n x n, ld n,
 // upper triangle read, R written over it, strictly lower part zeroed).
-// Per block of CB columns: CTA 0 factors the diagonal block in shared memory,
-// grid barrier; every CTA copies R11 to shared memory and every thread of the
-// grid solves R11^T R12 = W12 for some trailing columns, barrier; every CTA
-// stages the block rows R12 in shared memory (when they fit, else reads them
-// from W) and the grid applies W22 -= R12^T R12 (upper part), barrier.  On a non-positive pivot in the first attempt (shift_mode 1) all
-// CTAs restart from Wsave with the shifted-CholeskyQR diagonal shift.
+//
+// The FP64 pipe of an SM issues one warp instruction about every 64 cycles
+// per SM sub-partition, and a dependent FP64 operation waits as long (a
+// reciprocal or square root, several operations, ~430 cycles), whether one
+// lane or 32 are active.  So the n pivots, which are sequential, decide the
+// time, and the kernel keeps per pivot one reciprocal and two CTA barriers
+// on the critical path:
+//  (A) every CTA factors the diagonal block redundantly in shared memory in
+//      LDL^T form (thread 0 takes 1/d_j, all threads apply the rank-1 update
+//      with it), then scales: R11 = diag(sqrt d) L^T with the square roots
+//      taken in parallel.  No grid barrier is needed before the solves, as
+//      every CTA holds R11 and 1/R11(j, j).
+//  (B) R12 = R11^{-T} W12, one warp per column (lane i owns row i; x_u is
+//      broadcast by a shuffle), grid barrier;
+//  (C) W22 -= R12^T R12 (upper part), R12 staged in shared memory when it
+//      fits, grid barrier.
+// On a non-positive pivot in the first attempt (shift_mode 1) every CTA,
+// having met it in its own copy of the diagonal block, restarts from Wsave
+// with the shifted-CholeskyQR diagonal shift.
 constexpr int CB = 32;
 constexpr int CBT = 256;
 
@@ -101,11 +114,16 @@ k_cholesky_coop(int n, double* __restrict__ W, const double* __restrict__ Wsave,
     if (skip && *skip) return;                      // every CTA reads the same flag
     extern __shared__ double S[];                 // [CB][n - kb - b] block rows of R12
     __shared__ double D[CB][CB + 1];
-    __shared__ double rjj;
+    __shared__ double zinv[CB];                   // 1 / d_j
+    __shared__ double yinv[CB];                   // 1 / sqrt(d_j) = 1 / R11(j, j)
+    __shared__ int bad;
     const int t = threadIdx.x;
+    const int lane = t & 31;
     const int nb = gridDim.x;
     const int gtid = blockIdx.x * CBT + t;
     const int gthreads = nb * CBT;
+    const int gwarp = blockIdx.x * (CBT / 32) + (t >> 5);
+    const int gwarps = nb * (CBT / 32);
     unsigned nbar = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (attempt == 1) {
@@ -122,67 +140,66 @@ k_cholesky_coop(int n, double* __restrict__ W, const double* __restrict__ Wsave,
         bool broke = false;
         for (int kb = 0; kb < n; kb += CB) {
             const int b = min(CB, n - kb);
-            if (blockIdx.x == 0) {
-                for (int e = t; e < b * b; e += CBT) {
-                    const int a = e % b, c = e / b;
-                    D[a][c] = __ldcg(&W[(kb + a) + int64_t(kb + c) * n]);
+            // (A) the diagonal block, in every CTA
+            for (int e = t; e < CB * CB; e += CBT) {
+                const int a = e % CB, c = e / CB;
+                D[a][c] = (a <= c && c < b) ? __ldcg(&W[(kb + a) + int64_t(kb + c) * n]) : 0.0;
+            }
+            if (t == 0) bad = 0;
+            __syncthreads();
+            for (int j = 0; j < b; ++j) {
+                if (t == 0) {
+                    const double d = D[j][j];
+                    if (!(d > 0.0)) bad = 1;
+                    zinv[j] = d > 0.0 ? 1.0 / d : 0.0;
                 }
                 __syncthreads();
-                // the diagonal block by warp 0 alone (lane c owns column c), so
-                // a column step costs warp syncs, not CTA barriers
-                if (t < 32) {
-                    int bad = 0;
-                    for (int j = 0; j < b; ++j) {
-                        const double d = D[j][j];
-                        const double r = d > 0.0 ? sqrt(d) : 0.0;
-                        if (r == 0.0) { bad = 1; break; }      // same value in every lane
-                        __syncwarp();
-                        if (t == j) D[j][j] = r;
-                        if (t > j && t < b) D[j][t] /= r;
-                        __syncwarp();
-                        if (t > j && t < b) {
-                            const double rjc = D[j][t];
-                            for (int a = j + 1; a <= t; ++a) D[a][t] -= D[j][a] * rjc;
-                        }
-                        __syncwarp();
+                if (bad) break;                     // the same value in every thread
+                const double z = zinv[j];
+                // D(a, c) -= D(j, a) D(j, c) / d_j for j < a <= c < b: thread t
+                // takes columns c = j + 1 + (t % 32) .. and rows a in (j, c]
+                // strided by 8 (warps), so all four sub-partitions share the work
+                {
+                    const int c = j + 1 + lane;
+                    if (c < b) {
+                        const double wc = D[j][c] * z;
+                        for (int a = j + 1 + (t >> 5); a <= c; a += CBT / 32)
+                            D[a][c] = fma(-D[j][a], wc, D[a][c]);
                     }
-                    if (t == 0) rjj = bad ? 0.0 : 1.0;
                 }
                 __syncthreads();
+            }
+            if (bad) { broke = true; break; }
+            // R11 = diag(sqrt d) L^T: row j of the unscaled block times 1/sqrt(d_j)
+            if (t < b) yinv[t] = rsqrt(D[t][t]);
+            __syncthreads();
+            for (int e = t; e < b * b; e += CBT) {
+                const int a = e % b, c = e / b;
+                if (a <= c) D[a][c] *= yinv[a];
+            }
+            __syncthreads();
+            if (blockIdx.x == 0) {
                 for (int e = t; e < b * b; e += CBT) {
                     const int a = e % b, c = e / b;
                     if (a <= c) W[(kb + a) + int64_t(kb + c) * n] = D[a][c];
                 }
-                if (t == 0) ctl->broke = rjj == 0.0 ? 1 : 0;
             }
-            if (!grid_barrier(&ctl->barrier, ++nbar * nb, status, budget)) return;
-            if (ld_volatile_i32(&ctl->broke)) { broke = true; break; }
-            // R11 to shared memory, then R12(:, c) = R11^{-T} W12(:, c), one
-            // column per thread, the columns dealt round-robin over the CTAs
-            // (each SM's FP64 pipe takes a share of the solves)
-            for (int e = t; e < b * b; e += CBT) {
-                const int a = e % b, c = e / b;
-                D[a][c] = a <= c ? __ldcg(&W[(kb + a) + int64_t(kb + c) * n]) : 0.0;
-            }
-            __syncthreads();
-            for (int c = kb + b + blockIdx.x + nb * t; c < n; c += gthreads) {
-                double x[CB];
-#pragma unroll
-                for (int i = 0; i < CB; ++i) {
-                    if (i < b) {
-                        double acc = __ldcg(&W[(kb + i) + int64_t(c) * n]);
-                        for (int u = 0; u < i; ++u) acc = fma(-D[u][i], x[u], acc);
-                        x[i] = acc / D[i][i];
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < CB; ++i)
-                    if (i < b) W[(kb + i) + int64_t(c) * n] = x[i];
-            }
-            if (!grid_barrier(&ctl->barrier, ++nbar * nb, status, budget)) return;
-            // W22 -= R12^T R12 (upper triangle), R12 staged in shared memory
+            // (B) R12(:, c) = R11^{-T} W12(:, c), one warp per column
             const int m = n - kb - b;
             const int c0 = kb + b;
+            for (int cc = gwarp; cc < m; cc += gwarps) {
+                const int64_t col = int64_t(c0 + cc) * n + kb;
+                double acc = lane < b ? __ldcg(&W[col + lane]) : 0.0;
+                double x = 0.0;
+                for (int u = 0; u < b; ++u) {
+                    const double xu = __shfl_sync(0xffffffffu, acc * yinv[u], u);
+                    if (lane == u) x = xu;
+                    if (lane > u && lane < b) acc = fma(-D[u][lane], xu, acc);
+                }
+                if (lane < b) W[col + lane] = x;
+            }
+            if (!grid_barrier(&ctl->barrier, ++nbar * nb, status, budget)) return;
+            // (C) W22 -= R12^T R12 (upper triangle), R12 staged in shared memory
             if (stage_rows) {
                 for (int e = t; e < b * m; e += CBT) {
                     const int u = e % b, c = e / b;
@@ -223,12 +240,16 @@ __global__ void k_trinv_upper(int n, const double* __restrict__ R, double* __res
                               const int* __restrict__ skip) {
     if (skip && *skip) return;
     extern __shared__ double x[];
+    double* rd = x + n;                            // 1 / R(i, i), taken in parallel
     const int j = blockIdx.x;
     const int t = threadIdx.x;
-    for (int i = t; i < n; i += blockDim.x) x[i] = (i == j) ? 1.0 : 0.0;
+    for (int i = t; i < n; i += blockDim.x) {
+        x[i] = (i == j) ? 1.0 : 0.0;
+        if (i <= j) rd[i] = 1.0 / R[i + int64_t(i) * n];
+    }
     __syncthreads();
     for (int i = j; i >= 0; --i) {
-        if (t == 0) x[i] = x[i] / R[i + int64_t(i) * n];
+        if (t == 0) x[i] *= rd[i];
         __syncthreads();
         const double xi = x[i];
         for (int k = t; k < i; k += blockDim.x) x[k] -= xi * R[k + int64_t(i) * n];
@@ -246,10 +267,14 @@ __global__ void k_trinv_upper_staged(int n, const double* __restrict__ R,
     if (skip && *skip) return;
     extern __shared__ double sm[];
     double* x = sm;                                // n
-    double* Rc = sm + n;                           // cw columns of n
+    double* rd = sm + n;                           // n: 1 / R(i, i), taken in parallel
+    double* Rc = sm + 2 * n;                       // cw columns of n
     const int j = blockIdx.x;
     const int t = threadIdx.x;
-    for (int i = t; i < n; i += blockDim.x) x[i] = (i == j) ? 1.0 : 0.0;
+    for (int i = t; i < n; i += blockDim.x) {
+        x[i] = (i == j) ? 1.0 : 0.0;
+        if (i <= j) rd[i] = 1.0 / R[i + int64_t(i) * n];
+    }
     for (int hi = j; hi >= 0; hi -= cw) {
         const int lo = hi - cw + 1 > 0 ? hi - cw + 1 : 0;
         __syncthreads();                           // the previous chunk is no longer read
@@ -258,8 +283,9 @@ __global__ void k_trinv_upper_staged(int n, const double* __restrict__ R,
         __syncthreads();
         for (int i = hi; i >= lo; --i) {
             const double* col = Rc + (i - lo) * n;
-            // one thread divides (the FP64 pipe is narrow); the rest read x_i
-            if (t == 0) x[i] = x[i] / col[i];
+            // one thread scales by the reciprocal taken up front (a dependent
+            // FP64 division costs ~430 cycles, a multiply ~65); the rest read x_i
+            if (t == 0) x[i] *= rd[i];
             __syncthreads();
             const double xi = x[i];
             for (int k = t; k < i; k += blockDim.x) x[k] -= xi * col[k];
@@ -276,7 +302,7 @@ cudaError_t trinv_upper(int n, const double* R, double* Rinv, const int* skip, c
     count_launch();
     if (cw >= 8) {
         const int w = cw > 64 ? 64 : cw;
-        const size_t smem = size_t(n) * (w + 1) * sizeof(double);
+        const size_t smem = size_t(n) * (w + 2) * sizeof(double);
         cudaError_t e = cudaFuncSetAttribute(k_trinv_upper_staged,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(smem));
@@ -284,7 +310,7 @@ cudaError_t trinv_upper(int n, const double* R, double* Rinv, const int* skip, c
         k_trinv_upper_staged<<<n, tt, smem, s>>>(n, R, Rinv, skip, w);
         return cudaGetLastError();
     }
-    k_trinv_upper<<<n, tt, size_t(n) * sizeof(double), s>>>(n, R, Rinv, skip);
+    k_trinv_upper<<<n, tt, 2 * size_t(n) * sizeof(double), s>>>(n, R, Rinv, skip);
     return cudaGetLastError();
 }
 
