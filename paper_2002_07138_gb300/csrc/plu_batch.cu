@@ -47,6 +47,8 @@ struct GemmJob {
     int transA, transB, a_f32, accum, tri;
     int tiles_m, tiles_n;
     int64_t tile0;
+    const int* skip;     // nullable: when *skip, return (copy_on_skip: C = A instead)
+    int copy_on_skip;
 };
 
 struct LuJob {
@@ -70,12 +72,15 @@ struct CholJob {
     double* Wsave;
     int n;
     int64_t rows;
+    const int* skip;     // nullable: when *skip, return at once
+    int* decide;         // nullable: set to 1 when R's diagonal spread is <= 1e5
 };
 
 struct TrinvJob {
     const double* R;
     double* Rinv;
     int n;
+    const int* skip;
 };
 
 // --------------------------------------------------------- Gaussian
@@ -123,6 +128,18 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
     const int64_t i0 = (local % J.tiles_m) * BMV;
     const int64_t j0 = (local / J.tiles_m) * BNV;
     const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+    if (J.skip && *J.skip) {
+        // a skipped second CholeskyQR round: its X R^-1 becomes the copy
+        // C = A (A FP64, not transposed), the Gram does nothing
+        if (J.copy_on_skip) {
+            const double* Ad = static_cast<const double*>(J.A);
+            for (int e = t; e < BMV * BNV; e += GNT) {
+                const int64_t gi = i0 + e % BMV, gj = j0 + e / BMV;
+                if (gi < J.M && gj < J.N) J.C[gi + gj * J.ldc] = Ad[gi + gj * J.lda];
+            }
+        }
+        return;
+    }
     int64_t kend = J.K;
     if (J.tri == 2 && kend > j0 + BNV) kend = j0 + BNV;
     const bool skip = (J.tri == 1 && i0 >= j0 + BNV);
@@ -375,6 +392,7 @@ k_b_cholesky(const CholJob* __restrict__ jobs, int* __restrict__ status) {
     __shared__ int broke;
     __shared__ double rjj;
     const CholJob J = jobs[blockIdx.x];
+    if (J.skip && *J.skip) return;
     const int n = J.n;
     double* W = J.W;
     const int t = threadIdx.x;
@@ -394,22 +412,36 @@ k_b_cholesky(const CholJob* __restrict__ jobs, int* __restrict__ status) {
         }
         if (t == 0) broke = 0;
         __syncthreads();
+        // LDL^T order: one reciprocal 1/d_j per pivot on the critical path
+        // (thread 0), the rank-1 update with the unscaled row j, and the
+        // square roots and row scalings afterwards, in parallel
         for (int j = 0; j < n; ++j) {
             if (t == 0) {
                 const double d = W[j + int64_t(j) * n];
                 if (!(d > 0.0)) broke = 1;
-                rjj = (d > 0.0) ? sqrt(d) : 1.0;
-                W[j + int64_t(j) * n] = rjj;
+                rjj = (d > 0.0) ? 1.0 / d : 0.0;
             }
             __syncthreads();
             if (broke) break;
-            const double inv = 1.0 / rjj;
-            for (int c = j + 1 + t; c < n; c += CNT) W[j + int64_t(c) * n] *= inv;
-            __syncthreads();
+            const double z = rjj;
             const int m = n - j - 1;
             for (int64_t e = t; e < int64_t(m) * m; e += CNT) {
                 const int a = j + 1 + int(e % m), c = j + 1 + int(e / m);
-                if (a <= c) W[a + int64_t(c) * n] -= W[j + int64_t(a) * n] * W[j + int64_t(c) * n];
+                if (a <= c)
+                    W[a + int64_t(c) * n] =
+                        fma(-W[j + int64_t(a) * n] * z, W[j + int64_t(c) * n], W[a + int64_t(c) * n]);
+            }
+            __syncthreads();
+        }
+        if (!broke) {
+            // R(j, c) = W(j, c) / sqrt(d_j) for c >= j (R(j, j) = sqrt(d_j));
+            // 1/sqrt(d_j) goes to Wsave (no longer needed once the
+            // factorisation has succeeded) before any W entry changes
+            for (int a = t; a < n; a += CNT) J.Wsave[a] = rsqrt(W[a + int64_t(a) * n]);
+            __syncthreads();
+            for (int64_t e = t; e < int64_t(n) * n; e += CNT) {
+                const int a = int(e % n), c = int(e / n);
+                if (a <= c) W[e] *= J.Wsave[a];
             }
             __syncthreads();
         }
@@ -421,22 +453,44 @@ k_b_cholesky(const CholJob* __restrict__ jobs, int* __restrict__ status) {
         const int a = int(e % n), c = int(e / n);
         if (a > c) W[e] = 0.0;
     }
+    if (J.decide && t < 32) {
+        // the second CholeskyQR round is needed when max|r_ii| / min|r_ii|
+        // exceeds 1e5 (one round leaves an orthogonality loss ~spread^2 u)
+        double dmax = 0.0, dmin = 1.7976931348623157e308;
+        for (int i = t; i < n; i += 32) {
+            const double d = fabs(W[i + int64_t(i) * n]);
+            dmax = fmax(dmax, d);
+            dmin = fmin(dmin, d);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+            dmin = fmin(dmin, __shfl_xor_sync(0xffffffffu, dmin, off));
+        }
+        if (t == 0) *J.decide = (dmin > 0.0 && dmax <= 1e5 * dmin) ? 1 : 0;
+    }
 }
 
-// Rinv(:, j) = R^{-1} e_j, CTA (j, job).
+// Rinv(:, j) = R^{-1} e_j, CTA (j, job).  The reciprocals of the diagonal
+// are taken up front in parallel: a dependent FP64 division costs ~430
+// cycles of the narrow FP64 pipe, a multiply ~65.
 __global__ void k_b_trinv(const TrinvJob* __restrict__ jobs) {
-    extern __shared__ double x[];
+    extern __shared__ double x[];                 // x[n], then rd[n]
     const TrinvJob J = jobs[blockIdx.y];
     const int j = blockIdx.x;
-    if (j >= J.n) return;
+    if (j >= J.n || (J.skip && *J.skip)) return;
     const int n = J.n;
+    double* rd = x + n;
     const int t = threadIdx.x;
-    for (int i = t; i < n; i += blockDim.x) x[i] = (i == j) ? 1.0 : 0.0;
+    for (int i = t; i < n; i += blockDim.x) {
+        x[i] = (i == j) ? 1.0 : 0.0;
+        if (i <= j) rd[i] = 1.0 / J.R[i + int64_t(i) * n];
+    }
     __syncthreads();
     for (int i = j; i >= 0; --i) {
-        const double xi = x[i] / J.R[i + int64_t(i) * n];
+        if (t == 0) x[i] *= rd[i];
         __syncthreads();
-        if (t == 0) x[i] = xi;
+        const double xi = x[i];
         for (int k = t; k < i; k += blockDim.x) x[k] -= xi * J.R[k + int64_t(i) * n];
         __syncthreads();
     }
@@ -460,6 +514,7 @@ struct ProbWs {
     double *V, *Z, *X2, *L1, *U1T, *BT, *U2T, *W, *Wsave, *Rinv, *Rinv1, *T;
     int *pos, *piv;
     int32_t* info;
+    int* qskip;          // the second CholeskyQR round is skipped (FP32 passes)
 };
 
 struct LaunchRec {
@@ -605,6 +660,7 @@ static void plan_batch(const plu_batch_problem* P, int count, int prec, char* ws
         w.pos = ip;
         w.piv = ip + mx;
         w.info = ip + 2 * mx;
+        w.qskip = ip + 2 * mx + 2;
         cur += (size_t(2 * mx + 4) * sizeof(int) + 255) & ~size_t(255);
     }
     // per-problem op lists
@@ -686,7 +742,11 @@ static void plan_batch(const plu_batch_problem* P, int count, int prec, char* ws
                                    nullptr, W[i].pos, W[i].piv));
         }
         B.lu(lj);
-        // CholeskyQR2 (two rounds: X2 = X R1^-1, X = X2 R2^-1)
+        // CholeskyQR2 (two rounds: X2 = X R1^-1, X = X2 R2^-1).  With FP32
+        // passes the second round is skipped, per problem on the device, when
+        // R1's diagonal spread is at most 1e5 (as the mixed modes of
+        // plu_powerlu do): its Gram, Cholesky and inverse return at once and
+        // its X R^-1 becomes the copy X = X2.  FP64 batches keep both rounds.
         bool anyqr = false;
         for (int i = 0; i < count; ++i) anyqr |= ops[i][ph].kind == OP_QR;
         if (anyqr) {
@@ -698,14 +758,19 @@ static void plan_batch(const plu_batch_problem* P, int count, int prec, char* ws
                     const double* src = round == 0 ? o.P : W[i].X2;
                     gm.push_back(mk_gemm(src, o.prow, 0, 1, src, o.prow, 0, W[i].W, l, l, l,
                                          int(o.prow), 0, 1));
+                    if (round == 1 && tc32) gm.back().skip = W[i].qskip;
                 }
                 B.gemm(gm, 0);
                 for (int i = 0; i < count; ++i)
                     if (ops[i][ph].kind == OP_QR)
-                        cj.push_back(CholJob{W[i].W, W[i].Wsave, P[i].l, ops[i][ph].prow});
+                        cj.push_back(CholJob{W[i].W, W[i].Wsave, P[i].l, ops[i][ph].prow,
+                                             round == 1 && tc32 ? W[i].qskip : nullptr,
+                                             round == 0 && tc32 ? W[i].qskip : nullptr});
                 B.chol(cj);
                 for (int i = 0; i < count; ++i)
-                    if (ops[i][ph].kind == OP_QR) tj.push_back(TrinvJob{W[i].W, W[i].Rinv, P[i].l});
+                    if (ops[i][ph].kind == OP_QR)
+                        tj.push_back(TrinvJob{W[i].W, W[i].Rinv, P[i].l,
+                                              round == 1 && tc32 ? W[i].qskip : nullptr});
                 B.trinv(tj);
                 for (int i = 0; i < count; ++i) {
                     const Op& o = ops[i][ph];
@@ -715,6 +780,10 @@ static void plan_batch(const plu_batch_problem* P, int count, int prec, char* ws
                     double* dst = round == 0 ? W[i].X2 : o.P;
                     gm.push_back(mk_gemm(src, o.prow, 0, 0, W[i].Rinv, l, 0, dst, o.prow,
                                          int(o.prow), l, l, 0, 2));
+                    if (round == 1 && tc32) {
+                        gm.back().skip = W[i].qskip;
+                        gm.back().copy_on_skip = 1;
+                    }
                 }
                 B.gemm(gm, 0);
             }
@@ -739,11 +808,12 @@ static void plan_batch(const plu_batch_problem* P, int count, int prec, char* ws
                 B.gemm(gm, 0);
                 for (int i = 0; i < count; ++i)
                     if (ops[i][ph].kind == OP_SPTAIL)
-                        cj.push_back(CholJob{W[i].W, W[i].Wsave, P[i].k, P[i].n});
+                        cj.push_back(CholJob{W[i].W, W[i].Wsave, P[i].k, P[i].n, nullptr, nullptr});
                 B.chol(cj);
                 for (int i = 0; i < count; ++i)
                     if (ops[i][ph].kind == OP_SPTAIL)
-                        tj.push_back(TrinvJob{W[i].W, round == 0 ? W[i].Rinv1 : W[i].Rinv, P[i].k});
+                        tj.push_back(TrinvJob{W[i].W, round == 0 ? W[i].Rinv1 : W[i].Rinv, P[i].k,
+                                              nullptr});
                 B.trinv(tj);
                 for (int i = 0; i < count; ++i) {
                     if (ops[i][ph].kind != OP_SPTAIL) continue;
@@ -842,7 +912,7 @@ cudaError_t launch_batch_plan(const Builder& B, const char* dtab, int* dev_statu
                 break;
             case 4:
                 k_b_trinv<<<dim3(unsigned(r.maxn), unsigned(r.njobs)), 128,
-                            size_t(r.maxn) * sizeof(double), s>>>(
+                            2 * size_t(r.maxn) * sizeof(double), s>>>(
                     reinterpret_cast<const TrinvJob*>(tab));
                 break;
         }
