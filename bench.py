@@ -169,6 +169,8 @@ def run_batched(args):
             "rel_error_sample_max": max(errs), "rel_error_sample_median": statistics.median(errs),
             "gemm_tiles_autotuned": dict(collections.Counter(
                 "%dx%d" % t for t in plu.plu_batched_tiles(ctx))),
+            "gemm_splitk_autotuned": dict(collections.Counter(
+                ("k%d" % kc) if kc else "none" for kc in plu.plu_batched_splitk(ctx))),
             "gpu_launches": launches,
             "clocks": clk,
             "cpu_baseline": cpu,

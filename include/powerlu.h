@@ -371,9 +371,28 @@ plu_status plu_batched(plu_ctx* ctx, const plu_batch_problem* problems, int coun
 plu_status plu_batched_tiles(plu_ctx* ctx, int* bm, int* bn, int cap, int* count);
 
 /* Every grouped GEMM of later plu_batched calls on ctx takes the tile shape
- * bm x bn (64 x 32, 64 x 64 or 128 x 32; PLU_EINVAL otherwise) instead of the
- * autotuner's choice; bm = bn = 0 restores the autotuner. */
+ * bm x bn (64 x 32, 64 x 64 or 128 x 32; PLU_EINVAL otherwise), without
+ * split-K, instead of the autotuner's choice; bm = bn = 0 restores the
+ * autotuner. */
 plu_status plu_set_batched_tile(plu_ctx* ctx, int bm, int bn);
+
+/* The split-K choice of each grouped GEMM launch of the last plu_batched call
+ * on ctx, in launch order: kchunk[i] = the length of the K chunks its jobs
+ * with few output tiles (at most 8) and a longer K were cut into, 0 for no
+ * split.  The partial sums of the chunks are added in FP64 in chunk order
+ * by a second grouped launch.  The autotuner picks the split-K length (none,
+ * 1024, 256) together with the tile shape. */
+plu_status plu_batched_splitk(plu_ctx* ctx, int* kchunk, int cap, int* count);
+
+/* Persist the batched autotuner's choices in the text file at path (NULL or
+ * "" turns it off).  A batch signature met for the first time in ctx is
+ * looked up in the file before any timing, and a signature the autotuner
+ * times is appended to it, so a later process skips the timing.  The file
+ * must be openable for appending (PLU_EINVAL otherwise); its lines read
+ * "plu-batched-tune 1 <signature> <launches> <choice>...", the last line of a
+ * signature wins and malformed lines are ignored.  Processes that share the
+ * file may append at once; a line is written with one call. */
+plu_status plu_set_batched_tune_file(plu_ctx* ctx, const char* path);
 
 /* ---------------------------------------------------------------------
  * Allocation-free variant (the paper has no counterpart: this is a service

@@ -9,7 +9,7 @@ from ._binding import (  # noqa: F401
     lib, LIB_PATH, Context, PLUError, plu_matrix, plu_report, as_plu_matrix, colmajor_empty,
     plu_gaussian, plu_pass, plu_lu_reorth, plu_getrf, plu_qr, plu_cholqr1, plu_norm2, plu_rank,
     plu_powerlu, plu_powerlu_fp, plu_randlu, plu_singlepass, plu_batched, plu_batched_tiles,
-    plu_set_batched_tile,
+    plu_set_batched_tile, plu_batched_splitk, plu_set_batched_tune_file,
     plu_batch_problem,
     plu_csr, CsrMatrix, plu_spmm, plu_powerlu_csr, plu_powerlu_fp_csr,
     PREC, STATUS,

@@ -101,6 +101,8 @@ SIGNATURES = {
     "plu_set_batched_tile": (c_int, [c_vp, c_int, c_int]),
     "plu_batched_tiles": (c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_int,
                                   ctypes.POINTER(c_int)]),
+    "plu_batched_splitk": (c_int, [c_vp, ctypes.POINTER(c_int), c_int, ctypes.POINTER(c_int)]),
+    "plu_set_batched_tune_file": (c_int, [c_vp, ctypes.c_char_p]),
     "plu_batched": (c_int, [c_vp, ctypes.POINTER(plu_batch_problem), c_int, c_int,
                             ctypes.POINTER(plu_report)]),
 }
@@ -264,6 +266,23 @@ def plu_batched_tiles(ctx):
     bn = (c_int * max(n.value, 1))()
     ctx.check(lib().plu_batched_tiles(ctx.handle, bm, bn, n.value, ctypes.byref(n)))
     return [(bm[i], bn[i]) for i in range(n.value)]
+
+
+def plu_batched_splitk(ctx):
+    """K-chunk length of each grouped GEMM launch of the last plu_batched call
+    (0: no split-K), in launch order."""
+    n = c_int()
+    ctx.check(lib().plu_batched_splitk(ctx.handle, None, 0, ctypes.byref(n)))
+    kc = (c_int * max(n.value, 1))()
+    ctx.check(lib().plu_batched_splitk(ctx.handle, kc, n.value, ctypes.byref(n)))
+    return [kc[i] for i in range(n.value)]
+
+
+def plu_set_batched_tune_file(ctx, path):
+    """Persist the batched autotuner's choices in the text file `path`
+    (None turns it off)."""
+    ctx.check(lib().plu_set_batched_tune_file(
+        ctx.handle, None if path is None else str(path).encode()))
 
 
 def plu_cholqr1(ctx, X, tc=True):

@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 using namespace plu;
@@ -38,6 +39,9 @@ struct plu_ctx {
     std::map<uint64_t, std::vector<int>> batch_tiles;
     std::vector<int> last_tiles;
     int forced_tile = -1;             // a fixed tile shape instead of the autotuner
+    double* bpart = nullptr;          // batched split-K partials (grown on demand)
+    size_t bpart_cap = 0;
+    std::string tune_file;            // autotuner choices persisted here (empty: off)
     // panel LU trailing updates: -1 default (tensor cores in the mixed modes and
     // on the sparse path, FP64 FMAs in the FP64 path), 0 FP64 FMAs, 1 tensor cores
     int lu_tc = -1;
@@ -657,6 +661,7 @@ void plu_destroy(plu_ctx* c) {
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->capture) cudaStreamDestroy(c->capture);
+    if (c->bpart) cudaFree(c->bpart);
     delete c;
 }
 
@@ -1335,6 +1340,82 @@ plu_status plu_set_batched_tile(plu_ctx* c, int bm, int bn) {
     return fail(c, PLU_EINVAL, "no grouped-GEMM tile shape %d x %d", bm, bn);
 }
 
+plu_status plu_batched_splitk(plu_ctx* c, int* kchunk, int cap, int* count) {
+    if (!c || !count || cap < 0 || (cap > 0 && !kchunk)) return fail(c, PLU_EINVAL, "bad arguments");
+    const int n = int(c->last_tiles.size());
+    *count = n;
+    for (int i = 0; i < n && i < cap; ++i) {
+        kchunk[i] = batch_gemm_splitk(c->last_tiles[i]);
+        if (kchunk[i] < 0) return fail(c, PLU_EINVAL, "bad choice index");
+    }
+    return PLU_OK;
+}
+
+plu_status plu_set_batched_tune_file(plu_ctx* c, const char* path) {
+    if (!c) return PLU_EINVAL;
+    if (!path || !*path) {
+        c->tune_file.clear();
+        return PLU_OK;
+    }
+    FILE* f = fopen(path, "a");
+    if (!f) return fail(c, PLU_EINVAL, "cannot open the tuning file %s for appending", path);
+    fclose(f);
+    c->tune_file = path;
+    return PLU_OK;
+}
+
+namespace {
+// The autotuner's file: one line per batch signature,
+//   plu-batched-tune 1 <signature, 16 hex digits> <launches> <choice> ...
+// the last line of a signature wins; malformed lines are ignored.
+bool load_tuned(const std::string& path, uint64_t sig, std::vector<int>* out) {
+    FILE* f = fopen(path.c_str(), "r");
+    if (!f) return false;
+    char line[8192];
+    bool found = false;
+    while (fgets(line, sizeof(line), f)) {
+        unsigned long long fsig = 0;
+        int ver = 0, n = 0, used = 0;
+        if (sscanf(line, "plu-batched-tune %d %llx %d%n", &ver, &fsig, &n, &used) != 3) continue;
+        if (ver != 1 || fsig != sig || n < 1 || n > 4096) continue;
+        std::vector<int> v;
+        const char* p = line + used;
+        bool ok = true;
+        for (int i = 0; i < n && ok; ++i) {
+            int x = 0, u = 0;
+            if (sscanf(p, "%d%n", &x, &u) != 1 || x < 0 || x >= batch_gemm_choices()) ok = false;
+            else {
+                v.push_back(x);
+                p += u;
+            }
+        }
+        if (ok) {
+            *out = v;
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void save_tuned(const std::string& path, uint64_t sig, const std::vector<int>& v) {
+    std::string line;
+    char buf[64];
+    snprintf(buf, sizeof(buf), "plu-batched-tune 1 %016llx %d", (unsigned long long)sig,
+             int(v.size()));
+    line = buf;
+    for (int x : v) {
+        snprintf(buf, sizeof(buf), " %d", x);
+        line += buf;
+    }
+    line += "\n";
+    FILE* f = fopen(path.c_str(), "a");
+    if (!f) return;
+    fputs(line.c_str(), f);                 // one write per line
+    fclose(f);
+}
+}  // namespace
+
 plu_status plu_batched_tiles(plu_ctx* c, int* bm, int* bn, int cap, int* count) {
     if (!c || !count || cap < 0 || (cap > 0 && (!bm || !bn))) return fail(c, PLU_EINVAL, "bad arguments");
     const int n = int(c->last_tiles.size());
@@ -1399,10 +1480,18 @@ plu_status plu_batched(plu_ctx* c, const plu_batch_problem* P, int count, plu_pr
     }
     std::vector<int> forced;
     std::vector<int>& tiles = c->forced_tile >= 0 ? forced : c->batch_tiles[sig];
+    // a signature not tuned in this context may have been tuned before (the file)
+    const bool fresh = c->forced_tile < 0 && tiles.empty();
+    bool loaded = false;
+    if (fresh && !c->tune_file.empty()) loaded = load_tuned(c->tune_file, sig, &tiles);
     int nl = 0;
     float ms = 0.f;
+    const size_t before = tiles.size();
     PLU_CUDA(c, run_batch(P, count, prec, c->ws, c->ws + wsb, tb, c->d_status, c->num_sms, c->stream,
-                          c->capture, &nl, &ms, &tiles, c->forced_tile));
+                          c->capture, &nl, &ms, &tiles, c->forced_tile, &c->bpart, &c->bpart_cap));
+    // save what the autotuner chose (a loaded entry of the wrong length was retuned)
+    if (fresh && !c->tune_file.empty() && (!loaded || tiles.size() != before))
+        save_tuned(c->tune_file, sig, tiles);
     c->last_tiles = tiles;
     if (rep) {
         memset(rep, 0, sizeof(*rep));

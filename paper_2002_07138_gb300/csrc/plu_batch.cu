@@ -49,6 +49,19 @@ struct GemmJob {
     int64_t tile0;
     const int* skip;     // nullable: when *skip, return (copy_on_skip: C = A instead)
     int copy_on_skip;
+    int ksplit, kchunk;  // split-K: ksplit chunks of kchunk (a multiple of 16) of K
+    double* part;        // ksplit > 1: chunk c's M x N partial at part + c M N (ld M)
+};
+
+// C = (accum ? C : 0) + the sum of a split-K job's partials, in chunk order;
+// elements elem0 .. elem0 + M N - 1 of the grouped reduce.
+struct RedJob {
+    const double* part;
+    double* C;
+    int64_t ldc;
+    int M, N, ksplit, accum;
+    int64_t elem0;
+    const int* skip;     // the GEMM job's skip flag (nothing to reduce when set)
 };
 
 struct LuJob {
@@ -108,6 +121,15 @@ constexpr int GBK = 16, GNT = 256;
 constexpr int kGemmVariants = 3;
 constexpr int kVarBM[kGemmVariants] = {64, 64, 128};
 constexpr int kVarBN[kGemmVariants] = {32, 64, 32};
+// Split-K choices: no split, K chunks of 1024, of 256.  A choice is
+// variant + kGemmVariants * split index.  Only jobs with at most kSplitTiles
+// output tiles and a longer K are split (the Gram matrices X^T X of the
+// problems' CholeskyQR, whose few tiles otherwise each walk all of K), into
+// at most kMaxSplit chunks.
+constexpr int kSplitChoices = 3;
+constexpr int kSplitK[kSplitChoices] = {0, 1024, 256};
+constexpr int kGemmChoices = kGemmVariants * kSplitChoices;
+constexpr int kSplitTiles = 8, kMaxSplit = 32;
 
 template <typename TC, int BMV, int BNV>
 __global__ void __launch_bounds__(GNT)
@@ -115,7 +137,8 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
     constexpr int TM = BMV / 16, TN = BNV / 16;
     __shared__ TC As[2][GBK][BMV + 1];
     __shared__ TC Bs[2][GBK][BNV + 1];
-    // job of this tile: last job with tile0 <= blockIdx.x
+    // job of this tile: last job with tile0 <= blockIdx.x; the job's tiles
+    // run (row tile, column tile, K chunk), row tile fastest
     int lo = 0, hi = njobs - 1;
     const int64_t tile = blockIdx.x;
     while (lo < hi) {
@@ -125,8 +148,10 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
     }
     const GemmJob J = jobs[lo];
     const int64_t local = tile - J.tile0;
-    const int64_t i0 = (local % J.tiles_m) * BMV;
-    const int64_t j0 = (local / J.tiles_m) * BNV;
+    const int64_t mn_tiles = int64_t(J.tiles_m) * J.tiles_n;
+    const int kc = int(local / mn_tiles);
+    const int64_t i0 = (local % mn_tiles % J.tiles_m) * BMV;
+    const int64_t j0 = (local % mn_tiles / J.tiles_m) * BNV;
     const int t = threadIdx.x, tx = t % 16, ty = t / 16;
     if (J.skip && *J.skip) {
         // a skipped second CholeskyQR round: its X R^-1 becomes the copy
@@ -144,6 +169,8 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
     if (J.tri == 2 && kend > j0 + BNV) kend = j0 + BNV;
     const bool skip = (J.tri == 1 && i0 >= j0 + BNV);
     if (skip) kend = 0;
+    const int64_t kbeg = int64_t(kc) * J.kchunk;
+    if (J.ksplit > 1 && kend > kbeg + J.kchunk) kend = kbeg + J.kchunk;
     const float* Af = static_cast<const float*>(J.A);
     const double* Ad = static_cast<const double*>(J.A);
     // the next K step is loaded into registers while the current one is
@@ -195,12 +222,12 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
     for (int a = 0; a < TM; ++a)
 #pragma unroll
         for (int c = 0; c < TN; ++c) acc[a][c] = TC(0);
-    if (kend > 0) {
-        load(0);
+    if (kend > kbeg) {
+        load(kbeg);
         store(0);
         __syncthreads();
         int buf = 0;
-        for (int64_t k0 = 0; k0 < kend; k0 += GBK) {
+        for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
             const bool more = k0 + GBK < kend;
             if (more) load(k0 + GBK);
 #pragma unroll
@@ -220,6 +247,7 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
             buf ^= 1;
         }
     }
+    double* pc = J.ksplit > 1 ? J.part + int64_t(kc) * J.M * J.N : nullptr;
 #pragma unroll
     for (int a = 0; a < TM; ++a) {
         const int64_t gi = i0 + ty + 16 * a;
@@ -228,10 +256,34 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
         for (int c = 0; c < TN; ++c) {
             const int64_t gj = j0 + tx + 16 * c;
             if (gj >= J.N) continue;
-            double* cp = J.C + gi + gj * J.ldc;
-            *cp = J.accum ? *cp + double(acc[a][c]) : double(acc[a][c]);
+            if (pc) {
+                pc[gi + gj * J.M] = double(acc[a][c]);
+            } else {
+                double* cp = J.C + gi + gj * J.ldc;
+                *cp = J.accum ? *cp + double(acc[a][c]) : double(acc[a][c]);
+            }
         }
     }
+}
+
+// The split-K jobs' reduction (RedJob), one element per thread.
+__global__ void k_b_splitk_reduce(const RedJob* __restrict__ jobs, int njobs, int64_t total) {
+    const int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (e >= total) return;
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (jobs[mid].elem0 <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    const RedJob J = jobs[lo];
+    if (J.skip && *J.skip) return;
+    const int64_t x = e - J.elem0;
+    const int64_t mn = int64_t(J.M) * J.N;
+    double s = 0.0;
+    for (int c = 0; c < J.ksplit; ++c) s += J.part[int64_t(c) * mn + x];
+    double* cp = J.C + x % J.M + (x / J.M) * J.ldc;
+    *cp = J.accum ? *cp + s : s;
 }
 
 // One grouped GEMM launch in tile shape `variant` over a job table whose tile
@@ -525,20 +577,60 @@ struct LaunchRec {
     int maxn;          // trinv / lu smem
     int tc32;          // gemm arithmetic FP32
     int gidx = -1;     // gemm: index of its job list in Builder::gjobs
-    int variant = 0;   // gemm: tile shape (kVarBM / kVarBN)
+    int variant = 0;   // gemm: tile shape and split-K choice (lay_tiles)
+    size_t red_off = 0;  // gemm: split-K reduction table
+    int red_jobs = 0;
+    int64_t red_elems = 0;
 };
 
-// The tile fields of a grouped GEMM's jobs for tile shape `variant`; returns
-// the total number of tiles.
-int64_t lay_tiles(std::vector<GemmJob>& jobs, int variant) {
+// The tile and split-K fields of a grouped GEMM's jobs for `choice`; returns
+// the total number of tiles.  Split jobs take their partials from `part`
+// (consecutive, *part_elems doubles in all; part may be null when only the
+// size is wanted).  The split jobs' reduction table goes to *red.
+int64_t lay_tiles(std::vector<GemmJob>& jobs, int choice, double* part, int64_t* part_elems,
+                  std::vector<RedJob>* red) {
+    const int variant = choice % kGemmVariants;
+    const int kc = kSplitK[choice / kGemmVariants];
     const int bm = kVarBM[variant], bn = kVarBN[variant];
-    int64_t tiles = 0;
+    int64_t tiles = 0, pe = 0, elems = 0;
+    if (red) red->clear();
     for (auto& j : jobs) {
         j.tiles_m = (j.M + bm - 1) / bm;
         j.tiles_n = (j.N + bn - 1) / bn;
+        j.ksplit = 1;
+        j.kchunk = 0;
+        j.part = nullptr;
+        if (kc > 0 && !j.copy_on_skip && j.tiles_m * j.tiles_n <= kSplitTiles && j.K > kc) {
+            int ks = (j.K + kc - 1) / kc;
+            if (ks > kMaxSplit) ks = kMaxSplit;
+            j.kchunk = ((j.K + ks - 1) / ks + GBK - 1) / GBK * GBK;
+            j.ksplit = (j.K + j.kchunk - 1) / j.kchunk;
+            if (j.ksplit > 1) {
+                j.part = part ? part + pe : nullptr;
+                if (red) {
+                    RedJob r{};
+                    r.part = j.part;
+                    r.C = j.C;
+                    r.ldc = j.ldc;
+                    r.M = j.M;
+                    r.N = j.N;
+                    r.ksplit = j.ksplit;
+                    r.accum = j.accum;
+                    r.elem0 = elems;
+                    r.skip = j.skip;
+                    red->push_back(r);
+                }
+                pe += int64_t(j.ksplit) * j.M * j.N;
+                elems += int64_t(j.M) * j.N;
+            } else {
+                j.ksplit = 1;
+                j.kchunk = 0;
+            }
+        }
         j.tile0 = tiles;
-        tiles += int64_t(j.tiles_m) * j.tiles_n;
+        tiles += int64_t(j.tiles_m) * j.tiles_n * j.ksplit;
     }
+    if (part_elems) *part_elems = pe;
     return tiles;
 }
 
@@ -564,13 +656,24 @@ struct Builder {
         jobs.clear();
     }
     // every grouped GEMM's table, laid out for its chosen shape, into the blob
-    void place_gemms(const std::vector<int>& variant) {
+    // and the split jobs' reduction tables; the launches run one after the
+    // other, so all take their partials from the same `part` region.
+    // Returns the doubles of partials the largest launch needs.
+    int64_t place_gemms(const std::vector<int>& choice, double* part) {
+        int64_t most = 0;
         for (auto& r : recs) {
             if (r.kind != 1) continue;
-            r.variant = variant[r.gidx];
-            r.tiles = lay_tiles(gjobs[r.gidx], r.variant);
+            r.variant = choice[r.gidx];
+            int64_t pe = 0;
+            std::vector<RedJob> red;
+            r.tiles = lay_tiles(gjobs[r.gidx], r.variant, part, &pe, &red);
             r.off = put(gjobs[r.gidx]);
+            r.red_jobs = int(red.size());
+            r.red_elems = red.empty() ? 0 : red.back().elem0 + int64_t(red.back().M) * red.back().N;
+            if (!red.empty()) r.red_off = put(red);
+            if (pe > most) most = pe;
         }
+        return most;
     }
     void lu(std::vector<LuJob>& jobs) {
         if (jobs.empty()) return;
@@ -898,9 +1001,15 @@ cudaError_t launch_batch_plan(const Builder& B, const char* dtab, int* dev_statu
                     reinterpret_cast<const GaussJob*>(tab));
                 break;
             case 1:
-                e = launch_b_gemm(r.variant, r.tc32, reinterpret_cast<const GemmJob*>(tab),
-                                  r.njobs, r.tiles, s);
+                e = launch_b_gemm(r.variant % kGemmVariants, r.tc32,
+                                  reinterpret_cast<const GemmJob*>(tab), r.njobs, r.tiles, s);
                 if (e != cudaSuccess) return e;
+                if (r.red_jobs > 0) {
+                    count_launch();
+                    k_b_splitk_reduce<<<unsigned((r.red_elems + 255) / 256), 256, 0, s>>>(
+                        reinterpret_cast<const RedJob*>(dtab + r.red_off), r.red_jobs,
+                        r.red_elems);
+                }
                 break;
             case 2:
                 k_b_panel_lu<<<unsigned(r.njobs), LNT, size_t(r.maxn) * sizeof(double), s>>>(
@@ -922,14 +1031,30 @@ cudaError_t launch_batch_plan(const Builder& B, const char* dtab, int* dev_statu
     return cudaSuccess;
 }
 
+// The split-K partials live in a device buffer owned by the caller's
+// context, grown here when a plan needs more (after the stream drains).
+static cudaError_t grow_part(double** part, size_t* cap, int64_t elems, cudaStream_t s) {
+    const size_t need = size_t(elems > 0 ? elems : 1) * sizeof(double);
+    if (need <= *cap && *part) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (*part) cudaFree(*part);
+    *part = nullptr;
+    *cap = 0;
+    if ((e = cudaMalloc(reinterpret_cast<void**>(part), need)) != cudaSuccess) return e;
+    *cap = need;
+    return cudaSuccess;
+}
+
 // Plan, upload the job tables, capture the grouped launches in a CUDA graph
 // and launch it.  `tables` must hold batch_tables_bytes() bytes.
-// The autotuner: every grouped GEMM of the plan is timed alone in each tile
-// shape on its real job list (CUDA events, the better of two runs after one
-// warm-up; the operands may hold anything then, as the graph recomputes every
-// phase in order afterwards), and the fastest shape is kept.
+// The autotuner: every grouped GEMM of the plan is timed alone (with its
+// split-K reduction) for each tile shape and split-K choice on its real job
+// list (CUDA events, the better of two runs after one warm-up; the operands
+// may hold anything then, as the graph recomputes every phase in order
+// afterwards), and the fastest choice is kept.
 cudaError_t tune_gemms(Builder& B, char* tables, size_t tables_cap, cudaStream_t s,
-                       std::vector<int>* tuned) {
+                       std::vector<int>* tuned, double** part, size_t* part_cap) {
     const size_t base = (B.blob.size() + 255) & ~size_t(255);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return cudaErrorUnknown;
@@ -943,21 +1068,40 @@ cudaError_t tune_gemms(Builder& B, char* tables, size_t tables_cap, cudaStream_t
         if (r.kind != 1) continue;
         std::vector<GemmJob> jobs = B.gjobs[r.gidx];
         float best = 0.f;
-        for (int v = 0; v < kGemmVariants && e == cudaSuccess; ++v) {
-            const int64_t tiles = lay_tiles(jobs, v);
+        for (int v = 0; v < kGemmChoices && e == cudaSuccess; ++v) {
+            int64_t pe = 0;
+            lay_tiles(jobs, v, nullptr, &pe, nullptr);
+            // a split choice that splits nothing repeats the unsplit one
+            if (v >= kGemmVariants && pe == 0) continue;
+            if ((e = grow_part(part, part_cap, pe, s)) != cudaSuccess) break;
+            std::vector<RedJob> red;
+            const int64_t tiles = lay_tiles(jobs, v, *part, &pe, &red);
             const size_t bytes = jobs.size() * sizeof(GemmJob);
-            if (base + bytes > tables_cap) {
+            const size_t roff = (base + bytes + 255) & ~size_t(255);
+            const size_t rbytes = red.size() * sizeof(RedJob);
+            if (roff + rbytes > tables_cap) {
                 e = cudaErrorInvalidValue;
                 break;
             }
             GemmJob* tab = reinterpret_cast<GemmJob*>(tables + base);
+            RedJob* rtab = reinterpret_cast<RedJob*>(tables + roff);
             if ((e = cudaMemcpyAsync(tab, jobs.data(), bytes, cudaMemcpyHostToDevice, s)) !=
                 cudaSuccess)
                 break;
+            if (rbytes && (e = cudaMemcpyAsync(rtab, red.data(), rbytes, cudaMemcpyHostToDevice,
+                                               s)) != cudaSuccess)
+                break;
+            const int64_t relems =
+                red.empty() ? 0 : red.back().elem0 + int64_t(red.back().M) * red.back().N;
             float t_v = 0.f;
             for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
                 cudaEventRecord(e0, s);
-                e = launch_b_gemm(v, r.tc32, tab, int(jobs.size()), tiles, s);
+                e = launch_b_gemm(v % kGemmVariants, r.tc32, tab, int(jobs.size()), tiles, s);
+                if (e == cudaSuccess && !red.empty()) {
+                    k_b_splitk_reduce<<<unsigned((relems + 255) / 256), 256, 0, s>>>(
+                        rtab, int(red.size()), relems);
+                    e = cudaGetLastError();
+                }
                 cudaEventRecord(e1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 float ms = 0.f;
@@ -979,17 +1123,26 @@ cudaError_t tune_gemms(Builder& B, char* tables, size_t tables_cap, cudaStream_t
 cudaError_t run_batch(const plu_batch_problem* P, int count, int prec, char* ws, char* tables,
                       size_t tables_cap, int* dev_status, int num_sms, cudaStream_t s,
                       cudaStream_t cs, int* nlaunch, float* ms_graph, std::vector<int>* tuned,
-                      int forced) {
+                      int forced, double** part, size_t* part_cap) {
     Builder B;
     plan_batch(P, count, prec, ws, B);
     if (forced >= 0) {
         if (forced >= kGemmVariants) return cudaErrorInvalidValue;
         tuned->assign(B.gjobs.size(), forced);
     } else if (tuned->size() != B.gjobs.size()) {
-        const cudaError_t te = tune_gemms(B, tables, tables_cap, s, tuned);
+        const cudaError_t te = tune_gemms(B, tables, tables_cap, s, tuned, part, part_cap);
         if (te != cudaSuccess) return te;
     }
-    B.place_gemms(*tuned);
+    for (int c : *tuned)
+        if (c < 0 || c >= kGemmChoices) return cudaErrorInvalidValue;
+    {
+        // the partial region the chosen split-K needs, then the placement
+        Builder dry = B;
+        const int64_t need = dry.place_gemms(*tuned, nullptr);
+        const cudaError_t ge = grow_part(part, part_cap, need, s);
+        if (ge != cudaSuccess) return ge;
+    }
+    B.place_gemms(*tuned, *part);
     if (B.blob.size() > tables_cap) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemcpyAsync(tables, B.blob.data(), B.blob.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
@@ -1036,11 +1189,18 @@ size_t batch_tables_bytes(int count) {
     return size_t(count) * 72 * sizeof(GemmJob) + (1 << 20);
 }
 
-int batch_gemm_tile(int variant, int* bm, int* bn) {
-    if (variant < 0 || variant >= kGemmVariants) return 0;
-    *bm = kVarBM[variant];
-    *bn = kVarBN[variant];
+int batch_gemm_tile(int choice, int* bm, int* bn) {
+    if (choice < 0 || choice >= kGemmChoices) return 0;
+    *bm = kVarBM[choice % kGemmVariants];
+    *bn = kVarBN[choice % kGemmVariants];
     return 1;
 }
+
+int batch_gemm_splitk(int choice) {
+    if (choice < 0 || choice >= kGemmChoices) return -1;
+    return kSplitK[choice / kGemmVariants];
+}
+
+int batch_gemm_choices() { return kGemmChoices; }
 
 }  // namespace plu

@@ -406,14 +406,20 @@ cudaError_t launch_scatter_rows(int64_t rows, int cols, const int32_t* perm, con
 // ------------------------------------------------------------- batched
 size_t batch_workspace_bytes(const plu_batch_problem* P, int count);
 size_t batch_tables_bytes(int count);
-// tuned: the tile shape of every grouped GEMM of the plan; when it does not
-// match the plan's GEMM count the autotuner times the shapes and fills it.
-// forced >= 0 takes that shape for every grouped GEMM instead.
+// tuned: the tile shape and split-K choice of every grouped GEMM of the
+// plan; when it does not match the plan's GEMM count the autotuner times the
+// choices and fills it.  forced >= 0 takes that tile shape, unsplit, for every
+// grouped GEMM instead.  *part / *part_cap: the split-K partial buffer (device,
+// owned by the caller, grown here with cudaMalloc when too small).
 cudaError_t run_batch(const plu_batch_problem* P, int count, int prec, char* ws, char* tables,
                       size_t tables_cap, int* dev_status, int num_sms, cudaStream_t s,
                       cudaStream_t capture_stream, int* nlaunch, float* ms_graph,
-                      std::vector<int>* tuned, int forced);
-// Tile shape (rows, columns) of grouped-GEMM variant v; 0 for a bad index.
-int batch_gemm_tile(int variant, int* bm, int* bn);
+                      std::vector<int>* tuned, int forced, double** part, size_t* part_cap);
+// Tile shape (rows, columns) of grouped-GEMM choice c; 0 for a bad index.
+int batch_gemm_tile(int choice, int* bm, int* bn);
+// K-chunk length of choice c (0: no split-K); -1 for a bad index.
+int batch_gemm_splitk(int choice);
+// Number of grouped-GEMM choices (tile shapes x split-K lengths).
+int batch_gemm_choices();
 
 }  // namespace plu

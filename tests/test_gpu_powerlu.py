@@ -327,6 +327,69 @@ def test_batched_autotuner_choice_is_cached_and_valid(ctx):
         plu.plu_set_batched_tile(ctx, 48, 48)
 
 
+def _fp64_batch(cases):
+    mats, probs = [], []
+    for c in cases:
+        sig = synth.sigma_profile("expk", min(c["m"], c["n"]), k=c["k"])
+        A = synth.svd_matrix_np(c["m"], c["n"], sig, seed=c["seed"])
+        mats.append(A)
+        probs.append(dict(A=dev(A), k=c["k"], l=c["l"], v=c["v"], algo=c["algo"], seed=c["seed"]))
+    return mats, probs
+
+
+def test_batched_tune_file_persists_and_split_k_matches_oracle(ctx, tmp_path):
+    """The autotuner's choices go to the tuning file; a new context reads them
+    back without timing (no line added, same shapes and split-K).  A file
+    line that asks every launch for 64 x 32 tiles with K chunks of 256 (the
+    split-K reduction in FP64) gives identical pivots and factors to 1e-9
+    against the oracle."""
+    cases = _batch_cases()[2:]                  # a batch signature no other test uses
+    mats, probs = _fp64_batch(cases)
+    path = tmp_path / "tune.txt"
+    plu.plu_set_batched_tune_file(ctx, str(path))
+    try:
+        plu.plu_batched(ctx, probs, prec="fp64")
+        tiles, splits = plu.plu_batched_tiles(ctx), plu.plu_batched_splitk(ctx)
+    finally:
+        plu.plu_set_batched_tune_file(ctx, None)
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1
+    head = lines[0].split()
+    assert head[:2] == ["plu-batched-tune", "1"] and int(head[3]) == len(tiles) == len(splits)
+    assert set(splits) <= {0, 1024, 256}
+    c2 = plu.Context(0)
+    try:
+        plu.plu_set_batched_tune_file(c2, str(path))
+        plu.plu_batched(c2, probs, prec="fp64")
+        assert plu.plu_batched_tiles(c2) == tiles and plu.plu_batched_splitk(c2) == splits
+        assert path.read_text().splitlines() == lines
+    finally:
+        torch.cuda.synchronize()
+        c2.close()
+    # every launch: 64 x 32 tiles, K chunks of 256 (choice 0 + 3 * 2)
+    forced = " ".join(head[:4] + ["6"] * int(head[3]))
+    path.write_text(lines[0] + "\n" + forced + "\n")
+    c3 = plu.Context(0)
+    try:
+        plu.plu_set_batched_tune_file(c3, str(path))
+        outs, _ = plu.plu_batched(c3, probs, prec="fp64")
+        assert set(plu.plu_batched_splitk(c3)) == {256}
+    finally:
+        torch.cuda.synchronize()
+        c3.close()
+    for c, A, (gp, gq, gL, gU) in zip(cases, mats, outs):
+        if c["algo"] == 1:
+            ref = oracle.singlepass(A, c["k"], seed=c["seed"])
+        else:
+            ref = oracle.powerlu(A, c["k"], c["l"], c["v"], seed=c["seed"])
+        check_parity(A, (gp, gq, gL, gU), ref, tol=1e-9)
+
+
+def test_batched_tune_file_must_be_writable(ctx, tmp_path):
+    with pytest.raises(plu.PLUError):
+        plu.plu_set_batched_tune_file(ctx, str(tmp_path / "no" / "such" / "dir" / "t.txt"))
+
+
 def test_batched_fp32_error_close_to_fp64(ctx):
     cases = _batch_cases()[:8]
     probs32, probs64, mats = [], [], []
