@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -305,6 +306,11 @@ cudaError_t launch_b_gemm(int variant, int tc32, const GemmJob* tab, int njobs, 
 
 // ------------------------------------------- one-CTA partial-pivoting LU
 constexpr int LNT = 512;
+// multi-CTA LU: a panel with more than kMcWork FMAs of elimination gets
+// ceil(work / kMcWork) CTAs (at most kMcMaxG, at least kMcMinRows rows each)
+constexpr double kMcWork = 1.5e6;
+constexpr int kMcMaxG = 16, kMcMinRows = 256;
+constexpr int64_t kBatchSpin = 16LL << 20;   // spin limit of a group's column-step wait
 
 struct BCand {
     double v;
@@ -405,6 +411,157 @@ k_b_panel_lu(const LuJob* __restrict__ jobs) {
     if (t == 0 && J.info) *J.info = first_zero;
     const int r = steps;
     for (int64_t i = t; i < rows; i += LNT) {
+        const int s = J.pivstep[i];
+        if (J.mode == 0) {
+            if (s >= 0) {
+                X[i + int64_t(s) * J.ldx] = 1.0;
+                for (int c = s + 1; c < cols; ++c) X[i + int64_t(c) * J.ldx] = 0.0;
+            }
+            continue;
+        }
+        const int64_t pp = J.pos[i];
+        J.perm[pp] = int32_t(i);
+        for (int c = 0; c < r; ++c) {
+            double v;
+            if (s >= 0 && c == s) v = 1.0;
+            else if (s >= 0 && c > s) v = 0.0;
+            else v = X[i + int64_t(c) * J.ldx];
+            if (J.l_trans) J.L[c + pp * J.ldL] = v;
+            else J.L[pp + int64_t(c) * J.ldL] = v;
+        }
+        if (s >= 0) {
+            for (int c = 0; c < cols; ++c) {
+                const double v = (c >= s) ? X[i + int64_t(c) * J.ldx] : 0.0;
+                if (J.u_trans) J.U[c + int64_t(s) * J.ldU] = v;
+                else J.U[s + int64_t(c) * J.ldU] = v;
+            }
+        }
+    }
+}
+
+// ------------------------------- the LU of one problem over several CTAs
+// The large problems' panels: G CTAs of a cooperative launch share one
+// problem, each owning a contiguous run of its rows; a column step publishes
+// each CTA's candidate in a slot (two sets, by step parity, so a fast CTA
+// never overwrites slots a slow one still reads), counts arrivals on the
+// problem's counter (release), and every CTA, once all G have arrived
+// (acquire; bounded spin, PLU timeout status on expiry), reduces the G slots
+// to the same pivot.  The pivot's row is read from L2 (its owner updated it
+// before publishing).  Same pivot order, tie rule, multipliers and FMAs per
+// entry as k_b_panel_lu, so the same factors.
+struct McCta {
+    int job;
+    int rank, G;
+    int64_t r0, r1;      // rows [r0, r1) of the problem
+};
+
+struct McSync {
+    int64_t cnt_off;     // per job: byte offsets (from the table base) of the
+    int64_t slots_off;   // arrival counter and of its 2 x G candidate slots
+};
+
+__global__ void __launch_bounds__(LNT)
+k_b_panel_lu_mc(const LuJob* __restrict__ jobs, const McCta* __restrict__ ctas,
+                const McSync* __restrict__ syncs, unsigned char* __restrict__ base,
+                int* __restrict__ status, int64_t budget) {
+    extern __shared__ double urow[];
+    __shared__ BCand red[LNT / 32];
+    __shared__ BCand piv;
+    __shared__ int first_zero;
+    __shared__ int ok;
+    const McCta C = ctas[blockIdx.x];
+    const LuJob J = jobs[C.job];
+    unsigned* const cnt = reinterpret_cast<unsigned*>(base + syncs[C.job].cnt_off);
+    BCand* const slots = reinterpret_cast<BCand*>(base + syncs[C.job].slots_off);
+    const int t = threadIdx.x;
+    const int cols = J.cols;
+    const int steps = int(J.rows < int64_t(cols) ? J.rows : int64_t(cols));
+    double* X = J.X;
+    for (int64_t i = C.r0 + t; i < C.r1; i += LNT) {
+        J.pos[i] = int(i);
+        J.pivstep[i] = -1;
+    }
+    if (t == 0) {
+        first_zero = 0;
+        ok = 1;
+    }
+    __syncthreads();
+    for (int j = 0; j < steps; ++j) {
+        BCand best{-1.0, INT_MAX, -1};
+        for (int64_t i = C.r0 + t; i < C.r1; i += LNT) {
+            if (J.pivstep[i] >= 0) continue;
+            const BCand c{fabs(X[i + int64_t(j) * J.ldx]), J.pos[i], int(i)};
+            if (b_better(c, best)) best = c;
+        }
+        best = b_warp_best(best);
+        if ((t & 31) == 0) red[t >> 5] = best;
+        __syncthreads();
+        if (t < 32) {
+            BCand x = (t < LNT / 32) ? red[t] : BCand{-1.0, INT_MAX, -1};
+            x = b_warp_best(x);
+            if (t == 0) {
+                BCand* slot = slots + (j & 1) * C.G + C.rank;
+                slot->v = x.v;
+                slot->pos = x.pos;
+                slot->row = x.row;
+                __threadfence();
+                red_release_add_u32(cnt, 1u);
+                const unsigned target = unsigned(j + 1) * unsigned(C.G);
+                int64_t spins = 0;
+                while (ld_acquire_u32(cnt) < target) {
+                    if (ld_volatile_i32(status) != DEV_OK || ++spins > budget) {
+                        atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (!ok) return;
+        if (t < 32) {
+            BCand x{-1.0, INT_MAX, -1};
+            for (int g = t; g < C.G; g += 32) {
+                const BCand* sl = slots + (j & 1) * C.G + g;
+                const BCand c{__ldcg(&sl->v), __ldcg(&sl->pos), __ldcg(&sl->row)};
+                if (b_better(c, x)) x = c;
+            }
+            x = b_warp_best(x);
+            if (t == 0) piv = x;
+        }
+        __syncthreads();
+        const BCand pv = piv;
+        if (pv.row < 0) break;                        // no row left (cannot happen: rows >= steps)
+        for (int64_t i = C.r0 + t; i < C.r1; i += LNT) {
+            if (i == pv.row) {
+                J.pos[i] = j;
+                J.pivstep[i] = j;
+            } else if (J.pos[i] == j) {
+                J.pos[i] = pv.pos;
+            }
+        }
+        for (int c = j + t; c < cols; c += LNT) urow[c] = __ldcg(&X[pv.row + int64_t(c) * J.ldx]);
+        if (t == 0 && pv.v == 0.0 && first_zero == 0) first_zero = j + 1;
+        __syncthreads();
+        const double ujj = urow[j];
+        if (ujj != 0.0) {
+            const double rinv = 1.0 / ujj;
+            for (int64_t i = C.r0 + t; i < C.r1; i += LNT) {
+                if (J.pivstep[i] >= 0) continue;
+                double* xi = X + i;
+                const double lij = lu_multiplier(xi[int64_t(j) * J.ldx], ujj, rinv);
+                xi[int64_t(j) * J.ldx] = lij;
+                for (int c = j + 1; c < cols; ++c) {
+                    double* p = xi + int64_t(c) * J.ldx;
+                    *p = fma(-lij, urow[c], *p);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (t == 0 && J.info && C.rank == 0) *J.info = first_zero;
+    const int r = steps;
+    for (int64_t i = C.r0 + t; i < C.r1; i += LNT) {
         const int s = J.pivstep[i];
         if (J.mode == 0) {
             if (s >= 0) {
@@ -581,6 +738,8 @@ struct LaunchRec {
     size_t red_off = 0;  // gemm: split-K reduction table
     int red_jobs = 0;
     int64_t red_elems = 0;
+    size_t cta_off = 0, sync_off = 0, zero_off = 0, zero_bytes = 0;   // multi-CTA LU
+    int nctas = 0;
 };
 
 // The tile and split-K fields of a grouped GEMM's jobs for `choice`; returns
@@ -675,11 +834,73 @@ struct Builder {
         }
         return most;
     }
+    // co-resident CTAs of the multi-CTA LU (0: none)
+    int mc_cap = 0;
+    // A phase's LUs: the large panels (more than kMcWork FP64 FMAs of
+    // elimination) on G CTAs each (a cooperative launch, first), the rest one
+    // CTA each.
     void lu(std::vector<LuJob>& jobs) {
         if (jobs.empty()) return;
-        int maxc = 1;
-        for (auto& j : jobs) maxc = std::max(maxc, j.cols);
-        recs.push_back(LaunchRec{2, put(jobs), int(jobs.size()), 0, maxc, 0});
+        std::vector<LuJob> one, many;
+        std::vector<int> G;
+        for (auto& j : jobs) {
+            const double work = double(j.rows) * j.cols * j.cols / 2.0;
+            int g = int(std::min<double>(std::ceil(work / kMcWork), double(kMcMaxG)));
+            const int64_t rg = j.rows / kMcMinRows;
+            if (g > rg) g = int(rg);
+            if (mc_cap >= 2 && g >= 2) {
+                many.push_back(j);
+                G.push_back(g);
+            } else {
+                one.push_back(j);
+            }
+        }
+        // fit the co-resident capacity: shrink the groups, then drop the smallest
+        auto total = [&]() { int s = 0; for (int g : G) s += g; return s; };
+        while (!many.empty() && total() > mc_cap) {
+            int big = 0;
+            for (size_t i = 1; i < G.size(); ++i) if (G[i] > G[big]) big = int(i);
+            if (G[big] > 2) {
+                --G[big];
+            } else {
+                one.push_back(many.back());
+                many.pop_back();
+                G.pop_back();
+            }
+        }
+        if (!many.empty()) {
+            std::vector<McCta> ctas;
+            std::vector<McSync> syncs;
+            int maxc = 1;
+            size_t zbytes = 0;
+            std::vector<int64_t> cnt_rel, slot_rel;
+            for (size_t q = 0; q < many.size(); ++q) {
+                maxc = std::max(maxc, many[q].cols);
+                cnt_rel.push_back(int64_t(zbytes));
+                zbytes += 16;
+                slot_rel.push_back(int64_t(zbytes));
+                zbytes += size_t(2) * G[q] * sizeof(BCand);
+                const int64_t rows = many[q].rows;
+                for (int r = 0; r < G[q]; ++r)
+                    ctas.push_back(McCta{int(q), r, G[q], rows * r / G[q], rows * (r + 1) / G[q]});
+            }
+            std::vector<unsigned char> zeros((zbytes + 255) & ~size_t(255), 0);
+            LaunchRec rec{5, put(many), int(many.size()), 0, maxc, 0};
+            rec.cta_off = put(ctas);
+            rec.nctas = int(ctas.size());
+            rec.zero_off = put(zeros);
+            rec.zero_bytes = zeros.size();
+            for (size_t q = 0; q < many.size(); ++q)
+                syncs.push_back(McSync{int64_t(rec.zero_off) + cnt_rel[q],
+                                       int64_t(rec.zero_off) + slot_rel[q]});
+            rec.sync_off = put(syncs);
+            recs.push_back(rec);
+        }
+        if (!one.empty()) {
+            int maxc = 1;
+            for (auto& j : one) maxc = std::max(maxc, j.cols);
+            recs.push_back(LaunchRec{2, put(one), int(one.size()), 0, maxc, 0});
+        }
         jobs.clear();
     }
     void gauss(std::vector<GaussJob>& jobs) {
@@ -1015,6 +1236,31 @@ cudaError_t launch_batch_plan(const Builder& B, const char* dtab, int* dev_statu
                 k_b_panel_lu<<<unsigned(r.njobs), LNT, size_t(r.maxn) * sizeof(double), s>>>(
                     reinterpret_cast<const LuJob*>(tab));
                 break;
+            case 5: {
+                // zero the groups' counters and slots, then one cooperative
+                // launch (its CTAs wait on one another, so they must all be
+                // resident)
+                e = cudaMemsetAsync(const_cast<char*>(dtab) + r.zero_off, 0, r.zero_bytes, s);
+                if (e != cudaSuccess) return e;
+                const LuJob* jt = reinterpret_cast<const LuJob*>(tab);
+                const McCta* ct = reinterpret_cast<const McCta*>(dtab + r.cta_off);
+                const McSync* sy = reinterpret_cast<const McSync*>(dtab + r.sync_off);
+                unsigned char* bp = reinterpret_cast<unsigned char*>(const_cast<char*>(dtab));
+                int64_t budget = kBatchSpin;
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(unsigned(r.nctas));
+                cfg.blockDim = dim3(LNT);
+                cfg.dynamicSmemBytes = size_t(r.maxn) * sizeof(double);
+                cfg.stream = s;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeCooperative;
+                attr[0].val.cooperative = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                e = cudaLaunchKernelEx(&cfg, k_b_panel_lu_mc, jt, ct, sy, bp, dev_status, budget);
+                if (e != cudaSuccess) return e;
+                break;
+            }
             case 3:
                 k_b_cholesky<<<unsigned(r.njobs), CNT, 0, s>>>(reinterpret_cast<const CholJob*>(tab),
                                                               dev_status);
@@ -1125,6 +1371,15 @@ cudaError_t run_batch(const plu_batch_problem* P, int count, int prec, char* ws,
                       cudaStream_t cs, int* nlaunch, float* ms_graph, std::vector<int>* tuned,
                       int forced, double** part, size_t* part_cap) {
     Builder B;
+    {
+        // the multi-CTA LU's CTAs must all be resident at once
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_b_panel_lu_mc, LNT,
+                                                          size_t(1024) * sizeof(double)) !=
+            cudaSuccess)
+            nb = 0;
+        B.mc_cap = nb * num_sms;
+    }
     plan_batch(P, count, prec, ws, B);
     if (forced >= 0) {
         if (forced >= kGemmVariants) return cudaErrorInvalidValue;

@@ -385,6 +385,25 @@ def test_batched_tune_file_persists_and_split_k_matches_oracle(ctx, tmp_path):
         check_parity(A, (gp, gq, gL, gU), ref, tol=1e-9)
 
 
+def test_batched_large_panels_on_several_ctas_match_oracle(ctx):
+    """Panels with more than 1.5e6 FMAs of elimination are factored by groups
+    of CTAs that exchange column-step candidates (4096 x 74: 8 CTAs; the
+    single-pass and tail LUs of 3000 x 64 and 2500 x 64 too), beside small
+    problems factored by one CTA: identical pivots and factors to 1e-9."""
+    cases = [dict(m=4096, n=1500, k=64, l=74, v=3, algo=0, seed=41),
+             dict(m=3000, n=2500, k=64, l=64, v=1, algo=1, seed=42),
+             dict(m=700, n=500, k=12, l=18, v=2, algo=0, seed=43),
+             dict(m=2600, n=2600, k=40, l=50, v=4, algo=0, seed=44)]
+    mats, probs = _fp64_batch(cases)
+    outs, _ = plu.plu_batched(ctx, probs, prec="fp64")
+    for c, A, (gp, gq, gL, gU) in zip(cases, mats, outs):
+        if c["algo"] == 1:
+            ref = oracle.singlepass(A, c["k"], seed=c["seed"])
+        else:
+            ref = oracle.powerlu(A, c["k"], c["l"], c["v"], seed=c["seed"])
+        check_parity(A, (gp, gq, gL, gU), ref, tol=1e-9)
+
+
 def test_batched_tune_file_must_be_writable(ctx, tmp_path):
     with pytest.raises(plu.PLUError):
         plu.plu_set_batched_tune_file(ctx, str(tmp_path / "no" / "such" / "dir" / "t.txt"))
