@@ -717,7 +717,7 @@ def run_ours(args, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "bf16": "bf16",
-                      "fp8": "fp8e4m3"}[prec], "data": "synthetic",
+                      "fp8": "fp8e4m3", "tf32x3": "tf32x3"}[prec], "data": "synthetic",
             "config": {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "l": w.l, "v": w.v,
                        "sigma": w.sigma, "storage": "f32" if Ad.dtype == torch.float32 else "f64",
                        "pass_precision": prec, "between_passes": "f64",
@@ -810,7 +810,7 @@ def run_fixed_precision(args, w):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "bf16": "bf16",
-                      "fp8": "fp8e4m3"}[args.prec], "data": "synthetic",
+                      "fp8": "fp8e4m3", "tf32x3": "tf32x3"}[args.prec], "data": "synthetic",
             "config": {"workload": w.name, "m": w.m, "n": w.n, "eps": w.eps, "b": w.b, "l": w.l,
                        "v": w.v, "sigma": w.sigma, "pass_precision": args.prec,
                        "between_passes": "f64", "parallelism": "replicas" if ws > 1 else "single"},
@@ -837,7 +837,7 @@ def run_singlepass(args, w):
     torch.cuda.empty_cache()
     stream = torch.cuda.current_stream()
     ctx = plu.Context(local, stream.cuda_stream)
-    prec = args.prec if args.prec in ("fp64", "fp32", "tf32") else "tf32"
+    prec = args.prec if args.prec in ("fp64", "fp32", "tf32", "tf32x3") else "tf32"
 
     def timed(A, pr, steps, warmup):
         for i in range(warmup):
@@ -879,7 +879,8 @@ def run_singlepass(args, w):
             "metric": METRIC, "value": flops * ws / (ms / 1e3) / 1e12, "unit": "TFLOP/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32"}[prec], "data": "synthetic",
+            "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3"}[prec],
+            "data": "synthetic",
             "config": {"workload": w.name, "algo": "singlepass", "m": w.m, "n": w.n, "k": w.k,
                        "sigma": w.sigma, "pass_precision": prec, "between_passes": "f64",
                        "parallelism": "replicas" if ws > 1 else "single"},
@@ -1251,7 +1252,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixed_32768", choices=sorted(workloads()))
-    ap.add_argument("--prec", default="tf32", choices=["fp64", "fp32", "tf32", "bf16", "fp8"])
+    ap.add_argument("--prec", default="tf32", choices=["fp64", "fp32", "tf32", "bf16", "fp8",
+                                                         "tf32x3"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--algo", default="powerlu", choices=["powerlu", "singlepass", "randlu"],
