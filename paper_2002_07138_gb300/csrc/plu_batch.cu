@@ -132,6 +132,12 @@ constexpr int kSplitK[kSplitChoices] = {0, 1024, 256};
 constexpr int kGemmChoices = kGemmVariants * kSplitChoices;
 constexpr int kSplitTiles = 8, kMaxSplit = 32;
 
+// An FP64 operand value in the arithmetic type TC (FP32: on the integer pipe)
+template <typename TC> __device__ __forceinline__ TC b_to_tc(double v) {
+    if constexpr (sizeof(TC) == 4) return f64_to_f32_rn(v);
+    else return v;
+}
+
 template <typename TC, int BMV, int BNV>
 __global__ void __launch_bounds__(GNT)
 k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
@@ -187,7 +193,7 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
             TC v = TC(0);
             if (gi < J.M && gk < kend) {
                 const int64_t off = J.transA ? gk + gi * J.lda : gi + gk * J.lda;
-                v = J.a_f32 ? TC(Af[off]) : TC(Ad[off]);
+                v = J.a_f32 ? TC(Af[off]) : b_to_tc<TC>(Ad[off]);
             }
             ra[r] = v;
         }
@@ -198,7 +204,8 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
             else          { kk = t % 16; jj = t / 16 + 16 * r; }
             const int64_t gj = j0 + jj, gk = k0 + kk;
             TC v = TC(0);
-            if (gj < J.N && gk < kend) v = TC(J.transB ? J.B[gj + gk * J.ldb] : J.B[gk + gj * J.ldb]);
+            if (gj < J.N && gk < kend)
+                v = b_to_tc<TC>(J.transB ? J.B[gj + gk * J.ldb] : J.B[gk + gj * J.ldb]);
             rb[r] = v;
         }
     };

@@ -23,6 +23,12 @@ constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
 template <typename T> __device__ __forceinline__ T to_acc(float x) { return T(x); }
 
+// An operand value in the arithmetic type TC: FP64 to FP32 on the integer pipe
+template <typename TC, typename TS> __device__ __forceinline__ TC to_tc(TS v) {
+    if constexpr (sizeof(TC) == 4 && sizeof(TS) == 8) return f64_to_f32_rn(double(v));
+    else return TC(v);
+}
+
 // C partial (split z) = op(A)[M x Kz] * op(B)[Kz x N].
 //   op(A)(i, k) = TRANSA ? A[k + i*lda] : A[i + k*lda]
 //   op(B)(k, j) = TRANSB ? B[j + k*ldb] : B[k + j*ldb]
@@ -74,7 +80,7 @@ k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t l
                     if constexpr (sizeof(TA) == 4) nsq.add(float(a));
                     else nsq64 = fma(double(a), double(a), nsq64);
                 }
-                v = TC(a);
+                v = to_tc<TC>(a);
             }
             ra[r] = v;
         }
@@ -87,7 +93,7 @@ k_gemm_simt(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t l
             else        { kk = t % 16; jj = t / 16 + 16 * r; }
             const int64_t gj = j0 + jj, gk = k0 + kk;
             TC v = TC(0);
-            if (gj < N && gk < kend) v = TC(TRANSB ? B[gj + gk * ldb] : B[gk + gj * ldb]);
+            if (gj < N && gk < kend) v = to_tc<TC>(TRANSB ? B[gj + gk * ldb] : B[gk + gj * ldb]);
             rb[r] = v;
         }
     };
@@ -196,7 +202,7 @@ __global__ void k_f64_to_f32(int64_t rows, int64_t cols, const double* __restric
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
         const int64_t i = e % rows, j = e / rows;
-        Y[e] = float(X[i + j * ldx]);
+        Y[e] = f64_to_f32_rn(X[i + j * ldx]);
     }
 }
 

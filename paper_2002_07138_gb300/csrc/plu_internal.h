@@ -54,6 +54,51 @@ __device__ __forceinline__ double lu_multiplier(double x, double u, double rinv)
                                                                                      : x / u;
 }
 
+// x rounded to FP32 (to nearest, ties to even) on the integer pipe: a
+// conversion on GB300's FP64 pipe holds it like an FMA (~64 cycles per warp
+// instruction), and the FP32 GEMMs convert every FP64 operand they load.
+// Results in the normal FP32 range (including a rounding up to infinity) are
+// formed from the bits (IEEE 754 round to nearest even of the 52-bit
+// significand to 23 bits, the carry running into the exponent); zeros,
+// subnormal results, infinities and NaNs take the hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned hi = unsigned(b >> 32);
+    const int e = int((hi >> 20) & 0x7FF);
+    if (e < 897 || e > 1150) return __double2float_rn(x);     // |x| < 2^-126 or >= 2^128
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFULL;
+    const unsigned long long rem = m & 0x1FFFFFFFULL;           // the 29 bits dropped
+    unsigned bits = (unsigned(e - 1023 + 127) << 23) | unsigned(m >> 29);
+    if (rem > 0x10000000ULL || (rem == 0x10000000ULL && (bits & 1u))) bits += 1u;
+    return __uint_as_float(bits | (hi & 0x80000000u));
+}
+
+// x as FP64, exactly, on the integer pipe (zeros and normal numbers; a
+// subnormal, infinite or NaN x takes the hardware conversion).
+__device__ __forceinline__ double f32_to_f64(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xFFu;
+    if ((u & 0x7FFFFFFFu) == 0) return __hiloint2double(int(u), 0);
+    if (e == 0 || e == 255) return double(x);
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return __hiloint2double(int(hi), int(u << 29));
+}
+
+// A sum of FP32 values kept as an unevaluated pair s + c (Neumaier's
+// compensated summation, on the FP32 pipe): s + c equals the exact sum up to
+// a relative error of about n * 2^-48, so value() (one FP64 addition) is as
+// good as summing in FP64, without an FP64 conversion and addition per term.
+struct Sum2f {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = __fadd_rn(s, x);
+        c = fabsf(s) >= fabsf(x) ? __fadd_rn(c, __fadd_rn(__fsub_rn(s, t), x))
+                                 : __fadd_rn(c, __fadd_rn(__fsub_rn(x, t), s));
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return f32_to_f64(s) + f32_to_f64(c); }
+};
+
 // Sum of squares of FP32 values without the FP64 pipe: each square is split
 // exactly into its FP32 product and the product's FMA residual, and the
 // products are added with a compensated (error-free) FP32 sum whose errors,

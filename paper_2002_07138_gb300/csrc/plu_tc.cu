@@ -466,15 +466,17 @@ __global__ void __launch_bounds__(BM) k_tc_reduce(const float* __restrict__ part
     const int nj = min(RJT, l - j0);
     const int64_t c_lo = sh[0], c_hi = sh[1], pq = sh[2], pr = sh[3];
     int64_t cb = sh[4], rem = sh[5];
-    double acc[RJT];
-#pragma unroll
-    for (int q = 0; q < RJT; ++q) acc[q] = 0.0;
+    // compensated FP32 sums (Sum2f): the FP64 sum of the FP32 tiles without
+    // an FP64 conversion and addition per tile (GB300's FP64 pipe would bound
+    // this kernel); integer-valued tiles (the exact slice products) still
+    // add up exactly
+    Sum2f acc[RJT];
 #pragma unroll 4
     for (int64_t c = c_lo; c <= c_hi; ++c) {
         const float* src = part + ((c * max_segs + (blk - cb)) * npad + j0) * BM + r;
 #pragma unroll
         for (int q = 0; q < RJT; ++q)
-            if (q < nj) acc[q] += double(src[int64_t(q) * BM]);
+            if (q < nj) acc[q].add(src[int64_t(q) * BM]);
         cb += pq;
         rem += pr;
         if (rem >= ksteps) {
@@ -490,7 +492,7 @@ __global__ void __launch_bounds__(BM) k_tc_reduce(const float* __restrict__ part
 #pragma unroll
     for (int q = 0; q < RJT; ++q) {
         if (q < nj) {
-            double a = acc[q];
+            double a = acc[q].value();
             if (rowblk_scale) a *= rs;
             if (col_scale) a *= double(col_scale[j0 + q]);
             Y[i + int64_t(j0 + q) * ldy] = accum ? yv[q] + a : a;

@@ -562,20 +562,20 @@ __global__ void __launch_bounds__(BM) k_split_reduce(const float* __restrict__ p
     if (i >= M) return;
     const int j0 = blockIdx.y * RJ;
     const int nj = min(RJ, cols - j0);
-    double acc[RJ];
-#pragma unroll
-    for (int q = 0; q < RJ; ++q) acc[q] = 0.0;
+    // compensated FP32 sums: as accurate as FP64 sums of the FP32 tiles, with
+    // one FP64 addition per output instead of two FP64 operations per tile
+    Sum2f acc[RJ];
     for (int t = 0; t < nsrc; ++t) {
         const float* p = part + src[t] + int64_t(j0) * BM + r;
 #pragma unroll
         for (int q = 0; q < RJ; ++q)
-            if (q < nj) acc[q] += double(p[int64_t(q) * BM]);
+            if (q < nj) acc[q].add(p[int64_t(q) * BM]);
     }
 #pragma unroll
     for (int q = 0; q < RJ; ++q)
         if (q < nj) {
             double* y = Y + i + int64_t(j0 + q) * ldy;
-            *y = accum ? *y + acc[q] : acc[q];
+            *y = accum ? *y + acc[q].value() : acc[q].value();
         }
 }
 

@@ -200,6 +200,52 @@ def test_invalid_arguments_launch_nothing(ctx):
     assert ei.value.name == "PLU_EINVAL"
 
 
+def _fp64_values_for_rounding(rng, n):
+    """FP64 values whose FP32 rounding exercises every case: random
+    magnitudes over the normal FP32 range, exact ties between neighbouring
+    floats and values one double ulp either side, the binade edges, values
+    that round up into the next binade, near the largest float (below the
+    halfway point to infinity), around the smallest normal, subnormal
+    results and zeros."""
+    f = (rng.standard_normal(n) * np.exp2(rng.integers(-120, 120, size=n))).astype(np.float32)
+    g = np.nextafter(f, np.float32(np.inf), dtype=np.float32)
+    mid = (f.astype(np.float64) + g.astype(np.float64)) / 2.0          # exact ties
+    up = np.nextafter(mid, np.inf)
+    dn = np.nextafter(mid, -np.inf)
+    fmax = float(np.finfo(np.float32).max)
+    tiny = float(np.finfo(np.float32).tiny)
+    edges = np.array([1.0, -1.0, 2.0 - 2.0 ** -30, 1.0 + 2.0 ** -24, 1.0 + 2.0 ** -24 + 2.0 ** -52,
+                      fmax, fmax * (1 + 2.0 ** -25) - 2.0 ** 100, -fmax, tiny, tiny * (1 - 2.0 ** -30),
+                      tiny * (1 + 2.0 ** -30), tiny / 3.0, -tiny / 7.0, 2.0 ** -150, 2.0 ** -149,
+                      0.0, -0.0, 3.0e-42, 1e-300])
+    v = np.concatenate([f.astype(np.float64), mid, up, dn, -mid, edges])
+    return v[np.isfinite(v.astype(np.float32))]
+
+
+@pytest.mark.parametrize("trans", [0, 1])
+def test_fp32_pass_rounds_fp64_operands_to_nearest(ctx, trans):
+    """FP32 passes round FP64 operands to FP32 as IEEE round-to-nearest-even
+    does (the library forms the rounding on the integer pipe): with X's
+    columns unit vectors, Y holds the rounded entries of A bit for bit."""
+    rng = np.random.default_rng(17)
+    vals = _fp64_values_for_rounding(rng, 4000)
+    m, n = 384, 96
+    A = np.resize(vals, m * n).reshape(n, m).T.copy()
+    A[:, 0] = np.resize(vals[::-1], m)
+    js = [0, 1, 5, 47, 95] if trans == 0 else [0, 3, 200, 383]
+    K = n if trans == 0 else m
+    X = np.zeros((K, len(js)))
+    for c, j in enumerate(js):
+        X[j, c] = 1.0
+    got = host(plu.plu_pass(ctx, dev(A), trans, dev(X), "fp32"))
+    sel = A[:, js] if trans == 0 else A[js, :].T
+    # + 0.0: the product adds the one nonzero term to a +0 accumulator, so a
+    # rounded -0 comes out as +0
+    want = sel.astype(np.float32).astype(np.float64) + 0.0
+    bad = np.flatnonzero(got.view(np.int64) != want.view(np.int64))
+    assert bad.size == 0, (sel.ravel()[bad[:5]], got.ravel()[bad[:5]], want.ravel()[bad[:5]])
+
+
 # ------------------------------------------- a2/a4/a6 on tensor cores (TF32)
 def tf32_trunc(a):
     """float32 -> TF32 by dropping the 13 low mantissa bits (what the MMA reads)."""
