@@ -188,8 +188,16 @@ __global__ void k_reduce_splits(int64_t M, int64_t N, int splits, const TC* __re
         for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < M;
              i += int64_t(gridDim.x) * blockDim.x) {
             const int64_t e = i + j * M;
-            double sum = 0.0;
-            for (int z = 0; z < splits; ++z) sum += double(P[int64_t(z) * total + e]);
+            double sum;
+            if constexpr (sizeof(TC) == 4) {
+                // compensated FP32 sum: no FP64 conversion and addition per split
+                Sum2f acc;
+                for (int z = 0; z < splits; ++z) acc.add(P[int64_t(z) * total + e]);
+                sum = acc.value();
+            } else {
+                sum = 0.0;
+                for (int z = 0; z < splits; ++z) sum += double(P[int64_t(z) * total + e]);
+            }
             double* c = C + i + j * ldc;
             *c = accum > 0 ? *c + sum : accum < 0 ? *c - sum : sum;
         }

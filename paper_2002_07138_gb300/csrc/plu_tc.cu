@@ -442,7 +442,11 @@ __global__ void __launch_bounds__(BM) k_tc_reduce(const float* __restrict__ part
                                                   double* __restrict__ Y, int64_t ldy,
                                                   const float* __restrict__ rowblk_scale,
                                                   const float* __restrict__ col_scale, int accum) {
-    const int64_t blk = blockIdx.x;
+    // one CTA per (128-row block, RJT columns), the column groups of a block
+    // adjacent in launch order, so the CTAs that read the same partial tiles
+    // run together
+    const int ncg = (l + RJT - 1) / RJT;
+    const int64_t blk = blockIdx.x / ncg;
     const int r = threadIdx.x;
     const int64_t i = blk * BM + r;
     // the contributing CTAs of this row block, found once per CTA (64-bit
@@ -462,7 +466,7 @@ __global__ void __launch_bounds__(BM) k_tc_reduce(const float* __restrict__ part
     }
     __syncthreads();
     if (i >= M) return;
-    const int j0 = blockIdx.y * RJT;
+    const int j0 = int(blockIdx.x % ncg) * RJT;
     const int nj = min(RJT, l - j0);
     const int64_t c_lo = sh[0], c_hi = sh[1], pq = sh[2], pr = sh[3];
     int64_t cb = sh[4], rem = sh[5];
@@ -512,10 +516,11 @@ struct TcBands {
 __global__ void __launch_bounds__(BM) k_tc_reduce_bands(TcBands bands, int64_t M, int l,
                                                         double* __restrict__ Y, int64_t ldy) {
     constexpr int RJT = 8;
-    const int64_t blk = blockIdx.x;
+    const int ncg = (l + RJT - 1) / RJT;          // column groups of a block adjacent
+    const int64_t blk = blockIdx.x / ncg;
     const int r = threadIdx.x;
     const int64_t i = blk * BM + r;
-    __shared__ int64_t sh[kMaxBands][4];
+    __shared__ int64_t sh[kMaxBands][6];
     if (r < bands.n) {
         const TcPartials& B = bands.b[r];
         const int64_t first = blk * B.ksteps, last = min(B.total, first + B.ksteps) - 1;
@@ -526,36 +531,55 @@ __global__ void __launch_bounds__(BM) k_tc_reduce_bands(TcBands bands, int64_t M
         sh[r][1] = hi;
         sh[r][2] = (lo * B.per) / B.ksteps;
         sh[r][3] = (lo * B.per) % B.ksteps;
+        sh[r][4] = B.per / B.ksteps;
+        sh[r][5] = B.per % B.ksteps;
     }
     __syncthreads();
     if (i >= M) return;
-    const int j0 = blockIdx.y * RJT;
+    const int j0 = int(blockIdx.x % ncg) * RJT;
     const int nj = min(RJT, l - j0);
     double tot[RJT];
 #pragma unroll
     for (int q = 0; q < RJT; ++q) tot[q] = 0.0;
-    for (int bi = 0; bi < bands.n; ++bi) {
-        const TcPartials& B = bands.b[bi];
-        const int64_t pq = B.per / B.ksteps, pr = B.per % B.ksteps;
-        int64_t cb = sh[bi][2], rem = sh[bi][3];
-        double acc[RJT];
+    // the first partial tile of four bands at a time is loaded before any is
+    // added (memory latency), then each band's further tiles, bands in order
+    constexpr int BU = 4;
+    for (int b0 = 0; b0 < bands.n; b0 += BU) {
+        float v[BU][RJT];
 #pragma unroll
-        for (int q = 0; q < RJT; ++q) acc[q] = 0.0;
-#pragma unroll 4
-        for (int64_t c = sh[bi][0]; c <= sh[bi][1]; ++c) {
-            const float* src = B.part + ((c * B.max_segs + (blk - cb)) * B.npad + j0) * BM + r;
+        for (int u = 0; u < BU; ++u) {
+            const int bi = min(b0 + u, bands.n - 1);
+            const TcPartials& B = bands.b[bi];
+            const float* src =
+                B.part + ((sh[bi][0] * B.max_segs + (blk - sh[bi][2])) * B.npad + j0) * BM + r;
 #pragma unroll
-            for (int q = 0; q < RJT; ++q)
-                if (q < nj) acc[q] += double(src[int64_t(q) * BM]);
-            cb += pq;
-            rem += pr;
-            if (rem >= B.ksteps) {
-                rem -= B.ksteps;
-                ++cb;
-            }
+            for (int q = 0; q < RJT; ++q) v[u][q] = (q < nj) ? src[int64_t(q) * BM] : 0.f;
         }
 #pragma unroll
-        for (int q = 0; q < RJT; ++q) tot[q] = bi == 0 ? acc[q] : tot[q] + acc[q];
+        for (int u = 0; u < BU; ++u) {
+            const int bi = b0 + u;
+            if (bi >= bands.n) break;
+            const TcPartials& B = bands.b[bi];
+            Sum2f acc[RJT];                         // exact for the integer-valued tiles
+#pragma unroll
+            for (int q = 0; q < RJT; ++q) acc[q].add(v[u][q]);
+            int64_t cb = sh[bi][2], rem = sh[bi][3];
+            for (int64_t c = sh[bi][0] + 1; c <= sh[bi][1]; ++c) {
+                cb += sh[bi][4];
+                rem += sh[bi][5];
+                if (rem >= B.ksteps) {
+                    rem -= B.ksteps;
+                    ++cb;
+                }
+                const float* src = B.part + ((c * B.max_segs + (blk - cb)) * B.npad + j0) * BM + r;
+#pragma unroll
+                for (int q = 0; q < RJT; ++q)
+                    if (q < nj) acc[q].add(src[int64_t(q) * BM]);
+            }
+#pragma unroll
+            for (int q = 0; q < RJT; ++q)
+                tot[q] = bi == 0 ? acc[q].value() : tot[q] + acc[q].value();
+        }
     }
 #pragma unroll
     for (int q = 0; q < RJT; ++q)
@@ -789,12 +813,12 @@ cudaError_t launch_tc_reduce(const TcPartials& P, int64_t M, int cols, double* Y
     const bool wide = nblk * ((cols + 7) / 8) >= 2 * int64_t(num_sms);
     count_launch();
     if (!wide) {
-        k_tc_reduce<1><<<dim3(unsigned(nblk), unsigned(cols)), BM, 0, s>>>(
+        k_tc_reduce<1><<<unsigned(nblk * cols), BM, 0, s>>>(
             P.part, M, cols, P.npad, P.ksteps, P.total, P.per, P.max_segs, P.grid, Y, ldy,
             nullptr, nullptr, accum);
         return cudaGetLastError();
     }
-    k_tc_reduce<8><<<dim3(unsigned(nblk), unsigned((cols + 7) / 8)), BM, 0, s>>>(
+    k_tc_reduce<8><<<unsigned(nblk * ((cols + 7) / 8)), BM, 0, s>>>(
         P.part, M, cols, P.npad, P.ksteps, P.total, P.per, P.max_segs, P.grid, Y, ldy, nullptr,
         nullptr, accum);
     return cudaGetLastError();
@@ -1011,12 +1035,12 @@ cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t
     const bool wide = nblk * ((cols + 7) / 8) >= 2 * int64_t(num_sms);
     count_launch();
     if (!wide) {
-        k_tc_reduce<1><<<dim3(unsigned(nblk), unsigned(cols)), BM, 0, s>>>(
+        k_tc_reduce<1><<<unsigned(nblk * cols), BM, 0, s>>>(
             part, M, cols, p.npad, p.ksteps, p.total, p.per, p.max_segs, p.grid, Y, ldy, rowblk,
             KIND == KIND_FP8 ? colsc : nullptr, accum);
         return cudaGetLastError();
     }
-    k_tc_reduce<8><<<dim3(unsigned(nblk), unsigned((cols + 7) / 8)), BM, 0, s>>>(
+    k_tc_reduce<8><<<unsigned(nblk * ((cols + 7) / 8)), BM, 0, s>>>(
         part, M, cols, p.npad, p.ksteps, p.total, p.per, p.max_segs, p.grid, Y, ldy, rowblk,
         KIND == KIND_FP8 ? colsc : nullptr, accum);
     return cudaGetLastError();
@@ -1042,7 +1066,7 @@ cudaError_t launch_tc_reduce_bands(const TcPartials* bands, int nbands, int64_t 
     tb.n = nbands;
     for (int b = 0; b < nbands; ++b) tb.b[b] = bands[b];
     count_launch();
-    k_tc_reduce_bands<<<dim3(unsigned((M + BM - 1) / BM), unsigned((cols + 7) / 8)), BM, 0, s>>>(
+    k_tc_reduce_bands<<<unsigned((M + BM - 1) / BM * ((cols + 7) / 8)), BM, 0, s>>>(
         tb, M, cols, Y, ldy);
     return cudaGetLastError();
 }

@@ -532,7 +532,10 @@ __global__ void __launch_bounds__(BM) k_split_reduce(const float* __restrict__ p
                                                      int accum) {
     extern __shared__ int64_t src[];                 // part offsets of the tiles
     __shared__ int cnt[kMaxChunks + 1];
-    const int64_t blk = blockIdx.x;
+    // the column groups of a block adjacent in launch order (they read the
+    // same partial tiles)
+    const int ncg = (cols + RJ - 1) / RJ;
+    const int64_t blk = blockIdx.x / ncg;
     const int r = threadIdx.x;
     int64_t c_lo = 0, c_hi = -1, vb = 0;
     if (r < nkc) {
@@ -560,16 +563,29 @@ __global__ void __launch_bounds__(BM) k_split_reduce(const float* __restrict__ p
     const int nsrc = cnt[nkc];
     const int64_t i = blk * BM + r;
     if (i >= M) return;
-    const int j0 = blockIdx.y * RJ;
+    const int j0 = int(blockIdx.x % ncg) * RJ;
     const int nj = min(RJ, cols - j0);
     // compensated FP32 sums: as accurate as FP64 sums of the FP32 tiles, with
     // one FP64 addition per output instead of two FP64 operations per tile
     Sum2f acc[RJ];
-    for (int t = 0; t < nsrc; ++t) {
-        const float* p = part + src[t] + int64_t(j0) * BM + r;
+    // four tiles' loads in flight before their additions (the kernel waits on
+    // memory latency otherwise)
+    constexpr int TU = 4;
+    for (int t0 = 0; t0 < nsrc; t0 += TU) {
+        float v[TU][RJ];
 #pragma unroll
-        for (int q = 0; q < RJ; ++q)
-            if (q < nj) acc[q].add(p[int64_t(q) * BM]);
+        for (int u = 0; u < TU; ++u) {
+            const float* p = part + src[min(t0 + u, nsrc - 1)] + int64_t(j0) * BM + r;
+#pragma unroll
+            for (int q = 0; q < RJ; ++q) v[u][q] = (q < nj) ? p[int64_t(q) * BM] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < TU; ++u)
+            if (t0 + u < nsrc) {
+#pragma unroll
+                for (int q = 0; q < RJ; ++q)
+                    if (q < nj) acc[q].add(v[u][q]);
+            }
     }
 #pragma unroll
     for (int q = 0; q < RJ; ++q)
@@ -683,7 +699,7 @@ cudaError_t launch_tc_split_pass(int trans, int64_t m, int64_t n, const float* A
     if (norm && (e = launch_sum_partials(norm->parts, p.grid, norm->out, s)) != cudaSuccess)
         return e;
     count_launch();
-    k_split_reduce<<<dim3(unsigned(p.blocks), unsigned((cols + RJ - 1) / RJ)), BM,
+    k_split_reduce<<<unsigned(p.blocks * ((cols + RJ - 1) / RJ)), BM,
                      size_t(p.nkc + p.grid) * sizeof(int64_t), s>>>(
         part, M, cols, p.npad, p.sseg, p.nkc, p.per, p.max_segs, p.grid, Y, ldy, accum);
     return cudaGetLastError();
