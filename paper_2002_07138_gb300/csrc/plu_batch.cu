@@ -138,12 +138,37 @@ template <typename TC> __device__ __forceinline__ TC b_to_tc(double v) {
     else return v;
 }
 
+// n consecutive TC values from 16-byte (n * sizeof(TC) >= 16) or 8-byte
+// aligned shared memory, as one or more vector loads
+template <int N, typename TC> __device__ __forceinline__ void vload(const TC* p, TC* out) {
+    if constexpr (sizeof(TC) == 4 && N == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+    } else if constexpr (sizeof(TC) == 4 && N == 2) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        out[0] = v.x; out[1] = v.y;
+    } else if constexpr (sizeof(TC) == 8 && N == 2) {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        out[0] = v.x; out[1] = v.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[i] = p[i];
+    }
+}
+
 template <typename TC, int BMV, int BNV>
 __global__ void __launch_bounds__(GNT)
 k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
     constexpr int TM = BMV / 16, TN = BNV / 16;
-    __shared__ TC As[2][GBK][BMV + 1];
-    __shared__ TC Bs[2][GBK][BNV + 1];
+    // each thread owns TM consecutive rows and TN consecutive columns of the
+    // tile; its operands come in vector loads of up to 16 bytes
+    constexpr int VA = (TM * int(sizeof(TC))) >= 16 ? 16 / int(sizeof(TC)) : TM;
+    constexpr int VB = (TN * int(sizeof(TC))) >= 16 ? 16 / int(sizeof(TC)) : TN;
+    // rows padded to keep 16-byte alignment: each thread reads its TM (TN)
+    // consecutive outputs' operands with vector loads
+    constexpr int PAD = 16 / int(sizeof(TC));
+    __shared__ __align__(16) TC As[2][GBK][BMV + PAD];
+    __shared__ __align__(16) TC Bs[2][GBK][BNV + PAD];
     // job of this tile: last job with tile0 <= blockIdx.x; the job's tiles
     // run (row tile, column tile, K chunk), row tile fastest
     int lo = 0, hi = njobs - 1;
@@ -242,9 +267,11 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
             for (int kk = 0; kk < GBK; ++kk) {
                 TC av[TM], bv[TN];
 #pragma unroll
-                for (int a = 0; a < TM; ++a) av[a] = As[buf][kk][ty + 16 * a];
+                for (int a = 0; a < TM; a += VA)
+                    vload<VA>(&As[buf][kk][ty * TM + a], av + a);
 #pragma unroll
-                for (int c = 0; c < TN; ++c) bv[c] = Bs[buf][kk][tx + 16 * c];
+                for (int c = 0; c < TN; c += VB)
+                    vload<VB>(&Bs[buf][kk][tx * TN + c], bv + c);
 #pragma unroll
                 for (int a = 0; a < TM; ++a)
 #pragma unroll
@@ -258,11 +285,11 @@ k_b_gemm(const GemmJob* __restrict__ jobs, int njobs) {
     double* pc = J.ksplit > 1 ? J.part + int64_t(kc) * J.M * J.N : nullptr;
 #pragma unroll
     for (int a = 0; a < TM; ++a) {
-        const int64_t gi = i0 + ty + 16 * a;
+        const int64_t gi = i0 + ty * TM + a;
         if (gi >= J.M) continue;
 #pragma unroll
         for (int c = 0; c < TN; ++c) {
-            const int64_t gj = j0 + tx + 16 * c;
+            const int64_t gj = j0 + tx * TN + c;
             if (gj >= J.N) continue;
             if (pc) {
                 pc[gi + gj * J.M] = double(acc[a][c]);
