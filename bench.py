@@ -130,6 +130,13 @@ def run_batched(args):
     clk = clocks.stop()
     ms = dist_max(ws, statistics.mean(graph_ms))
     value = flops * ws / (ms / 1e3) / 1e12
+    hbm_peak, hbm_src = 6800.0, "fallback (6.8 TB/s)"
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                               "MEASURED_PEAKS.json")) as f:
+            hbm_peak, hbm_src = float(json.load(f)["hbm_gbs"]), "measured copy bandwidth"
+    except (OSError, KeyError, ValueError):
+        pass
     # accuracy over a sample of problems
     errs = []
     for i in range(0, len(specs), 32):
@@ -173,6 +180,14 @@ def run_batched(args):
                 ("k%d" % kc) if kc else "none" for kc in plu.plu_batched_splitk(ctx))),
             "gpu_launches": launches,
             "clocks": clk,
+            # the batch as a whole: the passes' algorithmic bytes (every read of
+            # every A) over the graph time, against the measured copy bandwidth
+            "roofline": {"bound": "hbm", "achieved": rep["bytes_passes"] / (ms / 1e3) / 1e9,
+                         "peak": hbm_peak, "unit": "GB/s",
+                         "frac": rep["bytes_passes"] / (ms / 1e3) / 1e9 / hbm_peak,
+                         "traffic": None, "peak_source": hbm_src,
+                         "kernel": "whole batch graph (the FP64 LUs and CholeskyQR products "
+                                   "between the passes bound it, not HBM)"},
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

@@ -338,6 +338,12 @@ PowerLUPlan plan_powerlu(int64_t m, int64_t n, int l, int kmax, int prec, int sm
         t = tail_scratch_max(m, n, kmax, sms, true);
         if (t > step) step = t;
     }
+    // the mixed modes' tail products as split-precision tensor-core products
+    if (prec != PLU_FP64 && !sparse && kmax <= 512) {
+        const int64_t mx = m > n ? m : n;
+        t = tcs_product_scratch_bytes(mx, kmax, sms);
+        if (t > step) step = t;
+    }
     // the mixed modes and the sparse path orthonormalise with tensor-core
     // products (the kmax leading columns at fixed rank, all l columns at
     // fixed precision)
@@ -517,11 +523,17 @@ plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const do
     pt.phase(PLU_PHASE_TAIL_LU);
     PLU_CUDA(c, launch_lu(c, prec, m, k, Y, m, 1, p, L1, m, 0, U1T, k, 1, info2dev, step, c->d_status,
                                 c->spin_budget, c->num_sms, c->stream));
-    // The two m x k x k products take FP32 FMAs when the passes are not FP64:
-    // Y itself then carries the pass precision's rounding (2^-11 relative for
-    // TF32), far above the ~1e-7 the FP32 products add.  The getrf steps stay
-    // FP64.
+    // The two m x k x k products are FP32-accurate when the passes are not
+    // FP64: Y itself then carries the pass precision's rounding (2^-11
+    // relative for TF32), far above the few 1e-7 these products add.  They
+    // run as split-precision tensor-core products (3xTF32 on an FP32 copy of
+    // the left operand) when the step scratch holds them, else with FP32
+    // FMAs.  The getrf steps stay FP64.
     const bool f32 = prec != PLU_FP64;
+    const bool tcs_bt = f32 && k <= 512 &&
+                        tcs_product_scratch_bytes(n, k, c->num_sms) <= pl.step_bytes;
+    const bool tcs_l = f32 && k <= 512 &&
+                       tcs_product_scratch_bytes(m, k, c->num_sms) <= pl.step_bytes;
     // oz: the FP64 products as FP64-accurate sums of exact BF16 slice
     // products on the tensor cores (U1^T and U2^T are stored whole, zeros
     // above the diagonal, so the dense slice product applies)
@@ -534,6 +546,9 @@ plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const do
     if (oz_bt)
         PLU_CUDA(c, launch_oz_xrinv(n, k, Vk, n, U1T, BT, n, step, pl.step_bytes, c->d_status,
                                     c->num_sms, c->stream));
+    else if (tcs_bt)
+        PLU_CUDA(c, launch_tcs_product(n, k, Vk, n, U1T, k, BT, n, step, pl.step_bytes,
+                                       c->d_status, c->num_sms, c->stream));
     else if (f32)
         PLU_CUDA(c, launch_gemm_f32_tri(3, n, k, k, Vk, n, U1T, k, BT, n, tp, pl.tailpart_bytes,
                                         c->num_sms, c->stream));
@@ -549,6 +564,9 @@ plu_status run_tail(plu_ctx* c, int64_t m, int64_t n, int k, double* Y, const do
     if (oz_l)
         PLU_CUDA(c, launch_oz_xrinv(m, k, L1, m, U2T, L, ldL, step, pl.step_bytes, c->d_status,
                                     c->num_sms, c->stream));
+    else if (tcs_l)
+        PLU_CUDA(c, launch_tcs_product(m, k, L1, m, U2T, k, L, ldL, step, pl.step_bytes,
+                                       c->d_status, c->num_sms, c->stream));
     else if (f32)
         PLU_CUDA(c, launch_gemm_f32_tri(3, m, k, k, L1, m, U2T, k, L, ldL, tp, pl.tailpart_bytes,
                                         c->num_sms, c->stream));

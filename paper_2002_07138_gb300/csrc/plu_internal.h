@@ -314,6 +314,13 @@ size_t tcs_scratch_bytes(int64_t M, int64_t K, int cols, int num_sms);
 size_t tcs_operand_bytes(int64_t K, int cols);
 cudaError_t launch_tcs_operand(int64_t K, int cols, const double* X, int64_t ldx, void* out,
                                int num_sms, cudaStream_t s);
+// Y (rows x k) = X T with X FP64 (rows x k) and T FP64 (k x k) as split-precision
+// tensor-core products: X is rounded to an FP32 copy in scratch (ld a
+// multiple of 4) and taken through launch_tc_split_pass (FP32-accurate).
+size_t tcs_product_scratch_bytes(int64_t rows, int k, int num_sms);
+cudaError_t launch_tcs_product(int64_t rows, int k, const double* X, int64_t ldx, const double* T,
+                               int64_t ldt, double* Y, int64_t ldy, void* scratch,
+                               size_t scratch_cap, int* dev_status, int num_sms, cudaStream_t s);
 // norm (nullable): ||A||_F^2 of the entries the pass reads, summed into *norm->out.
 cudaError_t launch_tc_split_pass(int trans, int64_t m, int64_t n, const float* A, int64_t lda,
                                  const double* X, int64_t ldx, int cols, double* Y, int64_t ldy,

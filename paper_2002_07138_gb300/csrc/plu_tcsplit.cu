@@ -595,7 +595,48 @@ __global__ void __launch_bounds__(BM) k_split_reduce(const float* __restrict__ p
         }
 }
 
+// Y (rows x cols, ld ldy) = X rounded to FP32 (nearest even), X FP64 (ld ldx).
+__global__ void k_to_f32_ld(int64_t rows, int cols, const double* __restrict__ X, int64_t ldx,
+                            float* __restrict__ Y, int64_t ldy) {
+    const int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = e % rows, j = e / rows;
+        Y[i + j * ldy] = f64_to_f32_rn(X[i + j * ldx]);
+    }
+}
+
 }  // namespace
+
+size_t tcs_product_scratch_bytes(int64_t rows, int k, int num_sms) {
+    const int64_t ld = (rows + 3) / 4 * 4;
+    return ((size_t(ld) * k * sizeof(float) + 255) & ~size_t(255)) +
+           tcs_scratch_bytes(rows, k, k, num_sms) + 256;
+}
+
+cudaError_t launch_tcs_product(int64_t rows, int k, const double* X, int64_t ldx, const double* T,
+                               int64_t ldt, double* Y, int64_t ldy, void* scratch,
+                               size_t scratch_cap, int* dev_status, int num_sms, cudaStream_t s) {
+    if (rows < 1 || k < 1) return cudaSuccess;
+    if (scratch_cap < tcs_product_scratch_bytes(rows, k, num_sms)) return cudaErrorInvalidValue;
+    const int64_t ld = (rows + 3) / 4 * 4;
+    const size_t xb = (size_t(ld) * k * sizeof(float) + 255) & ~size_t(255);
+    char* base = static_cast<char*>(scratch);
+    base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base) + 255) & ~uintptr_t(255));
+    float* X32 = reinterpret_cast<float*>(base);
+    if (!tcs_supported(rows, k, k, X32, ld, 0)) return cudaErrorInvalidValue;
+    {
+        int64_t b = (rows * k + 255) / 256;
+        if (b > int64_t(num_sms) * 16) b = int64_t(num_sms) * 16;
+        count_launch();
+        k_to_f32_ld<<<unsigned(b), 256, 0, s>>>(rows, k, X, ldx, X32, ld);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return launch_tc_split_pass(0, rows, k, X32, ld, T, ldt, k, Y, ldy, base + xb,
+                                scratch_cap - xb - size_t(base - static_cast<char*>(scratch)),
+                                dev_status, num_sms, s);
+}
 
 bool tcs_supported(int64_t M, int64_t K, int cols, const void* A, int64_t lda, int trans) {
     if (cols < 1 || cols > 512 || M < 1 || K < 1) return false;
