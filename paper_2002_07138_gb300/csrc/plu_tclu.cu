@@ -11,9 +11,9 @@
 //
 // Leaf (k_lu_leaf, cooperative, one CTA per SM).  Each CTA keeps its rows of
 // the leaf's columns in shared memory.  A column step is one grid-wide
-// candidate exchange (release-add on a counter, one polling thread, one warp
-// reading every CTA's slot).  Warp 0 runs the exchange; the other warps own
-// the rows.  Per step they eliminate only the next column, so that the next
+// candidate exchange: every CTA stores a tagged key, one warp per CTA polls
+// all keys until every tag is the step's, then reads the winner's record.
+// Warp 0 runs the exchange; the other warps own the rows.  Per step they eliminate only the next column, so that the next
 // candidate is ready, and apply the rest of the step's elimination to the
 // leaf's later columns while the exchange is in flight.  The candidate row's
 // later columns travel with its candidate, so the winner's U row needs no
@@ -50,7 +50,7 @@ constexpr int LW = 32;          // leaf width (columns)
 constexpr int LT = 256;         // leaf threads: warp 0 exchanges, warps 1-7 own rows
 constexpr int LROWT = LT - 32;  // row-owning threads
 constexpr int LMAXG = 256;      // largest leaf grid (one key per CTA, 8 per lane)
-constexpr int RECW = 2 + LW;    // record (uint4): |x|, (pos, row), the row's leaf columns
+constexpr int RECW = 3 + LW;    // record (uint4): |x|, (pos, row), the row's leaf columns, 1 / pivot
 
 constexpr int UM = 128;         // update tile rows (MMA M)
 constexpr int UNC = 32;         // update columns per MMA chunk (MMA N)
@@ -161,14 +161,6 @@ __device__ __forceinline__ void st_relaxed_v4(void* p, uint4 v) {
     asm volatile("st.relaxed.gpu.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y),
                  "r"(v.z), "r"(v.w)
                  : "memory");
-}
-__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void red_relaxed_add_u32(unsigned* p, unsigned v) {
-    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ uint4 tagged(unsigned long long b, unsigned tag) {
     return make_uint4(unsigned(b), tag, unsigned(b >> 32), tag);
@@ -360,9 +352,17 @@ k_lu_leaf(int64_t rows, int cols, double* __restrict__ X, int64_t ldx, int c0, i
             // carries the step's tag next to its value, so the arrival needs
             // no release and the reads no acquire: a reader polls until the
             // tags match.
+            // The key goes out first: the readers poll the keys before they
+            // read a record, so the record's stores and the reciprocal of the
+            // pivot (one FP64 division, here instead of on every reader's
+            // path) land while they poll.
             uint4* myrec = recs + (par + blockIdx.x) * RECW;
+            if (lane == 0)
+                st_relaxed_u64(keys + par + blockIdx.x,
+                               (unsigned long long)cand_key(cb) | ((unsigned long long)tag << 32));
+            double v = 0.0;
             if (rc >= 0 && lane >= sc && lane < w) {
-                double v = P[lane * per + rc];
+                v = P[lane * per + rc];
                 if (pend && lane > sc) {
                     v = fma(-P[(sc - 1) * per + rc], PR[(sc - 1) * LW + lane], v);
                     P[lane * per + rc] = v;
@@ -375,28 +375,17 @@ k_lu_leaf(int64_t rows, int cols, double* __restrict__ X, int64_t ldx, int c0, i
                               tagged((unsigned long long)unsigned(cb.pos) |
                                          ((unsigned long long)unsigned(cb.row) << 32),
                                      tag));
-                st_relaxed_u64(keys + par + blockIdx.x,
-                               (unsigned long long)cand_key(cb) | ((unsigned long long)tag << 32));
-                red_relaxed_add_u32(&head->barrier, 1u);
             }
-            // ---- (3) every CTA has published (one polling thread)
-            ++nbar;
+            if (rc >= 0 && lane == sc)
+                st_relaxed_v4(myrec + 2 + LW, tagged(__double_as_longlong(1.0 / v), tag));
+            // ---- (3) every key (slot lane + 32 k), all loads in flight, polled
+            // until each carries this step's tag (every CTA has published);
+            // then the records of the slots holding the largest key
             int good = 1;
-            if (lane == 0) {
-                int64_t spins = 0;
-                const unsigned target = nbar * unsigned(nb);
-                while (ld_relaxed_u32(&head->barrier) < target) {
-                    if (ld_volatile_i32(status) != DEV_OK) { good = 0; break; }
-                    if (++spins > budget) { good = 0; break; }
-                }
-            }
-            good = __shfl_sync(0xffffffffu, good, 0);
-            // ---- (4) every key (slot lane + 32 k), all loads in flight, then
-            // the records of the slots holding the largest key
             constexpr int KPL = LMAXG / 32;
             unsigned kv[KPL];
             int64_t spins = 0;
-            if (good) {
+            {
                 unsigned ready = 0;
 #pragma unroll
                 for (int k = 0; k < KPL; ++k) {
@@ -417,6 +406,11 @@ k_lu_leaf(int64_t rows, int cols, double* __restrict__ X, int64_t ldx, int c0, i
                     }
                     if (__all_sync(0xffffffffu, ready == (1u << KPL) - 1u)) break;
                     if (++spins > budget) { good = 0; break; }
+                    if ((spins & 63) == 0 &&
+                        __any_sync(0xffffffffu, lane == 0 && ld_volatile_i32(status) != DEV_OK)) {
+                        good = 0;     // another CTA gave up
+                        break;
+                    }
                 }
                 good = __all_sync(0xffffffffu, good);
             }
@@ -461,17 +455,20 @@ k_lu_leaf(int64_t rows, int cols, double* __restrict__ X, int64_t ldx, int c0, i
                 }
             }
             if (good && gs >= 0) {
-                // the winning record and its row (lane c: column c) in one round
+                // the winning record, its row (lane c: column c) and the
+                // reciprocal of its pivot in one round
                 const uint4* rb = recs + (par + gs) * RECW;
                 const bool want = lane >= sc && lane < w;
-                uint4 q0 = make_uint4(0, tag, 0, tag), q1 = q0, qr = q0;
+                uint4 q0 = make_uint4(0, tag, 0, tag), q1 = q0, qi = q0, qr = q0;
                 while (true) {
                     if (lane == 0) {
                         q0 = ld_relaxed_v4(rb);
                         q1 = ld_relaxed_v4(rb + 1);
+                        qi = ld_relaxed_v4(rb + 2 + LW);
                     }
                     if (want) qr = ld_relaxed_v4(rb + 2 + lane);
-                    const bool ok = has_tag(q0, tag) && has_tag(q1, tag) && has_tag(qr, tag);
+                    const bool ok = has_tag(q0, tag) && has_tag(q1, tag) && has_tag(qi, tag) &&
+                                    has_tag(qr, tag);
                     if (__all_sync(0xffffffffu, ok)) break;
                     if (++spins > budget) { good = 0; break; }
                 }
@@ -480,11 +477,8 @@ k_lu_leaf(int64_t rows, int cols, double* __restrict__ X, int64_t ldx, int c0, i
                 g.v = __shfl_sync(0xffffffffu, __longlong_as_double((long long)untag(q0)), 0);
                 g.pos = __shfl_sync(0xffffffffu, int(unsigned(pr)), 0);
                 g.row = __shfl_sync(0xffffffffu, int(unsigned(pr >> 32)), 0);
-                if (want) {
-                    const double u = __longlong_as_double((long long)untag(qr));
-                    PR[sc * LW + lane] = u;
-                    if (lane == sc) rinv_s = 1.0 / u;   // one FP64 division per step
-                }
+                if (want) PR[sc * LW + lane] = __longlong_as_double((long long)untag(qr));
+                if (lane == 0) rinv_s = __longlong_as_double((long long)untag(qi));
             }
             if (!good && lane == 0) atomicCAS(status, DEV_OK, DEV_TIMEOUT);
             if (lane == 0) {
@@ -949,7 +943,6 @@ cudaError_t launch_panel_lu_tc(int64_t rows, int cols, double* X, int64_t ldx, i
         e = cudaLaunchCooperativeKernel((const void*)k_lu_leaf, dim3(unsigned(nb)), dim3(LT), args,
                                         lsm, s);
         if (e != cudaSuccess) return e;
-        bar += unsigned(w);
         const int c1 = c0 + w;
         if (c1 >= cols) continue;
         bar += 1;
