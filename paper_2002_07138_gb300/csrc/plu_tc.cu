@@ -505,85 +505,122 @@ __global__ void __launch_bounds__(BM) k_tc_reduce(const float* __restrict__ part
 }
 
 // Y(i, j) = sum over bands b of (sum over the CTAs whose share touches block
-// i/128 of band b's partial tile, in CTA order), the bands added in order, in
-// FP64: the reduction of several passes into one Y with one write.  CTA
-// (blk, g): rows blk*128 + threadIdx.x, columns 8 g .. 8 g + 7.
+// i/128 of band b's partial tile), the bands added in order, in FP64: the
+// reduction of several passes into one Y with one write.  The partial tiles
+// hold integers (exact sums of slice products), so each band's sum over its
+// CTAs is exact in any order.  CTA (blk, g): rows blk*128 + (threadIdx.x %
+// 128) of columns RBC RBL g .. RBC RBL (g + 1) - 1, RBC columns at a time (one
+// output per thread), the CTA's setup (every band's contributors of block
+// blk) done once for all of them.  Per output the first RBU partial tiles of
+// RBG bands are loaded before any is added, so a thread keeps up to RBG x RBU
+// loads in flight.
 struct TcBands {
     TcPartials b[kMaxBands];
     int n;
 };
 
-__global__ void __launch_bounds__(BM) k_tc_reduce_bands(TcBands bands, int64_t M, int l,
-                                                        double* __restrict__ Y, int64_t ldy) {
-    constexpr int RJT = 8;
-    const int ncg = (l + RJT - 1) / RJT;          // column groups of a block adjacent
+constexpr int RBC = 2;      // columns at a time (BM threads each)
+constexpr int RBL = 8;      // column steps per CTA
+constexpr int RBG = 8;      // bands per group of loads
+constexpr int RBU = 3;      // partial tiles per band loaded up front
+
+__global__ void __launch_bounds__(BM * RBC) k_tc_reduce_bands(TcBands bands, int64_t M, int l,
+                                                              double* __restrict__ Y, int64_t ldy) {
+    const int ncg = (l + RBC * RBL - 1) / (RBC * RBL);   // column groups of a block adjacent
     const int64_t blk = blockIdx.x / ncg;
-    const int r = threadIdx.x;
+    const int r = threadIdx.x % BM;
+    const int jb = int(blockIdx.x % ncg) * RBC * RBL + threadIdx.x / BM;
     const int64_t i = blk * BM + r;
-    __shared__ int64_t sh[kMaxBands][6];
-    if (r < bands.n) {
-        const TcPartials& B = bands.b[r];
+    // per band: the float offset of the first contributing CTA's tile of
+    // block blk and of its column 0, row 0; how many CTAs contribute; and the
+    // offset steps between consecutive contributors (their first blocks
+    // advance by per / ksteps or one more)
+    __shared__ int64_t base[kMaxBands];
+    __shared__ int ncon[kMaxBands];
+    __shared__ int64_t cstep[kMaxBands][2];
+    __shared__ int pinfo[kMaxBands][3];      // (lo per) % ksteps, per % ksteps, per / ksteps
+    if (threadIdx.x < bands.n) {
+        const TcPartials& B = bands.b[threadIdx.x];
         const int64_t first = blk * B.ksteps, last = min(B.total, first + B.ksteps) - 1;
         const int64_t lo = first / B.per;
         int64_t hi = last / B.per;
         if (hi >= B.grid) hi = B.grid - 1;
-        sh[r][0] = lo;
-        sh[r][1] = hi;
-        sh[r][2] = (lo * B.per) / B.ksteps;
-        sh[r][3] = (lo * B.per) % B.ksteps;
-        sh[r][4] = B.per / B.ksteps;
-        sh[r][5] = B.per % B.ksteps;
+        const int64_t cb0 = (lo * B.per) / B.ksteps;
+        base[threadIdx.x] = (lo * B.max_segs + (blk - cb0)) * B.npad * BM;
+        ncon[threadIdx.x] = int(hi - lo + 1);
+        cstep[threadIdx.x][0] = int64_t(B.max_segs) * B.npad * BM;   // next CTA, same segment
+        cstep[threadIdx.x][1] = int64_t(B.npad) * BM;                // one segment
+        pinfo[threadIdx.x][0] = int((lo * B.per) % B.ksteps);
+        pinfo[threadIdx.x][1] = int(B.per % B.ksteps);
+        pinfo[threadIdx.x][2] = int(B.per / B.ksteps);
     }
     __syncthreads();
     if (i >= M) return;
-    const int j0 = int(blockIdx.x % ncg) * RJT;
-    const int nj = min(RJT, l - j0);
-    double tot[RJT];
+    const int nb = bands.n;
+    // contributor w + 1 of a band is the next CTA: its stage range starts per
+    // steps later, so its segment index for block blk is lower by the blocks
+    // it starts later
+    for (int step = 0; step < RBL; ++step) {
+        const int j = jb + step * RBC;
+        if (j >= l) break;
+        const int64_t colo = int64_t(j) * BM + r;
+        double tot = 0.0;
+        for (int b0 = 0; b0 < nb; b0 += RBG) {
+            float v[RBG][RBU];
 #pragma unroll
-    for (int q = 0; q < RJT; ++q) tot[q] = 0.0;
-    // the first partial tile of four bands at a time is loaded before any is
-    // added (memory latency), then each band's further tiles, bands in order
-    constexpr int BU = 4;
-    for (int b0 = 0; b0 < bands.n; b0 += BU) {
-        float v[BU][RJT];
+            for (int u = 0; u < RBG; ++u) {
+                const int bi = b0 + u;
 #pragma unroll
-        for (int u = 0; u < BU; ++u) {
-            const int bi = min(b0 + u, bands.n - 1);
-            const TcPartials& B = bands.b[bi];
-            const float* src =
-                B.part + ((sh[bi][0] * B.max_segs + (blk - sh[bi][2])) * B.npad + j0) * BM + r;
+                for (int w = 0; w < RBU; ++w) v[u][w] = 0.f;
+                if (bi >= nb) continue;
+                const float* part = bands.b[bi].part;
+                const int ks = bands.b[bi].ksteps;
+                int64_t off = base[bi] + colo;
+                int rk = pinfo[bi][0];
 #pragma unroll
-            for (int q = 0; q < RJT; ++q) v[u][q] = (q < nj) ? src[int64_t(q) * BM] : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < BU; ++u) {
-            const int bi = b0 + u;
-            if (bi >= bands.n) break;
-            const TcPartials& B = bands.b[bi];
-            Sum2f acc[RJT];                         // exact for the integer-valued tiles
-#pragma unroll
-            for (int q = 0; q < RJT; ++q) acc[q].add(v[u][q]);
-            int64_t cb = sh[bi][2], rem = sh[bi][3];
-            for (int64_t c = sh[bi][0] + 1; c <= sh[bi][1]; ++c) {
-                cb += sh[bi][4];
-                rem += sh[bi][5];
-                if (rem >= B.ksteps) {
-                    rem -= B.ksteps;
-                    ++cb;
+                for (int w = 0; w < RBU; ++w) {
+                    if (w >= ncon[bi]) break;
+                    v[u][w] = part[off];
+                    // the next contributor: CTA + 1, its segment of block blk
+                    rk += pinfo[bi][1];
+                    int adv = pinfo[bi][2];
+                    if (rk >= ks) {
+                        rk -= ks;
+                        ++adv;
+                    }
+                    off += cstep[bi][0] - int64_t(adv) * cstep[bi][1];
                 }
-                const float* src = B.part + ((c * B.max_segs + (blk - cb)) * B.npad + j0) * BM + r;
-#pragma unroll
-                for (int q = 0; q < RJT; ++q)
-                    if (q < nj) acc[q].add(src[int64_t(q) * BM]);
             }
 #pragma unroll
-            for (int q = 0; q < RJT; ++q)
-                tot[q] = bi == 0 ? acc[q].value() : tot[q] + acc[q].value();
-        }
-    }
+            for (int u = 0; u < RBG; ++u) {
+                const int bi = b0 + u;
+                if (bi >= nb) break;
+                Sum2f acc;                          // exact for the integer-valued tiles
 #pragma unroll
-    for (int q = 0; q < RJT; ++q)
-        if (q < nj) Y[i + int64_t(j0 + q) * ldy] = tot[q];
+                for (int w = 0; w < RBU; ++w) acc.add(v[u][w]);
+                if (ncon[bi] > RBU) {
+                    // contributors beyond the first RBU (a share shorter than
+                    // a third of a block's K steps)
+                    const float* part = bands.b[bi].part;
+                    const int ks = bands.b[bi].ksteps;
+                    int64_t off = base[bi] + colo;
+                    int rk = pinfo[bi][0];
+                    for (int w = 0; w < ncon[bi]; ++w) {
+                        if (w >= RBU) acc.add(part[off]);
+                        rk += pinfo[bi][1];
+                        int adv = pinfo[bi][2];
+                        if (rk >= ks) {
+                            rk -= ks;
+                            ++adv;
+                        }
+                        off += cstep[bi][0] - int64_t(adv) * cstep[bi][1];
+                    }
+                }
+                tot = bi == 0 ? acc.value() : tot + acc.value();
+            }
+        }
+        Y[i + int64_t(j) * ldy] = tot;
+    }
 }
 
 // Small operand X (FP64, K x cols, ldx) -> operand type, written as the
@@ -1066,8 +1103,8 @@ cudaError_t launch_tc_reduce_bands(const TcPartials* bands, int nbands, int64_t 
     tb.n = nbands;
     for (int b = 0; b < nbands; ++b) tb.b[b] = bands[b];
     count_launch();
-    k_tc_reduce_bands<<<unsigned((M + BM - 1) / BM * ((cols + 7) / 8)), BM, 0, s>>>(
-        tb, M, cols, Y, ldy);
+    k_tc_reduce_bands<<<unsigned((M + BM - 1) / BM * ((cols + RBC * RBL - 1) / (RBC * RBL))),
+                        BM * RBC, 0, s>>>(tb, M, cols, Y, ldy);
     return cudaGetLastError();
 }
 
