@@ -431,12 +431,13 @@ k_tc_pass(const __grid_constant__ CUtensorMap mapA, const unsigned char* __restr
 }
 
 // Y(i, j) = sum over the CTAs whose share touches block i/128 of their partial
-// tile, in CTA order, in FP64.  CTA (blk, g): rows blk*128 + threadIdx.x,
+// tile, in CTA order, in FP64 (many row blocks, few contributors each).  CTA
+// (blk, g): rows blk*128 + threadIdx.x,
 // columns g*RJT .. g*RJT + RJT - 1.  The segment index of CTA c in block blk
 // is blk - floor(c per / ksteps), stepped from one CTA to the next without
 // divisions; the loads of Y (accum) are issued before any store.
 template <int RJT>
-__global__ void __launch_bounds__(BM) k_tc_reduce(const float* __restrict__ part, int64_t M,
+__global__ void __launch_bounds__(BM) k_tc_reduce_wide(const float* __restrict__ part, int64_t M,
                                                   int l, int npad, int ksteps, int64_t total,
                                                   int64_t per, int max_segs, int grid,
                                                   double* __restrict__ Y, int64_t ldy,
@@ -501,6 +502,110 @@ __global__ void __launch_bounds__(BM) k_tc_reduce(const float* __restrict__ part
             if (col_scale) a *= double(col_scale[j0 + q]);
             Y[i + int64_t(j0 + q) * ldy] = accum ? yv[q] + a : a;
         }
+    }
+}
+
+// Y(i, j) = sum over the CTAs whose share touches block i/128 of their partial
+// tile, in CTA order, in FP64 (few row blocks, many contributors each: the
+// Gram matrices, the single-pass sweep).  CTA (blk, g): rows blk*128 + (threadIdx.x %
+// 128) of columns RRC RL g .. RRC RL (g + 1) - 1, RRC columns at a time (one
+// output per thread), the contributing CTAs of block blk found once per CTA
+// (64-bit divisions are long instruction sequences).  The segment index of
+// CTA c in block blk is blk - floor(c per / ksteps), stepped from one CTA to
+// the next without divisions.  The partial tiles of U contributors are
+// loaded for all RL columns before any of them is added (the adds stay in
+// CTA order), and Y (accum) before them.
+constexpr int RRC = 2;      // columns at a time (BM threads each)
+
+template <int RL, int U>
+__global__ void __launch_bounds__(BM * RRC) k_tc_reduce(const float* __restrict__ part, int64_t M,
+                                                        int l, int npad, int ksteps, int64_t total,
+                                                        int64_t per, int max_segs, int grid,
+                                                        double* __restrict__ Y, int64_t ldy,
+                                                        const float* __restrict__ rowblk_scale,
+                                                        const float* __restrict__ col_scale,
+                                                        int accum) {
+    // the column groups of a block adjacent in launch order, so the CTAs that
+    // read the same partial tiles run together
+    const int ncg = (l + RRC * RL - 1) / (RRC * RL);
+    const int64_t blk = blockIdx.x / ncg;
+    const int r = threadIdx.x % BM;
+    const int jb = int(blockIdx.x % ncg) * RRC * RL + threadIdx.x / BM;
+    const int64_t i = blk * BM + r;
+    __shared__ int64_t sh[4];
+    __shared__ int shi[3];
+    if (threadIdx.x == 0) {
+        const int64_t first = blk * ksteps, last = min(total, first + ksteps) - 1;
+        const int64_t lo = first / per;
+        int64_t hi = last / per;
+        if (hi >= grid) hi = grid - 1;
+        const int64_t cb0 = (lo * per) / ksteps;
+        sh[0] = (lo * max_segs + (blk - cb0)) * npad * BM;   // tile of the first contributor
+        sh[1] = int64_t(max_segs) * npad * BM;              // next CTA, same segment index
+        sh[2] = int64_t(npad) * BM;                         // one segment
+        sh[3] = hi - lo + 1;                                // contributors
+        shi[0] = int((lo * per) % ksteps);
+        shi[1] = int(per % ksteps);
+        shi[2] = int(per / ksteps);
+    }
+    __syncthreads();
+    if (i >= M) return;
+    const int64_t base = sh[0], cstep = sh[1], sstep = sh[2];
+    const int ncon = int(sh[3]);
+    const int rem0 = shi[0], pr = shi[1], pq = shi[2];
+    const double rs = rowblk_scale ? double(rowblk_scale[blk]) : 1.0;
+    // the contributors' tile offsets do not depend on the column: U of them
+    // at a time, then the RL columns' loads all issued before any add
+    double yv[RL];
+#pragma unroll
+    for (int st = 0; st < RL; ++st) {
+        const int j = jb + st * RRC;
+        yv[st] = (accum && j < l) ? Y[i + int64_t(j) * ldy] : 0.0;
+    }
+    // compensated FP32 sums (Sum2f): the FP64 sum of the FP32 tiles without
+    // an FP64 conversion and addition per tile (GB300's FP64 pipe would bound
+    // this kernel); integer-valued tiles (the exact slice products) still add
+    // up exactly
+    Sum2f acc[RL];
+    int64_t off = base;
+    int rk = rem0;
+    for (int c0 = 0; c0 < ncon; c0 += U) {
+        int64_t coff[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            coff[u] = off;
+            if (c0 + u < ncon) {
+                rk += pr;
+                int adv = pq;
+                if (rk >= ksteps) {
+                    rk -= ksteps;
+                    ++adv;
+                }
+                off += cstep - int64_t(adv) * sstep;
+            }
+        }
+        float v[RL][U];
+#pragma unroll
+        for (int st = 0; st < RL; ++st) {
+            const int j = jb + st * RRC;
+            const float* pj = part + int64_t(j) * BM + r;
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[st][u] = (j < l && c0 + u < ncon) ? pj[coff[u]] : 0.f;
+        }
+#pragma unroll
+        for (int st = 0; st < RL; ++st)
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (c0 + u < ncon) acc[st].add(v[st][u]);
+    }
+#pragma unroll
+    for (int st = 0; st < RL; ++st) {
+        const int j = jb + st * RRC;
+        if (j >= l) break;
+        double a = acc[st].value();
+        if (rowblk_scale) a *= rs;
+        if (col_scale) a *= double(col_scale[j]);
+        Y[i + int64_t(j) * ldy] = accum ? yv[st] + a : a;
     }
 }
 
@@ -844,21 +949,41 @@ bool tc_make_map_2d(CUtensorMap* map, int dtype_code, const void* base, uint64_t
     return make_map_2d(map, dt, base, dim0, dim1, stride1_bytes, box0, box1);
 }
 
-cudaError_t launch_tc_reduce(const TcPartials& P, int64_t M, int cols, double* Y, int64_t ldy,
-                             int accum, int num_sms, cudaStream_t s) {
+namespace {
+
+// The reduction of a pass's partial tiles: eight columns per thread when the
+// blocks are many (few contributors each), else one column per thread with
+// sixteen contributors' tiles in flight (many contributors each).
+cudaError_t tc_reduce_launch(const float* part, int64_t M, int cols, const TcPlan& p, double* Y,
+                             int64_t ldy, const float* rowblk, const float* colsc, int accum,
+                             int num_sms, cudaStream_t s) {
     const int64_t nblk = (M + BM - 1) / BM;
     const bool wide = nblk * ((cols + 7) / 8) >= 2 * int64_t(num_sms);
     count_launch();
     if (!wide) {
-        k_tc_reduce<1><<<unsigned(nblk * cols), BM, 0, s>>>(
-            P.part, M, cols, P.npad, P.ksteps, P.total, P.per, P.max_segs, P.grid, Y, ldy,
-            nullptr, nullptr, accum);
+        k_tc_reduce<1, 16><<<unsigned(nblk * ((cols + RRC - 1) / RRC)), BM * RRC, 0, s>>>(
+            part, M, cols, p.npad, p.ksteps, p.total, p.per, p.max_segs, p.grid, Y, ldy, rowblk,
+            colsc, accum);
         return cudaGetLastError();
     }
-    k_tc_reduce<8><<<unsigned(nblk * ((cols + 7) / 8)), BM, 0, s>>>(
-        P.part, M, cols, P.npad, P.ksteps, P.total, P.per, P.max_segs, P.grid, Y, ldy, nullptr,
-        nullptr, accum);
+    k_tc_reduce_wide<8><<<unsigned(nblk * ((cols + 7) / 8)), BM, 0, s>>>(
+        part, M, cols, p.npad, p.ksteps, p.total, p.per, p.max_segs, p.grid, Y, ldy, rowblk,
+        colsc, accum);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tc_reduce(const TcPartials& P, int64_t M, int cols, double* Y, int64_t ldy,
+                             int accum, int num_sms, cudaStream_t s) {
+    TcPlan p{};
+    p.npad = P.npad;
+    p.ksteps = P.ksteps;
+    p.total = P.total;
+    p.per = P.per;
+    p.max_segs = P.max_segs;
+    p.grid = P.grid;
+    return tc_reduce_launch(P.part, M, cols, p, Y, ldy, nullptr, nullptr, accum, num_sms, s);
 }
 
 bool tc_supported(int64_t M, int64_t K, int cols, const void* A, int64_t lda, int trans) {
@@ -1056,9 +1181,6 @@ cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // eight columns per CTA, or one when that leaves fewer than two CTAs per SM
-    // (few row blocks, each summed over many CTAs' partials)
-    const int64_t nblk = (M + BM - 1) / BM;
     if (keep) {              // the caller reduces later (launch_tc_reduce_bands)
         keep->part = part;
         keep->npad = p.npad;
@@ -1069,18 +1191,8 @@ cudaError_t tc_pass_kind(int trans, int64_t m, int64_t n, const void* A, int64_t
         keep->per = p.per;
         return cudaSuccess;
     }
-    const bool wide = nblk * ((cols + 7) / 8) >= 2 * int64_t(num_sms);
-    count_launch();
-    if (!wide) {
-        k_tc_reduce<1><<<unsigned(nblk * cols), BM, 0, s>>>(
-            part, M, cols, p.npad, p.ksteps, p.total, p.per, p.max_segs, p.grid, Y, ldy, rowblk,
-            KIND == KIND_FP8 ? colsc : nullptr, accum);
-        return cudaGetLastError();
-    }
-    k_tc_reduce<8><<<unsigned(nblk * ((cols + 7) / 8)), BM, 0, s>>>(
-        part, M, cols, p.npad, p.ksteps, p.total, p.per, p.max_segs, p.grid, Y, ldy, rowblk,
-        KIND == KIND_FP8 ? colsc : nullptr, accum);
-    return cudaGetLastError();
+    return tc_reduce_launch(part, M, cols, p, Y, ldy, rowblk, KIND == KIND_FP8 ? colsc : nullptr,
+                            accum, num_sms, s);
 }
 
 }  // namespace
