@@ -131,7 +131,14 @@ __global__ void k_oz_rowexp(int64_t rows, int cols, const double* __restrict__ X
 // reversed operand image img: nr / 64 K steps per block, each step npad rows
 // (columns of X) of 128 bytes holding 64 consecutive rows of X, 16-byte chunk
 // c of row j stored at chunk c ^ (j % 8) (the layout the pass kernel copies).
-// CTA row blockIdx.y = column a; x strides over the rows r < nr.
+// CTA row blockIdx.y = column a; a thread takes the row pairs (r, r + 1), r
+// even, x strided over nr / 2, and stores each slice's pair as one 4-byte word
+// (adjacent in Sv, and in one 16-byte chunk of the image).
+__device__ __forceinline__ __nv_bfloat16 oz_slice_value(int dig, int Es, int i, bool bad) {
+    return __float2bfloat16_rn(bad ? __int_as_float(0x7FC00000)
+                                   : ldexpf(float(dig), Es - OZ_BITS * (i + 1)));
+}
+
 __global__ void k_oz_slice_gram(int64_t rows, int64_t nr, const double* __restrict__ X,
                                 int64_t ldx, const int* __restrict__ Ecol,
                                 __nv_bfloat16* __restrict__ Sv, int64_t ldv,
@@ -139,44 +146,57 @@ __global__ void k_oz_slice_gram(int64_t rows, int64_t nr, const double* __restri
     const int a = blockIdx.y;
     const int E = Ecol[a];
     const int64_t steps = nr / 64;
-    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < nr;
-         r += int64_t(gridDim.x) * blockDim.x) {
-        int dig[OZ_S];
-        oz_digits(r < rows ? X[r + a * ldx] : 0.0, (r < rows && E != INT_MAX) ? E : INT_MIN,
-                  dig);
-        const int Es = (E == INT_MIN || E == INT_MAX) ? 0 : E;   // digits 0 then
-        const bool bad = E == INT_MAX && r < rows;                // inf / NaN column
+    const int Es = (E == INT_MIN || E == INT_MAX) ? 0 : E;   // digits 0 then
+    for (int64_t pr = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; pr < nr / 2;
+         pr += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = 2 * pr;
+        int d0[OZ_S], d1[OZ_S];
+        oz_digits(r < rows ? X[r + a * ldx] : 0.0, (r < rows && E != INT_MAX) ? E : INT_MIN, d0);
+        oz_digits(r + 1 < rows ? X[r + 1 + a * ldx] : 0.0,
+                  (r + 1 < rows && E != INT_MAX) ? E : INT_MIN, d1);
+        const bool bad0 = E == INT_MAX && r < rows;             // inf / NaN column
+        const bool bad1 = E == INT_MAX && r + 1 < rows;
         const int64_t s = r / 64;
         const int kk = int(r % 64);
         const int64_t in_step = int64_t(a) * 128 + (((kk / 8) ^ (a & 7)) << 4) + (kk % 8) * 2;
 #pragma unroll
         for (int i = 0; i < OZ_S; ++i) {
-            const __nv_bfloat16 v = __float2bfloat16_rn(
-                bad ? __int_as_float(0x7FC00000) : ldexpf(float(dig[i]), Es - OZ_BITS * (i + 1)));
-            Sv[int64_t(i) * nr + r + a * ldv] = v;
+            __nv_bfloat162 v;
+            v.x = oz_slice_value(d0[i], Es, i, bad0);
+            v.y = oz_slice_value(d1[i], Es, i, bad1);
+            *reinterpret_cast<__nv_bfloat162*>(Sv + int64_t(i) * nr + r + a * ldv) = v;
             const int64_t step = int64_t(OZ_S - 1 - i) * steps + s;
-            *reinterpret_cast<__nv_bfloat16*>(img + step * int64_t(npad) * 128 + in_step) = v;
+            *reinterpret_cast<__nv_bfloat162*>(img + step * int64_t(npad) * 128 + in_step) = v;
         }
     }
 }
 
 // X R^{-1} left operand, row exponents: slice i of X to columns
-// [i cols, (i + 1) cols) of Sh (rows x OZ_S cols, BF16, ld lds).
+// [i cols, (i + 1) cols) of Sh (rows x OZ_S cols, BF16, ld lds, a multiple of
+// 16).  A thread takes the row pairs (r, r + 1), r even, and stores each
+// slice's pair as one 4-byte word (a zero for row r + 1 = rows, inside lds).
 __global__ void k_oz_slice_rows(int64_t rows, int cols, const double* __restrict__ X,
                                 int64_t ldx, const int* __restrict__ Erow,
                                 __nv_bfloat16* __restrict__ Sh, int64_t lds) {
     const int a = blockIdx.y;
-    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < rows;
-         r += int64_t(gridDim.x) * blockDim.x) {
-        int dig[OZ_S];
-        const int E = Erow[r];
-        oz_digits(X[r + a * ldx], E == INT_MAX ? INT_MIN : E, dig);
-        const int Es = (E == INT_MIN || E == INT_MAX) ? 0 : E;   // digits 0 then
+    for (int64_t pr = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; pr < (rows + 1) / 2;
+         pr += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = 2 * pr;
+        const bool has1 = r + 1 < rows;
+        int d0[OZ_S], d1[OZ_S];
+        const int E0 = Erow[r];
+        const int E1 = has1 ? Erow[r + 1] : INT_MIN;
+        oz_digits(X[r + a * ldx], E0 == INT_MAX ? INT_MIN : E0, d0);
+        oz_digits(has1 ? X[r + 1 + a * ldx] : 0.0, E1 == INT_MAX ? INT_MIN : E1, d1);
+        const int Es0 = (E0 == INT_MIN || E0 == INT_MAX) ? 0 : E0;   // digits 0 then
+        const int Es1 = (E1 == INT_MIN || E1 == INT_MAX) ? 0 : E1;
 #pragma unroll
-        for (int i = 0; i < OZ_S; ++i)
-            Sh[r + (int64_t(i) * cols + a) * lds] = __float2bfloat16_rn(
-                E == INT_MAX ? __int_as_float(0x7FC00000)
-                             : ldexpf(float(dig[i]), Es - OZ_BITS * (i + 1)));
+        for (int i = 0; i < OZ_S; ++i) {
+            __nv_bfloat162 v;
+            v.x = oz_slice_value(d0[i], Es0, i, E0 == INT_MAX);
+            v.y = oz_slice_value(d1[i], Es1, i, E1 == INT_MAX);
+            *reinterpret_cast<__nv_bfloat162*>(Sh + r + (int64_t(i) * cols + a) * lds) = v;
+        }
     }
 }
 
@@ -306,7 +326,7 @@ cudaError_t launch_oz_gram(int64_t rows, int cols, const double* X, int64_t ldx,
     k_oz_colexp<<<cols, 256, 0, s>>>(rows, X, ldx, Ecol);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     count_launch();
-    k_oz_slice_gram<<<dim3(unsigned(grid_rows(L.nr, cols, num_sms)), unsigned(cols)), 256, 0, s>>>(
+    k_oz_slice_gram<<<dim3(unsigned(grid_rows(L.nr / 2, cols, num_sms)), unsigned(cols)), 256, 0, s>>>(
         rows, L.nr, X, ldx, Ecol, Sv, L.ldv, img, L.npad);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t step_bytes = size_t(L.npad) * 128;
@@ -341,7 +361,7 @@ cudaError_t launch_oz_xrinv(int64_t rows, int cols, const double* X, int64_t ldx
     k_oz_rowexp<<<grid_rows(rows, 1, num_sms), 256, 0, s>>>(rows, cols, X, ldx, Erow);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     count_launch();
-    k_oz_slice_rows<<<dim3(unsigned(grid_rows(rows, cols, num_sms)), unsigned(cols)), 256, 0, s>>>(
+    k_oz_slice_rows<<<dim3(unsigned(grid_rows((rows + 1) / 2, cols, num_sms)), unsigned(cols)), 256, 0, s>>>(
         rows, cols, X, ldx, Erow, Sh, L.lds);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     count_launch();
