@@ -113,14 +113,25 @@ __global__ void k_oz_colexp(int64_t rows, const double* __restrict__ X, int64_t 
     if (threadIdx.x == 0) Ecol[a] = oz_exponent(__longlong_as_double(red[0]));
 }
 
-// Per-row exponents of X (rows x cols): one thread per row.
-__global__ void k_oz_rowexp(int64_t rows, int cols, const double* __restrict__ X, int64_t ldx,
-                            int* __restrict__ Erow) {
-    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < rows;
-         r += int64_t(gridDim.x) * blockDim.x) {
-        long long mx = 0;
-#pragma unroll 16
-        for (int a = 0; a < cols; ++a) mx = max(mx, abs_bits(X[r + a * ldx]));
+// Per-row exponents of X (rows x cols): 64 rows per CTA, four threads per
+// row, each scanning every fourth column (more loads in flight than one
+// thread per row), their maxima combined in shared memory.
+constexpr int RX_ROWS = 64;
+__global__ void __launch_bounds__(RX_ROWS * 4) k_oz_rowexp(int64_t rows, int cols,
+                                                          const double* __restrict__ X,
+                                                          int64_t ldx, int* __restrict__ Erow) {
+    __shared__ long long part[4][RX_ROWS];
+    const int lr = threadIdx.x % RX_ROWS, q = threadIdx.x / RX_ROWS;
+    const int64_t r = int64_t(blockIdx.x) * RX_ROWS + lr;
+    long long mx = 0;
+    if (r < rows) {
+#pragma unroll 8
+        for (int a = q; a < cols; a += 4) mx = max(mx, abs_bits(X[r + a * ldx]));
+    }
+    part[q][lr] = mx;
+    __syncthreads();
+    if (q == 0 && r < rows) {
+        mx = max(max(part[0][lr], part[1][lr]), max(part[2][lr], part[3][lr]));
         Erow[r] = oz_exponent(__longlong_as_double(mx));
     }
 }
@@ -358,7 +369,8 @@ cudaError_t launch_oz_xrinv(int64_t rows, int cols, const double* X, int64_t ldx
     double* Trev = reinterpret_cast<double*>(base + L.b_off);
     cudaError_t e;
     count_launch();
-    k_oz_rowexp<<<grid_rows(rows, 1, num_sms), 256, 0, s>>>(rows, cols, X, ldx, Erow);
+    k_oz_rowexp<<<unsigned((rows + RX_ROWS - 1) / RX_ROWS), RX_ROWS * 4, 0, s>>>(rows, cols, X,
+                                                                              ldx, Erow);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     count_launch();
     k_oz_slice_rows<<<dim3(unsigned(grid_rows((rows + 1) / 2, cols, num_sms)), unsigned(cols)), 256, 0, s>>>(
