@@ -929,6 +929,9 @@ cudaError_t launch_panel_lu_tc(int64_t rows, int cols, double* X, int64_t ldx, i
     const int steps = int(rows < int64_t(cols) ? rows : int64_t(cols));
     const int64_t ntiles = (rows + UM - 1) / UM;
     const int ugrid = int(ntiles < num_sms ? ntiles : num_sms);
+    // grid barriers the leaves have passed on head->barrier: one per leaf
+    // that has later columns (the column steps themselves synchronise on the
+    // step-tagged keys)
     unsigned bar = 0;
     for (int c0 = 0; c0 < steps; c0 += LW) {
         const int w = steps - c0 < LW ? steps - c0 : LW;
