@@ -39,20 +39,44 @@ __global__ void k_gaussian(int64_t rows, int64_t cols, uint32_t k0, uint32_t k1,
     }
 }
 
+// Even column length: one thread per pair, both entries in the same column
+// (entry t = i + j rows with i even starts pair t / 2), converted to FP64 on
+// the integer pipe (exact).
+__global__ void k_gaussian_pairs(int64_t rows, int64_t cols, uint32_t k0, uint32_t k1,
+                                 uint32_t stream_id, double* __restrict__ out, int64_t ld) {
+    const int64_t half = rows / 2;
+    for (int64_t j = blockIdx.y; j < cols; j += gridDim.y) {
+        for (int64_t h = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; h < half;
+             h += int64_t(gridDim.x) * blockDim.x) {
+            const uint64_t q = uint64_t(j) * uint64_t(half) + uint64_t(h);
+            float ze, zo;
+            rng::gaussian_pair_f(q, k0, k1, stream_id, ze, zo);
+            double* o = out + 2 * h + j * ld;
+            o[0] = f32_to_f64(ze);
+            o[1] = f32_to_f64(zo);
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_gaussian(int64_t rows, int64_t cols, uint64_t seed, uint32_t stream_id,
                             double* out, int64_t ld, cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     // about 32 CTAs of 256 threads per SM over (row chunks) x (columns)
+    const bool pairs = rows % 2 == 0;
     int64_t gy = cols < 65535 ? cols : 65535;
-    int64_t gx = (rows + 255) / 256;
+    int64_t gx = ((pairs ? rows / 2 : rows) + 255) / 256;
     const int64_t want = int64_t(152) * 32;
     if (gx * gy > want) gx = (want + gy - 1) / gy;
     if (gx < 1) gx = 1;
     count_launch();
-    k_gaussian<<<dim3(unsigned(gx), unsigned(gy)), 256, 0, s>>>(
-        rows, cols, uint32_t(seed), uint32_t(seed >> 32), stream_id, out, ld);
+    if (pairs)
+        k_gaussian_pairs<<<dim3(unsigned(gx), unsigned(gy)), 256, 0, s>>>(
+            rows, cols, uint32_t(seed), uint32_t(seed >> 32), stream_id, out, ld);
+    else
+        k_gaussian<<<dim3(unsigned(gx), unsigned(gy)), 256, 0, s>>>(
+            rows, cols, uint32_t(seed), uint32_t(seed >> 32), stream_id, out, ld);
     return cudaGetLastError();
 }
 

@@ -85,10 +85,9 @@ __device__ __forceinline__ void sincos_turn(uint32_t x, float& so, float& co) {
     }
 }
 
-// Both Box-Muller outputs of pair q of stream (seed, stream_id), in float32,
-// returned exactly as doubles.
-__device__ __forceinline__ void gaussian_pair(uint64_t q, uint32_t k0, uint32_t k1,
-                                              uint32_t stream_id, double& z_even, double& z_odd) {
+// Both Box-Muller outputs of pair q of stream (seed, stream_id), in float32.
+__device__ __forceinline__ void gaussian_pair_f(uint64_t q, uint32_t k0, uint32_t k1,
+                                                uint32_t stream_id, float& z_even, float& z_odd) {
     uint32_t c0 = uint32_t(q), c1 = uint32_t(q >> 32), c2 = stream_id, c3 = 0;
     philox4x32_10(c0, c1, c2, c3, k0, k1);
     // u = ((w0 >> 8) + 1) 2^-24 in (0, 1], exact
@@ -96,8 +95,17 @@ __device__ __forceinline__ void gaussian_pair(uint64_t q, uint32_t k0, uint32_t 
     const float r = __fsqrt_rn(__fmul_rn(-2.0f, ln_unit(u)));
     float sn, cs;
     sincos_turn(c2, sn, cs);
-    z_even = double(__fmul_rn(r, cs));
-    z_odd = double(__fmul_rn(r, sn));
+    z_even = __fmul_rn(r, cs);
+    z_odd = __fmul_rn(r, sn);
+}
+
+// The same pair returned exactly as doubles.
+__device__ __forceinline__ void gaussian_pair(uint64_t q, uint32_t k0, uint32_t k1,
+                                              uint32_t stream_id, double& z_even, double& z_odd) {
+    float ze, zo;
+    gaussian_pair_f(q, k0, k1, stream_id, ze, zo);
+    z_even = double(ze);
+    z_odd = double(zo);
 }
 
 }  // namespace rng

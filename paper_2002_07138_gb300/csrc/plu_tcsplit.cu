@@ -596,14 +596,14 @@ __global__ void __launch_bounds__(BM) k_split_reduce(const float* __restrict__ p
 }
 
 // Y (rows x cols, ld ldy) = X rounded to FP32 (nearest even), X FP64 (ld ldx).
+// CTA row blockIdx.y strides over the columns, x over the rows (no division
+// per element).
 __global__ void k_to_f32_ld(int64_t rows, int cols, const double* __restrict__ X, int64_t ldx,
                             float* __restrict__ Y, int64_t ldy) {
-    const int64_t total = rows * cols;
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
-         e += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t i = e % rows, j = e / rows;
-        Y[i + j * ldy] = f64_to_f32_rn(X[i + j * ldx]);
-    }
+    for (int64_t j = blockIdx.y; j < cols; j += gridDim.y)
+        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < rows;
+             i += int64_t(gridDim.x) * blockDim.x)
+            Y[i + j * ldy] = f64_to_f32_rn(X[i + j * ldx]);
 }
 
 }  // namespace
@@ -626,10 +626,14 @@ cudaError_t launch_tcs_product(int64_t rows, int k, const double* X, int64_t ldx
     float* X32 = reinterpret_cast<float*>(base);
     if (!tcs_supported(rows, k, k, X32, ld, 0)) return cudaErrorInvalidValue;
     {
-        int64_t b = (rows * k + 255) / 256;
-        if (b > int64_t(num_sms) * 16) b = int64_t(num_sms) * 16;
+        // about 16 CTAs of 256 threads per SM over (row chunks) x (columns)
+        const int64_t gy = k < 65535 ? k : 65535;
+        int64_t gx = (rows + 255) / 256;
+        const int64_t want = int64_t(num_sms) * 16;
+        if (gx * gy > want) gx = (want + gy - 1) / gy;
+        if (gx < 1) gx = 1;
         count_launch();
-        k_to_f32_ld<<<unsigned(b), 256, 0, s>>>(rows, k, X, ldx, X32, ld);
+        k_to_f32_ld<<<dim3(unsigned(gx), unsigned(gy)), 256, 0, s>>>(rows, k, X, ldx, X32, ld);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
