@@ -38,13 +38,14 @@ def test_gaussian_bit_identical(ctx, rows, cols, seed, sid):
     assert np.array_equal(host(got), ref)
 
 
-def test_gaussian_with_leading_dimension(ctx):
+@pytest.mark.parametrize("rows", [33, 34])     # one entry per thread / one pair per thread
+def test_gaussian_with_leading_dimension(ctx, rows):
     buf = plu.colmajor_empty(40, 6)
     buf.fill_(7.0)
-    view = buf[:33, :]
-    plu.plu_gaussian(ctx, 33, 6, 11, 1, out=view)
-    assert np.array_equal(host(buf[:33]), oracle.gaussian_matrix(33, 6, 11, 1))
-    assert torch.all(buf[33:] == 7.0)
+    view = buf[:rows, :]
+    plu.plu_gaussian(ctx, rows, 6, 11, 1, out=view)
+    assert np.array_equal(host(buf[:rows]), oracle.gaussian_matrix(rows, 6, 11, 1))
+    assert torch.all(buf[rows:] == 7.0)
 
 
 # --------------------------------------------------------------- a2/a4/a6
